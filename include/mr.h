@@ -1,0 +1,217 @@
+/*
+ * mr.h — C ABI of the GB300 block-based multiresolution solver.
+ *
+ * The library advances  d_t phi = N(phi)  on a graded quad/octree of blocks
+ * (Sroka et al., arXiv:1902.00088).  One call of mr_step() is the paper's time
+ * step (Sec. 2.1): refine every block by one level (safety zone), synchronise
+ * ghost nodes and evolve with classic RK4 (Sec. 3, Sec. 4), then coarsen blocks
+ * whose wavelet details fall below eps (Sec. 2.3).  Everything runs in CUDA
+ * kernels on one GPU; the library owns all device memory.
+ *
+ * Conventions for every entry point
+ *   - Return value: MR_OK (0) or an mr_status error code; entry points never
+ *     abort.  mr_last_error() gives a static description of the last failure.
+ *   - A context lives on one CUDA device (the one current at mr_create) and
+ *     enqueues its work on the stream given in mr_params (NULL = legacy default
+ *     stream).  Calls return after enqueueing, except where noted
+ *     ("synchronises"): those wait for the stream and report device-side
+ *     errors (capacity exhausted, broken invariants, non-finite values).
+ *   - Host pointers are owned by the caller and only read/written during the
+ *     call.  Block lists are exported in canonical order: by tree, then by the
+ *     Hilbert index (Skilling 2004) of the block's lower-corner cell on the
+ *     tree's finest lattice (the paper orders blocks on a space-filling curve,
+ *     Sec. 2.5).
+ *   - Field layout of one block: [var][z][y][x] over the Bs^d interior nodes
+ *     (block nodes 0..Bs-1 per axis, Sec. 2.2); node (i,j,k) of a block at
+ *     level l with block coordinates (cx,cy,cz) sits at
+ *     x0 + ((cx*(Bs-1)+i), (cy*(Bs-1)+j), (cz*(Bs-1)+k)) * dx_l,
+ *     dx_l = L / (2^l (Bs-1)).
+ */
+#ifndef MR_H
+#define MR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mr_status;
+#define MR_OK 0
+#define MR_EINVAL 1     /* bad argument or parameter combination */
+#define MR_ENOMEM 2     /* device or host allocation failed */
+#define MR_ECAPACITY 3  /* block pool or free-slot stack exhausted */
+#define MR_ECUDA 4      /* a CUDA runtime call failed */
+#define MR_ETIMEOUT 5   /* a bounded device wait gave up */
+#define MR_ENAN 6       /* a non-finite value was found in a block norm */
+#define MR_EINTERNAL 7  /* a device-side invariant check failed (e.g. non-graded tree) */
+
+/* Arithmetic of the stored fields (Sec. 3 uses FP64 throughout). */
+#define MR_PREC_FP64 0       /* y_n, RK accumulator, stage fields and stencils in FP64 */
+#define MR_PREC_FP32 1       /* everything FP32 (details optionally FP64) */
+#define MR_PREC_FP32_ACC64 2 /* stage fields and stencils FP32; y_n and RK accumulator FP64 */
+
+/* Right-hand sides N(phi) (one kind per context). */
+#define MR_RHS_ADV 0    /* -u . grad phi, constant u = rhs[0..2] (Sec. 3 advection equation) */
+#define MR_RHS_SWIRL 1  /* -u . grad phi, u of Sec. 3 Eq. (1), t_a = rhs[0]; 2D only */
+#define MR_RHS_NS 2     /* compressible Navier-Stokes (Sec. 4), rhs = {gamma, mu, Pr}; 2D, nvar 4 */
+
+/* Initial conditions (evaluated on the device from per-lattice factor tables). */
+#define MR_IC_GAUSS 0   /* prod_a exp(-d_a^2/(2 sigma^2)), nearest periodic image:
+                           ic = {cx, cy, cz, sigma} (Sec. 3 uses beta = 2 sigma^2) */
+#define MR_IC_MIXING 1  /* temporal mixing layer: ic = {delta, U0, Mach, gamma, amp,
+                           a_1..a_8, phi_1..phi_8}; rho = 1 */
+#define MR_IC_NONE 2    /* no analytic field; blocks come from mr_set_blocks */
+
+/* mr_adapt modes (Sec. 2.1 / 2.3). */
+#define MR_ADAPT_REFINE_ALL 0      /* every block below Jmax gains one level */
+#define MR_ADAPT_REFINE_FLAGGED 1  /* blocks whose refinement mask is +1 (mr_set_refine_mask) */
+#define MR_ADAPT_COARSEN 2         /* detail thresholding + completeness/gradedness, merge */
+#define MR_ADAPT_FLAGS_ONLY 3      /* details and flags of the current grid, no merge (inspection) */
+
+typedef struct {
+  int32_t dim;          /* 2 or 3 */
+  int32_t Bs;           /* block points per direction: 17 or 33 (odd, Sec. 2.2) */
+  int32_t ng;           /* ghost layer width: 4 */
+  int32_t nvar;         /* variables per node: 1 (advection) or 4 (NS) */
+  int32_t precision;    /* MR_PREC_* */
+  int32_t detail_fp64;  /* 1: details of FP32 fields evaluated in FP64 */
+  int32_t rhs_kind;     /* MR_RHS_* */
+  int32_t ntrees;       /* independent trees advanced together (>= 1) */
+  int64_t capacity;     /* pool slots over all trees; a refine-all needs
+                           (1 + 2^d) x active blocks transiently */
+  int32_t max_rounds;   /* coarsening rounds per adapt; 0 = until stable (<= Jmax - Jmin) */
+  int32_t norm_kind;    /* 0: details unnormalised; 1: divided per variable by max |q_v| */
+  double L;             /* edge of the periodic domain */
+  void* stream;         /* cudaStream_t, NULL = legacy default stream */
+} mr_params;
+
+typedef struct {
+  int32_t Jmin, Jmax;   /* level range, 1 <= Jmin <= Jmax; level l has 2^l blocks per direction */
+  double eps;           /* detail threshold (Sec. 2.3, strict <) */
+  double x0[3];         /* domain origin */
+  int32_t ic_kind;      /* MR_IC_* */
+  double ic[32];        /* IC parameters, see MR_IC_* */
+  double rhs[8];        /* RHS parameters, see MR_RHS_* */
+} mr_tree_desc;
+
+typedef struct {
+  int32_t level;
+  int32_t tree;
+  uint64_t treecode;     /* Sec. 2.2: one base-2^d digit per level, digit = bx + 2by + 4bz */
+  int32_t coords[3];     /* block coordinates at its level */
+  int32_t pad;
+  uint64_t hilbert_key;  /* Hilbert index of the lower-corner cell at Jmax resolution */
+} mr_block_info;
+
+typedef struct mr_ctx_s* mr_ctx;
+
+/* Creates a context with ntrees trees described by trees[0..ntrees-1] and
+ * allocates the block pool (capacity slots).  Trees start empty: call
+ * mr_init_tree or mr_set_blocks.  Errors: MR_EINVAL (unsupported dim/Bs/ng/
+ * nvar/precision/rhs combination, Jmin < 1, Jmax > 10 (2D) / 7 (3D)),
+ * MR_ENOMEM, MR_ECUDA.  *out is NULL on failure. */
+mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out);
+void mr_destroy(mr_ctx ctx);
+const char* mr_last_error(mr_ctx ctx);
+
+/* Builds the initial grid of every tree (synchronises): uniform at Jmin with the
+ * analytic field, then Jmax-Jmin times refine all + analytic field + coarsen
+ * until stable.  (The paper does not describe its initialisation.) */
+mr_status mr_init_tree(mr_ctx ctx);
+
+/* Sets the RHS parameters of one tree (tree >= 0) or all trees (tree = -1);
+ * rhs_params has 8 doubles, meaning per MR_RHS_*.  The kind must equal
+ * mr_params.rhs_kind. */
+mr_status mr_set_rhs(mr_ctx ctx, int32_t rhs_kind, int32_t tree, const double* rhs_params);
+
+/* Ghost-node synchronisation of the current field (Sec. 2.2, 2.5): same-level
+ * copy, fine-to-coarse injection, coarse-to-fine 4th-order interpolating-
+ * wavelet prediction; block-edge (conditional) nodes shared with a finer block
+ * take the finer value.  The overwritten edge nodes are stored; ghost layers
+ * are written to the tile buffer read by mr_get_tiles. */
+mr_status mr_sync_ghosts(mr_ctx ctx);
+
+/* One classic RK4 step over all blocks without adaptation (ghosts synchronised
+ * before each stage).  t, dt: host arrays of ntrees doubles (time and step of
+ * each tree). */
+mr_status mr_rk_step(mr_ctx ctx, const double* t, const double* dt);
+
+/* Grid adaptation, mode MR_ADAPT_*.  COARSEN runs rounds of sync + details +
+ * flags + merge until no family merges (or max_rounds) and synchronises. */
+mr_status mr_adapt(mr_ctx ctx, int32_t mode);
+
+/* One full multiresolution step (Sec. 2.1): refine all, RK4, coarsen.
+ * Synchronises once per coarsening round when max_rounds = 0. */
+mr_status mr_step(mr_ctx ctx, const double* t, const double* dt);
+
+/* Number of blocks of a tree (tree = -1: all trees).  Synchronises. */
+mr_status mr_num_blocks(mr_ctx ctx, int32_t tree, int64_t* n);
+
+/* Copies the blocks of tree (or all, tree = -1) in canonical order to host
+ * buffers of room cap: info (nullable) and fields (nullable, n x nvar x Bs^d
+ * doubles, converted from the stored precision).  *n = number of blocks;
+ * MR_EINVAL if cap < *n.  Synchronises. */
+mr_status mr_get_blocks(mr_ctx ctx, int32_t tree, int64_t cap, int64_t* n,
+                        mr_block_info* info, double* fields);
+
+/* Synchronised tiles (n x nvar x (Bs+2ng)^d doubles, ghosts included) of the
+ * current field, canonical order.  Runs a ghost synchronisation first.  Synchronises. */
+mr_status mr_get_tiles(mr_ctx ctx, int32_t tree, int64_t cap, int64_t* n, double* tiles);
+
+/* Neighbour table (Sec. 2.2: 16 relations in 2D, 74 in 3D): nbr[b*R + r] is the
+ * canonical index (within the exported list of the same tree) of relation r of
+ * block b, or -1; dl the level difference (neighbour - block).  Relation order:
+ * faces, edges, corners (by number of nonzero direction components); directions
+ * with x varying fastest; a non-corner direction has one entry for a same-level
+ * or coarser neighbour then one per finer block touching the face/edge (x fastest
+ * over the free axes); a corner has one entry at any level.  Synchronises. */
+mr_status mr_get_neighbors(mr_ctx ctx, int32_t tree, int64_t cap, int32_t* nbr, int8_t* dl);
+int32_t mr_num_relations(int32_t dim);
+
+/* Refinement status and largest normalised detail of each block after the last
+ * details evaluation (mr_adapt COARSEN or mr_step): flag -2 = merged or can be
+ * coarsened, -1 unused, 0 keep, +1 refine.  Synchronises. */
+mr_status mr_get_flags(mr_ctx ctx, int32_t tree, int64_t cap, int8_t* flags, double* max_detail);
+
+/* Replaces all trees by the given blocks (restart/replay).  n blocks with
+ * levels, trees (nullable = all tree 0), coords (n x 3) and fields (nullable =
+ * zero; n x nvar x Bs^d doubles), any order.  The grid must be a complete,
+ * graded partition of each tree's domain (checked: MR_EINTERNAL).  Synchronises. */
+mr_status mr_set_blocks(mr_ctx ctx, int64_t n, const int32_t* level, const int32_t* tree,
+                        const int32_t* coords, const double* fields);
+
+/* Per-block refinement mask for MR_ADAPT_REFINE_FLAGGED, canonical order over
+ * all trees (n = total block count): +1 refine, 0 keep. */
+mr_status mr_set_refine_mask(mr_ctx ctx, int64_t n, const int8_t* mask);
+
+/* Error of tree against the analytic IC advected by constant u over time t (for
+ * the swirl pass t = 0 at t = t_a): out = {L2 abs, L2 of exact, Linf abs, Linf of
+ * exact}, unique nodes (each block's last node per axis dropped), weights dx^d.
+ * Synchronises. */
+mr_status mr_error(mr_ctx ctx, int32_t tree, double t, double* out);
+
+/* Kernel launches enqueued by this process so far (for throughput claims). */
+int64_t mr_launch_count(mr_ctx ctx);
+
+/* Phase timers and work counters (tracing).  Phases: 0 refine, 1 RK4 stages,
+ * 2 details + flags, 3 merge + list rebuild, 4 synchronisation/export.
+ * ms[p] is device time between CUDA events recorded on the context's stream
+ * around the phase (only while timing is enabled); stage_blocks counts the
+ * blocks processed by all RK stage launches, stage_launches those launches. */
+typedef struct {
+  double ms[5];
+  int64_t phase_calls[5];
+  int64_t stage_launches;
+  int64_t stage_blocks;
+  int64_t steps;
+} mr_stats;
+mr_status mr_enable_timing(mr_ctx ctx, int32_t on);
+/* Synchronises; accumulates pending timers into *out. */
+mr_status mr_get_stats(mr_ctx ctx, mr_stats* out);
+mr_status mr_reset_stats(mr_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MR_H */

@@ -1,0 +1,751 @@
+// Host side of the C ABI declared in include/mr.h: parameter validation,
+// device memory, per-tree constants and the order of kernel launches that
+// makes up a multiresolution step (Sec. 2.1 of Sroka et al., arXiv:1902.00088).
+//
+// Host code never computes field values.  It only prepares constants once per
+// context or per call: per-level coefficients 1/(12 dx), RK4 stage weights
+// dt/6, dt/3, dt/2, the swirl time factor cos(pi t_s / t_a), and per-lattice
+// tables of 1D transcendental factors (Gaussian, sin^2, tanh profiles) that the
+// device kernels multiply together.  Evaluating those factors with the host's
+// IEEE libm keeps the GPU fields bit-identical to an FP64 CPU evaluation of the
+// same formulas.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mr_internal.h"
+
+using namespace mr;
+
+struct mr_ctx_s {
+  mr_params p;
+  std::vector<mr_tree_desc> td;
+  std::vector<TreeDev> tdev;
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  LaunchCfg lc{};
+  int64_t S = 0, vs = 0, ntab = 0, ncells = 0, nlat = 0, nscan = 0;
+  size_t ts = 8, ty = 8;  // bytes of state / stage types
+  // device memory
+  void* y = nullptr; void* acc = nullptr; void* Ya = nullptr; void* Yb = nullptr;
+  int8_t *lvl = nullptr, *f1 = nullptr, *flag = nullptr, *mask = nullptr;
+  int16_t* tree = nullptr;
+  int32_t *crd = nullptr, *act = nullptr, *act_next = nullptr, *freelist = nullptr, *tab = nullptr,
+          *cells = nullptr, *emit = nullptr, *eoff = nullptr, *partial = nullptr, *pos = nullptr;
+  uint64_t* hkey = nullptr;
+  double *md = nullptr, *mdet = nullptr, *bmax = nullptr, *lat = nullptr, *svar = nullptr;
+  Counters* cnt = nullptr;
+  TreeDev* trees = nullptr;
+  int4* rel = nullptr;
+  int nrel = 0;
+  std::vector<void*> owned;
+  std::string err;
+  bool has_blocks = false;
+  // tracing
+  bool timing = false;
+  struct Pending { int phase; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  mr_stats stats{};
+  int64_t stage_launches = 0;
+};
+
+namespace {
+
+mr_status fail(mr_ctx c, mr_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, MR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(mr_ctx c, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n ? n * sizeof(T) : 16);
+  if (e == cudaSuccess) {
+    c->owned.push_back(q);
+    *p = (T*)q;
+  }
+  return e;
+}
+
+PoolView view(mr_ctx c) {
+  PoolView v{};
+  v.dim = c->p.dim; v.Bs = c->p.Bs; v.nvar = c->p.nvar; v.rhs_kind = c->p.rhs_kind;
+  v.norm_kind = c->p.norm_kind; v.prec = c->p.precision; v.ntrees = c->p.ntrees;
+  v.vs = c->vs; v.cap = c->S; v.trees = c->trees;
+  v.lvl = c->lvl; v.tree = c->tree; v.crd = c->crd; v.hkey = c->hkey; v.f1 = c->f1;
+  v.flag = c->flag; v.md = c->md; v.mdet = c->mdet; v.bmax = c->bmax; v.act = c->act;
+  v.act_next = c->act_next; v.freelist = c->freelist; v.tab = c->tab; v.lat = c->lat;
+  v.svar = c->svar; v.cells = c->cells; v.emit = c->emit; v.eoff = c->eoff;
+  v.partial = c->partial; v.pos_of_slot = c->pos; v.cnt = c->cnt;
+  return v;
+}
+Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb}; }
+
+int64_t pmodh(int64_t a, int64_t n) { int64_t r = a % n; return r < 0 ? r + n : r; }
+
+// 1D factor tables of one tree on its finest lattice (node index U in [0, N)).
+void lattice_tables(const mr_params& p, const mr_tree_desc& t, int64_t N, double* out) {
+  const double h = p.L / (double)N;
+  for (int64_t U = 0; U < N; ++U) {
+    double x[3];
+    for (int a = 0; a < 3; ++a) x[a] = t.x0[a] + (double)U * h;
+    if (t.ic_kind == MR_IC_GAUSS) {
+      const double s = t.ic[3];
+      for (int a = 0; a < 3; ++a) {
+        double dd = (x[a] - 0.0) - t.ic[a];
+        while (dd >= 0.5 * p.L) dd -= p.L;
+        while (dd < -0.5 * p.L) dd += p.L;
+        out[(kLatGx + a) * N + U] = std::exp(-(dd * dd) / (2.0 * s * s));
+      }
+    }
+    if (p.rhs_kind == MR_RHS_SWIRL) {
+      const double sv = std::sin(M_PI * x[0]);
+      out[kLatSwA * N + U] = sv * sv;
+      out[kLatSwB * N + U] = std::sin(2.0 * M_PI * x[0]);
+    }
+    if (t.ic_kind == MR_IC_MIXING) {
+      const double delta = t.ic[0], U0 = t.ic[1];
+      const double yy = x[1];
+      out[kLatNsU * N + U] = U0 * ((std::tanh(2.0 * yy / delta) - std::tanh(2.0 * (yy - 0.5) / delta)) -
+                                   std::tanh(2.0 * (yy + 0.5) / delta));
+      out[kLatNsE * N + U] = std::exp(-(yy / delta) * (yy / delta));
+      double s = 0.0;
+      for (int k = 0; k < 8; ++k)
+        s += t.ic[5 + k] * std::sin(2.0 * M_PI * (double)(k + 1) * x[0] + t.ic[13 + k]);
+      out[kLatNsS * N + U] = s;
+    }
+  }
+}
+
+// Relation list of Sec. 2.2 in the order documented in mr.h.
+std::vector<int4> relation_list(int dim) {
+  std::vector<int4> r;
+  for (int nnz = 1; nnz <= dim; ++nnz)
+    for (int sz = (dim == 3 ? -1 : 0); sz <= (dim == 3 ? 1 : 0); ++sz)
+      for (int sy = -1; sy <= 1; ++sy)
+        for (int sx = -1; sx <= 1; ++sx) {
+          if ((sx != 0) + (sy != 0) + (sz != 0) != nnz) continue;
+          r.push_back(make_int4(sx, sy, sz, -1));
+          if (nnz < dim)
+            for (int sub = 0; sub < (1 << (dim - nnz)); ++sub) r.push_back(make_int4(sx, sy, sz, sub));
+        }
+  return r;
+}
+
+mr_status check_device(mr_ctx ctx) {
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaGetLastError());
+  Counters h;
+  CK(cudaMemcpy(&h, ctx->cnt, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h.err) {
+    const int e = h.err;
+    cudaMemsetAsync(&ctx->cnt->err, 0, sizeof(int32_t), ctx->st);
+    cudaStreamSynchronize(ctx->st);
+    if (e & kErrCapacity) return fail(ctx, MR_ECAPACITY, "block pool exhausted (raise capacity)");
+    if (e & kErrNaN) return fail(ctx, MR_ENAN, "non-finite value in a block norm");
+    if (e & kErrTimeout) return fail(ctx, MR_ETIMEOUT, "device wait timed out");
+    if (e & kErrLayout) return fail(ctx, MR_EINTERNAL, "blocks are not a complete, non-overlapping partition");
+    return fail(ctx, MR_EINTERNAL, "tree is not graded (level jump > 1 between touching blocks)");
+  }
+  return MR_OK;
+}
+
+Counters read_counters(mr_ctx ctx) {
+  Counters h{};
+  cudaStreamSynchronize(ctx->st);
+  cudaMemcpy(&h, ctx->cnt, sizeof(h), cudaMemcpyDeviceToHost);
+  return h;
+}
+
+template <typename F2, typename F3>
+void by_dim(mr_ctx c, F2 f2, F3 f3) {
+  if (c->p.dim == 2) f2(); else f3();
+}
+
+// Records CUDA events around a phase on the context's stream when timing is on.
+struct PhaseTimer {
+  mr_ctx c;
+  int phase;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseTimer(mr_ctx c_, int ph) : c(c_), phase(ph) {
+    c->stats.phase_calls[ph] += 1;
+    if (!c->timing) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->st);
+  }
+  ~PhaseTimer() {
+    if (!c->timing) return;
+    cudaEventRecord(b, c->st);
+    c->pending.push_back({phase, a, b});
+  }
+};
+
+void flush_timers(mr_ctx c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.b);
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    c->stats.ms[p.phase] += ms;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  c->pending.clear();
+}
+
+void do_refine(mr_ctx c, int mode) {
+  PhaseTimer tm(c, 0);
+  PoolView pv = view(c);
+  by_dim(c, [&] { launch_refine<2>(pv, fields(c), mode, c->mask, c->lc, c->st); },
+         [&] { launch_refine<3>(pv, fields(c), mode, c->mask, c->lc, c->st); });
+}
+void do_ic(mr_ctx c) {
+  PoolView pv = view(c);
+  by_dim(c, [&] { launch_ic<2>(pv, fields(c), c->lc, c->st); },
+         [&] { launch_ic<3>(pv, fields(c), c->lc, c->st); });
+}
+void do_round(mr_ctx c, bool merge) {
+  PhaseTimer tm(c, 2);
+  PoolView pv = view(c);
+  const bool fp64 = c->p.detail_fp64 != 0;
+  by_dim(c, [&] { launch_coarsen_round<2>(pv, fields(c), fp64, merge, c->lc, c->st); },
+         [&] { launch_coarsen_round<3>(pv, fields(c), fp64, merge, c->lc, c->st); });
+}
+
+mr_status coarsen_until_stable(mr_ctx ctx) {
+  int jspan = 0;
+  for (auto& t : ctx->td) jspan = std::max(jspan, t.Jmax - t.Jmin);
+  const int rounds = ctx->p.max_rounds > 0 ? ctx->p.max_rounds : jspan;
+  for (int r = 0; r < rounds; ++r) {
+    do_round(ctx, true);
+    mr_status s = check_device(ctx);
+    if (s) return s;
+    if (read_counters(ctx).merged == 0) break;
+  }
+  return MR_OK;
+}
+
+mr_status rk_step(mr_ctx ctx, const double* t, const double* dt) {
+  PhaseTimer tm(ctx, 1);
+  ctx->stats.stage_launches += 4;
+  PoolView pv = view(ctx);
+  const Fields f = fields(ctx);
+  for (int s = 0; s < 4; ++s) {
+    StageArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    for (int k = 0; k < ctx->p.ntrees; ++k) {
+      const double h = dt[k];
+      const double ca[4] = {h / 6.0, h / 3.0, h / 3.0, h / 6.0};
+      const double cy[4] = {h / 2.0, h / 2.0, h, 0.0};
+      const double tsv[4] = {t[k], t[k] + 0.5 * h, t[k] + 0.5 * h, t[k] + h};
+      sa.ca[k] = ca[s];
+      sa.cy[k] = cy[s];
+      sa.ct[k] = ctx->p.rhs_kind == MR_RHS_SWIRL ? std::cos(M_PI * tsv[s] / ctx->td[k].rhs[0]) : 0.0;
+    }
+    by_dim(ctx, [&] { launch_stage<2>(pv, f, s, sa, ctx->lc, ctx->st); },
+           [&] { launch_stage<3>(pv, f, s, sa, ctx->lc, ctx->st); });
+  }
+  CK(cudaGetLastError());
+  return MR_OK;
+}
+
+mr_status set_blocks_dev(mr_ctx ctx, int64_t n, const int32_t* lvl, const int32_t* tree,
+                         const int32_t* crd, const double* fld) {
+  // Host arrays -> device staging, then the device builds the pool.
+  int32_t *dl = nullptr, *dt = nullptr, *dc = nullptr;
+  double* df = nullptr;
+  const int nv = ctx->p.nvar;
+  int64_t ni = 1;
+  for (int a = 0; a < ctx->p.dim; ++a) ni *= ctx->p.Bs;
+  CK(cudaMallocAsync((void**)&dl, std::max<int64_t>(n, 1) * 4, ctx->st));
+  CK(cudaMallocAsync((void**)&dc, std::max<int64_t>(n, 1) * 12, ctx->st));
+  if (tree) CK(cudaMallocAsync((void**)&dt, std::max<int64_t>(n, 1) * 4, ctx->st));
+  if (fld) CK(cudaMallocAsync((void**)&df, std::max<int64_t>(n, 1) * nv * ni * 8, ctx->st));
+  CK(cudaMemcpyAsync(dl, lvl, n * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(dc, crd, n * 12, cudaMemcpyHostToDevice, ctx->st));
+  if (tree) CK(cudaMemcpyAsync(dt, tree, n * 4, cudaMemcpyHostToDevice, ctx->st));
+  if (fld) CK(cudaMemcpyAsync(df, fld, n * nv * ni * 8, cudaMemcpyHostToDevice, ctx->st));
+  PoolView pv = view(ctx);
+  auto phase = [&](int ph) {
+    by_dim(ctx,
+           [&] { launch_set_blocks<2>(pv, fields(ctx), ph, n, dl, dt, dc, df, ctx->ncells, ctx->p.ntrees, ctx->ntab, ctx->lc, ctx->st); },
+           [&] { launch_set_blocks<3>(pv, fields(ctx), ph, n, dl, dt, dc, df, ctx->ncells, ctx->p.ntrees, ctx->ntab, ctx->lc, ctx->st); });
+  };
+  phase(1);
+  mr_status s0 = check_device(ctx);
+  if (s0 == MR_OK) {
+    phase(2);
+    s0 = check_device(ctx);
+  }
+  if (s0 != MR_OK) phase(0);  // rejected input: leave an empty, consistent pool
+  cudaFreeAsync(dl, ctx->st);
+  cudaFreeAsync(dc, ctx->st);
+  if (dt) cudaFreeAsync(dt, ctx->st);
+  if (df) cudaFreeAsync(df, ctx->st);
+  if (s0 != MR_OK) {
+    std::string msg = ctx->err;
+    check_device(ctx);
+    ctx->err = msg;
+    ctx->has_blocks = false;
+    return s0;
+  }
+  mr_status s = check_device(ctx);
+  ctx->has_blocks = s == MR_OK;
+  return s;
+}
+
+int64_t range_of_tree(mr_ctx ctx, int32_t tree, int64_t* first) {
+  // blocks are ordered by tree: find [first, first + count) from exported info
+  Counters h = read_counters(ctx);
+  *first = 0;
+  if (tree < 0) return h.n_act;
+  std::vector<int16_t> tr(h.n_act);
+  std::vector<int32_t> act(h.n_act);
+  cudaMemcpy(act.data(), ctx->act, h.n_act * 4, cudaMemcpyDeviceToHost);
+  std::vector<int16_t> all(ctx->S);
+  cudaMemcpy(all.data(), ctx->tree, ctx->S * 2, cudaMemcpyDeviceToHost);
+  int64_t f = -1, n = 0;
+  for (int64_t p = 0; p < h.n_act; ++p)
+    if (all[act[p]] == tree) {
+      if (f < 0) f = p;
+      ++n;
+    }
+  *first = f < 0 ? 0 : f;
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mr_last_error(mr_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+int32_t mr_num_relations(int32_t dim) { return dim == 2 ? 16 : (dim == 3 ? 74 : 0); }
+int64_t mr_launch_count(mr_ctx) { return kernel_launches(); }
+
+mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) {
+  if (!out) return MR_EINVAL;
+  *out = nullptr;
+  if (!p || !trees) return MR_EINVAL;
+  mr_ctx ctx = new mr_ctx_s();
+  ctx->p = *p;
+  const mr_params& P = ctx->p;
+  auto bad = [&](const char* m) { mr_status s = fail(ctx, MR_EINVAL, m); delete ctx; return s; };
+  if (P.dim != 2 && P.dim != 3) return bad("dim must be 2 or 3");
+  if (!(P.Bs == 17 || (P.Bs == 33 && P.dim == 2))) return bad("Bs must be 17 (2D/3D) or 33 (2D)");
+  if (P.ng != kG) return bad("ng must be 4");
+  if (P.ntrees < 1 || P.ntrees > kMaxTrees) return bad("ntrees out of range");
+  if (P.precision < 0 || P.precision > 2) return bad("unknown precision");
+  if (P.rhs_kind == MR_RHS_SWIRL && P.dim != 2) return bad("swirl is 2D");
+  if (P.rhs_kind == MR_RHS_NS) return bad("Navier-Stokes right-hand side not available in this build");
+  if (P.rhs_kind != MR_RHS_ADV && P.rhs_kind != MR_RHS_SWIRL) return bad("unknown rhs_kind");
+  if (P.nvar != 1) return bad("advection has nvar 1");
+  if (P.capacity < 1 || P.capacity > (1LL << 30)) return bad("capacity out of range");
+  if (!(P.L > 0)) return bad("L must be positive");
+  const int maxJ = P.dim == 2 ? 10 : 7;
+  for (int k = 0; k < P.ntrees; ++k) {
+    const mr_tree_desc& t = trees[k];
+    if (t.Jmin < 1 || t.Jmax < t.Jmin || t.Jmax > maxJ) return bad("need 1 <= Jmin <= Jmax <= 10 (2D) / 7 (3D)");
+    if (t.ic_kind < 0 || t.ic_kind > 2) return bad("unknown ic_kind");
+    if (t.ic_kind == MR_IC_GAUSS && !(t.ic[3] > 0)) return bad("Gaussian sigma must be positive");
+    if (P.rhs_kind == MR_RHS_SWIRL && !(t.rhs[0] > 0)) return bad("swirl period must be positive");
+    ctx->td.push_back(t);
+  }
+  mr_status st = MR_OK;
+  {
+    cudaGetDevice(&ctx->dev);
+    ctx->st = (cudaStream_t)P.stream;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->dev) != cudaSuccess) {
+      st = fail(ctx, MR_ECUDA, "no CUDA device");
+      delete ctx;
+      return st;
+    }
+    ctx->lc.num_sms = prop.multiProcessorCount;
+    ctx->lc.grid_mult = 0;
+  }
+  const int d = P.dim, B = P.Bs, nv = P.nvar;
+  int64_t ni = 1;
+  for (int a = 0; a < d; ++a) ni *= B;
+  ctx->vs = (ni + 3) & ~3LL;
+  ctx->S = P.capacity;
+  ctx->ts = P.precision == MR_PREC_FP32 ? 4 : 8;
+  ctx->ty = P.precision == MR_PREC_FP64 ? 8 : 4;
+  // per-tree constants
+  int64_t tab = 0, cells = 0, lat = 0;
+  for (int k = 0; k < P.ntrees; ++k) {
+    const mr_tree_desc& t = ctx->td[k];
+    TreeDev td{};
+    td.Jmin = t.Jmin; td.Jmax = t.Jmax; td.eps = t.eps;
+    td.N = (int64_t)(B - 1) << t.Jmax;
+    for (int l = 0; l <= kMaxLevel; ++l) {
+      td.tab_off[l] = tab;
+      if (l <= t.Jmax) tab += (int64_t)1 << (d * l);
+      const double dx = P.L / (double)((int64_t)(B - 1) << l);
+      td.dx[l] = dx;
+      td.cD[l] = 1.0 / (12.0 * dx);
+    }
+    td.lat_off = lat;
+    lat += (int64_t)kNumLat * td.N;
+    td.cell_off = cells;
+    cells += (int64_t)1 << (d * t.Jmax);
+    for (int a = 0; a < 8; ++a) td.rhs[a] = t.rhs[a];
+    for (int a = 0; a < 3; ++a) td.x0[a] = t.x0[a];
+    td.ic_kind = t.ic_kind;
+    if (t.ic_kind == MR_IC_MIXING) {
+      const double U0 = t.ic[1], Ma = t.ic[2], gam = t.ic[3];
+      const double c0 = U0 / Ma;
+      const double p0 = c0 * c0 / gam;
+      td.ic_e0 = p0 / (gam - 1.0);
+      td.ic_amp = t.ic[4];
+    }
+    ctx->tdev.push_back(td);
+  }
+  ctx->ntab = tab;
+  ctx->ncells = cells;
+  ctx->nlat = lat;
+  ctx->nscan = std::max<int64_t>(ctx->S, cells);
+  auto alloc_all = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    const int64_t S = ctx->S;
+    if ((e = dalloc(ctx, (char**)&ctx->y, S * nv * ctx->vs * ctx->ts))) return e;
+    if ((e = dalloc(ctx, (char**)&ctx->acc, S * nv * ctx->vs * ctx->ts))) return e;
+    if ((e = dalloc(ctx, (char**)&ctx->Ya, S * nv * ctx->vs * ctx->ty))) return e;
+    if ((e = dalloc(ctx, (char**)&ctx->Yb, S * nv * ctx->vs * ctx->ty))) return e;
+    if ((e = dalloc(ctx, &ctx->lvl, S))) return e;
+    if ((e = dalloc(ctx, &ctx->f1, S))) return e;
+    if ((e = dalloc(ctx, &ctx->flag, S))) return e;
+    if ((e = dalloc(ctx, &ctx->mask, S))) return e;
+    if ((e = dalloc(ctx, &ctx->tree, S))) return e;
+    if ((e = dalloc(ctx, &ctx->crd, 3 * S))) return e;
+    if ((e = dalloc(ctx, &ctx->hkey, S))) return e;
+    if ((e = dalloc(ctx, &ctx->md, S * nv))) return e;
+    if ((e = dalloc(ctx, &ctx->bmax, S * nv))) return e;
+    if ((e = dalloc(ctx, &ctx->mdet, S))) return e;
+    if ((e = dalloc(ctx, &ctx->act, S))) return e;
+    if ((e = dalloc(ctx, &ctx->act_next, S))) return e;
+    if ((e = dalloc(ctx, &ctx->freelist, S))) return e;
+    if ((e = dalloc(ctx, &ctx->pos, S))) return e;
+    if ((e = dalloc(ctx, &ctx->tab, ctx->ntab))) return e;
+    if ((e = dalloc(ctx, &ctx->cells, 2 * ctx->ncells))) return e;
+    if ((e = dalloc(ctx, &ctx->emit, 2 * ctx->nscan))) return e;
+    if ((e = dalloc(ctx, &ctx->eoff, 2 * ctx->nscan))) return e;
+    if ((e = dalloc(ctx, &ctx->partial, 2 * (ctx->nscan / kScanChunk + 2)))) return e;
+    if ((e = dalloc(ctx, &ctx->lat, ctx->nlat))) return e;
+    if ((e = dalloc(ctx, &ctx->svar, (int64_t)P.ntrees * nv))) return e;
+    if ((e = dalloc(ctx, &ctx->cnt, 1))) return e;
+    if ((e = dalloc(ctx, &ctx->trees, P.ntrees))) return e;
+    std::vector<int4> rel = relation_list(d);
+    ctx->nrel = (int)rel.size();
+    if ((e = dalloc(ctx, &ctx->rel, rel.size()))) return e;
+    if ((e = cudaMemcpy(ctx->rel, rel.data(), rel.size() * sizeof(int4), cudaMemcpyHostToDevice))) return e;
+    if ((e = cudaMemcpy(ctx->trees, ctx->tdev.data(), P.ntrees * sizeof(TreeDev), cudaMemcpyHostToDevice))) return e;
+    std::vector<double> hl(ctx->nlat, 0.0);
+    for (int k = 0; k < P.ntrees; ++k)
+      lattice_tables(P, ctx->td[k], ctx->tdev[k].N, hl.data() + ctx->tdev[k].lat_off);
+    if ((e = cudaMemcpy(ctx->lat, hl.data(), ctx->nlat * 8, cudaMemcpyHostToDevice))) return e;
+    if ((e = cudaMemset(ctx->cnt, 0, sizeof(Counters)))) return e;
+    if ((e = cudaMemset(ctx->mask, 0, S))) return e;
+    if ((e = cudaMemset(ctx->lvl, 0xff, S))) return e;
+    if ((e = cudaMemset(ctx->tab, 0xff, ctx->ntab * 4))) return e;
+    return cudaDeviceSynchronize();
+  };
+  cudaError_t e = alloc_all();
+  if (e != cudaSuccess) {
+    st = fail(ctx, e == cudaErrorMemoryAllocation ? MR_ENOMEM : MR_ECUDA, cudaGetErrorString(e));
+    cudaGetLastError();
+    mr_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return MR_OK;
+}
+
+void mr_destroy(mr_ctx ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  for (void* q : ctx->owned) cudaFree(q);
+  delete ctx;
+}
+
+mr_status mr_set_blocks(mr_ctx ctx, int64_t n, const int32_t* level, const int32_t* tree,
+                        const int32_t* coords, const double* flds) {
+  if (!ctx) return MR_EINVAL;
+  if (n < 1 || n > ctx->S || !level || !coords) return fail(ctx, MR_EINVAL, "bad block list");
+  return set_blocks_dev(ctx, n, level, tree, coords, flds);
+}
+
+mr_status mr_init_tree(mr_ctx ctx) {
+  if (!ctx) return MR_EINVAL;
+  // uniform grid at Jmin of every tree
+  std::vector<int32_t> lv, tr, cr;
+  for (int k = 0; k < ctx->p.ntrees; ++k) {
+    const int J = ctx->td[k].Jmin;
+    const int64_t n = (int64_t)1 << J;
+    for (int64_t z = 0; z < (ctx->p.dim == 3 ? n : 1); ++z)
+      for (int64_t yy = 0; yy < n; ++yy)
+        for (int64_t x = 0; x < n; ++x) {
+          lv.push_back(J); tr.push_back(k);
+          cr.push_back((int32_t)x); cr.push_back((int32_t)yy); cr.push_back((int32_t)z);
+        }
+  }
+  if ((int64_t)lv.size() > ctx->S) return fail(ctx, MR_ECAPACITY, "capacity below the Jmin grid");
+  mr_status s = set_blocks_dev(ctx, (int64_t)lv.size(), lv.data(), tr.data(), cr.data(), nullptr);
+  if (s) return s;
+  do_ic(ctx);
+  int jspan = 0;
+  for (auto& t : ctx->td) jspan = std::max(jspan, t.Jmax - t.Jmin);
+  for (int it = 0; it < jspan; ++it) {
+    do_refine(ctx, MR_ADAPT_REFINE_ALL);
+    if ((s = check_device(ctx))) return s;
+    do_ic(ctx);
+    if ((s = coarsen_until_stable(ctx))) return s;
+  }
+  return check_device(ctx);
+}
+
+mr_status mr_set_rhs(mr_ctx ctx, int32_t rhs_kind, int32_t tree, const double* rp) {
+  if (!ctx || !rp) return MR_EINVAL;
+  if (rhs_kind != ctx->p.rhs_kind) return fail(ctx, MR_EINVAL, "rhs kind differs from the context's");
+  if (tree < -1 || tree >= ctx->p.ntrees) return fail(ctx, MR_EINVAL, "tree out of range");
+  for (int k = 0; k < ctx->p.ntrees; ++k) {
+    if (tree >= 0 && k != tree) continue;
+    for (int a = 0; a < 8; ++a) { ctx->td[k].rhs[a] = rp[a]; ctx->tdev[k].rhs[a] = rp[a]; }
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->trees, ctx->tdev.data(), ctx->p.ntrees * sizeof(TreeDev),
+                                  cudaMemcpyHostToDevice, ctx->st);
+  if (e != cudaSuccess) return fail(ctx, MR_ECUDA, cudaGetErrorString(e));
+  if (ctx->p.rhs_kind == MR_RHS_SWIRL) {
+    // lattice tables do not depend on the swirl period; nothing else to rebuild
+  }
+  return cudaStreamSynchronize(ctx->st) == cudaSuccess ? MR_OK : fail(ctx, MR_ECUDA, "sync");
+}
+
+mr_status mr_sync_ghosts(mr_ctx ctx) {
+  if (!ctx) return MR_EINVAL;
+  PoolView pv = view(ctx);
+  by_dim(ctx, [&] { launch_sync<2>(pv, fields(ctx), nullptr, ctx->lc, ctx->st); },
+         [&] { launch_sync<3>(pv, fields(ctx), nullptr, ctx->lc, ctx->st); });
+  return cudaGetLastError() == cudaSuccess ? MR_OK : fail(ctx, MR_ECUDA, "launch");
+}
+
+mr_status mr_rk_step(mr_ctx ctx, const double* t, const double* dt) {
+  if (!ctx || !t || !dt) return MR_EINVAL;
+  return rk_step(ctx, t, dt);
+}
+
+mr_status mr_adapt(mr_ctx ctx, int32_t mode) {
+  if (!ctx) return MR_EINVAL;
+  if (mode == MR_ADAPT_REFINE_ALL || mode == MR_ADAPT_REFINE_FLAGGED) {
+    do_refine(ctx, mode);
+    return check_device(ctx);
+  }
+  if (mode == MR_ADAPT_COARSEN) return coarsen_until_stable(ctx);
+  if (mode == 3) {  // details and flags only (no merge), for inspection
+    do_round(ctx, false);
+    return check_device(ctx);
+  }
+  return fail(ctx, MR_EINVAL, "unknown adapt mode");
+}
+
+mr_status mr_step(mr_ctx ctx, const double* t, const double* dt) {
+  if (!ctx || !t || !dt) return MR_EINVAL;
+  ctx->stats.steps += 1;
+  do_refine(ctx, MR_ADAPT_REFINE_ALL);
+  mr_status s = rk_step(ctx, t, dt);
+  if (s) return s;
+  return coarsen_until_stable(ctx);
+}
+
+mr_status mr_num_blocks(mr_ctx ctx, int32_t tree, int64_t* n) {
+  if (!ctx || !n) return MR_EINVAL;
+  mr_status s = check_device(ctx);
+  if (s) return s;
+  int64_t first = 0;
+  *n = range_of_tree(ctx, tree, &first);
+  return MR_OK;
+}
+
+mr_status mr_get_blocks(mr_ctx ctx, int32_t tree, int64_t cap, int64_t* n, mr_block_info* info,
+                        double* flds) {
+  if (!ctx || !n) return MR_EINVAL;
+  mr_status s = check_device(ctx);
+  if (s) return s;
+  int64_t first = 0;
+  const int64_t cnt = range_of_tree(ctx, tree, &first);
+  *n = cnt;
+  if (cap < cnt) return fail(ctx, MR_EINVAL, "output buffer too small");
+  const Counters h = read_counters(ctx);
+  int64_t ni = 1;
+  for (int a = 0; a < ctx->p.dim; ++a) ni *= ctx->p.Bs;
+  const int64_t per = ctx->p.nvar * ni;
+  mr_block_info* dinfo = nullptr;
+  double* dfld = nullptr;
+  CK(cudaMalloc(&dinfo, std::max<int64_t>(h.n_act, 1) * sizeof(mr_block_info)));
+  if (flds) CK(cudaMalloc(&dfld, std::max<int64_t>(h.n_act, 1) * per * 8));
+  PoolView pv = view(ctx);
+  by_dim(ctx, [&] { launch_export<2>(pv, fields(ctx), dinfo, dfld, nullptr, nullptr, ctx->lc, ctx->st); },
+         [&] { launch_export<3>(pv, fields(ctx), dinfo, dfld, nullptr, nullptr, ctx->lc, ctx->st); });
+  CK(cudaStreamSynchronize(ctx->st));
+  if (info) CK(cudaMemcpy(info, dinfo + first, cnt * sizeof(mr_block_info), cudaMemcpyDeviceToHost));
+  if (flds) CK(cudaMemcpy(flds, dfld + first * per, cnt * per * 8, cudaMemcpyDeviceToHost));
+  cudaFree(dinfo);
+  if (dfld) cudaFree(dfld);
+  return MR_OK;
+}
+
+mr_status mr_get_tiles(mr_ctx ctx, int32_t tree, int64_t cap, int64_t* n, double* tiles) {
+  if (!ctx || !n || !tiles) return MR_EINVAL;
+  mr_status s = check_device(ctx);
+  if (s) return s;
+  int64_t first = 0;
+  const int64_t cnt = range_of_tree(ctx, tree, &first);
+  *n = cnt;
+  if (cap < cnt) return fail(ctx, MR_EINVAL, "output buffer too small");
+  const Counters h = read_counters(ctx);
+  int64_t tile = 1;
+  for (int a = 0; a < ctx->p.dim; ++a) tile *= ctx->p.Bs + 2 * ctx->p.ng;
+  const int64_t per = ctx->p.nvar * tile;
+  double* dt = nullptr;
+  CK(cudaMalloc(&dt, std::max<int64_t>(h.n_act, 1) * per * 8));
+  PoolView pv = view(ctx);
+  by_dim(ctx, [&] { launch_sync<2>(pv, fields(ctx), dt, ctx->lc, ctx->st); },
+         [&] { launch_sync<3>(pv, fields(ctx), dt, ctx->lc, ctx->st); });
+  s = check_device(ctx);
+  if (!s) CK(cudaMemcpy(tiles, dt + first * per, cnt * per * 8, cudaMemcpyDeviceToHost));
+  cudaFree(dt);
+  return s;
+}
+
+mr_status mr_get_neighbors(mr_ctx ctx, int32_t tree, int64_t cap, int32_t* nbr, int8_t* dl) {
+  if (!ctx || !nbr || !dl) return MR_EINVAL;
+  mr_status s = check_device(ctx);
+  if (s) return s;
+  int64_t first = 0;
+  const int64_t cnt = range_of_tree(ctx, tree, &first);
+  if (cap < cnt) return fail(ctx, MR_EINVAL, "output buffer too small");
+  const Counters h = read_counters(ctx);
+  const int R = ctx->nrel;
+  int32_t* dn = nullptr;
+  int8_t* dd = nullptr;
+  CK(cudaMalloc(&dn, std::max<int64_t>(h.n_act, 1) * R * 4));
+  CK(cudaMalloc(&dd, std::max<int64_t>(h.n_act, 1) * R));
+  // position of every slot in the list
+  std::vector<int32_t> act(h.n_act), pos(ctx->S, -1);
+  CK(cudaMemcpy(act.data(), ctx->act, h.n_act * 4, cudaMemcpyDeviceToHost));
+  for (int64_t p = 0; p < h.n_act; ++p) pos[act[p]] = (int32_t)(p - first);
+  CK(cudaMemcpy(ctx->pos, pos.data(), ctx->S * 4, cudaMemcpyHostToDevice));
+  PoolView pv = view(ctx);
+  by_dim(ctx, [&] { launch_neighbors<2>(pv, ctx->rel, R, dn, dd, ctx->lc, ctx->st); },
+         [&] { launch_neighbors<3>(pv, ctx->rel, R, dn, dd, ctx->lc, ctx->st); });
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaMemcpy(nbr, dn + first * R, cnt * R * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dl, dd + first * R, cnt * R, cudaMemcpyDeviceToHost));
+  cudaFree(dn);
+  cudaFree(dd);
+  return MR_OK;
+}
+
+mr_status mr_get_flags(mr_ctx ctx, int32_t tree, int64_t cap, int8_t* flg, double* mdet) {
+  if (!ctx) return MR_EINVAL;
+  mr_status s = check_device(ctx);
+  if (s) return s;
+  int64_t first = 0;
+  const int64_t cnt = range_of_tree(ctx, tree, &first);
+  if (cap < cnt) return fail(ctx, MR_EINVAL, "output buffer too small");
+  const Counters h = read_counters(ctx);
+  int8_t* df = nullptr;
+  double* dm = nullptr;
+  CK(cudaMalloc(&df, std::max<int64_t>(h.n_act, 1)));
+  CK(cudaMalloc(&dm, std::max<int64_t>(h.n_act, 1) * 8));
+  PoolView pv = view(ctx);
+  by_dim(ctx, [&] { launch_export<2>(pv, fields(ctx), nullptr, nullptr, df, dm, ctx->lc, ctx->st); },
+         [&] { launch_export<3>(pv, fields(ctx), nullptr, nullptr, df, dm, ctx->lc, ctx->st); });
+  CK(cudaStreamSynchronize(ctx->st));
+  if (flg) CK(cudaMemcpy(flg, df + first, cnt, cudaMemcpyDeviceToHost));
+  if (mdet) CK(cudaMemcpy(mdet, dm + first, cnt * 8, cudaMemcpyDeviceToHost));
+  cudaFree(df);
+  cudaFree(dm);
+  return MR_OK;
+}
+
+mr_status mr_set_refine_mask(mr_ctx ctx, int64_t n, const int8_t* mask) {
+  if (!ctx || !mask) return MR_EINVAL;
+  const Counters h = read_counters(ctx);
+  if (n != h.n_act) return fail(ctx, MR_EINVAL, "mask length differs from the block count");
+  CK(cudaMemcpyAsync(ctx->mask, mask, n, cudaMemcpyHostToDevice, ctx->st));
+  return check_device(ctx);
+}
+
+mr_status mr_error(mr_ctx ctx, int32_t tree, double t, double* out) {
+  if (!ctx || !out || tree < 0 || tree >= ctx->p.ntrees) return MR_EINVAL;
+  const mr_tree_desc& td = ctx->td[tree];
+  if (td.ic_kind != MR_IC_GAUSS) return fail(ctx, MR_EINVAL, "error needs the Gaussian IC");
+  const int64_t N = ctx->tdev[tree].N;
+  const double h = ctx->p.L / (double)N;
+  std::vector<double> ex(3 * N, 1.0);
+  for (int a = 0; a < ctx->p.dim; ++a) {
+    const double shift = ctx->p.rhs_kind == MR_RHS_ADV ? td.rhs[a] * t : 0.0;
+    for (int64_t U = 0; U < N; ++U) {
+      const double x = td.x0[a] + (double)U * h;
+      double dd = (x - shift) - td.ic[a];
+      while (dd >= 0.5 * ctx->p.L) dd -= ctx->p.L;
+      while (dd < -0.5 * ctx->p.L) dd += ctx->p.L;
+      const double s = td.ic[3];
+      ex[a * N + U] = std::exp(-(dd * dd) / (2.0 * s * s));
+    }
+  }
+  double *dex = nullptr, *dout = nullptr;
+  CK(cudaMalloc(&dex, 3 * N * 8));
+  CK(cudaMalloc(&dout, 4 * 8));
+  CK(cudaMemcpy(dex, ex.data(), 3 * N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemset(dout, 0, 32));
+  PoolView pv = view(ctx);
+  by_dim(ctx, [&] { launch_error<2>(pv, fields(ctx), tree, dex, dout, ctx->lc, ctx->st); },
+         [&] { launch_error<3>(pv, fields(ctx), tree, dex, dout, ctx->lc, ctx->st); });
+  CK(cudaStreamSynchronize(ctx->st));
+  double o[4];
+  CK(cudaMemcpy(o, dout, 32, cudaMemcpyDeviceToHost));
+  out[0] = std::sqrt(o[0]); out[1] = std::sqrt(o[1]); out[2] = o[2]; out[3] = o[3];
+  cudaFree(dex);
+  cudaFree(dout);
+  return MR_OK;
+}
+
+mr_status mr_enable_timing(mr_ctx ctx, int32_t on) {
+  if (!ctx) return MR_EINVAL;
+  ctx->timing = on != 0;
+  return MR_OK;
+}
+
+mr_status mr_get_stats(mr_ctx ctx, mr_stats* out) {
+  if (!ctx || !out) return MR_EINVAL;
+  mr_status s = check_device(ctx);
+  if (s) return s;
+  flush_timers(ctx);
+  Counters h = read_counters(ctx);
+  ctx->stats.stage_blocks = (int64_t)h.stage_blocks;
+  *out = ctx->stats;
+  return MR_OK;
+}
+
+mr_status mr_reset_stats(mr_ctx ctx) {
+  if (!ctx) return MR_EINVAL;
+  cudaStreamSynchronize(ctx->st);
+  flush_timers(ctx);
+  ctx->stats = mr_stats{};
+  unsigned long long z = 0;
+  cudaMemcpy(&ctx->cnt->stage_blocks, &z, sizeof(z), cudaMemcpyHostToDevice);
+  return MR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal definitions shared by the host API (mr_api.cu) and the kernels
+// (mr_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mr.h"
+
+namespace mr {
+
+constexpr int kMaxTrees = 128;
+constexpr int kMaxLevel = 11;  // 2D Jmax <= 10, 3D Jmax <= 7 (dense per-level tables)
+constexpr int kG = 4;          // ghost layer width
+
+// Device error codes (bit flags OR-ed into Counters::err).
+constexpr int kErrCapacity = 1;
+constexpr int kErrGraded = 2;    // ring cell without a leaf at l-1..l+1, stencil outside ring
+constexpr int kErrNaN = 4;
+constexpr int kErrLayout = 8;    // set_blocks: overlap / gap / unsorted input
+constexpr int kErrTimeout = 16;
+
+// Per-tree constants (device copy).
+struct TreeDev {
+  int32_t Jmin, Jmax;
+  double eps;
+  int64_t N;                        // finest-lattice intervals per axis: (Bs-1) << Jmax
+  int64_t tab_off[kMaxLevel + 1];   // offset of level l's dense slot table
+  int64_t lat_off;                  // offset of this tree's lattice tables (N entries each)
+  int64_t cell_off;                 // offset of this tree's finest-cell array (2^(d Jmax))
+  double cD[kMaxLevel + 1];         // 1 / (12 dx_l)
+  double dx[kMaxLevel + 1];         // dx_l = L / (2^l (Bs-1))
+  double rhs[8];
+  double x0[3];
+  int32_t ic_kind;
+  double ic_e0, ic_amp;             // mixing layer: p0/(gamma-1) and perturbation amplitude
+};
+
+// Device counters (one instance per context).
+struct Counters {
+  int32_t n_act;    // active blocks (all trees)
+  int32_t n_free;   // free-slot stack height
+  int32_t n_new;    // size of the list being built
+  int32_t n_alloc;  // slots requested by a refine
+  int32_t merged;   // families merged in the last coarsening round
+  int32_t err;      // kErr* bits
+  int32_t n_cells_bad;
+  int32_t pad;
+  unsigned long long stage_blocks;  // blocks processed by RK stage launches
+};
+
+// Lattice tables: per tree, kNumLat tables of N doubles, indexed by the node
+// index U in [0, N) on the finest lattice of the tree.
+enum LatTable {
+  kLatGx = 0, kLatGy, kLatGz,   // Gaussian factors (IC)
+  kLatSwA, kLatSwB,             // swirl factors sin^2(pi x), sin(2 pi x)
+  kLatNsU, kLatNsE, kLatNsS,    // mixing layer: u(y), exp(-(y/delta)^2), sum_k a_k sin(2 pi k x + phi_k)
+  kNumLat
+};
+
+// Per-stage RK4 scalars of every tree, passed by value to the stage kernel.
+struct StageArgs {
+  double ca[kMaxTrees];   // accumulator coefficient: dt/6, dt/3, dt/3, dt/6
+  double cy[kMaxTrees];   // next-stage coefficient: dt/2, dt/2, dt, (unused)
+  double ct[kMaxTrees];   // swirl time factor cos(pi t_s / t_a)
+};
+
+// Everything a kernel needs to know about the pool and the tree tables.
+struct PoolView {
+  int dim, Bs, nvar, rhs_kind, norm_kind, prec, ntrees;
+  int64_t vs;              // per-variable stride of a block in the pool (elements)
+  int64_t cap;             // slots
+  const TreeDev* trees;
+  int8_t* lvl;             // per slot, -1 unused
+  int16_t* tree;
+  int32_t* crd;            // per slot x3
+  uint64_t* hkey;
+  int8_t* f1;              // per slot, first flag pass
+  int8_t* flag;            // per slot
+  double* md;              // per slot x nvar, max |detail|
+  double* mdet;            // per slot
+  double* bmax;            // per slot x nvar, max |q_v| of the synchronised interior
+  int32_t* act;            // current active list (positions -> slot)
+  int32_t* act_next;
+  int32_t* freelist;
+  int32_t* tab;            // dense per-tree per-level leaf tables (-1 = no leaf)
+  const double* lat;       // lattice tables
+  double* svar;            // per tree x nvar threshold scale
+  int32_t* cells;          // finest-cell marks (set_blocks validation / ranking)
+  int32_t* emit;           // scan input  [cap] x2 (int2)
+  int32_t* eoff;           // scan output [cap] x2 (int2)
+  int32_t* partial;        // scan partials
+  int32_t* pos_of_slot;
+  Counters* cnt;
+};
+
+// ---------------------------------------------------------------- launchers --
+// Fields are passed as void* and interpreted by prec: y and acc hold the state
+// type (double for FP64 / FP32_ACC64, float for FP32), Ya/Yb the stage type
+// (double for FP64, float otherwise).
+struct Fields {
+  void* y;
+  void* acc;
+  void* Ya;
+  void* Yb;
+};
+
+struct LaunchCfg {
+  int num_sms;
+  int grid_mult;  // persistent CTAs per SM for the stage kernel (0 = occupancy)
+};
+
+// Per-dimension launchers (explicitly instantiated in mr_k2.cu / mr_k3.cu).
+template <int D> void launch_stage(const PoolView& pv, const Fields& f, int stage,
+                                   const StageArgs& sa, const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_refine(const PoolView& pv, const Fields& f, int mode,
+                                    const int8_t* mask, const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_ic(const PoolView& pv, const Fields& f, const LaunchCfg& lc,
+                                cudaStream_t st);
+template <int D> void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64,
+                                           bool merge, const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_sync(const PoolView& pv, const Fields& f, double* tiles,
+                                  const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_neighbors(const PoolView& pv, const int4* rel, int R, int32_t* nbr,
+                                       int8_t* dl, const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_export(const PoolView& pv, const Fields& f, mr_block_info* info,
+                                    double* fields, int8_t* flags, double* mdet,
+                                    const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_set_blocks(const PoolView& pv, const Fields& f, int phase, int64_t n,
+                                        const int32_t* lvl, const int32_t* tree,
+                                        const int32_t* crd, const double* fields, int64_t ncells,
+                                        int ntrees, int64_t ntab, const LaunchCfg& lc,
+                                        cudaStream_t st);
+template <int D> void launch_error(const PoolView& pv, const Fields& f, int tree, const double* ex,
+                                   double* out4, const LaunchCfg& lc, cudaStream_t st);
+
+// Exclusive scan of n int2 pairs (emit -> eoff); totals written to tot[0..1].
+// n_dev: device count (nullable), else n_host.
+// `partial` needs 2 * ceil(n_max / kScanChunk) + 2 ints.
+constexpr int kScanChunk = 2048;
+void launch_scan2(const int32_t* in, int32_t* out, int32_t* partial, const int32_t* n_dev,
+                  int64_t n_host, int32_t* tot, cudaStream_t st);
+void count_launch(int n = 1);
+int64_t kernel_launches();
+
+}  // namespace mr

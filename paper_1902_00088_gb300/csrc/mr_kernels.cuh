@@ -1,0 +1,700 @@
+// Kernel templates of the multiresolution step.  Instantiated per dimension in
+// mr_k2.cu / mr_k3.cu.  Every persistent kernel loops over the active list with
+// a grid-stride loop bounded by the device-side block count, so no launch
+// needs a host round trip.
+#pragma once
+#include "mr_device.cuh"
+
+namespace mr {
+
+constexpr int kRingBytes = 64 * 4 + 64 + 64;  // rslot[64] + rlvl[64] + pad (16-aligned)
+
+// ------------------------------------------------------------------ stage ----
+// One RK4 stage on every block (Sec. 3: 4th-order central FD + classic RK4):
+//   k = N(Y_s) on the synchronised tile, then the 3-register update
+//   s0: acc = y + dt/6 k, Y1 = y + dt/2 k      s1: acc += dt/3 k, Y2 = y + dt/2 k
+//   s2: acc += dt/3 k,    Y3 = y + dt k        s3: y = acc + dt/6 k
+// Advection RHS: -(u Dx phi + v Dy phi [+ w Dz phi]),
+//   D1 f = ((f[-2] - f[2]) + 8 (f[1] - f[-1])) / (12 dx).
+template <int D, int B, int RHS, typename TS, typename TY, typename TSRC>
+__global__ void k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
+                            TS* __restrict__ acc, TY* __restrict__ ynext, int stage, StageArgs sa) {
+  using Gm = Geo<D, B>;
+  using TC = TY;  // stencil arithmetic type
+  int* rslot = smem_as<int>(0);
+  int8_t* rlvl = smem_as<int8_t>(256);
+  TC* tile = smem_as<TC>(kRingBytes);
+  const int nact = pv.cnt->n_act;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    __syncthreads();
+    fill_tile<D, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, rslot, rlvl);
+    __syncthreads();
+    const TC c = (TC)td.cD[b.lvl];
+    const double ca = sa.ca[b.tree], cy = sa.cy[b.tree], ct = sa.ct[b.tree];
+    const int64_t base = (int64_t)b.slot * pv.vs;  // nvar == 1
+    const int sh = td.Jmax - b.lvl;
+    for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
+      const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
+      const TC* t0 = tile + Gm::tix(i, j, k);
+      const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
+      const TC dyv = ((t0[-2 * Gm::T] - t0[2 * Gm::T]) + TC(8) * (t0[Gm::T] - t0[-Gm::T])) * c;
+      TC dzv = TC(0);
+      if (D == 3) {
+        constexpr int P = Gm::T * Gm::T;
+        dzv = ((t0[-2 * P] - t0[2 * P]) + TC(8) * (t0[P] - t0[-P])) * c;
+      }
+      double u0, u1, u2 = 0.0;
+      if (RHS == MR_RHS_SWIRL) {
+        const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
+        const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
+        const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
+        const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
+        u0 = ct * (A[Ux] * Bt[Uy]);
+        u1 = -(ct * (A[Uy] * Bt[Ux]));
+      } else {
+        u0 = td.rhs[0];
+        u1 = td.rhs[1];
+        u2 = td.rhs[2];
+      }
+      TC s = (TC)u0 * dxv + (TC)u1 * dyv;
+      if (D == 3) s = s + (TC)u2 * dzv;
+      const TS kk = (TS)(-s);
+      const int64_t at = base + q;
+      if (stage == 0) {
+        const TS yv = y[at];  // committed (synchronised) y_n
+        acc[at] = yv + (TS)ca * kk;
+        ynext[at] = (TY)(yv + (TS)cy * kk);
+      } else if (stage == 1 || stage == 2) {
+        const TS yv = y[at];
+        acc[at] = acc[at] + (TS)ca * kk;
+        ynext[at] = (TY)(yv + (TS)cy * kk);
+      } else {
+        y[at] = acc[at] + (TS)ca * kk;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------- refine ----
+// Sec. 2.3: the synchronised mother tile is upsampled by the 4th-order
+// interpolating prediction and split into 2^d children (one treecode digit
+// appended); children are placed in the new active list in Hilbert order.
+template <int D, int B, typename TS>
+__global__ void k_refine(PoolView pv, TS* __restrict__ y) {
+  using Gm = Geo<D, B>;
+  int* rslot = smem_as<int>(0);
+  int8_t* rlvl = smem_as<int8_t>(256);
+  __shared__ int cslot[8];
+  TS* tile = smem_as<TS>(kRingBytes);
+  const int nact = pv.cnt->n_act;
+  const int n_alloc = pv.cnt->n_alloc, n_free = pv.cnt->n_free;
+  if (n_alloc > n_free) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_err(pv, kErrCapacity);
+    return;
+  }
+  const int nv = pv.nvar;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const int slot = pv.act[p];
+    const int e = pv.eoff[2 * p], a = pv.eoff[2 * p + 1];
+    if (pv.flag[slot] != 1) {
+      if (threadIdx.x == 0) pv.act_next[e] = slot;
+      continue;
+    }
+    const BlockInfo b = load_block(pv, slot);
+    const TreeDev& td = pv.trees[b.tree];
+    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    __syncthreads();
+    fill_tile<D, B, TS, TS>(pv, b, y, y, tile, false, rslot, rlvl);
+    if (threadIdx.x == 0) {
+      uint64_t key[8];
+      int32_t cc[8][3];
+      for (int ch = 0; ch < Gm::NCH; ++ch) {
+        cslot[ch] = pv.freelist[n_free - n_alloc + a + ch];
+        for (int ax = 0; ax < 3; ++ax)
+          cc[ch][ax] = ax < D ? (int32_t)(2 * b.c[ax] + ((ch >> ax) & 1)) : 0;
+        key[ch] = block_key<D>(cc[ch], b.lvl + 1, td.Jmax);
+      }
+      for (int ch = 0; ch < Gm::NCH; ++ch) {
+        int rank = 0;
+        for (int o = 0; o < Gm::NCH; ++o) rank += key[o] < key[ch];
+        const int cs = cslot[ch];
+        pv.act_next[e + rank] = cs;
+        pv.lvl[cs] = (int8_t)(b.lvl + 1);
+        pv.tree[cs] = (int16_t)b.tree;
+        for (int ax = 0; ax < 3; ++ax) pv.crd[3 * cs + ax] = cc[ch][ax];
+        pv.hkey[cs] = key[ch];
+        pv.flag[cs] = 0;
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Gm::NCH * Gm::NI; idx += blockDim.x) {
+      const int ch = idx / Gm::NI, q = idx % Gm::NI;
+      const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
+      const int o[3] = {((ch >> 0) & 1) * (B - 1) + i, ((ch >> 1) & 1) * (B - 1) + j,
+                        D == 3 ? ((ch >> 2) & 1) * (B - 1) + k : 0};
+      for (int v = 0; v < nv; ++v)
+        y[((int64_t)cslot[ch] * nv + v) * pv.vs + q] = predict_tile<D, B, TS>(tile + v * Gm::TILE, o, 1);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- details ----
+// Sec. 2.3: D = B - P(R(B)) on the synchronised tile (R keeps even tile nodes,
+// ghosts included; P predicts the odd ones).  Per block and variable the
+// largest |d| (warp-shuffle max, then across warps) and the largest |q_v|.
+template <int D, int B, typename TS, typename TD>
+__global__ void k_details(PoolView pv, TS* __restrict__ y) {
+  using Gm = Geo<D, B>;
+  int* rslot = smem_as<int>(0);
+  int8_t* rlvl = smem_as<int8_t>(256);
+  __shared__ double red[2][32];
+  TD* tile = smem_as<TD>(kRingBytes);
+  const int nact = pv.cnt->n_act;
+  const int nv = pv.nvar;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    __syncthreads();
+    fill_tile<D, B, TS, TD>(pv, b, y, y, tile, true, rslot, rlvl);
+    __syncthreads();
+    for (int v = 0; v < nv; ++v) {
+      const TD* tv = tile + v * Gm::TILE;
+      double md = 0.0, mq = 0.0;
+      for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
+        const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
+        const TD val = tv[Gm::tix(i, j, k)];
+        mq = fmax(mq, fabs((double)val));
+        if (((i | j | k) & 1) == 0) continue;
+        const int o[3] = {i, j, k};
+        const TD d = val - predict_tile<D, B, TD>(tv, o, 2);
+        md = fmax(md, fabs((double)d));
+      }
+      for (int s = 16; s > 0; s >>= 1) {
+        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, s));
+        mq = fmax(mq, __shfl_xor_sync(0xffffffffu, mq, s));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = md;
+        red[1][threadIdx.x >> 5] = mq;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+          md = fmax(md, red[0][w]);
+          mq = fmax(mq, red[1][w]);
+        }
+        // a NaN anywhere in the block makes its norm NaN (fmax drops NaN)
+        pv.md[(int64_t)b.slot * nv + v] = md;
+        pv.bmax[(int64_t)b.slot * nv + v] = mq;
+        if (pv.norm_kind == 1) atomic_max_pos(&pv.svar[b.tree * nv + v], mq);
+      }
+      __syncthreads();
+    }
+    // NaN detection: any non-finite interior value
+    bool bad = false;
+    for (int q = threadIdx.x; q < Gm::NI * nv; q += blockDim.x) {
+      const int v = q / Gm::NI, r = q % Gm::NI;
+      const int i = r % B, j = (r / B) % B, k = D == 3 ? r / (B * B) : 0;
+      const double val = (double)tile[v * Gm::TILE + Gm::tix(i, j, k)];
+      bad |= !isfinite(val);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+      pv.md[(int64_t)b.slot * nv] = __longlong_as_double(0x7ff8000000000000LL);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- coarsen ----
+// Sec. 2.3: 2^d sisters with status -2 merge into their mother by restriction
+// (every second node); a mother node on a line shared by two children is read
+// from the child in which it has local index 0.  The mother takes the slot of
+// the family member that comes first in Hilbert order.
+template <int D, int B, typename TS>
+__global__ void k_coarsen(PoolView pv, TS* __restrict__ y) {
+  using Gm = Geo<D, B>;
+  TS* buf = smem_as<TS>(0);
+  __shared__ int cs[8];
+  const int nact = pv.cnt->n_act;
+  const int nv = pv.nvar;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const int slot = pv.act[p];
+    const int emit = pv.emit[2 * p], e = pv.eoff[2 * p];
+    if (!emit) continue;
+    if (threadIdx.x == 0) pv.act_next[e] = slot;
+    if (pv.flag[slot] != -2) continue;
+    const BlockInfo b = load_block(pv, slot);
+    const TreeDev& td = pv.trees[b.tree];
+    if (threadIdx.x < Gm::NCH) {
+      int64_t c[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((threadIdx.x >> a) & 1);
+      cs[threadIdx.x] = tab_get<D>(pv, td, b.lvl, c);
+    }
+    __syncthreads();
+    bool missing = false;
+    for (int ch = 0; ch < Gm::NCH; ++ch) missing |= cs[ch] < 0;
+    if (missing) {  // cannot happen for a complete family; never read slot -1
+      if (threadIdx.x == 0) set_err(pv, kErrGraded);
+      __syncthreads();
+      continue;
+    }
+    for (int idx = threadIdx.x; idx < nv * Gm::NI; idx += blockDim.x) {
+      const int v = idx / Gm::NI, q = idx % Gm::NI;
+      const int I[3] = {q % B, (q / B) % B, D == 3 ? q / (B * B) : 0};
+      int cb = 0, li[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        const int bit = (2 * I[a] >= B - 1) ? 1 : 0;
+        cb |= bit << a;
+        li[a] = 2 * I[a] - bit * (B - 1);
+      }
+      buf[idx] = pool_at<D, B>(pv, y, cs[cb], v, li);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nv * Gm::NI; idx += blockDim.x) {
+      const int v = idx / Gm::NI, q = idx % Gm::NI;
+      y[((int64_t)slot * nv + v) * pv.vs + q] = buf[idx];
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------- IC ----
+// Analytic fields from per-lattice factor tables: Gaussian as the product of
+// its 1D factors (x, then y, then z); mixing layer q = (1, u(y), v, E) with
+// v = amp (s(x) e(y)), E = p0/(gamma-1) + (u u + v v)/2.
+template <int D, int B, typename TS>
+__global__ void k_ic(PoolView pv, TS* __restrict__ y) {
+  using Gm = Geo<D, B>;
+  const int nact = pv.cnt->n_act;
+  const int nv = pv.nvar;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    const int sh = td.Jmax - b.lvl;
+    const double* lat = pv.lat + td.lat_off;
+    for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
+      const int ijk[3] = {q % B, (q / B) % B, D == 3 ? q / (B * B) : 0};
+      int64_t U[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) U[a] = pmod64((b.c[a] * (B - 1) + ijk[a]) << sh, td.N);
+      const int64_t at = (int64_t)b.slot * nv * pv.vs + q;
+      if (td.ic_kind == MR_IC_GAUSS) {
+        double f = lat[kLatGx * td.N + U[0]] * lat[kLatGy * td.N + U[1]];
+        if (D == 3) f = f * lat[kLatGz * td.N + U[2]];
+        y[at] = (TS)f;
+      } else if (td.ic_kind == MR_IC_MIXING) {
+        const double u = lat[kLatNsU * td.N + U[1]];
+        const double v = td.ic_amp * (lat[kLatNsS * td.N + U[0]] * lat[kLatNsE * td.N + U[1]]);
+        const double E = td.ic_e0 + 0.5 * (u * u + v * v);
+        y[at] = (TS)1.0;
+        y[at + pv.vs] = (TS)u;
+        y[at + 2 * pv.vs] = (TS)v;
+        y[at + 3 * pv.vs] = (TS)E;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- sync export ---
+// Ghost synchronisation of the current field: commits the block-edge nodes
+// taken from finer blocks; optionally writes the full tile (double) to `tiles`
+// at the block's list position.
+template <int D, int B, typename TS>
+__global__ void k_sync(PoolView pv, TS* __restrict__ y, double* __restrict__ tiles) {
+  using Gm = Geo<D, B>;
+  int* rslot = smem_as<int>(0);
+  int8_t* rlvl = smem_as<int8_t>(256);
+  double* tile = smem_as<double>(kRingBytes);
+  const int nact = pv.cnt->n_act;
+  const int nv = pv.nvar;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    __syncthreads();
+    fill_tile<D, B, TS, double>(pv, b, y, y, tile, true, rslot, rlvl);
+    __syncthreads();
+    if (tiles)
+      for (int idx = threadIdx.x; idx < nv * Gm::TILE; idx += blockDim.x)
+        tiles[(int64_t)p * nv * Gm::TILE + idx] = tile[idx];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- export -----
+template <int D, int B, typename TS>
+__global__ void k_export_fields(PoolView pv, const TS* __restrict__ y, double* __restrict__ out) {
+  using Gm = Geo<D, B>;
+  const int nact = pv.cnt->n_act;
+  const int nv = pv.nvar;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const int slot = pv.act[p];
+    for (int idx = threadIdx.x; idx < nv * Gm::NI; idx += blockDim.x) {
+      const int v = idx / Gm::NI, q = idx % Gm::NI;
+      out[(int64_t)p * nv * Gm::NI + idx] = (double)y[((int64_t)slot * nv + v) * pv.vs + q];
+    }
+  }
+}
+
+template <int D, int B, typename TS>
+__global__ void k_import_fields(PoolView pv, TS* __restrict__ y, const double* __restrict__ in,
+                                int64_t n) {
+  using Gm = Geo<D, B>;
+  const int nv = pv.nvar;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int idx = threadIdx.x; idx < nv * Gm::NI; idx += blockDim.x) {
+      const int v = idx / Gm::NI, q = idx % Gm::NI;
+      y[(i * nv + v) * pv.vs + q] = (TS)in[i * nv * Gm::NI + idx];
+    }
+}
+
+// ----------------------------------------------------------------- error -----
+// Error against exact factor tables ex[3][N] of one tree over unique nodes
+// (each block's last node per axis dropped), weights dx^d.
+template <int D, int B, typename TS>
+__global__ void k_error(PoolView pv, const TS* __restrict__ y, int tree, const double* ex,
+                        double* out) {
+  const int nact = pv.cnt->n_act;
+  const TreeDev& td = pv.trees[tree];
+  constexpr int BZ = D == 3 ? B - 1 : 1;
+  const int NU = (B - 1) * (B - 1) * BZ;
+  double e2 = 0, x2 = 0, ei = 0, xi = 0;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    if (b.tree != tree) continue;
+    const int sh = td.Jmax - b.lvl;
+    const double dx = td.dx[b.lvl];
+    const double w = D == 3 ? dx * dx * dx : dx * dx;
+    for (int q = threadIdx.x; q < NU; q += blockDim.x) {
+      const int ijk[3] = {q % (B - 1), (q / (B - 1)) % (B - 1), D == 3 ? q / ((B - 1) * (B - 1)) : 0};
+      int64_t U[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) U[a] = pmod64((b.c[a] * (B - 1) + ijk[a]) << sh, td.N);
+      double e = ex[U[0]] * ex[td.N + U[1]];
+      if (D == 3) e = e * ex[2 * td.N + U[2]];
+      const double a = (double)y[(int64_t)b.slot * pv.nvar * pv.vs + Geo<D, B>::lin(ijk[0], ijk[1], ijk[2])];
+      e2 += w * (a - e) * (a - e);
+      x2 += w * e * e;
+      ei = fmax(ei, fabs(a - e));
+      xi = fmax(xi, fabs(e));
+    }
+  }
+  atomicAdd(&out[0], e2);
+  atomicAdd(&out[1], x2);
+  atomic_max_pos(&out[2], ei);
+  atomic_max_pos(&out[3], xi);
+}
+
+// ------------------------------------------------------- tree maintenance ----
+template <int D>
+__global__ void k_refine_count(PoolView pv, int mode, const int8_t* mask) {
+  const int nact = pv.cnt->n_act;
+  const int nch = 1 << D;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const int s = pv.act[p];
+    const int l = pv.lvl[s];
+    const TreeDev& td = pv.trees[pv.tree[s]];
+    const bool r = l < td.Jmax && (mode == MR_ADAPT_REFINE_ALL || (mask && mask[p] > 0));
+    pv.flag[s] = r ? 1 : 0;
+    pv.emit[2 * p] = r ? nch : 1;
+    pv.emit[2 * p + 1] = r ? nch : 0;
+  }
+}
+
+template <int D>
+__global__ void k_refine_finalize(PoolView pv) {
+  const int nact = pv.cnt->n_act;
+  const int n_alloc = pv.cnt->n_alloc, n_free = pv.cnt->n_free;
+  if (n_alloc > n_free) return;
+  const int nch = 1 << D;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const int s = pv.act[p];
+    if (pv.flag[s] != 1) continue;
+    const BlockInfo b = load_block(pv, s);
+    const TreeDev& td = pv.trees[b.tree];
+    pv.tab[td.tab_off[b.lvl] + (int64_t)morton<D>(b.c, b.lvl)] = -1;
+    const int e = pv.eoff[2 * p];
+    for (int r = 0; r < nch; ++r) {
+      const int cs = pv.act_next[e + r];
+      int64_t c[3] = {pv.crd[3 * cs], pv.crd[3 * cs + 1], pv.crd[3 * cs + 2]};
+      pv.tab[td.tab_off[b.lvl + 1] + (int64_t)morton<D>(c, b.lvl + 1)] = cs;
+    }
+    pv.freelist[n_free - n_alloc + pv.eoff[2 * p + 1] / nch] = s;
+    pv.lvl[s] = -1;
+    pv.flag[s] = 0;
+  }
+}
+
+__device__ __forceinline__ bool same_family(const PoolView& pv, int s, int t) {
+  if (pv.tree[s] != pv.tree[t] || pv.lvl[s] != pv.lvl[t]) return false;
+  for (int a = 0; a < 3; ++a)
+    if ((pv.crd[3 * s + a] >> 1) != (pv.crd[3 * t + a] >> 1)) return false;
+  return true;
+}
+
+// First flag pass: r = -1 if the block's largest normalised detail is below
+// eps (strict), it is above Jmin, all 2^d sisters are leaves, and no leaf one
+// level finer touches it (gradedness after the merge); else 0.
+template <int D>
+__global__ void k_flag_a(PoolView pv) {
+  const int nact = pv.cnt->n_act;
+  const int nv = pv.nvar;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    double m = 0.0;
+    bool nan = false;
+    for (int v = 0; v < nv; ++v) {
+      double sv = pv.svar[b.tree * nv + v];
+      if (sv == 0.0) sv = 1.0;
+      const double mv = pv.md[(int64_t)b.slot * nv + v];
+      nan |= isnan(mv);
+      m = fmax(m, mv / sv);
+    }
+    if (nan) {
+      m = __longlong_as_double(0x7ff8000000000000LL);
+      set_err(pv, kErrNaN);
+    }
+    pv.mdet[b.slot] = m;
+    bool ok = (m < td.eps) && b.lvl > td.Jmin;
+    for (int ch = 0; ok && ch < (1 << D); ++ch) {
+      int64_t c[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((ch >> a) & 1);
+      ok &= tab_get<D>(pv, td, b.lvl, c) >= 0;
+    }
+    constexpr int NR = D == 3 ? 64 : 16;
+    for (int r = 0; ok && r < NR; ++r) {
+      const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
+      bool inside = true;
+      int64_t cell[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        inside &= (q[a] == 0 || q[a] == 1);
+        cell[a] = 2 * b.c[a] + q[a];
+      }
+      if (!inside && tab_get<D>(pv, td, b.lvl + 1, cell) >= 0) ok = false;
+    }
+    pv.f1[b.slot] = ok ? -1 : 0;
+  }
+}
+
+// Second flag pass: completeness — a family coarsens only if every sister kept
+// -1 (the fixpoint of the paper's -2 assignment).  Emits the new-list counts.
+template <int D>
+__global__ void k_flag_b(PoolView pv) {
+  const int nact = pv.cnt->n_act;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    bool all = pv.f1[b.slot] == -1;
+    for (int ch = 0; all && ch < (1 << D); ++ch) {
+      int64_t c[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((ch >> a) & 1);
+      const int s = tab_get<D>(pv, td, b.lvl, c);
+      all &= s >= 0 && pv.f1[s] == -1;
+    }
+    pv.flag[b.slot] = all ? -2 : 0;
+    const bool first = all && (p == 0 || !same_family(pv, b.slot, pv.act[p - 1]));
+    pv.emit[2 * p] = (!all || first) ? 1 : 0;
+    pv.emit[2 * p + 1] = (all && !first) ? 1 : 0;
+  }
+}
+
+template <int D>
+__global__ void k_coarsen_finalize(PoolView pv) {
+  const int nact = pv.cnt->n_act;
+  const int n_free = pv.cnt->n_free;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const int s = pv.act[p];
+    if (pv.flag[s] != -2) continue;
+    const BlockInfo b = load_block(pv, s);
+    const TreeDev& td = pv.trees[b.tree];
+    pv.tab[td.tab_off[b.lvl] + (int64_t)morton<D>(b.c, b.lvl)] = -1;
+    if (pv.emit[2 * p]) {
+      int64_t pc[3] = {b.c[0] >> 1, b.c[1] >> 1, b.c[2] >> 1};
+      pv.tab[td.tab_off[b.lvl - 1] + (int64_t)morton<D>(pc, b.lvl - 1)] = s;
+      pv.lvl[s] = (int8_t)(b.lvl - 1);
+      int32_t c32[3] = {(int32_t)pc[0], (int32_t)pc[1], (int32_t)pc[2]};
+      for (int a = 0; a < 3; ++a) pv.crd[3 * s + a] = c32[a];
+      pv.hkey[s] = block_key<D>(c32, b.lvl - 1, td.Jmax);
+    } else {
+      pv.lvl[s] = -1;
+      pv.freelist[n_free + pv.eoff[2 * p + 1]] = s;
+    }
+  }
+}
+
+// Neighbour table (Sec. 2.2): rel[r] = (sx, sy, sz, sub), see mr.h for the order.
+template <int D>
+__global__ void k_neighbors(PoolView pv, const int4* rel, int R, int32_t* nbr, int8_t* dl) {
+  const int nact = pv.cnt->n_act;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < (int64_t)nact * R;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(w / R), r = (int)(w % R);
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    const int4 rr = rel[r];
+    const int s[3] = {rr.x, rr.y, rr.z};
+    int64_t k[3] = {0, 0, 0};
+    bool corner = true;
+    for (int a = 0; a < D; ++a) {
+      k[a] = b.c[a] + s[a];
+      corner &= s[a] != 0;
+    }
+    const int64_t n = (int64_t)1 << b.lvl;
+    auto child = [&](int sub, int64_t ch[3]) {
+      int z = 0;
+      for (int a = 0; a < D; ++a) {
+        int bit;
+        if (s[a] != 0) bit = s[a] < 0 ? 1 : 0;
+        else bit = (sub >> (z++)) & 1;
+        ch[a] = 2 * pmod64(k[a], n) + bit;
+      }
+    };
+    int found = -1, d = 0;
+    if (rr.w < 0) {
+      found = tab_get<D>(pv, td, b.lvl, k);
+      if (found < 0) {
+        int64_t pc[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) pc[a] = pmod64(k[a], n) >> 1;
+        found = tab_get<D>(pv, td, b.lvl - 1, pc);
+        d = -1;
+        if (found < 0 && corner) {
+          int64_t ch[3] = {0, 0, 0};
+          child(0, ch);
+          found = tab_get<D>(pv, td, b.lvl + 1, ch);
+          d = 1;
+        }
+      }
+    } else if (tab_get<D>(pv, td, b.lvl, k) < 0) {
+      int64_t ch[3] = {0, 0, 0};
+      child(rr.w, ch);
+      found = tab_get<D>(pv, td, b.lvl + 1, ch);
+      d = 1;
+    }
+    nbr[w] = found >= 0 ? pv.pos_of_slot[found] : -1;
+    dl[w] = found >= 0 ? (int8_t)d : 0;
+  }
+}
+
+template <int D>
+__global__ void k_export_info(PoolView pv, mr_block_info* info, int8_t* flags, double* mdet) {
+  const int nact = pv.cnt->n_act;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const int s = pv.act[p];
+    const BlockInfo b = load_block(pv, s);
+    if (info) {
+      mr_block_info o;
+      o.level = b.lvl;
+      o.tree = b.tree;
+      o.treecode = morton<D>(b.c, b.lvl);
+      for (int a = 0; a < 3; ++a) o.coords[a] = (int32_t)b.c[a];
+      o.pad = 0;
+      o.hilbert_key = pv.hkey[s];
+      info[p] = o;
+    }
+    if (flags) flags[p] = pv.flag[s];
+    if (mdet) mdet[p] = pv.mdet[s];
+  }
+}
+
+// set_blocks: place input block i in slot i, validate, mark its finest cells.
+template <int D>
+__global__ void k_sb_place(PoolView pv, int64_t n, const int32_t* lvl, const int32_t* tree,
+                           const int32_t* crd, int ntrees) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int t = tree ? tree[i] : 0;
+    if (t < 0 || t >= ntrees) { set_err(pv, kErrLayout); continue; }
+    const TreeDev& td = pv.trees[t];
+    const int l = lvl[i];
+    if (l < td.Jmin || l > td.Jmax) { set_err(pv, kErrLayout); continue; }
+    int32_t c32[3] = {0, 0, 0};
+    int64_t c[3] = {0, 0, 0};
+    bool bad = false;
+    for (int a = 0; a < D; ++a) {
+      c32[a] = crd[3 * i + a];
+      c[a] = c32[a];
+      bad |= c[a] < 0 || c[a] >= ((int64_t)1 << l);
+    }
+    if (bad) { set_err(pv, kErrLayout); continue; }
+    pv.lvl[i] = (int8_t)l;
+    pv.tree[i] = (int16_t)t;
+    for (int a = 0; a < 3; ++a) pv.crd[3 * i + a] = c32[a];
+    pv.hkey[i] = block_key<D>(c32, l, td.Jmax);
+    pv.flag[i] = 0;
+    pv.mdet[i] = 0.0;
+    int* e = &pv.tab[td.tab_off[l] + (int64_t)morton<D>(c, l)];
+    if (atomicCAS(e, -1, (int)i) != -1) set_err(pv, kErrLayout);
+  }
+}
+
+// Every finest cell of every block gets +1 (coverage check: all must be 1).
+template <int D>
+__global__ void k_sb_cover(PoolView pv, int64_t n) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const int l = pv.lvl[i];
+    if (l < 0) continue;
+    const TreeDev& td = pv.trees[pv.tree[i]];
+    const int sh = td.Jmax - l;
+    const int64_t per = (int64_t)1 << (D * sh);
+    for (int64_t r = threadIdx.x; r < per; r += blockDim.x) {
+      int64_t cell[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        int64_t off = 0;
+        for (int bb = 0; bb < sh; ++bb) off |= ((r >> (bb * D + a)) & 1) << bb;
+        cell[a] = ((int64_t)pv.crd[3 * i + a] << sh) + off;
+      }
+      atomicAdd(&pv.cells[2 * (td.cell_off + (int64_t)morton<D>(cell, td.Jmax))], 1);
+    }
+  }
+}
+
+template <int D>
+__global__ void k_sb_mark(PoolView pv, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (pv.lvl[i] < 0) continue;
+    const TreeDev& td = pv.trees[pv.tree[i]];
+    pv.cells[2 * (td.cell_off + (int64_t)pv.hkey[i])] = 1;
+  }
+}
+
+template <int D>
+__global__ void k_sb_order(PoolView pv, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (pv.lvl[i] < 0) continue;
+    const TreeDev& td = pv.trees[pv.tree[i]];
+    pv.act[pv.eoff[2 * (td.cell_off + (int64_t)pv.hkey[i])]] = (int32_t)i;
+  }
+}
+
+// Graded-tree check: every ring cell must be covered by a leaf at l-1..l+1.
+template <int D>
+__global__ void k_check_graded(PoolView pv) {
+  const int nact = pv.cnt->n_act;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    constexpr int NR = D == 3 ? 64 : 16;
+    for (int r = 0; r < NR; ++r) {
+      const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
+      const int64_t nl1 = (int64_t)1 << (b.lvl + 1);
+      int64_t cell[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, c2[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) {
+        cell[a] = pmod64(2 * b.c[a] + q[a], nl1);
+        c1[a] = cell[a] >> 1;
+        c2[a] = cell[a] >> 2;
+      }
+      if (tab_get<D>(pv, td, b.lvl + 1, cell) < 0 && tab_get<D>(pv, td, b.lvl, c1) < 0 &&
+          tab_get<D>(pv, td, b.lvl - 1, c2) < 0)
+        set_err(pv, kErrGraded);
+    }
+  }
+}
+
+}  // namespace mr

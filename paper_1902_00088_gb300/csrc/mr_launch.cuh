@@ -1,0 +1,320 @@
+// Host-side launchers of the kernel templates, dispatched over block size and
+// precision.  Included once per dimension (mr_k2.cu, mr_k3.cu).
+#pragma once
+#include <cstdio>
+
+#include "mr_kernels.cuh"
+
+namespace mr {
+
+template <typename K>
+static void prep_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, const LaunchCfg& lc, int mult) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  if (mult > 0 && mult < per_sm) per_sm = mult;
+  return lc.num_sms * per_sm;
+}
+
+static inline int flat_grid(const PoolView& pv, int threads) {
+  int64_t g = (pv.cap + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------- stage ------
+template <int D, int B, int RHS, typename TS, typename TY>
+static void stage_impl(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
+                       const LaunchCfg& lc, cudaStream_t st) {
+  constexpr int threads = D == 3 ? 512 : 256;
+  const int nv = 1;
+  const size_t smem = kRingBytes + sizeof(TY) * nv * Geo<D, B>::TILE;
+  TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
+  if (stage == 0) {
+    auto k = k_stage_adv<D, B, RHS, TS, TY, TS>;
+    prep_smem(k, smem);
+    const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
+    k<<<grid, threads, smem, st>>>(pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+  } else {
+    const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
+    auto k = k_stage_adv<D, B, RHS, TS, TY, TY>;
+    prep_smem(k, smem);
+    const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
+    k<<<grid, threads, smem, st>>>(pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+  }
+  count_launch();
+}
+
+template <int D, int B, int RHS>
+static void stage_prec(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
+                       const LaunchCfg& lc, cudaStream_t st) {
+  switch (pv.prec) {
+    case MR_PREC_FP64: stage_impl<D, B, RHS, double, double>(pv, f, stage, sa, lc, st); break;
+    case MR_PREC_FP32: stage_impl<D, B, RHS, float, float>(pv, f, stage, sa, lc, st); break;
+    default: stage_impl<D, B, RHS, double, float>(pv, f, stage, sa, lc, st); break;
+  }
+}
+
+template <int D>
+void launch_stage(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
+                  const LaunchCfg& lc, cudaStream_t st) {
+  if (D == 2) {
+    if (pv.Bs == 17) {
+      if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, 17, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
+      else stage_prec<D, 17, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
+    } else {
+      if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, 33, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
+      else stage_prec<D, 33, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
+    }
+  } else {
+    stage_prec<D, 17, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
+  }
+}
+
+// Dispatch helper over (Bs, state type): calls F<D, B, TS>::run(args...).
+template <int D, template <int, int, typename> class F, typename... A>
+static void dispatch_bs(const PoolView& pv, A&&... args) {
+  const bool st64 = pv.prec != MR_PREC_FP32;
+  if (D == 3 || pv.Bs == 17) {
+    if (st64) F<D, 17, double>::run(pv, args...);
+    else F<D, 17, float>::run(pv, args...);
+  } else {
+    if (st64) F<D, 33, double>::run(pv, args...);
+    else F<D, 33, float>::run(pv, args...);
+  }
+}
+
+// --------------------------------------------------------------- refine ------
+template <int D, int B, typename TS>
+struct RefineRun {
+  static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+    constexpr int threads = D == 3 ? 512 : 256;
+    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * Geo<D, B>::TILE;
+    auto k = k_refine<D, B, TS>;
+    prep_smem(k, smem);
+    const int grid = persistent_grid(k, threads, smem, lc, 0);
+    k<<<grid, threads, smem, st>>>(pv, (TS*)f.y);
+    count_launch();
+  }
+};
+
+__global__ void k_refine_counters(Counters* c, int nch);
+__global__ void k_coarsen_counters(Counters* c, int nch);
+__global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check_capacity);
+__global__ void k_set_svar(double* svar, int n, double v);
+
+template <int D>
+void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* mask,
+                   const LaunchCfg& lc, cudaStream_t st) {
+  const int nch = 1 << D;
+  k_refine_count<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv, mode, mask);
+  count_launch();
+  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st);
+  dispatch_bs<D, RefineRun>(pv, f, lc, st);
+  k_refine_finalize<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 1);
+  k_refine_counters<<<1, 1, 0, st>>>(pv.cnt, nch);
+  count_launch(3);
+}
+
+// ------------------------------------------------------------------- IC ------
+template <int D, int B, typename TS>
+struct IcRun {
+  static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+    k_ic<D, B, TS><<<lc.num_sms * 8, 256, 0, st>>>(pv, (TS*)f.y);
+    count_launch();
+  }
+};
+template <int D>
+void launch_ic(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+  dispatch_bs<D, IcRun>(pv, f, lc, st);
+}
+
+// --------------------------------------------------------------- coarsen -----
+template <int D, int B, typename TS>
+struct DetailsRun {
+  static void run(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
+                  cudaStream_t st) {
+    constexpr int threads = D == 3 ? 512 : 256;
+    if (fp64 || sizeof(TS) == 8) {
+      const size_t smem = kRingBytes + sizeof(double) * pv.nvar * Geo<D, B>::TILE;
+      auto k = k_details<D, B, TS, double>;
+      prep_smem(k, smem);
+      k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
+    } else {
+      const size_t smem = kRingBytes + sizeof(float) * pv.nvar * Geo<D, B>::TILE;
+      auto k = k_details<D, B, TS, float>;
+      prep_smem(k, smem);
+      k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
+    }
+    count_launch();
+  }
+};
+template <int D, int B, typename TS>
+struct CoarsenRun {
+  static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+    constexpr int threads = D == 3 ? 512 : 256;
+    const size_t smem = sizeof(TS) * pv.nvar * Geo<D, B>::NI;
+    auto k = k_coarsen<D, B, TS>;
+    prep_smem(k, smem);
+    k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
+    count_launch();
+  }
+};
+
+template <int D>
+void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool merge,
+                          const LaunchCfg& lc, cudaStream_t st) {
+  const int nch = 1 << D;
+  k_set_svar<<<1, 256, 0, st>>>(pv.svar, pv.ntrees * pv.nvar, pv.norm_kind == 1 ? 0.0 : 1.0);
+  count_launch();
+  dispatch_bs<D, DetailsRun>(pv, f, fp64, lc, st);
+  k_flag_a<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  k_flag_b<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  count_launch(2);
+  if (!merge) return;
+  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st);
+  dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
+  k_coarsen_finalize<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 0);
+  k_coarsen_counters<<<1, 1, 0, st>>>(pv.cnt, nch);
+  count_launch(3);
+}
+
+// ------------------------------------------------------------------ sync -----
+template <int D, int B, typename TS>
+struct SyncRun {
+  static void run(const PoolView& pv, const Fields& f, double* tiles, const LaunchCfg& lc,
+                  cudaStream_t st) {
+    constexpr int threads = D == 3 ? 512 : 256;
+    const size_t smem = kRingBytes + sizeof(double) * pv.nvar * Geo<D, B>::TILE;
+    auto k = k_sync<D, B, TS>;
+    prep_smem(k, smem);
+    k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y, tiles);
+    count_launch();
+  }
+};
+template <int D>
+void launch_sync(const PoolView& pv, const Fields& f, double* tiles, const LaunchCfg& lc,
+                 cudaStream_t st) {
+  dispatch_bs<D, SyncRun>(pv, f, tiles, lc, st);
+}
+
+template <int D>
+void launch_neighbors(const PoolView& pv, const int4* rel, int R, int32_t* nbr, int8_t* dl,
+                      const LaunchCfg& lc, cudaStream_t st) {
+  k_neighbors<D><<<lc.num_sms * 8, 256, 0, st>>>(pv, rel, R, nbr, dl);
+  count_launch();
+}
+
+// ---------------------------------------------------------------- export -----
+template <int D, int B, typename TS>
+struct ExportRun {
+  static void run(const PoolView& pv, const Fields& f, double* fields, const LaunchCfg& lc,
+                  cudaStream_t st) {
+    k_export_fields<D, B, TS><<<lc.num_sms * 8, 256, 0, st>>>(pv, (const TS*)f.y, fields);
+    count_launch();
+  }
+};
+template <int D>
+void launch_export(const PoolView& pv, const Fields& f, mr_block_info* info, double* fields,
+                   int8_t* flags, double* mdet, const LaunchCfg& lc, cudaStream_t st) {
+  k_export_info<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv, info, flags, mdet);
+  count_launch();
+  if (fields) dispatch_bs<D, ExportRun>(pv, f, fields, lc, st);
+}
+
+// ------------------------------------------------------------ set_blocks -----
+template <int D, int B, typename TS>
+struct ImportRun {
+  static void run(const PoolView& pv, const Fields& f, const double* fields, int64_t n,
+                  const LaunchCfg& lc, cudaStream_t st) {
+    k_import_fields<D, B, TS><<<lc.num_sms * 8, 256, 0, st>>>(pv, (TS*)f.y, fields, n);
+    count_launch();
+  }
+};
+
+__global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v);
+__global__ void k_fill_i8(int8_t* a, int64_t n, int8_t v);
+__global__ void k_sb_check(const int32_t* cells, int64_t ncells, Counters* c);
+__global__ void k_sb_counters(Counters* c, int32_t* freelist, int64_t n, int64_t cap);
+
+// Phase 1 (validate): place, detect duplicates, check the cells are covered once.
+// Phase 2 (after the host saw no error): canonical order, fields, gradedness.
+template <int D>
+void launch_set_blocks(const PoolView& pv, const Fields& f, int phase, int64_t n,
+                       const int32_t* lvl, const int32_t* tree, const int32_t* crd,
+                       const double* fields, int64_t ncells, int ntrees, int64_t ntab,
+                       const LaunchCfg& lc, cudaStream_t st) {
+  const int g = 1024;
+  if (phase == 0) {  // empty pool: no active block, every slot free
+    k_fill_i32<<<g, 256, 0, st>>>(pv.tab, ntab, -1);
+    k_fill_i8<<<g, 256, 0, st>>>(pv.lvl, pv.cap, (int8_t)-1);
+    k_sb_counters<<<g, 256, 0, st>>>(pv.cnt, pv.freelist, 0, pv.cap);
+    count_launch(3);
+    return;
+  }
+  if (phase == 1) {
+    k_fill_i32<<<g, 256, 0, st>>>(pv.tab, ntab, -1);
+    k_fill_i32<<<g, 256, 0, st>>>(pv.cells, 2 * ncells, 0);
+    k_fill_i8<<<g, 256, 0, st>>>(pv.lvl, pv.cap, (int8_t)-1);
+    k_sb_place<D><<<g, 256, 0, st>>>(pv, n, lvl, tree, crd, ntrees);
+    k_sb_cover<D><<<lc.num_sms * 4, 256, 0, st>>>(pv, n);
+    k_sb_check<<<g, 256, 0, st>>>(pv.cells, ncells, pv.cnt);
+    count_launch(6);
+    return;
+  }
+  k_fill_i32<<<g, 256, 0, st>>>(pv.cells, 2 * ncells, 0);
+  k_sb_mark<D><<<g, 256, 0, st>>>(pv, n);
+  count_launch(2);
+  launch_scan2(pv.cells, pv.eoff, pv.partial, nullptr, ncells, &pv.cnt->n_new, st);
+  k_sb_order<D><<<g, 256, 0, st>>>(pv, n);
+  k_sb_counters<<<g, 256, 0, st>>>(pv.cnt, pv.freelist, n, pv.cap);
+  count_launch(2);
+  if (fields) dispatch_bs<D, ImportRun>(pv, f, fields, n, lc, st);
+  k_check_graded<D><<<g, 256, 0, st>>>(pv);
+  count_launch();
+}
+
+// ----------------------------------------------------------------- error -----
+template <int D, int B, typename TS>
+struct ErrorRun {
+  static void run(const PoolView& pv, const Fields& f, int tree, const double* ex, double* out,
+                  const LaunchCfg& lc, cudaStream_t st) {
+    k_error<D, B, TS><<<lc.num_sms * 4, 256, 0, st>>>(pv, (const TS*)f.y, tree, ex, out);
+    count_launch();
+  }
+};
+template <int D>
+void launch_error(const PoolView& pv, const Fields& f, int tree, const double* ex, double* out4,
+                  const LaunchCfg& lc, cudaStream_t st) {
+  dispatch_bs<D, ErrorRun>(pv, f, tree, ex, out4, lc, st);
+}
+
+#define MR_INSTANTIATE(D)                                                                       \
+  template void launch_stage<D>(const PoolView&, const Fields&, int, const StageArgs&,         \
+                                const LaunchCfg&, cudaStream_t);                                \
+  template void launch_refine<D>(const PoolView&, const Fields&, int, const int8_t*,            \
+                                 const LaunchCfg&, cudaStream_t);                               \
+  template void launch_ic<D>(const PoolView&, const Fields&, const LaunchCfg&, cudaStream_t);   \
+  template void launch_coarsen_round<D>(const PoolView&, const Fields&, bool, bool,             \
+                                        const LaunchCfg&, cudaStream_t);                        \
+  template void launch_sync<D>(const PoolView&, const Fields&, double*, const LaunchCfg&,       \
+                               cudaStream_t);                                                   \
+  template void launch_neighbors<D>(const PoolView&, const int4*, int, int32_t*, int8_t*,       \
+                                    const LaunchCfg&, cudaStream_t);                            \
+  template void launch_export<D>(const PoolView&, const Fields&, mr_block_info*, double*,       \
+                                 int8_t*, double*, const LaunchCfg&, cudaStream_t);             \
+  template void launch_set_blocks<D>(const PoolView&, const Fields&, int, int64_t,              \
+                                     const int32_t*, const int32_t*, const int32_t*,            \
+                                     const double*, int64_t, int, int64_t, const LaunchCfg&,    \
+                                     cudaStream_t);                                             \
+  template void launch_error<D>(const PoolView&, const Fields&, int, const double*, double*,    \
+                                const LaunchCfg&, cudaStream_t);
+
+}  // namespace mr

@@ -1,0 +1,161 @@
+// Exclusive scan of int2 pairs and the small bookkeeping kernels of the tree
+// maintenance (counters, list copies, fills).
+#include <atomic>
+
+#include "mr_internal.h"
+
+namespace mr {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+int64_t kernel_launches() { return g_launches.load(); }
+
+constexpr int kScanThreads = 256;
+constexpr int kPer = kScanChunk / kScanThreads;  // 8 pairs per thread
+
+__device__ __forceinline__ int64_t scan_n(const int32_t* n_dev, int64_t n_host) {
+  return n_dev ? (int64_t)*n_dev : n_host;
+}
+
+// inclusive block scan of (a, b) over 256 threads
+__device__ __forceinline__ int2 block_incl_scan(int2 v, int2* warp_tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    int x = __shfl_up_sync(0xffffffffu, v.x, o), y = __shfl_up_sync(0xffffffffu, v.y, o);
+    if (lane >= o) { v.x += x; v.y += y; }
+  }
+  if (lane == 31) warp_tot[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int2 t = lane < (kScanThreads >> 5) ? warp_tot[lane] : make_int2(0, 0);
+    for (int o = 1; o < 8; o <<= 1) {
+      int x = __shfl_up_sync(0xffffffffu, t.x, o), y = __shfl_up_sync(0xffffffffu, t.y, o);
+      if (lane >= o) { t.x += x; t.y += y; }
+    }
+    if (lane < (kScanThreads >> 5)) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  if (w > 0) { v.x += warp_tot[w - 1].x; v.y += warp_tot[w - 1].y; }
+  return v;
+}
+
+__global__ void k_scan_reduce(const int32_t* in, const int32_t* n_dev, int64_t n_host, int32_t* partial) {
+  __shared__ int2 wt[kScanThreads / 32];
+  const int64_t n = scan_n(n_dev, n_host);
+  const int64_t start = (int64_t)blockIdx.x * kScanChunk;
+  int2 s = make_int2(0, 0);
+  for (int r = 0; r < kPer; ++r) {
+    const int64_t i = start + (int64_t)threadIdx.x * kPer + r;
+    if (i < n) { s.x += in[2 * i]; s.y += in[2 * i + 1]; }
+  }
+  s = block_incl_scan(s, wt);
+  if (threadIdx.x == kScanThreads - 1) {
+    partial[2 * blockIdx.x] = s.x;
+    partial[2 * blockIdx.x + 1] = s.y;
+  }
+}
+
+__global__ void k_scan_partials(int32_t* partial, int nchunks, int32_t* tot) {
+  __shared__ int2 wt[kScanThreads / 32];
+  __shared__ int2 carry;
+  if (threadIdx.x == 0) carry = make_int2(0, 0);
+  __syncthreads();
+  for (int base = 0; base < nchunks; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    int2 v = i < nchunks ? make_int2(partial[2 * i], partial[2 * i + 1]) : make_int2(0, 0);
+    const int2 inc = block_incl_scan(v, wt);
+    const int2 c = carry;
+    if (i < nchunks) {
+      partial[2 * i] = c.x + inc.x - v.x;
+      partial[2 * i + 1] = c.y + inc.y - v.y;
+    }
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) { carry.x = c.x + inc.x; carry.y = c.y + inc.y; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && tot) { tot[0] = carry.x; tot[1] = carry.y; }
+}
+
+__global__ void k_scan_final(const int32_t* in, int32_t* out, const int32_t* n_dev, int64_t n_host,
+                             const int32_t* partial) {
+  __shared__ int2 wt[kScanThreads / 32];
+  const int64_t n = scan_n(n_dev, n_host);
+  const int64_t start = (int64_t)blockIdx.x * kScanChunk;
+  if (start >= n) return;
+  int2 loc[kPer];
+  int2 s = make_int2(0, 0);
+  for (int r = 0; r < kPer; ++r) {
+    const int64_t i = start + (int64_t)threadIdx.x * kPer + r;
+    loc[r] = i < n ? make_int2(in[2 * i], in[2 * i + 1]) : make_int2(0, 0);
+    s.x += loc[r].x; s.y += loc[r].y;
+  }
+  const int2 inc = block_incl_scan(s, wt);
+  int2 run = make_int2(partial[2 * blockIdx.x] + inc.x - s.x, partial[2 * blockIdx.x + 1] + inc.y - s.y);
+  for (int r = 0; r < kPer; ++r) {
+    const int64_t i = start + (int64_t)threadIdx.x * kPer + r;
+    if (i < n) { out[2 * i] = run.x; out[2 * i + 1] = run.y; }
+    run.x += loc[r].x; run.y += loc[r].y;
+  }
+}
+
+void launch_scan2(const int32_t* in, int32_t* out, int32_t* partial, const int32_t* n_dev,
+                  int64_t n_host, int32_t* tot, cudaStream_t st) {
+  const int nchunks = (int)((n_host + kScanChunk - 1) / kScanChunk);
+  const int g = nchunks < 1 ? 1 : nchunks;
+  k_scan_reduce<<<g, kScanThreads, 0, st>>>(in, n_dev, n_host, partial);
+  k_scan_partials<<<1, kScanThreads, 0, st>>>(partial, g, tot);
+  k_scan_final<<<g, kScanThreads, 0, st>>>(in, out, n_dev, n_host, partial);
+  count_launch(3);
+}
+
+__global__ void k_refine_counters(Counters* c, int nch) {
+  if (c->n_alloc > c->n_free) return;
+  c->n_free = c->n_free - c->n_alloc + c->n_alloc / nch;
+  c->n_act = c->n_new;
+}
+
+__global__ void k_coarsen_counters(Counters* c, int nch) {
+  c->merged = (c->n_act - c->n_new) / (nch - 1);
+  c->n_free = c->n_free + c->n_alloc;
+  c->n_act = c->n_new;
+}
+
+// Copies the n_new entries of the list just built; after a refine that failed
+// for lack of free slots (check_capacity) the current list is kept.
+__global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check_capacity) {
+  if (check_capacity && c->n_alloc > c->n_free) return;
+  const int n = c->n_new;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+__global__ void k_set_svar(double* svar, int n, double v) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) svar[i] = v;
+}
+
+__global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;
+}
+__global__ void k_fill_i8(int8_t* a, int64_t n, int8_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;
+}
+
+__global__ void k_sb_check(const int32_t* cells, int64_t ncells, Counters* c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncells; i += (int64_t)gridDim.x * blockDim.x)
+    if (cells[2 * i] != 1) atomicOr(&c->err, kErrLayout);
+}
+
+__global__ void k_sb_counters(Counters* c, int32_t* freelist, int64_t n, int64_t cap) {
+  const int64_t nf = cap - n;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nf; j += (int64_t)gridDim.x * blockDim.x)
+    freelist[j] = (int32_t)(cap - 1 - j);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (c->n_new != n) atomicOr(&c->err, kErrLayout);
+    c->n_act = (int32_t)n;
+    c->n_free = (int32_t)nf;
+    c->n_new = (int32_t)n;
+    c->n_alloc = 0;
+    c->merged = 0;
+  }
+}
+
+}  // namespace mr

@@ -1,0 +1,256 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+FP64 fields are compared bit for bit (the library is compiled without FMA
+contraction and evaluates the same IEEE operations in the same order); trees,
+treecodes, Hilbert keys, neighbour tables and flags bit for bit as well.
+FP32 forms are compared within a tolerance stated per test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import treegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1902_00088_gb300 import build as b
+    b.build()
+    import paper_1902_00088_gb300 as m
+    return m
+
+
+def cfg2d(**kw):
+    c = dict(dim=2, Jmin=2, Jmax=5, eps=1e-3, rhs="adv", rhs_params=(1.0, 0.5, 0.0),
+             ic="gauss", ic_params=(0.5, 0.5, 0.0, 0.05))
+    c.update(kw)
+    return c
+
+
+def make_pair(mr, oracle_mod, cfg, precision="fp64", capacity=1 << 15, **fkw):
+    o = oracle_mod.Oracle(cfg)
+    tree = dict(Jmin=cfg["Jmin"], Jmax=cfg["Jmax"], eps=cfg["eps"], ic=cfg.get("ic", "gauss"),
+                ic_params=cfg.get("ic_params", ()), rhs_params=cfg.get("rhs_params", ()),
+                x0=cfg.get("x0", (0.0, 0.0, 0.0)))
+    g = mr.Forest(dim=cfg["dim"], Bs=cfg.get("Bs", 17), nvar=cfg.get("nvar", 1), precision=precision,
+                  rhs=cfg.get("rhs", "adv"), trees=[tree], capacity=capacity,
+                  max_rounds=cfg.get("max_rounds", 0), norm_kind=cfg.get("norm_kind", 0), **fkw)
+    return o, g
+
+
+def assert_same_tree(o, g):
+    ob = o.blocks()
+    info, f = g.get_blocks()
+    assert len(info) == o.n, (len(info), o.n)
+    assert np.array_equal(info["level"], ob["level"])
+    assert np.array_equal(info["coords"].astype(np.int64), ob["coords"])
+    assert np.array_equal(info["treecode"], ob["treecode"])
+    assert np.array_equal(info["hilbert_key"], ob["hkey"])
+    return ob, f
+
+
+def test_init_tree_bit_exact(mr, oracle_mod):
+    o, g = make_pair(mr, oracle_mod, cfg2d())
+    o.init_tree()
+    g.init_tree()
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+    assert o.errors == 0
+
+
+def test_sync_tiles_bit_exact_on_random_adaptive_tree(mr, oracle_mod):
+    rng = np.random.default_rng(5)
+    leaves = treegen.random_graded_tree(2, 1, 5, 8, 21)
+    lvl, crd = treegen.as_arrays(leaves)
+    fields = rng.standard_normal((len(leaves), 1, 17, 17))
+    o, g = make_pair(mr, oracle_mod, cfg2d(Jmin=1, Jmax=5, ic="none"))
+    o.set_blocks(lvl, crd, fields)
+    # the library takes blocks in any order and sorts them canonically
+    g.set_blocks(lvl, crd, fields)
+    assert_same_tree(o, g)
+    o.sync()
+    ot = o.tiles()
+    gt = g.get_tiles()
+    assert o.errors == 0
+    assert gt.shape == ot.shape
+    bad = np.argwhere(gt != ot)
+    assert len(bad) == 0, bad[:10]
+    # committed edge nodes: interiors after the sync agree too
+    ob = o.blocks()
+    _, f = g.get_blocks()
+    assert np.array_equal(f, ob["fields"])
+
+
+def test_neighbors_bit_exact(mr, oracle_mod):
+    for dim, jmax, seed in ((2, 5, 3), (3, 3, 4)):
+        leaves = treegen.random_graded_tree(dim, 1, jmax, 8 if dim == 2 else 3, seed)
+        lvl, crd = treegen.as_arrays(leaves)
+        o, g = make_pair(mr, oracle_mod, cfg2d(dim=dim, Jmin=1, Jmax=jmax, ic="none"))
+        o.set_blocks(lvl, crd)
+        g.set_blocks(lvl, crd)
+        assert_same_tree(o, g)
+        on, od = o.neighbors()
+        gn, gd = g.get_neighbors()
+        assert np.array_equal(on, gn)
+        assert np.array_equal(od, gd)
+
+
+def test_step_bit_exact_fp64_2d(mr, oracle_mod):
+    c = cfg2d()
+    o, g = make_pair(mr, oracle_mod, c)
+    o.init_tree()
+    g.init_tree()
+    dt = 0.5 * (1.0 / (16 * 32)) / math.hypot(1.0, 0.5)
+    for s in range(4):
+        o.step(s * dt, dt)
+        g.step(s * dt, dt)
+        ob, f = assert_same_tree(o, g)
+        assert np.array_equal(f, ob["fields"]), np.abs(f - ob["fields"]).max()
+    assert o.errors == 0
+
+
+def test_refine_rk_flags_bit_exact(mr, oracle_mod):
+    c = cfg2d(eps=1e-4)
+    o, g = make_pair(mr, oracle_mod, c)
+    o.init_tree()
+    g.init_tree()
+    o.refine(0)
+    g.adapt("refine_all")
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+    o.rk4(0.0, 1e-3)
+    g.rk_step(0.0, 1e-3)
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+    o.details()
+    o.flags(0)
+    g.adapt("flags_only")
+    ob = o.blocks()
+    gf, gm = g.get_flags()
+    assert np.array_equal(gm, ob["mdet"])
+    assert np.array_equal(gf, ob["flag"])
+    assert (gf == -2).any() and (gf == 0).any()
+
+
+def test_swirl_steps_bit_exact(mr, oracle_mod):
+    c = cfg2d(rhs="swirl", rhs_params=(5.0,), ic_params=(0.5, 0.75, 0.0, math.sqrt(0.005)),
+              Jmin=2, Jmax=6, eps=1e-4)
+    o, g = make_pair(mr, oracle_mod, c)
+    o.init_tree()
+    g.init_tree()
+    dt = 0.5 / (16 * 64)
+    for s in range(3):
+        o.step(s * dt, dt)
+        g.step(s * dt, dt)
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+
+
+def test_3d_init_and_step_bit_exact(mr, oracle_mod):
+    c = dict(dim=3, Jmin=1, Jmax=3, eps=1e-3, rhs="adv", rhs_params=(1.0, 1.0, 1.0),
+             ic="gauss", ic_params=(0.5, 0.5, 0.5, 0.08))
+    o, g = make_pair(mr, oracle_mod, c)
+    o.init_tree()
+    g.init_tree()
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+    dt = 0.5 / (16 * 8) / math.sqrt(3.0)
+    o.step(0.0, dt)
+    g.step(0.0, dt)
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_acc64"])
+def test_fp32_forms_within_tolerance(mr, oracle_mod, precision):
+    # Uniform grid (no adaptation), both sides set up independently from the IC:
+    # relative L2 difference of the fields <= 1e-5 after 4 RK4 steps.
+    c = cfg2d(Jmin=4, Jmax=4)
+    o, g = make_pair(mr, oracle_mod, c, precision=precision)
+    o.init_tree()
+    g.init_tree()
+    dt = 0.5 * (1.0 / (16 * 16)) / math.hypot(1.0, 0.5)
+    for s in range(4):
+        o.rk4(s * dt, dt)
+        g.rk_step(s * dt, dt)
+    ob, f = assert_same_tree(o, g)
+    ref = ob["fields"]
+    rel = np.linalg.norm(f - ref) / np.linalg.norm(ref)
+    assert rel < 1e-5, rel
+
+
+def test_fp32_adaptive_steps_match_tree(mr, oracle_mod):
+    # FP32 stencils with FP64 details: the adapted tree equals the FP64 oracle's
+    # (no block sits within FP32 rounding of eps here) and fields agree to 1e-5.
+    c = cfg2d()
+    o, g = make_pair(mr, oracle_mod, c, precision="fp32", detail_fp64=True)
+    o.init_tree()
+    g.init_tree()
+    dt = 0.5 * (1.0 / (16 * 32)) / math.hypot(1.0, 0.5)
+    for s in range(3):
+        o.step(s * dt, dt)
+        g.step(s * dt, dt)
+    ob, f = assert_same_tree(o, g)
+    rel = np.linalg.norm(f - ob["fields"]) / np.linalg.norm(ob["fields"])
+    assert rel < 1e-5, rel
+
+
+def test_uniform_tree_without_adaptation(mr, oracle_mod):
+    c = cfg2d(Jmin=3, Jmax=3)
+    o, g = make_pair(mr, oracle_mod, c)
+    o.init_tree()
+    g.init_tree()
+    for s in range(2):
+        o.step(s * 1e-3, 1e-3)
+        g.step(s * 1e-3, 1e-3)
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+    assert len(f) == 64
+
+
+def test_error_codes(mr, oracle_mod):
+    # invalid parameters
+    with pytest.raises(mr.MRError) as e:
+        mr.Forest(dim=2, Bs=15, trees=[dict(Jmin=2, Jmax=4)])
+    assert e.value.status == mr.MR_EINVAL
+    with pytest.raises(mr.MRError):
+        mr.Forest(dim=2, trees=[dict(Jmin=0, Jmax=4)])
+    # capacity exhausted by a refine-all
+    g = mr.Forest(dim=2, trees=[dict(Jmin=2, Jmax=4, ic_params=(0.5, 0.5, 0.0, 0.05))], capacity=40)
+    lvl, crd = treegen.as_arrays(sorted(treegen.uniform_tree(2, 2)))
+    g.set_blocks(lvl, crd)
+    with pytest.raises(mr.MRError) as e:
+        g.adapt("refine_all")
+    assert e.value.status == mr.MR_ECAPACITY
+    assert g.num_blocks() == 16  # tree unchanged
+    # non-graded tree rejected
+    leaves = set(treegen.uniform_tree(2, 1))
+    leaves.remove((1, (0, 0)))
+    leaves.update(treegen.refine_leaf(2, (1, (0, 0))))
+    leaves.remove((2, (1, 1)))
+    leaves.update(treegen.refine_leaf(2, (2, (1, 1))))
+    lvl, crd = treegen.as_arrays(sorted(leaves))
+    g2 = mr.Forest(dim=2, trees=[dict(Jmin=1, Jmax=4, ic="none")], capacity=1000)
+    with pytest.raises(mr.MRError) as e:
+        g2.set_blocks(lvl, crd)
+    assert e.value.status == mr.MR_EINTERNAL
+    # overlapping blocks rejected
+    lvl, crd = treegen.as_arrays(sorted(treegen.uniform_tree(2, 1)) + [(2, (0, 0))])
+    with pytest.raises(mr.MRError) as e:
+        g2.set_blocks(lvl, crd)
+    assert e.value.status == mr.MR_EINTERNAL
+    # NaN in a field is reported by the detail norm
+    lvl, crd = treegen.as_arrays(sorted(treegen.uniform_tree(2, 2)))
+    f = np.zeros((16, 1, 17, 17))
+    f[3, 0, 5, 5] = np.nan
+    g3 = mr.Forest(dim=2, trees=[dict(Jmin=1, Jmax=4, ic="none")], capacity=1000)
+    g3.set_blocks(lvl, crd, f)
+    with pytest.raises(mr.MRError) as e:
+        g3.adapt("coarsen")
+    assert e.value.status == mr.MR_ENAN
