@@ -28,21 +28,21 @@ WORKLOADS = {
     "adv3d": dict(dim=3, Bs=17, precision="fp32", detail_fp64=True, rhs="adv",
                   tree=dict(Jmin=2, Jmax=6, eps=1e-4, ic="gauss",
                             ic_params=(0.5, 0.5, 0.5, 0.04), rhs_params=(1.0, 1.0, 1.0)),
-                  umax=math.sqrt(3.0), capacity=400_000,
+                  umax=math.sqrt(3.0), capacity=20_000,
                   name="3D advection, Gaussian sigma 0.04, u=(1,1,1), 17^3 blocks, ng 4, "
                        "Jmin 2, Jmax 6, eps 1e-4, FP32 RHS + FP64 details, CFL 0.5"),
     # 2D swirl (Sec. 3, Eq. 1), t_a = 5, 17^2 blocks, Jmax 8, eps 1e-4, FP32 + FP64 details
     "swirl": dict(dim=2, Bs=17, precision="fp32", detail_fp64=True, rhs="swirl",
                   tree=dict(Jmin=1, Jmax=8, eps=1e-4, ic="gauss",
                             ic_params=(0.5, 0.75, 0.0, math.sqrt(0.005)), rhs_params=(5.0,)),
-                  umax=1.0, capacity=600_000,
+                  umax=1.0, capacity=60_000, full_time=5.0,
                   name="2D swirl t_a=5, blob (0.5,0.75) beta 0.01, 17^2 blocks, Jmax 8, eps 1e-4, "
                        "FP32 RHS + FP64 details, CFL 0.5"),
     # 2D constant advection, plain FP64
     "adv2d": dict(dim=2, Bs=17, precision="fp64", detail_fp64=False, rhs="adv",
                   tree=dict(Jmin=2, Jmax=5, eps=1e-3, ic="gauss",
                             ic_params=(0.5, 0.5, 0.0, 0.05), rhs_params=(1.0, 0.5, 0.0)),
-                  umax=math.hypot(1.0, 0.5), capacity=200_000,
+                  umax=math.hypot(1.0, 0.5), capacity=20_000,
                   name="2D advection u=(1,0.5), sigma 0.05, 17^2 blocks, Jmin 2, Jmax 5, eps 1e-3, FP64"),
 }
 
@@ -175,7 +175,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="adv3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="swirl", choices=sorted(WORKLOADS))
+    ap.add_argument("--capacity", type=int, default=0)
+    ap.add_argument("--eps", type=float, default=0.0)
+    ap.add_argument("--no-full", action="store_true",
+                    help="swirl: do not run on to t = t_a for the error (timed window only)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
@@ -185,7 +189,13 @@ def main():
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    w["tree"] = dict(w["tree"])
+    if args.eps > 0:
+        w["tree"]["eps"] = args.eps
+        w["name"] = w["name"].replace("eps %g" % WORKLOADS[args.workload]["tree"]["eps"], "eps %g" % args.eps)
+    if args.capacity > 0:
+        w["capacity"] = args.capacity
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
@@ -212,7 +222,17 @@ def main():
     dt = dt_of(w)
     g.init_tree()
     t = 0.0
-    spin = args.spinup if args.spinup >= 0 else 0
+    full = "full_time" in w and not args.no_full
+    nfull = int(math.ceil(w["full_time"] / dt)) if "full_time" in w else 0
+    if full:
+        dt = w["full_time"] / nfull  # land exactly on t = t_a
+    if args.spinup >= 0:
+        spin = args.spinup
+    elif "full_time" in w:
+        # time the window around t_a / 2, where the deformation and the grid peak
+        spin = max(0, nfull // 2 - args.warmup - args.steps // 2)
+    else:
+        spin = 0
     for _ in range(spin + args.warmup):
         g.step(t, dt)
         t += dt
@@ -259,6 +279,13 @@ def main():
     achieved = stage_bytes / (stage_ms / 1e3) / 1e9 if stage_ms > 0 else 0.0
     per_launch_us = stage_ms * 1e3 / max(1, st["stage_launches"])
     err = g.error(0, t) if w["rhs"] == "adv" else None
+    nsteps_done = spin + args.warmup + args.steps
+    if full:
+        # continue untimed to t = t_a, where the swirl returns to the initial state
+        for s_ in range(nsteps_done, nfull):
+            g.step(s_ * dt, dt)
+        t = nfull * dt
+        err = g.error(0, 0.0)
 
     # ---- end-to-end through the C ABI with pinned host buffers ----
     e2e = None
@@ -309,6 +336,9 @@ def main():
                                    "refined grid) exceeds the 129 MB L2" if args.workload == "adv3d"
                                    else "no flush; small working set (L2-resident)",
                        "l2_rel_error": None if err is None else err["l2"],
+                       "linf_rel_error": None if err is None else err["linf"],
+                       "error_at_t": t if err is not None else None,
+                       "timed_window_t": [(spin + args.warmup) * dt, (spin + args.warmup + args.steps) * dt],
                        "phase_ms": st["ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,

@@ -227,10 +227,22 @@ struct Tree {
   // Ghost-node synchronisation (Sec. 2.2 conditional ghost nodes, Sec. 2.5).
   // Pass 1: every ghost node that is a node of its owner (same or finer level,
   // or a coarse node of a coarser owner) is copied from the owner; every
-  // conditional (block-edge) node that also lies in a finer leaf is overwritten
-  // by the finer value.  Same-level redundant nodes are not rewritten.
+  // conditional (block-edge) node whose owner is another block (a finer one,
+  // or an equal-level one holding it at its lower edge) takes the owner's value.
   // Pass 2, by ascending level: ghost nodes whose owner is coarser and that are
-  // not coarse nodes are predicted from the owner's (already synchronised) tile.
+  // not coarse nodes are predicted from the coarse lattice around them.  Each
+  // coarse stencil node takes the value of its own owner (finest leaf holding
+  // it), which is what the coarse block's synchronised tile holds there; the
+  // paper assumes equal-level redundant nodes identical (Sec. 2.5), so the tie
+  // rule of owner() decides only between values it takes to be equal.
+  double coarse_value(int64_t const Q[3], int v, int min_level) {
+    std::vector<Cand> cs = containing(Q);
+    const Cand* o = owner(cs, 0);
+    if (!o || o->m < min_level) { ++err; return 0.0; }
+    int li[3];
+    local_index(*o->f, Q, li);
+    return val(*o->f, v, li);
+  }
   void sync() {
     struct W1 { Leaf* b; size_t at; double v; };
     struct W2 { Leaf* b; int ijk[3]; Leaf* f; };
@@ -263,8 +275,13 @@ struct Tree {
                 w2[b.lvl].push_back(w);
               }
             } else {
-              const Cand* o = owner(cs, b.lvl + 1);
-              if (!o) continue;
+              // block-edge node: the finer block's value (Sec. 2.2 rule 2); an
+              // equal-level redundant copy is made identical by taking the
+              // canonical owner's value (the paper assumes the copies equal,
+              // Sec. 2.5, but a refinement next to an existing block creates
+              // children whose edge nodes were interpolated, not evolved)
+              const Cand* o = owner(cs, b.lvl);
+              if (!o || o->f == &b) continue;
               int li[3];
               local_index(*o->f, U, li);
               for (int v = 0; v < nv; ++v) w1.push_back({&b, ix(v, i, j, k), val(*o->f, v, li)});
@@ -275,17 +292,49 @@ struct Tree {
     for (auto& lvlw : w2) {  // ascending level
       std::vector<W1> out;
       for (const W2& w : lvlw.second) {
+        if (w.f->lvl != w.b->lvl - 1) ++err;  // owner must be one level coarser (graded)
         int64_t U[3];
         node_pos(*w.b, w.ijk, U);
-        if (w.f->lvl != w.b->lvl - 1) ++err;  // owner must be one level coarser (graded)
+        const int64_t hs = step(w.b->lvl), cs = step(w.f->lvl);
+        // half-coarse position of the point relative to the coarse owner's origin
         int o[3] = {0, 0, 0};
-        int64_t hs = step(w.b->lvl);
         for (int a = 0; a < d; ++a) o[a] = (int)(pmod(U[a] - w.f->c[a] * width(w.f->lvl), N) / hs);
-        for (int v = 0; v < nv; ++v)
-          out.push_back({w.b, ix(v, w.ijk[0], w.ijk[1], w.ijk[2]), predict(*w.f, v, o)});
+        for (int v = 0; v < nv; ++v) {
+          auto node = [&](const int n[3]) {
+            int64_t Q[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) Q[a] = w.f->c[a] * width(w.f->lvl) + (int64_t)n[a] * cs;
+            return coarse_value(Q, v, w.f->lvl);
+          };
+          out.push_back({w.b, ix(v, w.ijk[0], w.ijk[1], w.ijk[2]), predict_nodes(node, o)});
+        }
       }
       for (const W1& w : out) w.b->t[w.at] = w.v;
     }
+  }
+  // Tensor-product prediction at half-coarse position o from coarse node values
+  // node(n): x first, then y, then z (reading c1: the paper states "4th order").
+  template <typename F>
+  double predict_nodes(F node, const int o[3]) const {
+    int ns[3] = {1, 1, 1}, base[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+      int q = o[a];
+      int fl = (q >= 0) ? q / 2 : -((-q + 1) / 2);
+      if (q & 1) { ns[a] = 4; base[a] = fl - 1; } else base[a] = fl;
+    }
+    double vx[4][4];
+    for (int sz = 0; sz < ns[2]; ++sz)
+      for (int sy = 0; sy < ns[1]; ++sy) {
+        double w[4];
+        for (int sx = 0; sx < ns[0]; ++sx) {
+          int n[3] = {base[0] + sx, base[1] + sy, base[2] + sz};
+          w[sx] = node(n);
+        }
+        vx[sz][sy] = ns[0] == 4 ? dd4(w[0], w[1], w[2], w[3]) : w[0];
+      }
+    double vy[4];
+    for (int sz = 0; sz < ns[2]; ++sz)
+      vy[sz] = ns[1] == 4 ? dd4(vx[sz][0], vx[sz][1], vx[sz][2], vx[sz][3]) : vx[sz][0];
+    return ns[2] == 4 ? dd4(vy[0], vy[1], vy[2], vy[3]) : vy[0];
   }
 
   // ------------------------------------------------------------- refine -----

@@ -99,6 +99,15 @@ struct Geo {
   static constexpr int NR = D == 3 ? 64 : 16;  // ring of level l+1 cells, [-1,2]^d
   static constexpr int NCH = 1 << D;
   static_assert(G + 2 < (B - 1) / 2, "prediction stencils of ghosts must stay in the ring");
+  // coarse box: level l-1 nodes around the block that prediction stencils of
+  // ghost nodes can touch, coarse index n in [CLO, CLO + CB) relative to the
+  // block origin
+  static constexpr int CLO = -(G / 2) - 1;
+  static constexpr int CB = (B - 1) / 2 + G + 3;
+  static constexpr int CBOX = CB * CB * (D == 3 ? CB : 1);
+  __device__ static __forceinline__ int cix(int i, int j, int k) {
+    return ((D == 3 ? k - CLO : 0) * CB + (j - CLO)) * CB + (i - CLO);
+  }
   __device__ static __forceinline__ int tix(int i, int j, int k) {
     return ((k + GZ) * T + (j + G)) * T + (i + G);
   }
@@ -124,26 +133,40 @@ __device__ __forceinline__ void set_err(const PoolView& pv, int bits) {
 }
 
 // Ring map: for every level-(l+1) cell q in [-1,2]^d around the block (its own
-// 2^d child cells included) the leaf covering it, searched at l+1, l, l-1.
-// These are exactly the 16 (2D) / 74 (3D) relations of Sec. 2.2 seen cell by
-// cell.  A cell covered by no leaf in that range means a non-graded tree.
+// 2^d child cells included) the leaf covering it, searched at l+1, l, l-1,
+// with the leaf's origin relative to the block origin in level-(l+1) node
+// units (periodic images resolved once here, so per-point work needs no
+// modulo).  These cells carry exactly the 16 (2D) / 74 (3D) relations of
+// Sec. 2.2.  A cell covered by no leaf in that range means a non-graded tree.
+struct Ring {
+  int slot[64];
+  int org[64][3];
+  int8_t lvl[64];
+  int finer;    // some leaf one level finer touches the block
+  int coarser;  // some leaf one level coarser touches the block
+};
+
 template <int D, int B>
-__device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b,
-                           int* rslot, int8_t* rlvl) {
+__device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, Ring& R) {
   using Gm = Geo<D, B>;
+  if (threadIdx.x == 0) R.finer = R.coarser = 0;
+  __syncthreads();
   for (int r = threadIdx.x; r < Gm::NR; r += blockDim.x) {
     const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
     bool inside = true;
     for (int a = 0; a < D; ++a) inside &= (q[a] == 0 || q[a] == 1);
     if (inside) {
-      rslot[r] = b.slot;
-      rlvl[r] = (int8_t)b.lvl;
+      R.slot[r] = b.slot;
+      R.lvl[r] = (int8_t)b.lvl;
+      for (int a = 0; a < 3; ++a) R.org[r][a] = 0;
       continue;
     }
     const int64_t nl1 = (int64_t)1 << (b.lvl + 1);
     int64_t cell[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, c2[3] = {0, 0, 0};
+    int un[3] = {0, 0, 0};
     for (int a = 0; a < D; ++a) {
-      cell[a] = pmod64(2 * b.c[a] + q[a], nl1);
+      un[a] = (int)(2 * b.c[a] + q[a]);
+      cell[a] = (int64_t)(un[a]) & (nl1 - 1);
       c1[a] = cell[a] >> 1;
       c2[a] = cell[a] >> 2;
     }
@@ -154,8 +177,15 @@ __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInf
       set_err(pv, kErrGraded);
       m = -1;
     }
-    rslot[r] = s;
-    rlvl[r] = (int8_t)m;
+    if (m == b.lvl + 1) R.finer = 1;  // benign races: all writers store 1
+    if (m == b.lvl - 1) R.coarser = 1;
+    const int sh = b.lvl + 1 - m;
+    for (int a = 0; a < 3; ++a) {
+      const int oc = a < D && m >= 0 ? ((un[a] >> sh) << sh) - (int)(2 * b.c[a]) : 0;
+      R.org[r][a] = oc * (B - 1);
+    }
+    R.slot[r] = s;
+    R.lvl[r] = (int8_t)m;
   }
 }
 
@@ -169,50 +199,89 @@ struct Own {
   int off[3];
 };
 
+template <int B>
+struct Log2B {
+  static constexpr int value = B == 17 ? 4 : (B == 33 ? 5 : -1);
+};
+
 template <int D, int B>
-__device__ __forceinline__ bool owner(const BlockInfo& b, const int h[3], int min_m,
-                                      const int* rslot, const int8_t* rlvl, Own& o) {
+__device__ __forceinline__ bool owner(const BlockInfo& b, const int h[3], int min_m, const Ring& R,
+                                      Own& o) {
+  constexpr int P = Log2B<B>::value;
+  static_assert(P > 0, "Bs - 1 must be a power of two");
   int c0[3] = {0, 0, 0};
   bool onb[3] = {false, false, false};
+  bool any = false;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    c0[a] = floordiv(h[a], B - 1);
-    onb[a] = (h[a] - c0[a] * (B - 1)) == 0;
+    c0[a] = h[a] >> P;
+    onb[a] = (h[a] & (B - 2)) == 0;
+    any |= onb[a];
   }
+  // Candidate A: the ring cell holding the point at its lower edge or inside.
+  // In its leaf the point is never the upper edge node, so A has the smallest
+  // combo; it is the owner unless another candidate is finer.
+  const int rA = (c0[0] + 1) + 4 * (c0[1] + 1) + 16 * (D == 3 ? c0[2] + 1 : 0);
+  const int mA = R.lvl[rA];
+  int mmax = R.slot[rA] >= 0 ? mA : -1;
+  if (any) {
+#pragma unroll
+    for (int combo = 1; combo < (1 << D); ++combo) {
+      bool ok = true;
+      int r = 0, mul = 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int bit = (combo >> a) & 1;
+        if (bit && !onb[a]) ok = false;
+        const int q = c0[a] - bit;
+        if (q < -1) ok = false;
+        r += (q + 1) * mul;
+        mul *= 4;
+      }
+      if (ok && R.slot[r] >= 0 && R.lvl[r] > mmax) mmax = R.lvl[r];
+    }
+  }
+  if (mmax < 0 || mmax < min_m) {
+    o.m = -1;
+    return false;
+  }
+  const int l1 = b.lvl + 1;
+  if (mA == mmax && R.slot[rA] >= 0) {
+    o.m = mA;
+    o.combo = 0;
+    o.slot = R.slot[rA];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o.off[a] = a < D ? h[a] - R.org[rA][a] : 0;
+    return true;
+  }
+  // a finer leaf shares the point: smallest combo among the finest candidates
   o.m = -1;
   o.combo = 1 << 30;
-  const int l1 = b.lvl + 1;
-  const int64_t N1 = (int64_t)(B - 1) << l1, n1 = (int64_t)1 << l1;
 #pragma unroll
-  for (int combo = 0; combo < (1 << D); ++combo) {
+  for (int combo = 1; combo < (1 << D); ++combo) {
     bool ok = true;
-    int q[3] = {0, 0, 0};
+    int r = 0, mul = 1;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const int bit = (combo >> a) & 1;
       if (bit && !onb[a]) ok = false;
-      q[a] = c0[a] - bit;
-      if (q[a] < -1 || q[a] > 2) ok = false;
+      const int q = c0[a] - bit;
+      if (q < -1) ok = false;
+      r += (q + 1) * mul;
+      mul *= 4;
     }
-    if (!ok) continue;
-    const int r = (q[0] + 1) + 4 * (q[1] + 1) + 16 * (D == 3 ? q[2] + 1 : 0);
-    const int s = rslot[r], m = rlvl[r];
-    if (s < 0 || m < min_m) continue;
-    const int sh = l1 - m;
+    if (!ok || R.slot[r] < 0 || R.lvl[r] != mmax) continue;
+    const int W = (B - 1) << (l1 - mmax);
     int oc = 0, off[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const int64_t cabs = pmod64(2 * b.c[a] + q[a], n1);
-      const int64_t origin = ((cabs >> sh) * (B - 1)) << sh;
-      const int64_t pabs = pmod64(2 * b.c[a] * (B - 1) + h[a], N1);
-      const int64_t of = pmod64(pabs - origin, N1);
-      off[a] = (int)of;
-      if (of == ((int64_t)(B - 1) << sh)) oc |= 1 << a;
+      off[a] = h[a] - R.org[r][a];
+      if (off[a] == W) oc |= 1 << a;
     }
-    if (m > o.m || (m == o.m && oc < o.combo)) {
-      o.m = m;
+    if (oc < o.combo) {
+      o.m = mmax;
       o.combo = oc;
-      o.slot = s;
+      o.slot = R.slot[r];
 #pragma unroll
       for (int a = 0; a < 3; ++a) o.off[a] = off[a];
     }
@@ -233,70 +302,28 @@ __device__ __forceinline__ TF pool_at(const PoolView& pv, const TF* F, int slot,
   return F[((int64_t)slot * pv.nvar + v) * pv.vs + Geo<D, B>::lin(li[0], li[1], D == 3 ? li[2] : 0)];
 }
 
-// Ghost value predicted from a coarser owner f (level l-1).  Stencil nodes are
-// f's tile values: f's own node, unless a finer leaf shares it (then the finer
-// value, Sec. 2.2 rule 2); nodes outside f come from their own owner.
-template <int D, int B, typename TF, typename TT>
-__device__ TT predict_ghost(const PoolView& pv, const BlockInfo& b, const int h[3], const Own& f,
-                            int v, const TF* F, const int* rslot, const int8_t* rlvl) {
+// Coarse-lattice prediction at half-coarse position o (relative to the block
+// origin) from the staged coarse box: x first, then y, then z.
+template <int D, int B, typename TT>
+__device__ __forceinline__ TT predict_box(const TT* box, const int o[3]) {
+  using Gm = Geo<D, B>;
   int base[3] = {0, 0, 0}, ns[3] = {1, 1, 1};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int q4 = f.off[a] >> 2;
-    if ((f.off[a] & 3) == 2) { ns[a] = 4; base[a] = q4 - 1; }
-    else base[a] = q4;
+    const int fl = o[a] >> 1;
+    if (o[a] & 1) { ns[a] = 4; base[a] = fl - 1; }
+    else base[a] = fl;
   }
   TT vx[4][4];
   for (int sz = 0; sz < ns[2]; ++sz)
     for (int sy = 0; sy < ns[1]; ++sy) {
-      TT w[4];
-      for (int sx = 0; sx < ns[0]; ++sx) {
-        const int n[3] = {base[0] + sx, base[1] + sy, base[2] + sz};
-        bool inside = true, strict = true;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          inside &= (n[a] >= 0 && n[a] <= B - 1);
-          strict &= (n[a] >= 1 && n[a] <= B - 2);
-        }
-        TT val;
-        if (strict) {
-          val = (TT)pool_at<D, B>(pv, F, f.slot, v, n);
-        } else {
-          int hq[3] = {0, 0, 0};
-          bool in_ring = true;
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            hq[a] = h[a] + 4 * n[a] - f.off[a];
-            in_ring &= (hq[a] > -(B - 1) && hq[a] < 3 * (B - 1));
-          }
-          if (!in_ring) {
-            set_err(pv, kErrGraded);
-            val = TT(0);
-          } else {
-            Own o;
-            if (inside) {
-              if (owner<D, B>(b, hq, b.lvl, rslot, rlvl, o)) {
-                const int sh = b.lvl + 1 - o.m;
-                int li[3] = {o.off[0] >> sh, o.off[1] >> sh, o.off[2] >> sh};
-                val = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
-              } else {
-                val = (TT)pool_at<D, B>(pv, F, f.slot, v, n);
-              }
-            } else {
-              if (owner<D, B>(b, hq, 0, rslot, rlvl, o) && o.m >= b.lvl - 1) {
-                const int sh = b.lvl + 1 - o.m;
-                int li[3] = {o.off[0] >> sh, o.off[1] >> sh, o.off[2] >> sh};
-                val = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
-              } else {
-                set_err(pv, kErrGraded);
-                val = TT(0);
-              }
-            }
-          }
-        }
-        w[sx] = val;
+      const int y = base[1] + sy, z = base[2] + sz;
+      if (ns[0] == 4) {
+        const TT* r = box + Gm::cix(base[0], y, z);
+        vx[sz][sy] = dd4(r[0], r[1], r[2], r[3]);
+      } else {
+        vx[sz][sy] = box[Gm::cix(base[0], y, z)];
       }
-      vx[sz][sy] = ns[0] == 4 ? dd4(w[0], w[1], w[2], w[3]) : w[0];
     }
   TT vy[4];
   for (int sz = 0; sz < ns[2]; ++sz)
@@ -305,14 +332,36 @@ __device__ TT predict_ghost(const PoolView& pv, const BlockInfo& b, const int h[
 }
 
 // Fills the synchronised tile (nvar x T^d, type TT) of block b from field F.
-// commit: block-edge nodes taken from a finer leaf are also written back into
-// F (the paper's synchronisation overwrites them in the block).  ghost_out
-// (optional, double): the tile is also written there (mr_get_tiles).
+// Block-edge nodes owned by another block (a finer one, Sec. 2.2 rule 2, or an
+// equal-level one that holds the node at its lower edge, which keeps redundant
+// copies identical as Sec. 2.5 assumes) take the owner's value; with commit
+// they are also written back into F when they differ.  cbox: scratch
+// of nvar x CBOX values for the coarse lattice (used when a coarser leaf
+// touches the block): every coarse node takes its owner's value, and ghost
+// nodes between coarse nodes are predicted from it.
 template <int D, int B, typename TF, typename TT>
 __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, TF* Fw, TT* tile,
-                          bool commit, const int* rslot, const int8_t* rlvl) {
+                          bool commit, const Ring& R, TT* cbox) {
   using Gm = Geo<D, B>;
   const int nv = pv.nvar;
+  const int64_t own = (int64_t)b.slot * nv * pv.vs;
+  if (R.coarser) {
+    for (int idx = threadIdx.x; idx < Gm::CBOX; idx += blockDim.x) {
+      const int n[3] = {idx % Gm::CB + Gm::CLO, (idx / Gm::CB) % Gm::CB + Gm::CLO,
+                        D == 3 ? idx / (Gm::CB * Gm::CB) + Gm::CLO : 0};
+      const int h[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
+      Own o;
+      if (!owner<D, B>(b, h, 0, R, o) || o.m < b.lvl - 1) {
+        set_err(pv, kErrGraded);
+        for (int v = 0; v < nv; ++v) cbox[v * Gm::CBOX + idx] = TT(0);
+        continue;
+      }
+      const int sh = b.lvl + 1 - o.m;
+      const int li[3] = {o.off[0] >> sh, o.off[1] >> sh, o.off[2] >> sh};
+      for (int v = 0; v < nv; ++v) cbox[v * Gm::CBOX + idx] = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
+    }
+    __syncthreads();
+  }
   for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x) {
     const int i = idx % Gm::T - Gm::G;
     const int j = (idx / Gm::T) % Gm::T - Gm::G;
@@ -324,30 +373,27 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       if (ijk[a] < 0 || ijk[a] > B - 1) ghost = true;
       else if (ijk[a] == 0 || ijk[a] == B - 1) edge = true;
     }
+    const int h[3] = {2 * i, 2 * j, 2 * k};
     if (!ghost) {
       const int64_t at = Gm::lin(i, j, k);
       Own o;
-      bool finer = false;
-      if (edge) {
-        const int h[3] = {2 * i, 2 * j, 2 * k};
-        finer = owner<D, B>(b, h, b.lvl + 1, rslot, rlvl, o);
-      }
+      const bool over = edge && owner<D, B>(b, h, b.lvl, R, o) && o.slot != b.slot;
       for (int v = 0; v < nv; ++v) {
         TF val;
-        if (finer) {
-          const int li[3] = {o.off[0], o.off[1], o.off[2]};
+        if (over) {
+          const int shv = b.lvl + 1 - o.m;
+          const int li[3] = {o.off[0] >> shv, o.off[1] >> shv, o.off[2] >> shv};
           val = pool_at<D, B>(pv, F, o.slot, v, li);
-          if (commit) Fw[((int64_t)b.slot * nv + v) * pv.vs + at] = val;
+          if (commit && F[own + (int64_t)v * pv.vs + at] != val) Fw[own + (int64_t)v * pv.vs + at] = val;
         } else {
-          val = F[((int64_t)b.slot * nv + v) * pv.vs + at];
+          val = F[own + (int64_t)v * pv.vs + at];
         }
         tile[v * Gm::TILE + idx] = (TT)val;
       }
       continue;
     }
-    const int h[3] = {2 * i, 2 * j, 2 * k};
     Own o;
-    if (!owner<D, B>(b, h, 0, rslot, rlvl, o)) {
+    if (!owner<D, B>(b, h, 0, R, o)) {
       set_err(pv, kErrGraded);
       for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = TT(0);
       continue;
@@ -361,8 +407,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
     } else {
       if (o.m != b.lvl - 1) set_err(pv, kErrGraded);
-      for (int v = 0; v < nv; ++v)
-        tile[v * Gm::TILE + idx] = predict_ghost<D, B, TF, TT>(pv, b, h, o, v, F, rslot, rlvl);
+      for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = predict_box<D, B, TT>(cbox + v * Gm::CBOX, ijk);
     }
   }
 }
@@ -371,29 +416,29 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
 // coarse nodes) from a tile whose coarse node n sits at tile index n*stride.
 // x first, then y, then z.  Used by refinement (stride 1: the mother's tile) and
 // by the details (stride 2: even nodes of the block's own tile).
-template <int D, int B, typename TT>
-__device__ __forceinline__ TT predict_tile(const TT* tile, const int o[3], int stride) {
+template <int D, int B, typename TT, typename TA = TT>
+__device__ __forceinline__ TA predict_tile(const TT* tile, const int o[3], int stride) {
   using Gm = Geo<D, B>;
   int base[3] = {0, 0, 0}, ns[3] = {1, 1, 1};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int fl = floordiv(o[a], 2);
+    const int fl = o[a] >> 1;  // floor(o / 2)
     if (o[a] & 1) { ns[a] = 4; base[a] = fl - 1; }
     else base[a] = fl;
   }
-  TT vx[4][4];
+  TA vx[4][4];
   for (int sz = 0; sz < ns[2]; ++sz)
     for (int sy = 0; sy < ns[1]; ++sy) {
       const int y = stride * (base[1] + sy), z = D == 3 ? stride * (base[2] + sz) : 0;
       if (ns[0] == 4) {
         const int x0 = stride * base[0];
-        vx[sz][sy] = dd4(tile[Gm::tix(x0, y, z)], tile[Gm::tix(x0 + stride, y, z)],
-                         tile[Gm::tix(x0 + 2 * stride, y, z)], tile[Gm::tix(x0 + 3 * stride, y, z)]);
+        vx[sz][sy] = dd4((TA)tile[Gm::tix(x0, y, z)], (TA)tile[Gm::tix(x0 + stride, y, z)],
+                         (TA)tile[Gm::tix(x0 + 2 * stride, y, z)], (TA)tile[Gm::tix(x0 + 3 * stride, y, z)]);
       } else {
-        vx[sz][sy] = tile[Gm::tix(stride * base[0], y, z)];
+        vx[sz][sy] = (TA)tile[Gm::tix(stride * base[0], y, z)];
       }
     }
-  TT vy[4];
+  TA vy[4];
   for (int sz = 0; sz < ns[2]; ++sz)
     vy[sz] = ns[1] == 4 ? dd4(vx[sz][0], vx[sz][1], vx[sz][2], vx[sz][3]) : vx[sz][0];
   return ns[2] == 4 ? dd4(vy[0], vy[1], vy[2], vy[3]) : vy[0];

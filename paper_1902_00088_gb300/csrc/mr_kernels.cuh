@@ -7,7 +7,7 @@
 
 namespace mr {
 
-constexpr int kRingBytes = 64 * 4 + 64 + 64;  // rslot[64] + rlvl[64] + pad (16-aligned)
+constexpr int kRingBytes = (int)((sizeof(Ring) + 15) / 16 * 16);
 
 // ------------------------------------------------------------------ stage ----
 // One RK4 stage on every block (Sec. 3: 4th-order central FD + classic RK4):
@@ -17,21 +17,21 @@ constexpr int kRingBytes = 64 * 4 + 64 + 64;  // rslot[64] + rlvl[64] + pad (16-
 // Advection RHS: -(u Dx phi + v Dy phi [+ w Dz phi]),
 //   D1 f = ((f[-2] - f[2]) + 8 (f[1] - f[-1])) / (12 dx).
 template <int D, int B, int RHS, typename TS, typename TY, typename TSRC>
-__global__ void k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
+__global__ void __launch_bounds__(256) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
                             TS* __restrict__ acc, TY* __restrict__ ynext, int stage, StageArgs sa) {
   using Gm = Geo<D, B>;
   using TC = TY;  // stencil arithmetic type
-  int* rslot = smem_as<int>(0);
-  int8_t* rlvl = smem_as<int8_t>(256);
+  Ring& R = *smem_as<Ring>(0);
   TC* tile = smem_as<TC>(kRingBytes);
+  TC* cbox = tile + pv.nvar * Gm::TILE;
   const int nact = pv.cnt->n_act;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
     const TreeDev& td = pv.trees[b.tree];
-    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, rslot, rlvl);
+    fill_tile<D, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
     __syncthreads();
     const TC c = (TC)td.cD[b.lvl];
     const double ca = sa.ca[b.tree], cy = sa.cy[b.tree], ct = sa.ct[b.tree];
@@ -85,12 +85,12 @@ __global__ void k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __res
 // interpolating prediction and split into 2^d children (one treecode digit
 // appended); children are placed in the new active list in Hilbert order.
 template <int D, int B, typename TS>
-__global__ void k_refine(PoolView pv, TS* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_refine(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
-  int* rslot = smem_as<int>(0);
-  int8_t* rlvl = smem_as<int8_t>(256);
+  Ring& R = *smem_as<Ring>(0);
   __shared__ int cslot[8];
   TS* tile = smem_as<TS>(kRingBytes);
+  TS* cbox = tile + pv.nvar * Gm::TILE;
   const int nact = pv.cnt->n_act;
   const int n_alloc = pv.cnt->n_alloc, n_free = pv.cnt->n_free;
   if (n_alloc > n_free) {
@@ -107,9 +107,9 @@ __global__ void k_refine(PoolView pv, TS* __restrict__ y) {
     }
     const BlockInfo b = load_block(pv, slot);
     const TreeDev& td = pv.trees[b.tree];
-    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TS, TS>(pv, b, y, y, tile, false, rslot, rlvl);
+    fill_tile<D, B, TS, TS>(pv, b, y, y, tile, false, R, cbox);
     if (threadIdx.x == 0) {
       uint64_t key[8];
       int32_t cc[8][3];
@@ -148,32 +148,74 @@ __global__ void k_refine(PoolView pv, TS* __restrict__ y) {
 // Sec. 2.3: D = B - P(R(B)) on the synchronised tile (R keeps even tile nodes,
 // ghosts included; P predicts the odd ones).  Per block and variable the
 // largest |d| (warp-shuffle max, then across warps) and the largest |q_v|.
+// P is evaluated separably in the fixed order x, then y, then z: the x pass
+// over all coarse rows is stored in shared memory (X), the y and z passes run
+// per point; every output sees the same operations as the point-wise tensor
+// product.
+template <int D, int B>
+struct DetGeo {
+  static constexpr int NC = (B + 1) / 2 + 2;  // coarse rows -1 .. (B+1)/2
+  static constexpr int NX = NC * B * (D == 3 ? NC : 1);
+};
+
 template <int D, int B, typename TS, typename TD>
-__global__ void k_details(PoolView pv, TS* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_details(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
-  int* rslot = smem_as<int>(0);
-  int8_t* rlvl = smem_as<int8_t>(256);
+  using DG = DetGeo<D, B>;
+  Ring& R = *smem_as<Ring>(0);
   __shared__ double red[2][32];
-  TD* tile = smem_as<TD>(kRingBytes);
+  TS* tile = smem_as<TS>(kRingBytes);  // storage type; TD is the arithmetic type
+  TS* cbox = tile + pv.nvar * Gm::TILE;
+  TD* X = reinterpret_cast<TD*>(cbox + pv.nvar * Gm::CBOX + 2);  // 16-byte aligned below
+  X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(X) + 15) & ~(uintptr_t)15);
   const int nact = pv.cnt->n_act;
   const int nv = pv.nvar;
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
     const TreeDev& td = pv.trees[b.tree];
-    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TS, TD>(pv, b, y, y, tile, true, rslot, rlvl);
+    fill_tile<D, B, TS, TS>(pv, b, y, y, tile, true, R, cbox);
     __syncthreads();
     for (int v = 0; v < nv; ++v) {
-      const TD* tv = tile + v * Gm::TILE;
+      const TS* tv = tile + v * Gm::TILE;
+      // x pass on coarse rows (yc, zc) in [-1, NC-2]
+      for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
+        const int x = idx % B, yc = (idx / B) % DG::NC - 1, zc = D == 3 ? idx / (B * DG::NC) - 1 : 0;
+        const int yy = 2 * yc, zz = 2 * zc;
+        TD val;
+        if ((x & 1) == 0) {
+          val = (TD)tv[Gm::tix(x, yy, zz)];
+        } else {
+          const int n0 = (x - 1) / 2;
+          val = dd4((TD)tv[Gm::tix(2 * n0 - 2, yy, zz)], (TD)tv[Gm::tix(2 * n0, yy, zz)],
+                    (TD)tv[Gm::tix(2 * n0 + 2, yy, zz)], (TD)tv[Gm::tix(2 * n0 + 4, yy, zz)]);
+        }
+        X[idx] = val;
+      }
+      __syncthreads();
+      auto xat = [&](int x, int yc, int zc) {
+        return X[((D == 3 ? (zc + 1) * DG::NC : 0) + (yc + 1)) * B + x];
+      };
       double md = 0.0, mq = 0.0;
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-        const TD val = tv[Gm::tix(i, j, k)];
+        const TD val = (TD)tv[Gm::tix(i, j, k)];
         mq = fmax(mq, fabs((double)val));
         if (((i | j | k) & 1) == 0) continue;
-        const int o[3] = {i, j, k};
-        const TD d = val - predict_tile<D, B, TD>(tv, o, 2);
+        auto ypass = [&](int zc) -> TD {
+          if ((j & 1) == 0) return xat(i, j / 2, zc);
+          const int m0 = (j - 1) / 2;
+          return dd4(xat(i, m0 - 1, zc), xat(i, m0, zc), xat(i, m0 + 1, zc), xat(i, m0 + 2, zc));
+        };
+        TD pr;
+        if (D == 2 || (k & 1) == 0) {
+          pr = ypass(k / 2);
+        } else {
+          const int k0 = (k - 1) / 2;
+          pr = dd4(ypass(k0 - 1), ypass(k0), ypass(k0 + 1), ypass(k0 + 2));
+        }
+        const TD d = val - pr;
         md = fmax(md, fabs((double)d));
       }
       for (int s = 16; s > 0; s >>= 1) {
@@ -190,24 +232,21 @@ __global__ void k_details(PoolView pv, TS* __restrict__ y) {
           md = fmax(md, red[0][w]);
           mq = fmax(mq, red[1][w]);
         }
-        // a NaN anywhere in the block makes its norm NaN (fmax drops NaN)
         pv.md[(int64_t)b.slot * nv + v] = md;
         pv.bmax[(int64_t)b.slot * nv + v] = mq;
         if (pv.norm_kind == 1) atomic_max_pos(&pv.svar[b.tree * nv + v], mq);
       }
       __syncthreads();
     }
-    // NaN detection: any non-finite interior value
+    // NaN detection: any non-finite interior value makes the block norm NaN
     bool bad = false;
     for (int q = threadIdx.x; q < Gm::NI * nv; q += blockDim.x) {
       const int v = q / Gm::NI, r = q % Gm::NI;
       const int i = r % B, j = (r / B) % B, k = D == 3 ? r / (B * B) : 0;
-      const double val = (double)tile[v * Gm::TILE + Gm::tix(i, j, k)];
-      bad |= !isfinite(val);
+      bad |= !isfinite((double)tile[v * Gm::TILE + Gm::tix(i, j, k)]);
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
       pv.md[(int64_t)b.slot * nv] = __longlong_as_double(0x7ff8000000000000LL);
-    }
   }
 }
 
@@ -217,7 +256,7 @@ __global__ void k_details(PoolView pv, TS* __restrict__ y) {
 // from the child in which it has local index 0.  The mother takes the slot of
 // the family member that comes first in Hilbert order.
 template <int D, int B, typename TS>
-__global__ void k_coarsen(PoolView pv, TS* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
   TS* buf = smem_as<TS>(0);
   __shared__ int cs[8];
@@ -305,19 +344,19 @@ __global__ void k_ic(PoolView pv, TS* __restrict__ y) {
 // taken from finer blocks; optionally writes the full tile (double) to `tiles`
 // at the block's list position.
 template <int D, int B, typename TS>
-__global__ void k_sync(PoolView pv, TS* __restrict__ y, double* __restrict__ tiles) {
+__global__ void __launch_bounds__(256) k_sync(PoolView pv, TS* __restrict__ y, double* __restrict__ tiles) {
   using Gm = Geo<D, B>;
-  int* rslot = smem_as<int>(0);
-  int8_t* rlvl = smem_as<int8_t>(256);
+  Ring& R = *smem_as<Ring>(0);
   double* tile = smem_as<double>(kRingBytes);
+  double* cbox = tile + pv.nvar * Gm::TILE;
   const int nact = pv.cnt->n_act;
   const int nv = pv.nvar;
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
     const TreeDev& td = pv.trees[b.tree];
-    build_ring<D, B>(pv, td, b, rslot, rlvl);
+    build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TS, double>(pv, b, y, y, tile, true, rslot, rlvl);
+    fill_tile<D, B, TS, double>(pv, b, y, y, tile, true, R, cbox);
     __syncthreads();
     if (tiles)
       for (int idx = threadIdx.x; idx < nv * Gm::TILE; idx += blockDim.x)

@@ -31,9 +31,9 @@ static inline int flat_grid(const PoolView& pv, int threads) {
 template <int D, int B, int RHS, typename TS, typename TY>
 static void stage_impl(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
                        const LaunchCfg& lc, cudaStream_t st) {
-  constexpr int threads = D == 3 ? 512 : 256;
+  constexpr int threads = 256;
   const int nv = 1;
-  const size_t smem = kRingBytes + sizeof(TY) * nv * Geo<D, B>::TILE;
+  const size_t smem = kRingBytes + sizeof(TY) * nv * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
   TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
   if (stage == 0) {
     auto k = k_stage_adv<D, B, RHS, TS, TY, TS>;
@@ -63,7 +63,7 @@ static void stage_prec(const PoolView& pv, const Fields& f, int stage, const Sta
 template <int D>
 void launch_stage(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
                   const LaunchCfg& lc, cudaStream_t st) {
-  if (D == 2) {
+  if constexpr (D == 2) {
     if (pv.Bs == 17) {
       if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, 17, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
       else stage_prec<D, 17, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
@@ -80,12 +80,17 @@ void launch_stage(const PoolView& pv, const Fields& f, int stage, const StageArg
 template <int D, template <int, int, typename> class F, typename... A>
 static void dispatch_bs(const PoolView& pv, A&&... args) {
   const bool st64 = pv.prec != MR_PREC_FP32;
-  if (D == 3 || pv.Bs == 17) {
+  if constexpr (D == 3) {
     if (st64) F<D, 17, double>::run(pv, args...);
     else F<D, 17, float>::run(pv, args...);
   } else {
-    if (st64) F<D, 33, double>::run(pv, args...);
-    else F<D, 33, float>::run(pv, args...);
+    if (pv.Bs == 17) {
+      if (st64) F<D, 17, double>::run(pv, args...);
+      else F<D, 17, float>::run(pv, args...);
+    } else {
+      if (st64) F<D, 33, double>::run(pv, args...);
+      else F<D, 33, float>::run(pv, args...);
+    }
   }
 }
 
@@ -93,8 +98,8 @@ static void dispatch_bs(const PoolView& pv, A&&... args) {
 template <int D, int B, typename TS>
 struct RefineRun {
   static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
-    constexpr int threads = D == 3 ? 512 : 256;
-    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * Geo<D, B>::TILE;
+    constexpr int threads = 256;
+    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
     auto k = k_refine<D, B, TS>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, 0);
@@ -140,15 +145,16 @@ template <int D, int B, typename TS>
 struct DetailsRun {
   static void run(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
                   cudaStream_t st) {
-    constexpr int threads = D == 3 ? 512 : 256;
-    if (fp64 || sizeof(TS) == 8) {
-      const size_t smem = kRingBytes + sizeof(double) * pv.nvar * Geo<D, B>::TILE;
+    constexpr int threads = 256;
+    const bool d64 = fp64 || sizeof(TS) == 8;
+    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX) + 32 +
+                        (d64 ? 8 : sizeof(TS)) * DetGeo<D, B>::NX;
+    if (d64) {
       auto k = k_details<D, B, TS, double>;
       prep_smem(k, smem);
       k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
     } else {
-      const size_t smem = kRingBytes + sizeof(float) * pv.nvar * Geo<D, B>::TILE;
-      auto k = k_details<D, B, TS, float>;
+      auto k = k_details<D, B, TS, TS>;
       prep_smem(k, smem);
       k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
     }
@@ -158,7 +164,7 @@ struct DetailsRun {
 template <int D, int B, typename TS>
 struct CoarsenRun {
   static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
-    constexpr int threads = D == 3 ? 512 : 256;
+    constexpr int threads = 256;
     const size_t smem = sizeof(TS) * pv.nvar * Geo<D, B>::NI;
     auto k = k_coarsen<D, B, TS>;
     prep_smem(k, smem);
@@ -191,8 +197,8 @@ template <int D, int B, typename TS>
 struct SyncRun {
   static void run(const PoolView& pv, const Fields& f, double* tiles, const LaunchCfg& lc,
                   cudaStream_t st) {
-    constexpr int threads = D == 3 ? 512 : 256;
-    const size_t smem = kRingBytes + sizeof(double) * pv.nvar * Geo<D, B>::TILE;
+    constexpr int threads = 256;
+    const size_t smem = kRingBytes + sizeof(double) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
     auto k = k_sync<D, B, TS>;
     prep_smem(k, smem);
     k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y, tiles);

@@ -254,3 +254,18 @@ def test_error_codes(mr, oracle_mod):
     with pytest.raises(mr.MRError) as e:
         g3.adapt("coarsen")
     assert e.value.status == mr.MR_ENAN
+
+
+def test_adaptive_swirl_stays_bounded(mr):
+    # Property at a size the oracle cannot run: the adaptive swirl (Sec. 3) with a
+    # small threshold through its strongest deformation keeps max|phi| <= 1 (+1%).
+    g = mr.Forest(dim=2, precision="fp64", rhs="swirl", capacity=100_000,
+                  trees=[dict(Jmin=1, Jmax=6, eps=1e-5, ic="gauss",
+                              ic_params=(0.5, 0.75, 0.0, math.sqrt(0.005)), rhs_params=(5.0,))])
+    g.init_tree()
+    dt = 0.5 / (16 * 64)
+    for s in range(3200):
+        g.step(s * dt, dt)
+    info, f = g.get_blocks()
+    assert np.isfinite(f).all() and np.abs(f).max() < 1.01, np.abs(f).max()
+    assert len(info) > 500  # the grid did refine around the filament

@@ -94,10 +94,17 @@ def test_details_of_quartic_closed_form(oracle_mod):
 def test_refine_then_coarsen_returns_mother_bit_exactly(oracle_mod, dim):
     B, g = (17, 4) if dim == 2 else (9, 2)
     o = mk(oracle_mod, dim=dim, Bs=B, ng=g, Jmin=2, Jmax=3, eps=1e300)
+    # random values on the global level-2 lattice (redundant block-edge nodes
+    # hold one value, as Sec. 2.5 assumes), sampled by every block
     rng = np.random.default_rng(7)
     leaves = sorted(treegen.uniform_tree(dim, 2))
     lvl, crd = treegen.as_arrays(leaves)
-    fields = rng.standard_normal((len(leaves), 1) + (B,) * dim)
+    n = (B - 1) * 4
+    glob = rng.standard_normal((n,) * dim)
+    fields = np.zeros((len(leaves), 1) + (B,) * dim)
+    for q in range(len(leaves)):
+        idx = [np.mod(crd[q, a] * (B - 1) + np.arange(B), n) for a in range(dim)]
+        fields[q, 0] = glob[np.ix_(*idx[::-1])]
     o.set_blocks(lvl, crd, fields)
     before = o.blocks()
     o.refine(0)
@@ -376,3 +383,26 @@ def test_compression_tends_to_one(oracle_mod):
         counts.append(o.n)
     assert counts[0] <= counts[1] <= counts[2]
     assert counts[2] == 4 ** 4
+
+
+def test_sync_makes_redundant_edge_nodes_single_valued(oracle_mod):
+    # Sec. 2.2/2.5: a node on the edge shared by blocks holds one value after a
+    # synchronisation (finer block first, equal-level copies from the block that
+    # holds the node at its lower edge).  Start from independent random blocks.
+    rng = np.random.default_rng(3)
+    leaves = treegen.random_graded_tree(2, 1, 4, 6, 9)
+    lvl, crd = treegen.as_arrays(leaves)
+    o = mk(oracle_mod, Jmin=1, Jmax=4)
+    o.set_blocks(lvl, crd, rng.standard_normal((len(leaves), 1, 17, 17)))
+    o.sync()
+    b = o.blocks()
+    vals = {}
+    for n in range(o.n):
+        lv, (cx, cy) = int(b["level"][n]), b["coords"][n][:2]
+        s = 1 << (4 - lv)  # node spacing in level-4 units
+        for j in (0, 16):
+            for i in range(17):
+                for (ii, jj) in ((i, j), (j, i)):
+                    key = (((cx * 16 + ii) * s) % 256, ((cy * 16 + jj) * s) % 256)
+                    v = b["fields"][n, 0, jj, ii]
+                    assert vals.setdefault(key, v) == v, (key, v, vals[key])
