@@ -21,7 +21,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Synthetic workloads shaped like the paper's runs (see the design doc for the recipe).
+# Synthetic workloads shaped like the paper's runs: analytic initial fields, seeded parameters.
 WORKLOADS = {
     # 3D linear advection, Gaussian sigma 0.04, u = (1,1,1), 17^3 blocks, Jmax 6,
     # eps 1e-4, FP32 stencils + FP64 details, Hilbert-ordered pool.

@@ -196,7 +196,7 @@ struct Tree {
 
   // Tensor-product prediction from a coarse tile: positions given in units of
   // half a coarse spacing (o[a] odd = between coarse nodes).  x first, then y,
-  // then z (reading c1 of the build notes: the paper states only "4th order").
+  // then z (the paper states only a central "4th order" interpolation).
   double predict(const Leaf& f, int v, const int o[3]) const {
     int ns[3] = {1, 1, 1}, base[3] = {0, 0, 0};
     for (int a = 0; a < d; ++a) {
@@ -312,7 +312,7 @@ struct Tree {
     }
   }
   // Tensor-product prediction at half-coarse position o from coarse node values
-  // node(n): x first, then y, then z (reading c1: the paper states "4th order").
+  // node(n): x first, then y, then z (the paper states only "4th order").
   template <typename F>
   double predict_nodes(F node, const int o[3]) const {
     int ns[3] = {1, 1, 1}, base[3] = {0, 0, 0};
@@ -622,7 +622,7 @@ struct Tree {
     double s = p.ic[3];
     return std::exp(-(dd * dd) / (2.0 * s * s));
   }
-  // Temporal mixing layer (periodic pair of tanh layers, see build notes c16).
+  // Temporal mixing layer: a periodic pair of tanh shear layers (y = 0 and y = +-1/2).
   void mixing_layer(double x, double y, double q[4]) const {
     double delta = p.ic[0], U0 = p.ic[1], Ma = p.ic[2], gam = p.ic[3], amp = p.ic[4];
     double u = U0 * ((std::tanh(2.0 * y / delta) - std::tanh(2.0 * (y - 0.5) / delta)) -
