@@ -39,12 +39,25 @@ WORKLOADS = {
                   name="2D swirl t_a=5, blob (0.5,0.75) beta 0.01, 17^2 blocks, Jmax 8, eps 1e-4, "
                        "FP32 RHS + FP64 details, CFL 0.5"),
     # 2D constant advection, plain FP64
+    # 64 independent 2D advection instances (seeded), one context, graph replays
+    "forest": dict(dim=2, Bs=17, precision="fp32", detail_fp64=True, rhs="adv",
+                   trees=None, capacity=600_000,
+                   name="64 independent 2D advection trees (seeded: sigma 0.02-0.1, |u_i|<=1, "
+                        "Jmax 4-8, eps 1e-5..1e-3), 17^2 blocks, FP32 RHS + FP64 details"),
     "adv2d": dict(dim=2, Bs=17, precision="fp64", detail_fp64=False, rhs="adv",
                   tree=dict(Jmin=2, Jmax=5, eps=1e-3, ic="gauss",
                             ic_params=(0.5, 0.5, 0.0, 0.05), rhs_params=(1.0, 0.5, 0.0)),
                   umax=math.hypot(1.0, 0.5), capacity=20_000,
                   name="2D advection u=(1,0.5), sigma 0.05, 17^2 blocks, Jmin 2, Jmax 5, eps 1e-3, FP64"),
 }
+
+
+def _forest_trees():
+    from paper_1902_00088_gb300 import inputs
+    return inputs.forest_trees(64)
+
+
+WORKLOADS["forest"]["trees"] = _forest_trees()
 
 
 def dt_of(w):
@@ -123,7 +136,8 @@ def oracle_sample(w, seconds_target=15.0):
     workload: same physics, Jmax reduced so a step takes seconds; returns
     (points x stages / s, description)."""
     import oracle
-    t = dict(w["tree"])
+    t = dict(w["tree"] if "tree" in w else w["trees"][0])
+    umax = w.get("umax") or math.hypot(*t["rhs_params"][:2]) or 1.0
     jmax = {3: 3, 2: 5}[w["dim"]]
     jmin = min(t["Jmin"], jmax - 1)
     cfg = dict(dim=w["dim"], Bs=w["Bs"], Jmin=jmin, Jmax=jmax, eps=t["eps"], rhs=w["rhs"],
@@ -131,7 +145,7 @@ def oracle_sample(w, seconds_target=15.0):
     o = oracle.Oracle(cfg)
     o.init_tree()
     dx = 1.0 / ((w["Bs"] - 1) * (1 << jmax))
-    dt = 0.5 * dx / w["umax"]
+    dt = 0.5 * dx / umax
     pts, steps, t0 = 0, 0, time.perf_counter()
     while True:
         pts += o.n * w["Bs"] ** w["dim"] * 4
@@ -170,6 +184,17 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def trees_of(w):
+    return w["trees"] if "trees" in w else [w["tree"]]
+
+
+def dts_of(w):
+    if "trees" in w:
+        from paper_1902_00088_gb300 import inputs
+        return [inputs.cfl_dt(t, w["Bs"]) for t in w["trees"]]
+    return [dt_of(w)]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +205,8 @@ def main():
     ap.add_argument("--eps", type=float, default=0.0)
     ap.add_argument("--no-full", action="store_true",
                     help="swirl: do not run on to t = t_a for the error (timed window only)")
+    ap.add_argument("--eager", action="store_true", help="host-driven steps instead of CUDA graph replays")
+    ap.add_argument("--autotune", type=int, default=-1, help="steps per autotuner candidate (0 = off)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
@@ -190,18 +217,19 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     w = dict(WORKLOADS[args.workload])
-    w["tree"] = dict(w["tree"])
-    if args.eps > 0:
-        w["tree"]["eps"] = args.eps
-        w["name"] = w["name"].replace("eps %g" % WORKLOADS[args.workload]["tree"]["eps"], "eps %g" % args.eps)
+    if "tree" in w:
+        w["tree"] = dict(w["tree"])
+        if args.eps > 0:
+            w["tree"]["eps"] = args.eps
+            w["name"] = w["name"].replace("eps %g" % WORKLOADS[args.workload]["tree"]["eps"], "eps %g" % args.eps)
     if args.capacity > 0:
         w["capacity"] = args.capacity
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
 
-    import torch
     import numpy as np
+    import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if world > 1:
@@ -212,20 +240,20 @@ def main():
     import paper_1902_00088_gb300 as mr
 
     stream = torch.cuda.Stream()
-    # Independent replicas per rank (the path has no exchange between trees);
-    # each rank advances its own instance: weak scaling.
+    trees = trees_of(w)
+    nt = len(trees)
+    # Independent replicas per rank (trees never exchange data): weak scaling.
     g = mr.Forest(dim=w["dim"], Bs=w["Bs"], precision=w["precision"], detail_fp64=w["detail_fp64"],
-                  rhs=w["rhs"], trees=[w["tree"]], capacity=w["capacity"],
-                  stream=stream.cuda_stream)
+                  rhs=w["rhs"], trees=trees, capacity=w["capacity"], stream=stream.cuda_stream)
     B, d = w["Bs"], w["dim"]
     npts = B ** d
-    dt = dt_of(w)
+    dts = np.array(dts_of(w))
+    graph = not args.eager
     g.init_tree()
-    t = 0.0
     full = "full_time" in w and not args.no_full
-    nfull = int(math.ceil(w["full_time"] / dt)) if "full_time" in w else 0
+    nfull = int(math.ceil(w["full_time"] / dts[0])) if "full_time" in w else 0
     if full:
-        dt = w["full_time"] / nfull  # land exactly on t = t_a
+        dts[:] = w["full_time"] / nfull  # land exactly on t = t_a
     if args.spinup >= 0:
         spin = args.spinup
     elif "full_time" in w:
@@ -233,58 +261,105 @@ def main():
         spin = max(0, nfull // 2 - args.warmup - args.steps // 2)
     else:
         spin = 0
-    for _ in range(spin + args.warmup):
-        g.step(t, dt)
-        t += dt
+    t = np.zeros(nt)
+    tuned = None
+    steps_done = 0
+    if graph:
+        g.set_time(t, dts)
+        autotune = args.autotune if args.autotune >= 0 else (3 if "trees" in w else 0)
+        if autotune > 0:
+            tuned = g.autotune(autotune)
+            steps_done += 7 * (autotune + 1) + 0
+        g.step_graph(spin + args.warmup)
+        steps_done += spin + args.warmup
+    else:
+        for _ in range(spin + args.warmup):
+            g.step(t, dts)
+            t = t + dts
+        steps_done += spin + args.warmup
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
 
     # ---- timed region: K full steps, device timing with CUDA events ----
     g.reset_stats()
-    g.enable_timing(True)
+    g.enable_timing(not graph)
+    g.step_history(reset=True)
     launches0 = g.launch_count()
-    nb = g.num_blocks()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nb0 = g.num_blocks()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     points = 0
     with Clocks(local) as clk:
         torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            points += nb * npts * 4
-            g.step(t, dt)
-            t += dt
-            nb = g.num_blocks()
-        ev1.record(stream)
+        evs[0].record(stream)
+        if graph:
+            for k in range(args.steps):
+                g.step_graph(1)
+                evs[k + 1].record(stream)
+        else:
+            nb = nb0
+            for k in range(args.steps):
+                points += nb * npts * 4
+                g.step(t, dts)
+                t = t + dts
+                evs[k + 1].record(stream)
+                nb = g.num_blocks()
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms = evs[0].elapsed_time(evs[-1])
+    per_step = sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps))
     launches = g.launch_count() - launches0
-    st = g.stats()
+    if graph:
+        hist = g.step_history(reset=True)
+        points = int(hist.astype(np.int64).sum()) * npts * 4
+    steps_done += args.steps
+    nb = g.num_blocks()
     g.enable_timing(False)
+    st = g.stats()
     ms_t = torch.tensor([ms], device="cuda")
     if world > 1:
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
     ms_max = float(ms_t.item())
     value = points * world / (ms_max / 1e3)
 
-    # roofline of the dominant kernel (RK stage): algorithmic bytes / stage time
+    # Roofline of the dominant kernel (RK stage): algorithmic bytes / stage time.
+    # The stage time comes from CUDA events around the RK phase in a separate
+    # eager pass over the same grid (graph replays carry no per-phase events).
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
+    if graph:
+        g.reset_stats()
+        g.enable_timing(True)
+        tt = g.get_time()
+        for k in range(3):
+            g.step(tt, dts)
+            tt = tt + dts
+        g.enable_timing(False)
+        st = g.stats()
+        g.set_time(tt, dts)
+        steps_done += 3
     stage_ms = st["ms"]["stage"]
     stage_bytes = st["stage_blocks"] * bytes_per_stage_block(w)
     achieved = stage_bytes / (stage_ms / 1e3) / 1e9 if stage_ms > 0 else 0.0
     per_launch_us = stage_ms * 1e3 / max(1, st["stage_launches"])
-    err = g.error(0, t) if w["rhs"] == "adv" else None
-    nsteps_done = spin + args.warmup + args.steps
+
+    err = None
+    tnow = g.get_time() if graph else t
+    if w["rhs"] == "adv" and nt == 1:
+        err = g.error(0, float(tnow[0]))
     if full:
         # continue untimed to t = t_a, where the swirl returns to the initial state
-        for s_ in range(nsteps_done, nfull):
-            g.step(s_ * dt, dt)
-        t = nfull * dt
+        remaining = nfull - steps_done
+        if remaining > 0:
+            if graph:
+                g.step_graph(remaining)
+            else:
+                for s_ in range(remaining):
+                    g.step(tnow, dts)
+                    tnow = tnow + dts
         err = g.error(0, 0.0)
 
     # ---- end-to-end through the C ABI with pinned host buffers ----
@@ -294,18 +369,23 @@ def main():
         k2 = max(1, min(args.steps, 5))
         ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         pts2, bi, bo = 0, 0, 0
+        tt = g.get_time() if graph else tnow
         torch.cuda.synchronize()
         ev2.record(stream)
         for _ in range(k2):
             n = len(info)
             lvl = torch.from_numpy(np.ascontiguousarray(info["level"])).pin_memory().numpy()
+            trs = torch.from_numpy(np.ascontiguousarray(info["tree"])).pin_memory().numpy()
             crd = torch.from_numpy(np.ascontiguousarray(info["coords"])).pin_memory().numpy()
             fld = torch.from_numpy(f).pin_memory().numpy()
-            g.set_blocks(lvl, crd, fld)
-            bi += lvl.nbytes + crd.nbytes + fld.nbytes
+            g.set_blocks(lvl, crd, fld, tree=trs)
+            bi += lvl.nbytes + trs.nbytes + crd.nbytes + fld.nbytes
             pts2 += n * npts * 4
-            g.step(t, dt)
-            t += dt
+            if graph:
+                g.step_graph(1)
+            else:
+                g.step(tt, dts)
+                tt = tt + dts
             info, f = g.get_blocks()
             bo += info.nbytes + f.nbytes
         ev3.record(stream)
@@ -322,6 +402,7 @@ def main():
                "sample": desc + ", %.1f s" % el}
 
     if rank == 0:
+        pct = lambda q: per_step[min(len(per_step) - 1, int(round(q * (len(per_step) - 1))))]
         line = {
             "metric": "adaptive grid-points x RK-stages/sec",
             "value": value, "unit": "points*stages/s", "n_gpus": world,
@@ -330,20 +411,22 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32 (f64 details)", "fp64": "f64", "fp32_acc64": "f32/f64"}[w["precision"]],
             "data": "synthetic",
-            "config": {"workload": w["name"], "blocks_at_end": nb, "Bs": B, "dim": d,
-                       "dt": dt, "parallelism": "replicas" if world > 1 else "single",
-                       "l2_flush": "no flush; working set per step (stage fields over the "
-                                   "refined grid) exceeds the 129 MB L2" if args.workload == "adv3d"
-                                   else "no flush; small working set (L2-resident)",
+            "config": {"workload": w["name"], "trees": nt, "blocks_at_start": nb0, "blocks_at_end": nb,
+                       "Bs": B, "dim": d, "dt": float(dts[0]) if nt == 1 else "per tree",
+                       "mode": "eager" if not graph else "cuda-graph step replay",
+                       "autotuned_ctas_per_sm": tuned,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2_flush": "none: inputs resident; working set noted in blocks_at_*",
+                       "step_ms_p50": pct(0.5), "step_ms_p99": pct(0.99),
                        "l2_rel_error": None if err is None else err["l2"],
                        "linf_rel_error": None if err is None else err["linf"],
-                       "error_at_t": t if err is not None else None,
-                       "timed_window_t": [(spin + args.warmup) * dt, (spin + args.warmup + args.steps) * dt],
-                       "phase_ms": st["ms"]},
+                       "error_at_t": None if err is None else (w.get("full_time") if full else float(tnow[0])),
+                       "phase_ms_eager_probe": st["ms"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "k_stage_adv (RK stage incl. fused ghost gather)",
-                         "stage_launch_us": per_launch_us, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                         "stage_launch_us": per_launch_us,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "gpu_launches": launches,
             "e2e": e2e,
             "cpu_baseline": cpu,

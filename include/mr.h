@@ -207,6 +207,26 @@ typedef struct {
   int64_t steps;
 } mr_stats;
 mr_status mr_enable_timing(mr_ctx ctx, int32_t on);
+
+/* Graph-captured stepping (batched serving).  The time and step of every tree
+ * live on the device (mr_set_time); mr_step_graph enqueues nsteps full steps
+ * (refine all, RK4, coarsening rounds, time advance) as replays of one CUDA
+ * graph captured at the first call, with no host synchronisation: every launch
+ * loops over device-side block counts, and the coarsening rounds (max_rounds, or
+ * Jmax - Jmin) become empty once a round merged nothing.  The swirl time factor
+ * is evaluated with the device cos in this mode.  Errors are reported by the next
+ * synchronising call.  The graph is captured on a private stream and replayed on
+ * the context's stream. */
+mr_status mr_set_time(mr_ctx ctx, const double* t, const double* dt);  /* ntrees each; synchronises */
+mr_status mr_get_time(mr_ctx ctx, double* t);                          /* synchronises */
+mr_status mr_step_graph(mr_ctx ctx, int64_t nsteps);
+/* Blocks of the adapted grid at the start of every graph step since the last
+ * reset (up to 65536 entries); *n = entries recorded.  Synchronises. */
+mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n, int32_t reset);
+/* Times graph steps with 1, 2, 3, 4, 6, 8 and occupancy-limited CTAs per SM for
+ * the block kernels (steps steps each; the solution advances during tuning) and
+ * keeps the fastest; *best = CTAs per SM (0 = occupancy).  Synchronises. */
+mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best);
 /* Synchronises; accumulates pending timers into *out. */
 mr_status mr_get_stats(mr_ctx ctx, mr_stats* out);
 mr_status mr_reset_stats(mr_ctx ctx);

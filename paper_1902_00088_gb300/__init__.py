@@ -80,6 +80,11 @@ SIGNATURES = {
     "mr_error": (_i32, [_vp, _i32, C.c_double, _dp]),
     "mr_launch_count": (_i64, [_vp]),
     "mr_enable_timing": (_i32, [_vp, _i32]),
+    "mr_set_time": (_i32, [_vp, _dp, _dp]),
+    "mr_get_time": (_i32, [_vp, _dp]),
+    "mr_step_graph": (_i32, [_vp, _i64]),
+    "mr_get_step_history": (_i32, [_vp, _i64, _vp, C.POINTER(C.c_int64), _i32]),
+    "mr_autotune": (_i32, [_vp, _i32, C.POINTER(C.c_int32)]),
     "mr_get_stats": (_i32, [_vp, C.POINTER(Stats)]),
     "mr_reset_stats": (_i32, [_vp]),
 }
@@ -247,6 +252,30 @@ class Forest:
 
     def launch_count(self):
         return int(self.lib.mr_launch_count(self.h))
+
+    def set_time(self, t, dt):
+        t, dt = self._td(t, dt)
+        self._ck(self.lib.mr_set_time(self.h, _ptr(t), _ptr(dt)))
+
+    def get_time(self):
+        t = np.zeros(self.ntrees, np.float64)
+        self._ck(self.lib.mr_get_time(self.h, _ptr(t)))
+        return t
+
+    def step_graph(self, nsteps=1):
+        self._ck(self.lib.mr_step_graph(self.h, nsteps))
+
+    def step_history(self, reset=True):
+        n = C.c_int64()
+        self._ck(self.lib.mr_get_step_history(self.h, 0, None, C.byref(n), 0))
+        out = np.zeros(max(1, n.value), np.int32)
+        self._ck(self.lib.mr_get_step_history(self.h, len(out), _ptr(out), C.byref(n), int(reset)))
+        return out[:min(n.value, len(out))]
+
+    def autotune(self, steps=5):
+        best = C.c_int32()
+        self._ck(self.lib.mr_autotune(self.h, steps, C.byref(best)))
+        return best.value
 
     def enable_timing(self, on=True):
         self._ck(self.lib.mr_enable_timing(self.h, int(bool(on))))

@@ -49,7 +49,20 @@ struct mr_ctx_s {
   std::vector<Pending> pending;
   mr_stats stats{};
   int64_t stage_launches = 0;
+  // graph-captured steps
+  TreeTime* ttime = nullptr;
+  int32_t* hist = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_kernels = 0;  // kernel nodes of the captured step
+  bool capturing = false;
 };
+
+namespace mr {
+__global__ void k_step_begin(Counters* c, int32_t* hist);
+__global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int swirl);
+__global__ void k_time_advance(TreeTime* tt, int ntrees);
+}
 
 namespace {
 
@@ -178,13 +191,13 @@ struct PhaseTimer {
   cudaEvent_t a = nullptr, b = nullptr;
   PhaseTimer(mr_ctx c_, int ph) : c(c_), phase(ph) {
     c->stats.phase_calls[ph] += 1;
-    if (!c->timing) return;
+    if (!c->timing || c->capturing) return;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaEventRecord(a, c->st);
   }
   ~PhaseTimer() {
-    if (!c->timing) return;
+    if (!c->timing || c->capturing) return;
     cudaEventRecord(b, c->st);
     c->pending.push_back({phase, a, b});
   }
@@ -221,10 +234,17 @@ void do_round(mr_ctx c, bool merge) {
          [&] { launch_coarsen_round<3>(pv, fields(c), fp64, merge, c->lc, c->st); });
 }
 
-mr_status coarsen_until_stable(mr_ctx ctx) {
+int max_rounds_of(mr_ctx ctx) {
   int jspan = 0;
   for (auto& t : ctx->td) jspan = std::max(jspan, t.Jmax - t.Jmin);
-  const int rounds = ctx->p.max_rounds > 0 ? ctx->p.max_rounds : jspan;
+  const int r = ctx->p.max_rounds > 0 ? ctx->p.max_rounds : jspan;
+  return r < 1 ? 1 : r;
+}
+
+mr_status coarsen_until_stable(mr_ctx ctx) {
+  const int rounds = max_rounds_of(ctx);
+  k_step_begin<<<1, 1, 0, ctx->st>>>(ctx->cnt, nullptr);
+  count_launch();
   for (int r = 0; r < rounds; ++r) {
     do_round(ctx, true);
     mr_status s = check_device(ctx);
@@ -443,6 +463,9 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if ((e = dalloc(ctx, &ctx->svar, (int64_t)P.ntrees * nv))) return e;
     if ((e = dalloc(ctx, &ctx->cnt, 1))) return e;
     if ((e = dalloc(ctx, &ctx->trees, P.ntrees))) return e;
+    if ((e = dalloc(ctx, &ctx->ttime, P.ntrees))) return e;
+    if ((e = dalloc(ctx, &ctx->hist, kMaxHist))) return e;
+    if ((e = cudaMemset(ctx->ttime, 0, P.ntrees * sizeof(TreeTime)))) return e;
     std::vector<int4> rel = relation_list(d);
     ctx->nrel = (int)rel.size();
     if ((e = dalloc(ctx, &ctx->rel, rel.size()))) return e;
@@ -473,6 +496,8 @@ void mr_destroy(mr_ctx ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   else cudaDeviceSynchronize();
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (void* q : ctx->owned) cudaFree(q);
   delete ctx;
 }
@@ -551,6 +576,7 @@ mr_status mr_adapt(mr_ctx ctx, int32_t mode) {
   }
   if (mode == MR_ADAPT_COARSEN) return coarsen_until_stable(ctx);
   if (mode == 3) {  // details and flags only (no merge), for inspection
+    k_step_begin<<<1, 1, 0, ctx->st>>>(ctx->cnt, nullptr);
     do_round(ctx, false);
     return check_device(ctx);
   }
@@ -719,6 +745,138 @@ mr_status mr_error(mr_ctx ctx, int32_t tree, double t, double* out) {
   cudaFree(dex);
   cudaFree(dout);
   return MR_OK;
+}
+
+mr_status mr_set_time(mr_ctx ctx, const double* t, const double* dt) {
+  if (!ctx || !t || !dt) return MR_EINVAL;
+  std::vector<TreeTime> h(ctx->p.ntrees);
+  for (int k = 0; k < ctx->p.ntrees; ++k) {
+    h[k] = TreeTime{};
+    h[k].t = t[k];
+    h[k].dt = dt[k];
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaMemcpy(ctx->ttime, h.data(), h.size() * sizeof(TreeTime), cudaMemcpyHostToDevice));
+  return MR_OK;
+}
+
+mr_status mr_get_time(mr_ctx ctx, double* t) {
+  if (!ctx || !t) return MR_EINVAL;
+  std::vector<TreeTime> h(ctx->p.ntrees);
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaMemcpy(h.data(), ctx->ttime, h.size() * sizeof(TreeTime), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < ctx->p.ntrees; ++k) t[k] = h[k].t;
+  return MR_OK;
+}
+
+namespace {
+// One step with no host synchronisation, for capture: time coefficients from
+// the device, refine all, four stages, a fixed number of coarsening rounds that
+// become empty once a round merged nothing, time advance.
+void enqueue_graph_step(mr_ctx ctx, cudaStream_t st) {
+  PoolView pv = view(ctx);
+  pv.tt = ctx->ttime;
+  const Fields f = fields(ctx);
+  const int nt = ctx->p.ntrees;
+  k_step_begin<<<1, 1, 0, st>>>(ctx->cnt, ctx->hist);
+  k_time_coef<<<(nt + 127) / 128, 128, 0, st>>>(ctx->ttime, ctx->trees, nt, ctx->p.rhs_kind == MR_RHS_SWIRL);
+  count_launch(2);
+  by_dim(ctx, [&] { launch_refine<2>(pv, f, MR_ADAPT_REFINE_ALL, ctx->mask, ctx->lc, st); },
+         [&] { launch_refine<3>(pv, f, MR_ADAPT_REFINE_ALL, ctx->mask, ctx->lc, st); });
+  StageArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  for (int s = 0; s < 4; ++s)
+    by_dim(ctx, [&] { launch_stage<2>(pv, f, s, sa, ctx->lc, st); },
+           [&] { launch_stage<3>(pv, f, s, sa, ctx->lc, st); });
+  const bool fp64 = ctx->p.detail_fp64 != 0;
+  for (int r = 0; r < max_rounds_of(ctx); ++r)
+    by_dim(ctx, [&] { launch_coarsen_round<2>(pv, f, fp64, true, ctx->lc, st); },
+           [&] { launch_coarsen_round<3>(pv, f, fp64, true, ctx->lc, st); });
+  k_time_advance<<<(nt + 127) / 128, 128, 0, st>>>(ctx->ttime, nt);
+  count_launch();
+}
+
+mr_status build_graph(mr_ctx ctx) {
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  CK(cudaStreamSynchronize(ctx->st));
+  cudaGraph_t g = nullptr;
+  ctx->capturing = true;
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int64_t k0 = kernel_launches();
+  enqueue_graph_step(ctx, ctx->cap_stream);
+  ctx->graph_kernels = kernel_launches() - k0;
+  count_launch((int)-ctx->graph_kernels);  // capture enqueues nothing; replays are counted
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  ctx->capturing = false;
+  if (e != cudaSuccess) return fail(ctx, MR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, MR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return MR_OK;
+}
+}  // namespace
+
+mr_status mr_step_graph(mr_ctx ctx, int64_t nsteps) {
+  if (!ctx || nsteps < 0) return MR_EINVAL;
+  if (!ctx->gexec) {
+    mr_status s = build_graph(ctx);
+    if (s) return s;
+  }
+  for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+  count_launch((int)(ctx->graph_kernels * nsteps));
+  ctx->stats.steps += nsteps;
+  ctx->stats.stage_launches += 4 * nsteps;
+  return MR_OK;
+}
+
+mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n, int32_t reset) {
+  if (!ctx || !n) return MR_EINVAL;
+  mr_status s = check_device(ctx);
+  if (s) return s;
+  const Counters h = read_counters(ctx);
+  *n = h.hist_n;
+  if (out && cap > 0) CK(cudaMemcpy(out, ctx->hist, std::min<int64_t>(cap, h.hist_n) * 4, cudaMemcpyDeviceToHost));
+  if (reset) {
+    int32_t z = 0;
+    CK(cudaMemcpy(&ctx->cnt->hist_n, &z, 4, cudaMemcpyHostToDevice));
+  }
+  return MR_OK;
+}
+
+mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
+  if (!ctx || steps < 1) return MR_EINVAL;
+  const int cand[] = {1, 2, 3, 4, 6, 8, 0};
+  float best = 1e30f;
+  int bestm = 0;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  for (int m : cand) {
+    ctx->lc.grid_mult = m;
+    mr_status s = build_graph(ctx);
+    if (s) return s;
+    CK(cudaGraphLaunch(ctx->gexec, ctx->st));  // warm
+    CK(cudaEventRecord(a, ctx->st));
+    for (int i = 0; i < steps; ++i) CK(cudaGraphLaunch(ctx->gexec, ctx->st));
+    count_launch((int)(ctx->graph_kernels * (steps + 1)));
+    CK(cudaEventRecord(b, ctx->st));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    ctx->stats.steps += steps + 1;
+    if (ms < best) { best = ms; bestm = m; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ctx->lc.grid_mult = bestm;
+  mr_status s = build_graph(ctx);
+  if (s) return s;
+  if (best_out) *best_out = bestm;
+  return check_device(ctx);
 }
 
 mr_status mr_enable_timing(mr_ctx ctx, int32_t on) {

@@ -43,9 +43,19 @@ struct Counters {
   int32_t n_alloc;  // slots requested by a refine
   int32_t merged;   // families merged in the last coarsening round
   int32_t err;      // kErr* bits
-  int32_t n_cells_bad;
-  int32_t pad;
+  int32_t n_round;  // blocks a coarsening round works on (0 once no family merged)
+  int32_t done;     // a coarsening round merged nothing: later rounds of the step skip
   unsigned long long stage_blocks;  // blocks processed by RK stage launches
+  int32_t hist_n;   // entries written to the step history
+  int32_t pad2;
+};
+constexpr int kMaxHist = 1 << 16;  // step history: blocks of the adapted grid before each step
+
+// Device-resident time of every tree (graph-captured steps advance it on the
+// device): t, dt, and the RK stage coefficients of the current step.
+struct TreeTime {
+  double t, dt;
+  double ca[4], cy[4], ct[4];
 };
 
 // Lattice tables: per tree, kNumLat tables of N doubles, indexed by the node
@@ -91,6 +101,7 @@ struct PoolView {
   int32_t* partial;        // scan partials
   int32_t* pos_of_slot;
   Counters* cnt;
+  const TreeTime* tt;      // stage coefficients from device memory (graph mode), or null
 };
 
 // ---------------------------------------------------------------- launchers --

@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(256) k_stage_adv(PoolView pv, const TSRC* __re
     fill_tile<D, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
     __syncthreads();
     const TC c = (TC)td.cD[b.lvl];
-    const double ca = sa.ca[b.tree], cy = sa.cy[b.tree], ct = sa.ct[b.tree];
+    const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
+    const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
+    const double ct = pv.tt ? pv.tt[b.tree].ct[stage] : sa.ct[b.tree];
     const int64_t base = (int64_t)b.slot * pv.vs;  // nvar == 1
     const int sh = td.Jmax - b.lvl;
     for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(256) k_details(PoolView pv, TS* __restrict__ y
   TS* cbox = tile + pv.nvar * Gm::TILE;
   TD* X = reinterpret_cast<TD*>(cbox + pv.nvar * Gm::CBOX + 2);  // 16-byte aligned below
   X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(X) + 15) & ~(uintptr_t)15);
-  const int nact = pv.cnt->n_act;
+  const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y
   using Gm = Geo<D, B>;
   TS* buf = smem_as<TS>(0);
   __shared__ int cs[8];
-  const int nact = pv.cnt->n_act;
+  const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const int slot = pv.act[p];
@@ -480,7 +482,7 @@ __device__ __forceinline__ bool same_family(const PoolView& pv, int s, int t) {
 // level finer touches it (gradedness after the merge); else 0.
 template <int D>
 __global__ void k_flag_a(PoolView pv) {
-  const int nact = pv.cnt->n_act;
+  const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
@@ -524,7 +526,7 @@ __global__ void k_flag_a(PoolView pv) {
 // -1 (the fixpoint of the paper's -2 assignment).  Emits the new-list counts.
 template <int D>
 __global__ void k_flag_b(PoolView pv) {
-  const int nact = pv.cnt->n_act;
+  const int nact = pv.cnt->n_round;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
     const TreeDev& td = pv.trees[b.tree];
@@ -544,7 +546,7 @@ __global__ void k_flag_b(PoolView pv) {
 
 template <int D>
 __global__ void k_coarsen_finalize(PoolView pv) {
-  const int nact = pv.cnt->n_act;
+  const int nact = pv.cnt->n_round;
   const int n_free = pv.cnt->n_free;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];

@@ -102,7 +102,7 @@ struct RefineRun {
     const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
     auto k = k_refine<D, B, TS>;
     prep_smem(k, smem);
-    const int grid = persistent_grid(k, threads, smem, lc, 0);
+    const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
     k<<<grid, threads, smem, st>>>(pv, (TS*)f.y);
     count_launch();
   }
@@ -111,7 +111,7 @@ struct RefineRun {
 __global__ void k_refine_counters(Counters* c, int nch);
 __global__ void k_coarsen_counters(Counters* c, int nch);
 __global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check_capacity);
-__global__ void k_set_svar(double* svar, int n, double v);
+__global__ void k_round_begin(Counters* c, double* svar, int n, double v);
 
 template <int D>
 void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* mask,
@@ -152,11 +152,11 @@ struct DetailsRun {
     if (d64) {
       auto k = k_details<D, B, TS, double>;
       prep_smem(k, smem);
-      k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
+      k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
     } else {
       auto k = k_details<D, B, TS, TS>;
       prep_smem(k, smem);
-      k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
+      k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
     }
     count_launch();
   }
@@ -177,17 +177,17 @@ template <int D>
 void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool merge,
                           const LaunchCfg& lc, cudaStream_t st) {
   const int nch = 1 << D;
-  k_set_svar<<<1, 256, 0, st>>>(pv.svar, pv.ntrees * pv.nvar, pv.norm_kind == 1 ? 0.0 : 1.0);
+  k_round_begin<<<1, 256, 0, st>>>(pv.cnt, pv.svar, pv.ntrees * pv.nvar, pv.norm_kind == 1 ? 0.0 : 1.0);
   count_launch();
   dispatch_bs<D, DetailsRun>(pv, f, fp64, lc, st);
   k_flag_a<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
   k_flag_b<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
   count_launch(2);
   if (!merge) return;
-  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st);
+  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st);
   dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
   k_coarsen_finalize<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
-  k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 0);
+  k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 2);
   k_coarsen_counters<<<1, 1, 0, st>>>(pv.cnt, nch);
   count_launch(3);
 }

@@ -115,22 +115,55 @@ __global__ void k_refine_counters(Counters* c, int nch) {
 }
 
 __global__ void k_coarsen_counters(Counters* c, int nch) {
+  if (c->done) return;
   c->merged = (c->n_act - c->n_new) / (nch - 1);
   c->n_free = c->n_free + c->n_alloc;
   c->n_act = c->n_new;
+  if (c->merged == 0) c->done = 1;
+}
+
+// Start of a coarsening round: the round works on all blocks unless an earlier
+// round of this step merged nothing (then every kernel of the round is empty).
+__global__ void k_round_begin(Counters* c, double* svar, int n, double v) {
+  if (threadIdx.x == 0) c->n_round = c->done ? 0 : c->n_act;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) svar[i] = v;
+}
+
+// Start of a step: coarsening rounds enabled again; hist (nullable) records the
+// number of blocks of the adapted grid the step starts from.
+__global__ void k_step_begin(Counters* c, int32_t* hist) {
+  c->done = 0;
+  if (hist && c->hist_n < kMaxHist) hist[c->hist_n++] = c->n_act;
+}
+
+// Stage coefficients of every tree from its device-resident (t, dt); the swirl
+// factor uses the device cos (graph-captured steps).
+__global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int swirl) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ntrees) return;
+  TreeTime& T = tt[k];
+  const double h = T.dt;
+  const double ts[4] = {T.t, T.t + 0.5 * h, T.t + 0.5 * h, T.t + h};
+  T.ca[0] = h / 6.0; T.ca[1] = h / 3.0; T.ca[2] = h / 3.0; T.ca[3] = h / 6.0;
+  T.cy[0] = h / 2.0; T.cy[1] = h / 2.0; T.cy[2] = h; T.cy[3] = 0.0;
+  for (int s = 0; s < 4; ++s) T.ct[s] = swirl ? cos(M_PI * ts[s] / trees[k].rhs[0]) : 0.0;
+}
+__global__ void k_time_advance(TreeTime* tt, int ntrees) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < ntrees) tt[k].t = tt[k].t + tt[k].dt;
 }
 
 // Copies the n_new entries of the list just built; after a refine that failed
 // for lack of free slots (check_capacity) the current list is kept.
-__global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check_capacity) {
-  if (check_capacity && c->n_alloc > c->n_free) return;
+// check: 1 after a refine (skip on capacity failure), 2 after a coarsening
+// round (skip when the round was empty).
+__global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check) {
+  if (check == 1 && c->n_alloc > c->n_free) return;
+  if (check == 2 && c->done) return;
   const int n = c->n_new;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
-__global__ void k_set_svar(double* svar, int n, double v) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) svar[i] = v;
-}
 
 __global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;

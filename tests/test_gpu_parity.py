@@ -269,3 +269,51 @@ def test_adaptive_swirl_stays_bounded(mr):
     info, f = g.get_blocks()
     assert np.isfinite(f).all() and np.abs(f).max() < 1.01, np.abs(f).max()
     assert len(info) > 500  # the grid did refine around the filament
+
+
+def test_graph_steps_equal_eager_steps(mr):
+    # Graph replays (device-side time, fixed coarsening rounds that skip once
+    # nothing merges) give the same grid and fields as host-driven steps.
+    tree = dict(Jmin=2, Jmax=5, eps=1e-4, ic="gauss", ic_params=(0.4, 0.6, 0.0, 0.05),
+                rhs_params=(1.0, 0.5, 0.0))
+    a = mr.Forest(dim=2, precision="fp64", trees=[tree], capacity=20000)
+    b = mr.Forest(dim=2, precision="fp64", trees=[tree], capacity=20000)
+    a.init_tree()
+    b.init_tree()
+    dt = 0.5 / (16 * 32) / math.hypot(1.0, 0.5)
+    t = 0.0
+    for s in range(6):
+        a.step(t, dt)
+        t += dt
+    b.set_time(0.0, dt)
+    b.step_graph(6)
+    ia, fa = a.get_blocks()
+    ib, fb = b.get_blocks()
+    assert np.array_equal(ia, ib) and np.array_equal(fa, fb)
+    assert abs(b.get_time()[0] - t) <= 1e-15
+    hist = b.step_history()
+    assert len(hist) == 6 and hist[0] > 0
+
+
+def test_forest_trees_are_independent_and_match_oracle(mr, oracle_mod):
+    from paper_1902_00088_gb300 import inputs
+    trees = inputs.forest_trees(3, seed=11)
+    for t in trees:
+        t["Jmax"] = min(t["Jmax"], 5)
+    f = mr.Forest(dim=2, precision="fp64", trees=trees, capacity=60000)
+    f.init_tree()
+    dts = [inputs.cfl_dt(t) for t in trees]
+    for s in range(2):
+        f.step([s * d for d in dts], dts)
+    for k, t in enumerate(trees):
+        o = oracle_mod.Oracle(dict(dim=2, Jmin=t["Jmin"], Jmax=t["Jmax"], eps=t["eps"], rhs="adv",
+                                   rhs_params=t["rhs_params"], ic="gauss", ic_params=t["ic_params"]))
+        o.init_tree()
+        for s in range(2):
+            o.step(s * dts[k], dts[k])
+        ob = o.blocks()
+        info, fl = f.get_blocks(tree=k)
+        assert np.array_equal(info["level"], ob["level"])
+        assert np.array_equal(info["coords"].astype(np.int64), ob["coords"])
+        assert (info["tree"] == k).all()
+        assert np.array_equal(fl, ob["fields"])

@@ -1,0 +1,19 @@
+"""Seeded input generators: splitmix64 / xoshiro256** from their published
+definitions (first splitmix64 outputs for seed 0 are the published values)."""
+from paper_1902_00088_gb300 import inputs
+
+
+def test_splitmix64_seed_zero_published_sequence():
+    g = inputs.Xoshiro256ss(0)
+    assert g.s[:3] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_forest_parameters_in_ranges():
+    trees = inputs.forest_trees(64)
+    assert len(trees) == 64
+    for t in trees:
+        assert 4 <= t["Jmax"] <= 8 and t["Jmin"] == 2
+        assert 1e-5 <= t["eps"] <= 1e-3
+        assert 0.02 <= t["ic_params"][3] <= 0.1
+        assert all(-1 <= u <= 1 for u in t["rhs_params"][:2])
+    assert inputs.forest_trees(4, seed=5) == inputs.forest_trees(4, seed=5)
