@@ -365,9 +365,10 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
   if (P.ntrees < 1 || P.ntrees > kMaxTrees) return bad("ntrees out of range");
   if (P.precision < 0 || P.precision > 2) return bad("unknown precision");
   if (P.rhs_kind == MR_RHS_SWIRL && P.dim != 2) return bad("swirl is 2D");
-  if (P.rhs_kind == MR_RHS_NS) return bad("Navier-Stokes right-hand side not available in this build");
-  if (P.rhs_kind != MR_RHS_ADV && P.rhs_kind != MR_RHS_SWIRL) return bad("unknown rhs_kind");
-  if (P.nvar != 1) return bad("advection has nvar 1");
+  if (P.rhs_kind == MR_RHS_NS && (P.dim != 2 || P.nvar != 4)) return bad("Navier-Stokes is 2D with nvar 4");
+  if (P.rhs_kind != MR_RHS_ADV && P.rhs_kind != MR_RHS_SWIRL && P.rhs_kind != MR_RHS_NS)
+    return bad("unknown rhs_kind");
+  if (P.rhs_kind != MR_RHS_NS && P.nvar != 1) return bad("advection has nvar 1");
   if (P.capacity < 1 || P.capacity > (1LL << 30)) return bad("capacity out of range");
   if (!(P.L > 0)) return bad("L must be positive");
   const int maxJ = P.dim == 2 ? 10 : 7;
@@ -377,6 +378,9 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if (t.ic_kind < 0 || t.ic_kind > 2) return bad("unknown ic_kind");
     if (t.ic_kind == MR_IC_GAUSS && !(t.ic[3] > 0)) return bad("Gaussian sigma must be positive");
     if (P.rhs_kind == MR_RHS_SWIRL && !(t.rhs[0] > 0)) return bad("swirl period must be positive");
+    if (P.rhs_kind == MR_RHS_NS && !(t.rhs[0] > 1.0 && t.rhs[1] >= 0.0 && t.rhs[2] > 0.0))
+      return bad("Navier-Stokes needs gamma > 1, mu >= 0, Pr > 0");
+    if (P.rhs_kind == MR_RHS_NS && t.ic_kind == MR_IC_GAUSS) return bad("Navier-Stokes needs the mixing-layer IC or set_blocks");
     ctx->td.push_back(t);
   }
   mr_status st = MR_OK;

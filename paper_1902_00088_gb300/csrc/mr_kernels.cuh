@@ -82,6 +82,138 @@ __global__ void __launch_bounds__(256) k_stage_adv(PoolView pv, const TSRC* __re
   }
 }
 
+// ------------------------------------------------------------- NS stage ----
+// One RK4 stage of the 2D compressible Navier-Stokes equations (Sec. 4), ideal
+// gas with constant c_p, in conservative flux form, q = (rho, rho u, rho v, E):
+//   N(q) = -(dF/dx + dG/dy),
+//   F = (rho u, rho u u + p - txx, rho u v - txy, (E + p) u - (u txx + v txy) - kap dth/dx),
+//   G = (rho v, rho v u - txy, rho v v + p - tyy, (E + p) v - (u txy + v tyy) - kap dth/dy),
+//   txx = mu (2 ux - 2/3 div), tyy = mu (2 vy - 2/3 div), txy = mu (uy + vx),
+//   p = (gamma - 1)(E - (rho u u + rho v v)/2), th = p / rho,
+//   kap = mu gamma / ((gamma - 1) Pr)  (R_s cancels in the heat flux),
+// every derivative the 4th-order central D1.  Primitives on the whole tile,
+// gradients and fluxes on nodes -2..B+1, flux divergence on the interior; the
+// RK4 update is the same 3-register form as for advection, on 4 variables.
+template <int B>
+struct NsGeo {
+  static constexpr int NF = (B + 4) * B;  // F on i in [-2, B+1], j in [0, B-1]
+  static constexpr int NG = B * (B + 4);  // G on i in [0, B-1], j in [-2, B+1]
+};
+
+template <int B, typename TS, typename TY, typename TSRC>
+__global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __restrict__ src,
+                                                  TS* __restrict__ y, TS* __restrict__ acc,
+                                                  TY* __restrict__ ynext, int stage, StageArgs sa) {
+  using Gm = Geo<2, B>;
+  using NG = NsGeo<B>;
+  using TC = TY;
+  constexpr int T = Gm::T, G = Gm::G;
+  Ring& R = *smem_as<Ring>(0);
+  TC* tile = smem_as<TC>(kRingBytes);     // 4 x TILE conserved variables
+  TC* cbox = tile + 4 * Gm::TILE;         // 4 x CBOX
+  TC* pu = cbox + 4 * Gm::CBOX;           // primitives u, v, p, th: 4 x TILE
+  TC* pvv = pu + Gm::TILE;
+  TC* pp = pvv + Gm::TILE;
+  TC* pth = pp + Gm::TILE;
+  TC* F = pth + Gm::TILE;                 // 4 x NF
+  TC* Gf = F + 4 * NG::NF;                // 4 x NG
+  const int nact = pv.cnt->n_act;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
+  auto I = [&](int i, int j) { return (j + G) * T + (i + G); };
+  auto fI = [&](int i, int j) { return j * (B + 4) + (i + 2); };
+  auto gI = [&](int i, int j) { return (j + 2) * B + i; };
+  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+    const BlockInfo b = load_block(pv, pv.act[p]);
+    const TreeDev& td = pv.trees[b.tree];
+    build_ring<2, B>(pv, td, b, R);
+    __syncthreads();
+    fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
+    __syncthreads();
+    const double gam = td.rhs[0], mud = td.rhs[1], Pr = td.rhs[2];
+    const TC gm1 = (TC)(gam - 1.0);
+    const TC mu = (TC)mud;
+    const TC kap = (TC)(mud * gam / ((gam - 1.0) * Pr));
+    const TC c23 = (TC)(2.0 / 3.0);
+    const TC c = (TC)td.cD[b.lvl];
+    const TC* r_ = tile;
+    const TC* m1_ = tile + Gm::TILE;
+    const TC* m2_ = tile + 2 * Gm::TILE;
+    const TC* E_ = tile + 3 * Gm::TILE;
+    for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x) {
+      const TC r = r_[idx], m1 = m1_[idx], m2 = m2_[idx], E = E_[idx];
+      const TC uu = m1 / r, vv = m2 / r;
+      const TC prs = gm1 * (E - TC(0.5) * (m1 * uu + m2 * vv));
+      pu[idx] = uu;
+      pvv[idx] = vv;
+      pp[idx] = prs;
+      pth[idx] = prs / r;
+    }
+    __syncthreads();
+    auto dx = [&](const TC* f, int i, int j) {
+      return ((f[I(i - 2, j)] - f[I(i + 2, j)]) + TC(8) * (f[I(i + 1, j)] - f[I(i - 1, j)])) * c;
+    };
+    auto dy = [&](const TC* f, int i, int j) {
+      return ((f[I(i, j - 2)] - f[I(i, j + 2)]) + TC(8) * (f[I(i, j + 1)] - f[I(i, j - 1)])) * c;
+    };
+    constexpr int W = B + 4;
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+      const int i = idx % W - 2, j = idx / W - 2;
+      const bool needF = j >= 0 && j < B, needG = i >= 0 && i < B;
+      if (!needF && !needG) continue;
+      const TC ux = dx(pu, i, j), vx = dx(pvv, i, j), uy = dy(pu, i, j), vy = dy(pvv, i, j);
+      const TC div = ux + vy;
+      const TC txy = mu * (uy + vx);
+      const int t0 = I(i, j);
+      const TC m1 = m1_[t0], m2 = m2_[t0], E = E_[t0];
+      const TC uu = pu[t0], vv = pvv[t0], prs = pp[t0];
+      if (needF) {
+        const TC txx = mu * (TC(2) * ux - c23 * div);
+        const TC thx = dx(pth, i, j);
+        const int f0 = fI(i, j);
+        F[f0] = m1;
+        F[NG::NF + f0] = m1 * uu + prs - txx;
+        F[2 * NG::NF + f0] = m1 * vv - txy;
+        F[3 * NG::NF + f0] = (E + prs) * uu - (uu * txx + vv * txy) - kap * thx;
+      }
+      if (needG) {
+        const TC tyy = mu * (TC(2) * vy - c23 * div);
+        const TC thy = dy(pth, i, j);
+        const int g0 = gI(i, j);
+        Gf[g0] = m2;
+        Gf[NG::NG + g0] = m2 * uu - txy;
+        Gf[2 * NG::NG + g0] = m2 * vv + prs - tyy;
+        Gf[3 * NG::NG + g0] = (E + prs) * vv - (uu * txy + vv * tyy) - kap * thy;
+      }
+    }
+    __syncthreads();
+    const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
+    const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
+    const int64_t base = (int64_t)b.slot * 4 * pv.vs;
+    for (int idx = threadIdx.x; idx < 4 * Gm::NI; idx += blockDim.x) {
+      const int v = idx / Gm::NI, q = idx % Gm::NI;
+      const int i = q % B, j = q / B;
+      const TC* Fv = F + v * NG::NF;
+      const TC* Gv = Gf + v * NG::NG;
+      const TC dFx = ((Fv[fI(i - 2, j)] - Fv[fI(i + 2, j)]) + TC(8) * (Fv[fI(i + 1, j)] - Fv[fI(i - 1, j)])) * c;
+      const TC dGy = ((Gv[gI(i, j - 2)] - Gv[gI(i, j + 2)]) + TC(8) * (Gv[gI(i, j + 1)] - Gv[gI(i, j - 1)])) * c;
+      const TS kk = (TS)(-(dFx + dGy));
+      const int64_t at = base + (int64_t)v * pv.vs + q;
+      if (stage == 0) {
+        const TS yv = y[at];
+        acc[at] = yv + (TS)ca * kk;
+        ynext[at] = (TY)(yv + (TS)cy * kk);
+      } else if (stage == 1 || stage == 2) {
+        const TS yv = y[at];
+        acc[at] = acc[at] + (TS)ca * kk;
+        ynext[at] = (TY)(yv + (TS)cy * kk);
+      } else {
+        y[at] = acc[at] + (TS)ca * kk;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ----------------------------------------------------------------- refine ----
 // Sec. 2.3: the synchronised mother tile is upsampled by the 4th-order
 // interpolating prediction and split into 2^d children (one treecode digit

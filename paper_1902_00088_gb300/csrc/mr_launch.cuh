@@ -60,10 +60,48 @@ static void stage_prec(const PoolView& pv, const Fields& f, int stage, const Sta
   }
 }
 
+template <int B, typename TS, typename TY>
+static void stage_ns_impl(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
+                          const LaunchCfg& lc, cudaStream_t st) {
+  using Gm = Geo<2, B>;
+  constexpr int threads = 256;
+  const size_t smem = kRingBytes + sizeof(TY) * (4 * Gm::TILE + 4 * Gm::CBOX + 4 * Gm::TILE +
+                                                 4 * NsGeo<B>::NF + 4 * NsGeo<B>::NG);
+  TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
+  if (stage == 0) {
+    auto k = k_stage_ns<B, TS, TY, TS>;
+    prep_smem(k, smem);
+    k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(
+        pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+  } else {
+    const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
+    auto k = k_stage_ns<B, TS, TY, TY>;
+    prep_smem(k, smem);
+    k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(
+        pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+  }
+  count_launch();
+}
+
+template <int B>
+static void stage_ns(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
+                     const LaunchCfg& lc, cudaStream_t st) {
+  switch (pv.prec) {
+    case MR_PREC_FP64: stage_ns_impl<B, double, double>(pv, f, stage, sa, lc, st); break;
+    case MR_PREC_FP32: stage_ns_impl<B, float, float>(pv, f, stage, sa, lc, st); break;
+    default: stage_ns_impl<B, double, float>(pv, f, stage, sa, lc, st); break;
+  }
+}
+
 template <int D>
 void launch_stage(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
                   const LaunchCfg& lc, cudaStream_t st) {
   if constexpr (D == 2) {
+    if (pv.rhs_kind == MR_RHS_NS) {
+      if (pv.Bs == 17) stage_ns<17>(pv, f, stage, sa, lc, st);
+      else stage_ns<33>(pv, f, stage, sa, lc, st);
+      return;
+    }
     if (pv.Bs == 17) {
       if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, 17, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
       else stage_prec<D, 17, MR_RHS_ADV>(pv, f, stage, sa, lc, st);

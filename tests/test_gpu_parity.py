@@ -317,3 +317,88 @@ def test_forest_trees_are_independent_and_match_oracle(mr, oracle_mod):
         assert np.array_equal(info["coords"].astype(np.int64), ob["coords"])
         assert (info["tree"] == k).all()
         assert np.array_equal(fl, ob["fields"])
+
+
+def ns_cfg(Bs=17, Jmin=2, Jmax=4, eps=1e-3, seed=20190201):
+    from paper_1902_00088_gb300 import inputs
+    a, phi = inputs.mixing_layer_perturbation(seed)
+    delta, U0, Ma, gam, amp = 0.1, 0.5, 0.3, 1.4, 1e-3
+    return dict(dim=2, Bs=Bs, nvar=4, Jmin=Jmin, Jmax=Jmax, eps=eps, rhs="ns",
+                rhs_params=(gam, U0 * delta / 1000.0, 0.71), ic="mixing",
+                ic_params=(delta, U0, Ma, gam, amp) + tuple(a) + tuple(phi),
+                x0=(0.0, -0.5, 0.0), norm_kind=1)
+
+
+def ns_dt(c):
+    U0, Ma = c["ic_params"][1], c["ic_params"][2]
+    return 0.5 / ((c["Bs"] - 1) * (1 << c["Jmax"])) / (U0 + U0 / Ma)
+
+
+@pytest.mark.parametrize("Bs", [17, 33])
+def test_ns_mixing_layer_bit_exact_fp64(mr, oracle_mod, Bs):
+    c = ns_cfg(Bs=Bs, Jmax=4, eps=1e-4)  # levels 3 and 4 in both cases
+    o, g = make_pair(mr, oracle_mod, c)
+    o.init_tree()
+    g.init_tree()
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+    dt = ns_dt(c)
+    for s in range(2):
+        o.step(s * dt, dt)
+        g.step(s * dt, dt)
+        ob, f = assert_same_tree(o, g)
+        assert np.array_equal(f, ob["fields"]), np.abs(f - ob["fields"]).max()
+    o.details()
+    o.flags(0)
+    g.adapt("flags_only")
+    gf, gm = g.get_flags()
+    ob = o.blocks(fields=False)
+    assert np.array_equal(gm, ob["mdet"]) and np.array_equal(gf, ob["flag"])
+
+
+def test_ns_fp32_acc64_within_tolerance(mr, oracle_mod):
+    # FP32 stencils, FP64 state/accumulator, 3 steps on a uniform grid.  FP32
+    # rounding acts on the O(1) pressure and momentum fluxes, so the error of
+    # each conserved variable is measured against the scale of its group
+    # (density, momentum vector, energy): relative L2 <= 1e-5.
+    c = ns_cfg(Bs=17, Jmin=3, Jmax=3)
+    o, g = make_pair(mr, oracle_mod, c, precision="fp32_acc64", detail_fp64=True)
+    o.init_tree()
+    g.init_tree()
+    dt = ns_dt(c)
+    for s in range(3):
+        o.rk4(s * dt, dt)
+        g.rk_step(s * dt, dt)
+    ob, f = assert_same_tree(o, g)
+    ref = ob["fields"]
+    scale = [np.linalg.norm(ref[:, 0]), np.linalg.norm(ref[:, 1:3]), np.linalg.norm(ref[:, 1:3]),
+             np.linalg.norm(ref[:, 3])]
+    for v in range(4):
+        rel = np.linalg.norm(f[:, v] - ref[:, v]) / scale[v]
+        assert rel < 1e-5, (v, rel)
+
+
+def test_ns_uniform_grid_conserves_and_preserves_free_stream(mr):
+    # Properties at a size beyond the oracle: sum of each conserved variable over
+    # unique nodes is constant on a uniform periodic grid; a uniform state stays
+    # exactly uniform.
+    c = ns_cfg(Bs=33, Jmin=5, Jmax=5)
+    tree = dict(Jmin=5, Jmax=5, eps=1e-3, ic="mixing", ic_params=c["ic_params"],
+                rhs_params=c["rhs_params"], x0=c["x0"])
+    g = mr.Forest(dim=2, Bs=33, nvar=4, precision="fp64", rhs="ns", trees=[tree], capacity=8000,
+                  norm_kind=1)
+    g.init_tree()
+    info, f0 = g.get_blocks()
+    s0 = f0[:, :, :32, :32].sum(axis=(0, 2, 3))
+    dt = ns_dt(c)
+    for s in range(3):
+        g.rk_step(s * dt, dt)
+    info, f1 = g.get_blocks()
+    s1 = f1[:, :, :32, :32].sum(axis=(0, 2, 3))
+    assert np.all(np.abs(s1 - s0) <= 1e-11 * np.abs(s0).max()), (s0, s1)
+    f = np.zeros_like(f0)
+    f[:, 0], f[:, 1], f[:, 2], f[:, 3] = 1.2, 0.36, -0.12, 2.5
+    g.set_blocks(info["level"], info["coords"], f)
+    g.rk_step(0.0, dt)
+    _, f2 = g.get_blocks()
+    assert np.array_equal(f2, f)
