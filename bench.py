@@ -53,7 +53,7 @@ WORKLOADS = {
 
 
 def _forest_trees():
-    from paper_1902_00088_gb300 import inputs
+    import synthetic as inputs
     return inputs.forest_trees(64)
 
 
@@ -190,7 +190,7 @@ def trees_of(w):
 
 def dts_of(w):
     if "trees" in w:
-        from paper_1902_00088_gb300 import inputs
+        import synthetic as inputs
         return [inputs.cfl_dt(t, w["Bs"]) for t in w["trees"]]
     return [dt_of(w)]
 

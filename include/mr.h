@@ -231,6 +231,54 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best);
 mr_status mr_get_stats(mr_ctx ctx, mr_stats* out);
 mr_status mr_reset_stats(mr_ctx ctx);
 
+/* ------------------------------------------------------------------------
+ * Learned refinement proposal (2D).  Refine-all (Sec. 2.1 step 1) refines every
+ * block for safety; most of that refinement is removed again by the coarsening
+ * of the same step.  A small per-block CNN (three 3x3 convolutions with 16
+ * channels, the last two with stride 2, ReLU, global max pool, linear, sigmoid;
+ * 4961 parameters, FP32 master weights, BF16-rounded weights with FP32
+ * accumulation at inference) reads the synchronised tile of a block (channel 0:
+ * variable 0 minus its centre value over its largest deviation; channel 1:
+ * log10(1e-3 + |d|/(s_v eps)) of the block's details) and predicts p = P(the
+ * refinement is kept).  In mode 1 a block below Jmax is refined when p >= tau
+ * OR its own largest detail is >= eps (exact fallback); the +1 flags are then
+ * closed under gradedness.  After the step a block left unrefined whose details
+ * are >= eps counts as a miss (the judge). */
+#define MR_REFINE_ALL 0
+#define MR_REFINE_LEARNED 1
+mr_status mr_set_refine_mode(mr_ctx ctx, int32_t mode);  /* MR_EINVAL without a network */
+
+/* Training data: while on, every mr_step records (features, label) of each
+ * block before the refinement; label 1 iff the refinement was needed: after the
+ * step the block's region is subdivided (the refinement was kept), or the block
+ * is a leaf again with details >= eps (the judge's miss event); 0 otherwise; no
+ * label for blocks at Jmax or with own details >= eps (the fallback refines
+ * those anyway).
+ * capacity: samples to reserve (device memory: capacity x 2 x (Bs+8)^2 floats). */
+mr_status mr_proposal_collect(mr_ctx ctx, int32_t on, int64_t capacity);
+mr_status mr_proposal_dataset(mr_ctx ctx, int64_t* n_labelled, int64_t* n_positive);
+
+/* Trains on the collected samples with the library's forward/backward kernels
+ * and Adam (lr, betas 0.9/0.999): weighted binary cross entropy (positives
+ * weighted w_pos; w_pos <= 0 weights them by n_negative / n_positive),
+ * mini-batches of `batch` in a fixed interleaved order.  init (nullable, 4961
+ * floats): starting parameters (else continue from the current ones).  A
+ * `holdout` fraction of each class (every k-th sample) is not trained on; tau
+ * is the largest threshold with recall >= `recall` on the held-out positives
+ * (with the BF16 inference weights).  Synchronises. */
+mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32_t batch, float lr,
+                            float w_pos, float recall, float holdout, float* tau, float* loss);
+mr_status mr_proposal_set(mr_ctx ctx, const float* params /* nullable */, float tau);
+mr_status mr_proposal_get(mr_ctx ctx, float* params, float* tau);
+/* Counters since the last reset: {blocks below Jmax considered, refined by the
+ * network, refined by the fallback only, misses, added by the gradedness closure}. */
+mr_status mr_proposal_stats(mr_ctx ctx, int64_t* out5, int32_t reset);
+/* Forward and backward of the network on host inputs x (n x 2 x (Bs+8)^2),
+ * labels y (n): probabilities, gradient of the mean weighted BCE (4961 floats)
+ * and the loss.  Synchronises. */
+mr_status mr_cnn_eval(mr_ctx ctx, const float* params, const float* x, const float* y, int64_t n,
+                      float w_pos, float* prob, float* grad, float* loss);
+
 #ifdef __cplusplus
 }
 #endif

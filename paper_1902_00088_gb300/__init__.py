@@ -85,6 +85,15 @@ SIGNATURES = {
     "mr_step_graph": (_i32, [_vp, _i64]),
     "mr_get_step_history": (_i32, [_vp, _i64, _vp, C.POINTER(C.c_int64), _i32]),
     "mr_autotune": (_i32, [_vp, _i32, C.POINTER(C.c_int32)]),
+    "mr_set_refine_mode": (_i32, [_vp, _i32]),
+    "mr_proposal_collect": (_i32, [_vp, _i32, _i64]),
+    "mr_proposal_dataset": (_i32, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mr_proposal_train": (_i32, [_vp, _vp, _i32, _i32, C.c_float, C.c_float, C.c_float, C.c_float,
+                                 C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "mr_proposal_set": (_i32, [_vp, _vp, C.c_float]),
+    "mr_proposal_get": (_i32, [_vp, _vp, C.POINTER(C.c_float)]),
+    "mr_proposal_stats": (_i32, [_vp, _vp, _i32]),
+    "mr_cnn_eval": (_i32, [_vp, _vp, _vp, _vp, _i64, C.c_float, _vp, _vp, C.POINTER(C.c_float)]),
     "mr_get_stats": (_i32, [_vp, C.POINTER(Stats)]),
     "mr_reset_stats": (_i32, [_vp]),
 }
@@ -276,6 +285,56 @@ class Forest:
         best = C.c_int32()
         self._ck(self.lib.mr_autotune(self.h, steps, C.byref(best)))
         return best.value
+
+    # ------------------------------------------------- learned proposal --
+    CNN_PARAMS = 4961
+
+    def set_refine_mode(self, mode):
+        self._ck(self.lib.mr_set_refine_mode(self.h, {"all": 0, "learned": 1}.get(mode, mode)))
+
+    def proposal_collect(self, on=True, capacity=0):
+        self._ck(self.lib.mr_proposal_collect(self.h, int(bool(on)), capacity))
+
+    def proposal_dataset(self):
+        n, p = C.c_int64(), C.c_int64()
+        self._ck(self.lib.mr_proposal_dataset(self.h, C.byref(n), C.byref(p)))
+        return n.value, p.value
+
+    def proposal_train(self, init=None, epochs=5, batch=256, lr=1e-3, w_pos=4.0, recall=0.999,
+                       holdout=0.2):
+        tau, loss = C.c_float(), C.c_float()
+        ini = None if init is None else np.ascontiguousarray(init, np.float32)
+        self._ck(self.lib.mr_proposal_train(self.h, _ptr(ini), epochs, batch, lr, w_pos, recall, holdout,
+                                            C.byref(tau), C.byref(loss)))
+        return tau.value, loss.value
+
+    def proposal_set(self, params=None, tau=0.5):
+        pr = None if params is None else np.ascontiguousarray(params, np.float32)
+        self._ck(self.lib.mr_proposal_set(self.h, _ptr(pr), tau))
+
+    def proposal_get(self):
+        w = np.zeros(self.CNN_PARAMS, np.float32)
+        tau = C.c_float()
+        self._ck(self.lib.mr_proposal_get(self.h, _ptr(w), C.byref(tau)))
+        return w, tau.value
+
+    def proposal_stats(self, reset=True):
+        out = np.zeros(5, np.int64)
+        self._ck(self.lib.mr_proposal_stats(self.h, _ptr(out), int(reset)))
+        return dict(considered=int(out[0]), network=int(out[1]), fallback=int(out[2]),
+                    misses=int(out[3]), closure=int(out[4]))
+
+    def cnn_eval(self, params, x, y, w_pos=4.0):
+        x = np.ascontiguousarray(x, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        params = np.ascontiguousarray(params, np.float32)
+        n = len(y)
+        prob = np.zeros(n, np.float32)
+        grad = np.zeros(self.CNN_PARAMS, np.float32)
+        loss = C.c_float()
+        self._ck(self.lib.mr_cnn_eval(self.h, _ptr(params), _ptr(x), _ptr(y), n, w_pos, _ptr(prob),
+                                      _ptr(grad), C.byref(loss)))
+        return prob, grad, loss.value
 
     def enable_timing(self, on=True):
         self._ck(self.lib.mr_enable_timing(self.h, int(bool(on))))

@@ -9,12 +9,15 @@
 // device kernels multiply together.  Evaluating those factors with the host's
 // IEEE libm keeps the GPU fields bit-identical to an FP64 CPU evaluation of the
 // same formulas.
+#include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include "mr_cnn.h"
 #include "mr_internal.h"
 
 using namespace mr;
@@ -56,6 +59,22 @@ struct mr_ctx_s {
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_kernels = 0;  // kernel nodes of the captured step
   bool capturing = false;
+  // learned refinement proposal
+  int refine_mode = 0;  // 0 refine all (Sec. 2.1), 1 learned proposal + fallback + closure
+  float* cnn_w = nullptr; float* cnn_m = nullptr; float* cnn_v = nullptr; float* cnn_g = nullptr;
+  __nv_bfloat16* cnn_wb = nullptr;
+  float cnn_tau = 0.5f;
+  int cnn_t = 0;
+  bool cnn_ready = false;
+  float *feat = nullptr, *prob = nullptr, *mpre = nullptr;
+  int64_t feat_cap = 0;
+  int8_t* skip = nullptr;
+  int32_t *skip_key = nullptr, *pcounts = nullptr, *changed = nullptr;
+  int64_t prop_stats[5] = {0, 0, 0, 0, 0};
+  bool collect = false;
+  float *ds_feat = nullptr, *ds_label = nullptr, *ds_mpre = nullptr;
+  int32_t* ds_key = nullptr;
+  int64_t ds_cap = 0, ds_n = 0;
 };
 
 namespace mr {
@@ -250,6 +269,119 @@ mr_status coarsen_until_stable(mr_ctx ctx) {
     mr_status s = check_device(ctx);
     if (s) return s;
     if (read_counters(ctx).merged == 0) break;
+  }
+  return MR_OK;
+}
+
+
+// ------------------------------------------------ learned proposal (host) ---
+int64_t feat_len(mr_ctx c) {
+  const int64_t T = cnn_tile(c->p.Bs);
+  return 2 * T * T;
+}
+
+mr_status ensure_cnn(mr_ctx ctx) {
+  if (ctx->cnn_w) return MR_OK;
+  if (ctx->p.dim != 2) return fail(ctx, MR_EINVAL, "the learned proposal is 2D");
+  CK(cudaMalloc(&ctx->cnn_w, kCnnParams * 4));
+  CK(cudaMalloc(&ctx->cnn_m, kCnnParams * 4));
+  CK(cudaMalloc(&ctx->cnn_v, kCnnParams * 4));
+  CK(cudaMalloc(&ctx->cnn_g, kCnnParams * 4));
+  CK(cudaMalloc(&ctx->cnn_wb, kCnnParams * 2));
+  CK(cudaMalloc(&ctx->skip, ctx->S));
+  CK(cudaMalloc(&ctx->skip_key, ctx->S * 4));
+  CK(cudaMalloc(&ctx->pcounts, 4 * 4));
+  CK(cudaMalloc(&ctx->changed, 4));
+  CK(cudaMemset(ctx->cnn_w, 0, kCnnParams * 4));
+  CK(cudaMemset(ctx->cnn_m, 0, kCnnParams * 4));
+  CK(cudaMemset(ctx->cnn_v, 0, kCnnParams * 4));
+  CK(cudaMemset(ctx->cnn_g, 0, kCnnParams * 4));
+  CK(cudaMemset(ctx->skip, 0, ctx->S));
+  for (void* q : {(void*)ctx->cnn_w, (void*)ctx->cnn_m, (void*)ctx->cnn_v, (void*)ctx->cnn_g,
+                  (void*)ctx->cnn_wb, (void*)ctx->skip, (void*)ctx->skip_key, (void*)ctx->pcounts,
+                  (void*)ctx->changed})
+    ctx->owned.push_back(q);
+  return MR_OK;
+}
+
+// per-step feature buffer for n blocks (grows; freed with the context)
+mr_status ensure_feat(mr_ctx ctx, int64_t n) {
+  if (n <= ctx->feat_cap) return MR_OK;
+  const int64_t cap = std::max<int64_t>(n, ctx->feat_cap * 2);
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->feat) { cudaFree(ctx->feat); cudaFree(ctx->prob); cudaFree(ctx->mpre); }
+  CK(cudaMalloc(&ctx->feat, cap * feat_len(ctx) * 4));
+  CK(cudaMalloc(&ctx->prob, cap * 4));
+  CK(cudaMalloc(&ctx->mpre, cap * 4));
+  ctx->feat_cap = cap;
+  return MR_OK;
+}
+
+// Refinement of a step: refine all, or the learned proposal (network or
+// fallback), closed under gradedness, with the unrefined blocks remembered for
+// the judge.  Also records training samples when collecting.
+mr_status refine_for_step(mr_ctx ctx, int64_t* collected) {
+  *collected = 0;
+  if (ctx->refine_mode == 0 && !ctx->collect) {
+    do_refine(ctx, MR_ADAPT_REFINE_ALL);
+    return MR_OK;
+  }
+  const Counters h = read_counters(ctx);
+  const int64_t n = h.n_act;
+  PoolView pv = view(ctx);
+  float* fbuf = nullptr;
+  if (ctx->collect && ctx->ds_n + n <= ctx->ds_cap) {
+    fbuf = ctx->ds_feat + ctx->ds_n * feat_len(ctx);
+    launch_sample_keys(pv, ctx->ds_key, ctx->ds_n, ctx->st);
+    *collected = n;
+  }
+  mr_status s = ensure_feat(ctx, n);
+  if (s) return s;
+  launch_features(pv, ctx->y, fbuf ? fbuf : ctx->feat, ctx->mpre, 0, ctx->lc.num_sms, ctx->st);
+  if (fbuf) CK(cudaMemcpyAsync(ctx->ds_mpre + ctx->ds_n, ctx->mpre, n * 4, cudaMemcpyDeviceToDevice, ctx->st));
+  if (ctx->refine_mode == 0) {
+    do_refine(ctx, MR_ADAPT_REFINE_ALL);
+    return MR_OK;
+  }
+  launch_infer(pv, ctx->p.Bs, fbuf ? fbuf : ctx->feat, ctx->cnn_wb, ctx->prob, -1, ctx->lc.num_sms, ctx->st);
+  CK(cudaMemsetAsync(ctx->pcounts, 0, 16, ctx->st));
+  launch_propose(pv, ctx->prob, ctx->mpre, ctx->cnn_tau, ctx->skip, ctx->pcounts, ctx->st);
+  int jspan = 0;
+  for (auto& t : ctx->td) jspan = std::max(jspan, t.Jmax - t.Jmin);
+  int added = 0;
+  for (int it = 0; it <= jspan + 1; ++it) {
+    CK(cudaMemsetAsync(ctx->changed, 0, 4, ctx->st));
+    launch_close(pv, ctx->skip, ctx->changed, ctx->st);
+    int ch = 0;
+    CK(cudaMemcpyAsync(&ch, ctx->changed, 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    added += ch;
+    if (ch == 0) break;
+  }
+  launch_skip_key(pv, ctx->skip, ctx->skip_key, ctx->st);
+  int32_t cnt[4];
+  CK(cudaMemcpyAsync(cnt, ctx->pcounts, 16, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int k = 0; k < 3; ++k) ctx->prop_stats[k] += cnt[k];
+  ctx->prop_stats[4] += added;
+  do_refine(ctx, 2);
+  return MR_OK;
+}
+
+mr_status after_step(mr_ctx ctx, int64_t collected) {
+  PoolView pv = view(ctx);
+  if (collected > 0) {
+    launch_label(pv, ctx->ds_key + 4 * ctx->ds_n, ctx->ds_mpre + ctx->ds_n, collected,
+                 ctx->ds_label + ctx->ds_n, ctx->st);
+    ctx->ds_n += collected;
+  }
+  if (ctx->refine_mode == 1) {
+    CK(cudaMemsetAsync(ctx->pcounts, 0, 16, ctx->st));
+    launch_judge(pv, ctx->skip, ctx->skip_key, ctx->pcounts, ctx->st);
+    int32_t cnt[4];
+    CK(cudaMemcpyAsync(cnt, ctx->pcounts, 16, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->prop_stats[3] += cnt[3];
   }
   return MR_OK;
 }
@@ -502,6 +634,8 @@ void mr_destroy(mr_ctx ctx) {
   else cudaDeviceSynchronize();
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->feat) { cudaFree(ctx->feat); cudaFree(ctx->prob); cudaFree(ctx->mpre); }
+  if (ctx->ds_feat) { cudaFree(ctx->ds_feat); cudaFree(ctx->ds_label); cudaFree(ctx->ds_mpre); cudaFree(ctx->ds_key); }
   for (void* q : ctx->owned) cudaFree(q);
   delete ctx;
 }
@@ -590,10 +724,14 @@ mr_status mr_adapt(mr_ctx ctx, int32_t mode) {
 mr_status mr_step(mr_ctx ctx, const double* t, const double* dt) {
   if (!ctx || !t || !dt) return MR_EINVAL;
   ctx->stats.steps += 1;
-  do_refine(ctx, MR_ADAPT_REFINE_ALL);
-  mr_status s = rk_step(ctx, t, dt);
+  int64_t collected = 0;
+  mr_status s = refine_for_step(ctx, &collected);
   if (s) return s;
-  return coarsen_until_stable(ctx);
+  s = rk_step(ctx, t, dt);
+  if (s) return s;
+  s = coarsen_until_stable(ctx);
+  if (s) return s;
+  return after_step(ctx, collected);
 }
 
 mr_status mr_num_blocks(mr_ctx ctx, int32_t tree, int64_t* n) {
@@ -881,6 +1019,210 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
   if (s) return s;
   if (best_out) *best_out = bestm;
   return check_device(ctx);
+}
+
+
+mr_status mr_set_refine_mode(mr_ctx ctx, int32_t mode) {
+  if (!ctx || (mode != 0 && mode != 1)) return MR_EINVAL;
+  if (mode == 1) {
+    mr_status s = ensure_cnn(ctx);
+    if (s) return s;
+    if (!ctx->cnn_ready) return fail(ctx, MR_EINVAL, "no trained or loaded proposal network");
+  }
+  ctx->refine_mode = mode;
+  return MR_OK;
+}
+
+mr_status mr_proposal_collect(mr_ctx ctx, int32_t on, int64_t capacity) {
+  if (!ctx) return MR_EINVAL;
+  mr_status s = ensure_cnn(ctx);
+  if (s) return s;
+  if (on && capacity > ctx->ds_cap) {
+    CK(cudaStreamSynchronize(ctx->st));
+    float *f = nullptr, *l = nullptr, *mp = nullptr;
+    int32_t* k = nullptr;
+    CK(cudaMalloc(&f, capacity * feat_len(ctx) * 4));
+    CK(cudaMalloc(&l, capacity * 4));
+    CK(cudaMalloc(&mp, capacity * 4));
+    CK(cudaMalloc(&k, capacity * 16));
+    if (ctx->ds_n > 0) {
+      CK(cudaMemcpy(f, ctx->ds_feat, ctx->ds_n * feat_len(ctx) * 4, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(l, ctx->ds_label, ctx->ds_n * 4, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(mp, ctx->ds_mpre, ctx->ds_n * 4, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(k, ctx->ds_key, ctx->ds_n * 16, cudaMemcpyDeviceToDevice));
+    }
+    if (ctx->ds_feat) { cudaFree(ctx->ds_feat); cudaFree(ctx->ds_label); cudaFree(ctx->ds_mpre); cudaFree(ctx->ds_key); }
+    ctx->ds_feat = f; ctx->ds_label = l; ctx->ds_mpre = mp; ctx->ds_key = k;
+    ctx->ds_cap = capacity;
+  }
+  ctx->collect = on != 0;
+  return MR_OK;
+}
+
+mr_status mr_proposal_dataset(mr_ctx ctx, int64_t* n, int64_t* npos) {
+  if (!ctx || !n) return MR_EINVAL;
+  CK(cudaStreamSynchronize(ctx->st));
+  std::vector<float> l(ctx->ds_n);
+  if (ctx->ds_n) CK(cudaMemcpy(l.data(), ctx->ds_label, ctx->ds_n * 4, cudaMemcpyDeviceToHost));
+  int64_t nv = 0, np = 0;
+  for (float v : l) { if (v >= 0.f) ++nv; if (v > 0.5f) ++np; }
+  *n = nv;
+  if (npos) *npos = np;
+  return MR_OK;
+}
+
+mr_status mr_proposal_set(mr_ctx ctx, const float* params, float tau) {
+  if (!ctx) return MR_EINVAL;
+  mr_status s = ensure_cnn(ctx);
+  if (s) return s;
+  if (params) {
+    CK(cudaMemcpy(ctx->cnn_w, params, kCnnParams * 4, cudaMemcpyHostToDevice));
+    launch_to_bf16(ctx->cnn_w, ctx->cnn_wb, ctx->st);
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->cnn_ready = true;
+  }
+  ctx->cnn_tau = tau;
+  return MR_OK;
+}
+
+mr_status mr_proposal_get(mr_ctx ctx, float* params, float* tau) {
+  if (!ctx || !ctx->cnn_w) return MR_EINVAL;
+  CK(cudaStreamSynchronize(ctx->st));
+  if (params) CK(cudaMemcpy(params, ctx->cnn_w, kCnnParams * 4, cudaMemcpyDeviceToHost));
+  if (tau) *tau = ctx->cnn_tau;
+  return MR_OK;
+}
+
+mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32_t batch, float lr,
+                            float w_pos, float recall, float holdout, float* tau_out, float* loss_out) {
+  if (!ctx || epochs < 0 || batch < 1 || !(recall > 0.f && recall <= 1.f) || !(holdout >= 0.f && holdout < 1.f))
+    return MR_EINVAL;
+  mr_status s = ensure_cnn(ctx);
+  if (s) return s;
+  CK(cudaStreamSynchronize(ctx->st));
+  // labelled samples (blocks below Jmax), in collection order; the last
+  // `holdout` fraction chooses the threshold
+  std::vector<float> lab(ctx->ds_n);
+  if (ctx->ds_n) CK(cudaMemcpy(lab.data(), ctx->ds_label, ctx->ds_n * 4, cudaMemcpyDeviceToHost));
+  // stratified split: every k-th positive and every k-th negative is held out
+  std::vector<int32_t> train_ids, hold_ids;
+  int64_t npos = 0, nneg = 0;
+  const int64_t every = holdout > 0.f ? std::max<int64_t>(2, (int64_t)std::llround(1.0 / holdout)) : 0;
+  for (int64_t i = 0; i < ctx->ds_n; ++i) {
+    if (lab[i] < 0.f) continue;
+    const bool pos = lab[i] > 0.5f;
+    const int64_t r = pos ? npos++ : nneg++;
+    if (every && r % every == every - 1) hold_ids.push_back((int32_t)i);
+    else train_ids.push_back((int32_t)i);
+  }
+  if (npos == 0 || nneg == 0) return fail(ctx, MR_EINVAL, "need labelled samples of both classes");
+  if (!(w_pos > 0.f)) w_pos = (float)nneg / (float)npos;  // balance the classes
+  std::vector<int32_t> valid(train_ids);
+  valid.insert(valid.end(), hold_ids.begin(), hold_ids.end());
+  const int64_t nv = (int64_t)valid.size();
+  const int64_t nho = (int64_t)hold_ids.size();
+  const int64_t ntr = nv - nho;
+  if (ntr < 1) return fail(ctx, MR_EINVAL, "no labelled samples collected");
+  // training order: a fixed interleave of the training samples (stride coprime
+  // with their count), so batches mix steps without a random draw
+  std::vector<int32_t> order(ntr);
+  int64_t stride = 7919;
+  while (std::gcd(stride, ntr) != 1) ++stride;
+  for (int64_t i = 0; i < ntr; ++i) order[i] = valid[(i * stride) % ntr];
+  int32_t* didx = nullptr;
+  float *dloss = nullptr, *dprob = nullptr;
+  CK(cudaMalloc(&didx, std::max<int64_t>(nv, 1) * 4));
+  CK(cudaMalloc(&dloss, 4));
+  CK(cudaMalloc(&dprob, std::max<int64_t>(nv, 1) * 4));
+  CK(cudaMemcpy(didx, order.data(), ntr * 4, cudaMemcpyHostToDevice));
+  if (nho > 0) CK(cudaMemcpy(didx + ntr, valid.data() + ntr, nho * 4, cudaMemcpyHostToDevice));
+  if (init) {
+    CK(cudaMemcpy(ctx->cnn_w, init, kCnnParams * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->cnn_m, 0, kCnnParams * 4));
+    CK(cudaMemset(ctx->cnn_v, 0, kCnnParams * 4));
+    ctx->cnn_t = 0;
+  }
+  CK(cudaMemset(ctx->cnn_g, 0, kCnnParams * 4));
+  float last = 0.f;
+  for (int e = 0; e < epochs; ++e) {
+    CK(cudaMemsetAsync(dloss, 0, 4, ctx->st));
+    for (int64_t s0 = 0; s0 < ntr; s0 += batch) {
+      const int nb = (int)std::min<int64_t>(batch, ntr - s0);
+      launch_train(ctx->p.Bs, ctx->ds_feat, ctx->ds_label, didx, s0, nb, ctx->cnn_w, w_pos, ctx->cnn_g,
+                   dloss, nullptr, ctx->lc.num_sms, ctx->st);
+      launch_adam(ctx->cnn_w, ctx->cnn_m, ctx->cnn_v, ctx->cnn_g, lr, ++ctx->cnn_t, ctx->cnn_wb, ctx->st);
+    }
+    CK(cudaMemcpyAsync(&last, dloss, 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  launch_to_bf16(ctx->cnn_w, ctx->cnn_wb, ctx->st);
+  // threshold: largest tau keeping recall >= target on the held-out samples
+  // (all samples when there is no hold-out), with the BF16 inference weights
+  const int64_t ne = nho > 0 ? nho : ntr;
+  const int32_t* eidx = nho > 0 ? didx + ntr : didx;
+  float* gfeat = nullptr;
+  CK(cudaMalloc(&gfeat, ne * feat_len(ctx) * 4));
+  std::vector<int32_t> hidx(ne);
+  CK(cudaMemcpy(hidx.data(), eidx, ne * 4, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < ne; ++i)
+    CK(cudaMemcpyAsync(gfeat + i * feat_len(ctx), ctx->ds_feat + (int64_t)hidx[i] * feat_len(ctx),
+                       feat_len(ctx) * 4, cudaMemcpyDeviceToDevice, ctx->st));
+  PoolView pv = view(ctx);
+  launch_infer(pv, ctx->p.Bs, gfeat, ctx->cnn_wb, dprob, ne, ctx->lc.num_sms, ctx->st);
+  std::vector<float> pr(ne);
+  CK(cudaMemcpyAsync(pr.data(), dprob, ne * 4, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  std::vector<float> ppos;
+  for (int64_t i = 0; i < ne; ++i) if (lab[hidx[i]] > 0.5f) ppos.push_back(pr[i]);
+  float tau = 0.5f;
+  if (!ppos.empty()) {
+    std::sort(ppos.begin(), ppos.end());
+    const int64_t miss = (int64_t)std::floor((1.0 - recall) * (double)ppos.size());
+    tau = std::nextafter(ppos[miss], 0.f);
+  }
+  ctx->cnn_tau = tau;
+  ctx->cnn_ready = true;
+  cudaFree(gfeat);
+  cudaFree(didx);
+  cudaFree(dloss);
+  cudaFree(dprob);
+  if (tau_out) *tau_out = tau;
+  if (loss_out) *loss_out = last;
+  return MR_OK;
+}
+
+mr_status mr_proposal_stats(mr_ctx ctx, int64_t* out, int32_t reset) {
+  if (!ctx || !out) return MR_EINVAL;
+  for (int k = 0; k < 5; ++k) out[k] = ctx->prop_stats[k];
+  if (reset) for (int k = 0; k < 5; ++k) ctx->prop_stats[k] = 0;
+  return MR_OK;
+}
+
+mr_status mr_cnn_eval(mr_ctx ctx, const float* params, const float* x, const float* y, int64_t n,
+                      float w_pos, float* prob, float* grad, float* loss) {
+  if (!ctx || !params || !x || !y || n < 1) return MR_EINVAL;
+  mr_status s = ensure_cnn(ctx);
+  if (s) return s;
+  const int64_t fl = feat_len(ctx);
+  float *dx = nullptr, *dy = nullptr, *dw = nullptr, *dg = nullptr, *dl = nullptr, *dp = nullptr;
+  CK(cudaMalloc(&dx, n * fl * 4));
+  CK(cudaMalloc(&dy, n * 4));
+  CK(cudaMalloc(&dw, kCnnParams * 4));
+  CK(cudaMalloc(&dg, kCnnParams * 4));
+  CK(cudaMalloc(&dl, 4));
+  CK(cudaMalloc(&dp, n * 4));
+  CK(cudaMemcpy(dx, x, n * fl * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dy, y, n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dw, params, kCnnParams * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemset(dg, 0, kCnnParams * 4));
+  CK(cudaMemset(dl, 0, 4));
+  launch_train(ctx->p.Bs, dx, dy, nullptr, 0, (int)n, dw, w_pos, dg, dl, dp, ctx->lc.num_sms, ctx->st);
+  CK(cudaStreamSynchronize(ctx->st));
+  if (prob) CK(cudaMemcpy(prob, dp, n * 4, cudaMemcpyDeviceToHost));
+  if (grad) CK(cudaMemcpy(grad, dg, kCnnParams * 4, cudaMemcpyDeviceToHost));
+  if (loss) CK(cudaMemcpy(loss, dl, 4, cudaMemcpyDeviceToHost));
+  for (float* q : {dx, dy, dw, dg, dl, dp}) cudaFree(q);
+  return MR_OK;
 }
 
 mr_status mr_enable_timing(mr_ctx ctx, int32_t on) {

@@ -145,6 +145,7 @@ struct Ring {
   int finer;    // some leaf one level finer touches the block
   int coarser;  // some leaf one level coarser touches the block
 };
+constexpr int kRingBytes = (int)((sizeof(Ring) + 15) / 16 * 16);
 
 template <int D, int B>
 __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, Ring& R) {

@@ -7,7 +7,6 @@
 
 namespace mr {
 
-constexpr int kRingBytes = (int)((sizeof(Ring) + 15) / 16 * 16);
 
 // ------------------------------------------------------------------ stage ----
 // One RK4 stage on every block (Sec. 3: 4th-order central FD + classic RK4):
@@ -571,7 +570,8 @@ __global__ void k_refine_count(PoolView pv, int mode, const int8_t* mask) {
     const int s = pv.act[p];
     const int l = pv.lvl[s];
     const TreeDev& td = pv.trees[pv.tree[s]];
-    const bool r = l < td.Jmax && (mode == MR_ADAPT_REFINE_ALL || (mask && mask[p] > 0));
+    // mode 2: flags already set on the device (learned proposal + closure)
+    const bool r = l < td.Jmax && (mode == MR_ADAPT_REFINE_ALL || (mode == 2 ? pv.flag[s] == 1 : (mask && mask[p] > 0)));
     pv.flag[s] = r ? 1 : 0;
     pv.emit[2 * p] = r ? nch : 1;
     pv.emit[2 * p + 1] = r ? nch : 0;

@@ -1,5 +1,8 @@
 """Seeded synthetic inputs (no arithmetic of the method).
 
+A module of its own: the CUDA library and the oracle never import it; tests
+and the benchmark draw instances here and pass the same numbers to both.
+
 Random parameters are drawn with splitmix64 (to seed) and xoshiro256**
 (Blackman & Vigna, "Scrambled linear pseudorandom number generators", 2018),
 written here from their published definitions, so that every consumer of a
@@ -78,3 +81,34 @@ def mixing_layer_perturbation(seed=DEFAULT_SEED, modes=8):
     a = [g.uniform(-1.0, 1.0) for _ in range(modes)]
     phi = [g.uniform(0.0, 2.0 * math.pi) for _ in range(modes)]
     return a, phi
+
+
+def cnn_init_params(nparam_shapes, seed=DEFAULT_SEED):
+    """He-normal initial weights of the proposal network (biases zero), drawn
+    with Box-Muller from the seeded generator.  nparam_shapes: list of shapes in
+    packing order; 4-D shapes are convolutions (fan-in = in_channels * 9), the
+    last 1-D shape of length > 1 is the linear layer (fan-in = its length)."""
+    import numpy as np
+    g = Xoshiro256ss(seed)
+
+    def normal(n):
+        out = np.empty(n)
+        for i in range(0, n, 2):
+            u1 = max(g.uniform(), 1e-300)
+            u2 = g.uniform()
+            r = math.sqrt(-2.0 * math.log(u1))
+            out[i] = r * math.cos(2 * math.pi * u2)
+            if i + 1 < n:
+                out[i + 1] = r * math.sin(2 * math.pi * u2)
+        return out
+    parts = []
+    linear = max(k for k, s in enumerate(nparam_shapes) if len(s) == 1 and s[0] > 1)
+    for k, s in enumerate(nparam_shapes):
+        n = int(np.prod(s))
+        if len(s) == 4:
+            parts.append(normal(n) * math.sqrt(2.0 / (s[1] * 9)))
+        elif k == linear:
+            parts.append(normal(n) * math.sqrt(1.0 / s[0]))
+        else:
+            parts.append(np.zeros(n))
+    return np.concatenate(parts)

@@ -296,7 +296,7 @@ def test_graph_steps_equal_eager_steps(mr):
 
 
 def test_forest_trees_are_independent_and_match_oracle(mr, oracle_mod):
-    from paper_1902_00088_gb300 import inputs
+    import synthetic as inputs
     trees = inputs.forest_trees(3, seed=11)
     for t in trees:
         t["Jmax"] = min(t["Jmax"], 5)
@@ -320,7 +320,7 @@ def test_forest_trees_are_independent_and_match_oracle(mr, oracle_mod):
 
 
 def ns_cfg(Bs=17, Jmin=2, Jmax=4, eps=1e-3, seed=20190201):
-    from paper_1902_00088_gb300 import inputs
+    import synthetic as inputs
     a, phi = inputs.mixing_layer_perturbation(seed)
     delta, U0, Ma, gam, amp = 0.1, 0.5, 0.3, 1.4, 1e-3
     return dict(dim=2, Bs=Bs, nvar=4, Jmin=Jmin, Jmax=Jmax, eps=eps, rhs="ns",

@@ -1,6 +1,6 @@
 """Seeded input generators: splitmix64 / xoshiro256** from their published
 definitions (first splitmix64 outputs for seed 0 are the published values)."""
-from paper_1902_00088_gb300 import inputs
+import synthetic as inputs
 
 
 def test_splitmix64_seed_zero_published_sequence():
