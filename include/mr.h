@@ -191,6 +191,21 @@ mr_status mr_set_refine_mask(mr_ctx ctx, int64_t n, const int8_t* mask);
  * Synchronises. */
 mr_status mr_error(mr_ctx ctx, int32_t tree, double t, double* out);
 
+/* Same result as mr_error (up to the rounding of the exact field's exp, which
+ * is evaluated on the device here, and the order of the atomic sums) without
+ * allocating device memory, for callers that cannot call cudaMalloc/cudaFree:
+ * processes whose device memory is fully held by another allocator, or code
+ * that must avoid the device synchronisation of cudaFree.  No counterpart in
+ * the paper.  Its scratch (three factor tables and four accumulators) lives in
+ * one file-scope device array of 3 * 16384 + 4 doubles that every GPU loading
+ * the library keeps until exit; (Bs-1) * 2^Jmax of the tree must be <= 16384,
+ * else MR_EINVAL.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture.  All calls on a device share the array; the accumulators are cleared
+ * at the start of each call, and calls that overlap on the GPU race on it.
+ * Synchronises. */
+mr_status mr_error_noalloc(mr_ctx ctx, int32_t tree, double t, double* out);
+
 /* Kernel launches enqueued by this process so far (for throughput claims). */
 int64_t mr_launch_count(mr_ctx ctx);
 

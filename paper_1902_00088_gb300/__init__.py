@@ -78,6 +78,7 @@ SIGNATURES = {
     "mr_set_blocks": (_i32, [_vp, _i64, _vp, _vp, _vp, _dp]),
     "mr_set_refine_mask": (_i32, [_vp, _i64, _vp]),
     "mr_error": (_i32, [_vp, _i32, C.c_double, _dp]),
+    "mr_error_noalloc": (_i32, [_vp, _i32, C.c_double, _dp]),
     "mr_launch_count": (_i64, [_vp]),
     "mr_enable_timing": (_i32, [_vp, _i32]),
     "mr_set_time": (_i32, [_vp, _dp, _dp]),
@@ -258,6 +259,12 @@ class Forest:
         out = np.zeros(4, np.float64)
         self._ck(self.lib.mr_error(self.h, tree, t, _ptr(out)))
         return dict(l2=out[0] / out[1], linf=out[2] / out[3], l2_abs=out[0], linf_abs=out[2])
+
+    def error_noalloc(self, tree, t):
+        """mr_error without device allocation (scratch in a static device array)."""
+        out = np.zeros(4, np.float64)
+        self._ck(self.lib.mr_error_noalloc(self.h, tree, t, _ptr(out)))
+        return out
 
     def launch_count(self):
         return int(self.lib.mr_launch_count(self.h))

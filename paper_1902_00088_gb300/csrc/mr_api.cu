@@ -1253,3 +1253,98 @@ mr_status mr_reset_stats(mr_ctx ctx) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Error norms without device allocation (mr_error_noalloc).
+//
+// mr_error above allocates its scratch (the exact-field factor tables and the
+// four accumulators) with cudaMalloc on every call.  Some callers cannot do
+// that: processes whose device memory is fully reserved by another allocator
+// (a framework's caching allocator that owns the pool), or callers that must
+// not pay the device-wide synchronisation that cudaFree implies.  This variant
+// keeps its scratch in one file-scope device array instead.
+//
+// Scratch: 3 factor tables of N = (Bs - 1) 2^Jmax doubles (one per axis) plus
+// 4 accumulators, N <= kNoAllocMaxN.  Every GPU that loads the library holds
+// the array (3 * 16384 + 4 doubles = 393,248 bytes) until the process exits.
+// All calls on a device share it and it keeps the last call's contents: the
+// accumulators are cleared at the start of each call, and calls whose work
+// overlaps on the GPU (different streams or threads without ordering) race on
+// it.
+constexpr int64_t kNoAllocMaxN = 16384;
+static __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMaxN + 4];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device.  In host code
+// the array's name is only a stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// Factor tables of the exact field (Gaussian advected by constant u over t):
+// ex[a][U] = exp(-d^2 / (2 sigma^2)), d the nearest periodic image of
+// x0_a + U h - u_a t - c_a; axes beyond the dimension hold 1.
+__global__ void k_noalloc_tables(double* ex, int64_t N, int dim, double L, double x00, double x01,
+                                 double x02, double s0, double s1, double s2, double c0, double c1,
+                                 double c2, double sigma) {
+  const double x0[3] = {x00, x01, x02}, sh[3] = {s0, s1, s2}, c[3] = {c0, c1, c2};
+  const double h = L / (double)N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 3 * N;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(q / N);
+    const int64_t U = q % N;
+    if (a >= dim) { ex[q] = 1.0; continue; }
+    const double x = x0[a] + (double)U * h;
+    double dd = (x - sh[a]) - c[a];
+    while (dd >= 0.5 * L) dd -= L;
+    while (dd < -0.5 * L) dd += L;
+    ex[q] = exp(-(dd * dd) / (2.0 * sigma * sigma));
+  }
+}
+
+}  // namespace
+
+extern "C" mr_status mr_error_noalloc(mr_ctx ctx, int32_t tree, double t, double* out) {
+  if (!ctx || !out || tree < 0 || tree >= ctx->p.ntrees) return MR_EINVAL;
+  const mr_tree_desc& td = ctx->td[tree];
+  if (td.ic_kind != MR_IC_GAUSS) return fail(ctx, MR_EINVAL, "error needs the Gaussian IC");
+  const int64_t N = ctx->tdev[tree].N;
+  if (N > kNoAllocMaxN)
+    return fail(ctx, MR_EINVAL, "mr_error_noalloc: (Bs-1)*2^Jmax = " + std::to_string(N) +
+                                    " exceeds its scratch limit of " + std::to_string(kNoAllocMaxN));
+  double* scratch = nullptr;
+  CK(noalloc_scratch(&scratch));
+  double* ex = scratch;
+  double* acc = scratch + 3 * kNoAllocMaxN;
+  double sh[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < ctx->p.dim; ++a) sh[a] = ctx->p.rhs_kind == MR_RHS_ADV ? td.rhs[a] * t : 0.0;
+  CK(cudaMemsetAsync(acc, 0, 4 * sizeof(double), ctx->st));
+  k_noalloc_tables<<<ctx->lc.num_sms * 2, 256, 0, ctx->st>>>(ex, N, ctx->p.dim, ctx->p.L, td.x0[0], td.x0[1],
+                                                            td.x0[2], sh[0], sh[1], sh[2], td.ic[0], td.ic[1],
+                                                            td.ic[2], td.ic[3]);
+  count_launch();
+  PoolView pv = view(ctx);
+  by_dim(ctx, [&] { launch_error<2>(pv, fields(ctx), tree, ex, acc, ctx->lc, ctx->st); },
+         [&] { launch_error<3>(pv, fields(ctx), tree, ex, acc, ctx->lc, ctx->st); });
+  double o[4];
+  CK(cudaMemcpyAsync(o, acc, sizeof(o), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  out[0] = std::sqrt(o[0]); out[1] = std::sqrt(o[1]); out[2] = o[2]; out[3] = o[3];
+  return MR_OK;
+}
