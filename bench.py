@@ -44,6 +44,16 @@ WORKLOADS = {
                    trees=None, capacity=600_000,
                    name="64 independent 2D advection trees (seeded: sigma 0.02-0.1, |u_i|<=1, "
                         "Jmax 4-8, eps 1e-5..1e-3), 17^2 blocks, FP32 RHS + FP64 details"),
+    # 2D compressible Navier-Stokes temporal mixing layer (Sec. 4 setup, reduced):
+    # u = 0.5 tanh(2y/delta), delta 0.1, Mach 0.3, Re 1000, seeded perturbation
+    # 1e-3; 4 conserved variables, FP32 stages with FP64 state/accumulator and
+    # details; 33^2 blocks, Jmax 7, eps 1e-3; learned refinement proposal
+    # trained on the run's own adapt decisions.
+    "ns": dict(dim=2, Bs=33, nvar=4, norm_kind=1, precision="fp32_acc64", detail_fp64=True, rhs="ns",
+               tree=None, capacity=20_000, oracle_jmax=4, learned=dict(collect_steps=60, epochs=6),
+               name="2D NS temporal mixing layer (delta 0.1, Ma 0.3, Re 1000, seeded perturbation 1e-3), "
+                    "33^2 blocks, Jmin 2, Jmax 7, eps 1e-3, FP32 stages + FP64 state/acc/details, "
+                    "learned proposal, CFL 0.5"),
     "adv2d": dict(dim=2, Bs=17, precision="fp64", detail_fp64=False, rhs="adv",
                   tree=dict(Jmin=2, Jmax=5, eps=1e-3, ic="gauss",
                             ic_params=(0.5, 0.5, 0.0, 0.05), rhs_params=(1.0, 0.5, 0.0)),
@@ -60,6 +70,19 @@ def _forest_trees():
 WORKLOADS["forest"]["trees"] = _forest_trees()
 
 
+def _mixing_layer_tree(seed=20190201):
+    import synthetic as inputs
+    a, phi = inputs.mixing_layer_perturbation(seed)
+    delta, U0, Ma, gam, amp = 0.1, 0.5, 0.3, 1.4, 1e-3
+    return dict(Jmin=2, Jmax=7, eps=1e-3, ic="mixing",
+                ic_params=(delta, U0, Ma, gam, amp) + tuple(a) + tuple(phi),
+                rhs_params=(gam, U0 * delta / 1000.0, 0.71), x0=(0.0, -0.5, 0.0))
+
+
+WORKLOADS["ns"]["tree"] = _mixing_layer_tree()
+WORKLOADS["ns"]["umax"] = 0.5 + 0.5 / 0.3  # |u| + c0
+
+
 def dt_of(w):
     t = w["tree"]
     dx = 1.0 / ((w["Bs"] - 1) * (1 << t["Jmax"]))
@@ -69,7 +92,7 @@ def dt_of(w):
 def bytes_per_stage_block(w):
     """Algorithmic bytes of one RK stage over one block, averaged over the 4
     stages: 16 array passes per step over Bs^d nodes (3 + 5 + 5 + 3)."""
-    n = w["Bs"] ** w["dim"]
+    n = w["Bs"] ** w["dim"] * w.get("nvar", 1)
     if w["precision"] == "fp64":
         return 16 * n * 8 / 4
     if w["precision"] == "fp32":
@@ -138,10 +161,13 @@ def oracle_sample(w, seconds_target=15.0):
     import oracle
     t = dict(w["tree"] if "tree" in w else w["trees"][0])
     umax = w.get("umax") or math.hypot(*t["rhs_params"][:2]) or 1.0
-    jmax = {3: 3, 2: 5}[w["dim"]]
+    jmax = w.get("oracle_jmax") or {3: 3, 2: 5}[w["dim"]]
     jmin = min(t["Jmin"], jmax - 1)
-    cfg = dict(dim=w["dim"], Bs=w["Bs"], Jmin=jmin, Jmax=jmax, eps=t["eps"], rhs=w["rhs"],
-               rhs_params=t["rhs_params"], ic="gauss", ic_params=t["ic_params"])
+    cfg = dict(dim=w["dim"], Bs=w["Bs"], nvar=w.get("nvar", 1), Jmin=jmin, Jmax=jmax, eps=t["eps"],
+               rhs=w["rhs"], rhs_params=t["rhs_params"], ic=t.get("ic", "gauss"), ic_params=t["ic_params"],
+               norm_kind=w.get("norm_kind", 0))
+    if "x0" in t:
+        cfg["x0"] = t["x0"]
     o = oracle.Oracle(cfg)
     o.init_tree()
     dx = 1.0 / ((w["Bs"] - 1) * (1 << jmax))
@@ -210,6 +236,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
+    ap.add_argument("--save-state", default="", help="write the state reached after spin-up + warm-up (npz)")
+    ap.add_argument("--load-state", default="", help="start from a saved state instead of init + spin-up")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -264,6 +292,12 @@ def main():
     t = np.zeros(nt)
     tuned = None
     steps_done = 0
+    if args.load_state:
+        z = np.load(args.load_state)
+        g.set_blocks(z["level"], z["coords"], z["fields"], tree=z["tree"])
+        t = z["t"].copy()
+        steps_done = int(z["steps_done"])
+        spin = 0
     if graph:
         g.set_time(t, dts)
         autotune = args.autotune if args.autotune >= 0 else (3 if "trees" in w else 0)
@@ -277,6 +311,11 @@ def main():
             g.step(t, dts)
             t = t + dts
         steps_done += spin + args.warmup
+    if args.save_state:
+        info, fl = g.get_blocks()
+        tt = g.get_time() if graph else t
+        np.savez(args.save_state, level=info["level"], tree=info["tree"], coords=info["coords"],
+                 fields=fl, t=tt, steps_done=steps_done)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -413,7 +452,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": w["name"], "trees": nt, "blocks_at_start": nb0, "blocks_at_end": nb,
                        "Bs": B, "dim": d, "dt": float(dts[0]) if nt == 1 else "per tree",
-                       "mode": "eager" if not graph else "cuda-graph step replay",
+                       "mode": "eager" if not graph else "cuda-graph step replay (%s rounds)" % g.graph_mode(),
                        "autotuned_ctas_per_sm": tuned,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2_flush": "none: inputs resident; working set noted in blocks_at_*",

@@ -231,10 +231,20 @@ mr_status mr_enable_timing(mr_ctx ctx, int32_t on);
  * Jmax - Jmin) become empty once a round merged nothing.  The swirl time factor
  * is evaluated with the device cos in this mode.  Errors are reported by the next
  * synchronising call.  The graph is captured on a private stream and replayed on
- * the context's stream. */
+ * the context's stream.  In MR_REFINE_LEARNED mode the captured step runs the
+ * proposal (features, network, fallback, gradedness closure) and the judge on
+ * the device; mr_set_refine_mode, mr_proposal_set with a new tau and
+ * mr_proposal_train make the next call capture the step again.  While training
+ * samples are being collected (mr_proposal_collect) this call fails with
+ * MR_EINVAL: collection runs in mr_step. */
 mr_status mr_set_time(mr_ctx ctx, const double* t, const double* dt);  /* ntrees each; synchronises */
 mr_status mr_get_time(mr_ctx ctx, double* t);                          /* synchronises */
 mr_status mr_step_graph(mr_ctx ctx, int64_t nsteps);
+/* Form of the captured step: 1 = coarsening rounds in a conditional while-node
+ * (rounds run only while a family merged), 0 = a fixed number of rounds that
+ * become empty once nothing merges (used where conditional nodes are not
+ * available), -1 = no graph captured yet. */
+int32_t mr_graph_mode(mr_ctx ctx);
 /* Blocks of the adapted grid at the start of every graph step since the last
  * reset (up to 65536 entries); *n = entries recorded.  Synchronises. */
 mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n, int32_t reset);

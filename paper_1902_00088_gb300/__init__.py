@@ -84,6 +84,7 @@ SIGNATURES = {
     "mr_set_time": (_i32, [_vp, _dp, _dp]),
     "mr_get_time": (_i32, [_vp, _dp]),
     "mr_step_graph": (_i32, [_vp, _i64]),
+    "mr_graph_mode": (_i32, [_vp]),
     "mr_get_step_history": (_i32, [_vp, _i64, _vp, C.POINTER(C.c_int64), _i32]),
     "mr_autotune": (_i32, [_vp, _i32, C.POINTER(C.c_int32)]),
     "mr_set_refine_mode": (_i32, [_vp, _i32]),
@@ -281,6 +282,9 @@ class Forest:
     def step_graph(self, nsteps=1):
         self._ck(self.lib.mr_step_graph(self.h, nsteps))
 
+    def graph_mode(self):
+        return {1: "while-node", 0: "fixed-rounds", -1: None}[int(self.lib.mr_graph_mode(self.h))]
+
     def step_history(self, reset=True):
         n = C.c_int64()
         self._ck(self.lib.mr_get_step_history(self.h, 0, None, C.byref(n), 0))
@@ -295,6 +299,8 @@ class Forest:
 
     # ------------------------------------------------- learned proposal --
     CNN_PARAMS = 4961
+    # parameter packing of the proposal network: W1, b1, W2, b2, W3, b3, wl, bl
+    CNN_SHAPES = [(16, 2, 3, 3), (16,), (16, 16, 3, 3), (16,), (16, 16, 3, 3), (16,), (16,), (1,)]
 
     def set_refine_mode(self, mode):
         self._ck(self.lib.mr_set_refine_mode(self.h, {"all": 0, "learned": 1}.get(mode, mode)))

@@ -35,6 +35,7 @@ struct mr_ctx_s {
   void* y = nullptr; void* acc = nullptr; void* Ya = nullptr; void* Yb = nullptr;
   int8_t *lvl = nullptr, *f1 = nullptr, *flag = nullptr, *mask = nullptr;
   int16_t* tree = nullptr;
+  int32_t* stamp = nullptr;
   int32_t *crd = nullptr, *act = nullptr, *act_next = nullptr, *freelist = nullptr, *tab = nullptr,
           *cells = nullptr, *emit = nullptr, *eoff = nullptr, *partial = nullptr, *pos = nullptr;
   uint64_t* hkey = nullptr;
@@ -56,6 +57,8 @@ struct mr_ctx_s {
   TreeTime* ttime = nullptr;
   int32_t* hist = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t body_stream = nullptr;
+  bool graph_while = true;  // coarsening rounds as a conditional while-node (else fixed rounds)
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_kernels = 0;  // kernel nodes of the captured step
   bool capturing = false;
@@ -70,6 +73,7 @@ struct mr_ctx_s {
   int64_t feat_cap = 0;
   int8_t* skip = nullptr;
   int32_t *skip_key = nullptr, *pcounts = nullptr, *changed = nullptr;
+  int32_t* gcounts = nullptr;  // proposal counters of graph replays (5, folded into prop_stats)
   int64_t prop_stats[5] = {0, 0, 0, 0, 0};
   bool collect = false;
   float *ds_feat = nullptr, *ds_label = nullptr, *ds_mpre = nullptr;
@@ -81,6 +85,7 @@ namespace mr {
 __global__ void k_step_begin(Counters* c, int32_t* hist);
 __global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int swirl);
 __global__ void k_time_advance(TreeTime* tt, int ntrees);
+__global__ void k_round_continue(Counters* c, cudaGraphConditionalHandle h, int max_rounds);
 }
 
 namespace {
@@ -117,7 +122,7 @@ PoolView view(mr_ctx c) {
   v.flag = c->flag; v.md = c->md; v.mdet = c->mdet; v.bmax = c->bmax; v.act = c->act;
   v.act_next = c->act_next; v.freelist = c->freelist; v.tab = c->tab; v.lat = c->lat;
   v.svar = c->svar; v.cells = c->cells; v.emit = c->emit; v.eoff = c->eoff;
-  v.partial = c->partial; v.pos_of_slot = c->pos; v.cnt = c->cnt;
+  v.partial = c->partial; v.pos_of_slot = c->pos; v.cnt = c->cnt; v.stamp = c->stamp;
   return v;
 }
 Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb}; }
@@ -292,6 +297,8 @@ mr_status ensure_cnn(mr_ctx ctx) {
   CK(cudaMalloc(&ctx->skip_key, ctx->S * 4));
   CK(cudaMalloc(&ctx->pcounts, 4 * 4));
   CK(cudaMalloc(&ctx->changed, 4));
+  CK(cudaMalloc(&ctx->gcounts, 5 * 4));
+  CK(cudaMemset(ctx->gcounts, 0, 5 * 4));
   CK(cudaMemset(ctx->cnn_w, 0, kCnnParams * 4));
   CK(cudaMemset(ctx->cnn_m, 0, kCnnParams * 4));
   CK(cudaMemset(ctx->cnn_v, 0, kCnnParams * 4));
@@ -299,7 +306,7 @@ mr_status ensure_cnn(mr_ctx ctx) {
   CK(cudaMemset(ctx->skip, 0, ctx->S));
   for (void* q : {(void*)ctx->cnn_w, (void*)ctx->cnn_m, (void*)ctx->cnn_v, (void*)ctx->cnn_g,
                   (void*)ctx->cnn_wb, (void*)ctx->skip, (void*)ctx->skip_key, (void*)ctx->pcounts,
-                  (void*)ctx->changed})
+                  (void*)ctx->changed, (void*)ctx->gcounts})
     ctx->owned.push_back(q);
   return MR_OK;
 }
@@ -590,6 +597,8 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if ((e = dalloc(ctx, &ctx->act_next, S))) return e;
     if ((e = dalloc(ctx, &ctx->freelist, S))) return e;
     if ((e = dalloc(ctx, &ctx->pos, S))) return e;
+    if ((e = dalloc(ctx, &ctx->stamp, S))) return e;
+    if ((e = cudaMemset(ctx->stamp, 0, S * 4))) return e;
     if ((e = dalloc(ctx, &ctx->tab, ctx->ntab))) return e;
     if ((e = dalloc(ctx, &ctx->cells, 2 * ctx->ncells))) return e;
     if ((e = dalloc(ctx, &ctx->emit, 2 * ctx->nscan))) return e;
@@ -634,6 +643,7 @@ void mr_destroy(mr_ctx ctx) {
   else cudaDeviceSynchronize();
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
   if (ctx->feat) { cudaFree(ctx->feat); cudaFree(ctx->prob); cudaFree(ctx->mpre); }
   if (ctx->ds_feat) { cudaFree(ctx->ds_feat); cudaFree(ctx->ds_label); cudaFree(ctx->ds_mpre); cudaFree(ctx->ds_key); }
   for (void* q : ctx->owned) cudaFree(q);
@@ -915,7 +925,7 @@ namespace {
 // One step with no host synchronisation, for capture: time coefficients from
 // the device, refine all, four stages, a fixed number of coarsening rounds that
 // become empty once a round merged nothing, time advance.
-void enqueue_graph_step(mr_ctx ctx, cudaStream_t st) {
+void enqueue_graph_prologue(mr_ctx ctx, cudaStream_t st) {
   PoolView pv = view(ctx);
   pv.tt = ctx->ttime;
   const Fields f = fields(ctx);
@@ -923,36 +933,133 @@ void enqueue_graph_step(mr_ctx ctx, cudaStream_t st) {
   k_step_begin<<<1, 1, 0, st>>>(ctx->cnt, ctx->hist);
   k_time_coef<<<(nt + 127) / 128, 128, 0, st>>>(ctx->ttime, ctx->trees, nt, ctx->p.rhs_kind == MR_RHS_SWIRL);
   count_launch(2);
-  by_dim(ctx, [&] { launch_refine<2>(pv, f, MR_ADAPT_REFINE_ALL, ctx->mask, ctx->lc, st); },
-         [&] { launch_refine<3>(pv, f, MR_ADAPT_REFINE_ALL, ctx->mask, ctx->lc, st); });
+  int mode = MR_ADAPT_REFINE_ALL;
+  if (ctx->refine_mode == 1) {
+    // learned proposal with the exact fallback, closed under gradedness: the
+    // closure is monotone, so a fixed number of passes (one more than the
+    // level span) reaches its fixpoint and later passes change nothing
+    launch_features(pv, ctx->y, ctx->feat, ctx->mpre, 0, ctx->lc.num_sms, st);
+    launch_infer(pv, ctx->p.Bs, ctx->feat, ctx->cnn_wb, ctx->prob, -1, ctx->lc.num_sms, st);
+    launch_propose(pv, ctx->prob, ctx->mpre, ctx->cnn_tau, ctx->skip, ctx->gcounts, st);
+    int jspan = 0;
+    for (auto& t : ctx->td) jspan = std::max(jspan, t.Jmax - t.Jmin);
+    for (int it = 0; it <= jspan; ++it) launch_close(pv, ctx->skip, ctx->gcounts + 4, st);
+    launch_skip_key(pv, ctx->skip, ctx->skip_key, st);
+    mode = 2;
+  }
+  by_dim(ctx, [&] { launch_refine<2>(pv, f, mode, ctx->mask, ctx->lc, st); },
+         [&] { launch_refine<3>(pv, f, mode, ctx->mask, ctx->lc, st); });
   StageArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   for (int s = 0; s < 4; ++s)
     by_dim(ctx, [&] { launch_stage<2>(pv, f, s, sa, ctx->lc, st); },
            [&] { launch_stage<3>(pv, f, s, sa, ctx->lc, st); });
+}
+
+void enqueue_round(mr_ctx ctx, cudaStream_t st) {
+  PoolView pv = view(ctx);
+  pv.tt = ctx->ttime;
+  const Fields f = fields(ctx);
   const bool fp64 = ctx->p.detail_fp64 != 0;
-  for (int r = 0; r < max_rounds_of(ctx); ++r)
-    by_dim(ctx, [&] { launch_coarsen_round<2>(pv, f, fp64, true, ctx->lc, st); },
-           [&] { launch_coarsen_round<3>(pv, f, fp64, true, ctx->lc, st); });
+  by_dim(ctx, [&] { launch_coarsen_round<2>(pv, f, fp64, true, ctx->lc, st); },
+         [&] { launch_coarsen_round<3>(pv, f, fp64, true, ctx->lc, st); });
+}
+
+void enqueue_epilogue(mr_ctx ctx, cudaStream_t st) {
+  const int nt = ctx->p.ntrees;
+  if (ctx->refine_mode == 1) {
+    PoolView pv = view(ctx);
+    launch_judge(pv, ctx->skip, ctx->skip_key, ctx->gcounts, st);
+  }
   k_time_advance<<<(nt + 127) / 128, 128, 0, st>>>(ctx->ttime, nt);
   count_launch();
 }
 
-mr_status build_graph(mr_ctx ctx) {
+// One step with no host synchronisation, for capture: time coefficients from
+// the device, refine all, four stages, coarsening rounds, time advance.  The
+// rounds are a conditional while-node (a round runs again only after a round
+// that merged a family, at most max_rounds times); without conditional nodes
+// they are a fixed number of rounds that become empty once one merged nothing.
+cudaError_t capture_step(mr_ctx ctx, cudaGraph_t* out, bool use_while) {
+  cudaStream_t cs = ctx->cap_stream;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  enqueue_graph_prologue(ctx, cs);
+  if (use_while) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edata = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t cn = nullptr;
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, &edata, &nd);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cn, g, deps, edata, nd, &cp);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(ctx->body_stream, cp.conditional.phGraph_out[0], nullptr,
+                                                            nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      enqueue_round(ctx, ctx->body_stream);
+      k_round_continue<<<1, 1, 0, ctx->body_stream>>>(ctx->cnt, h, max_rounds_of(ctx));
+      count_launch();
+      cudaGraph_t body = nullptr;
+      e = cudaStreamEndCapture(ctx->body_stream, &body);
+    }
+    if (e != cudaSuccess) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(cs, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      cudaGetLastError();
+      return e;
+    }
+  } else {
+    for (int r = 0; r < max_rounds_of(ctx); ++r) enqueue_round(ctx, cs);
+  }
+  enqueue_epilogue(ctx, cs);
+  return cudaStreamEndCapture(cs, out);
+}
+
+// The captured step bakes in the refinement mode and the threshold tau; a
+// change of either captures the step again at the next replay.
+void drop_graph(mr_ctx ctx) {
   if (ctx->gexec) {
+    cudaStreamSynchronize(ctx->st);
     cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
   }
+}
+
+mr_status build_graph(mr_ctx ctx) {
+  drop_graph(ctx);
+  if (ctx->collect) return fail(ctx, MR_EINVAL, "training samples are collected by host-driven steps (mr_step)");
+  if (ctx->refine_mode == 1) {
+    mr_status s = ensure_feat(ctx, ctx->S);
+    if (s) return s;
+  }
   if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  if (!ctx->body_stream) CK(cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking));
   CK(cudaStreamSynchronize(ctx->st));
   cudaGraph_t g = nullptr;
   ctx->capturing = true;
-  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
   const int64_t k0 = kernel_launches();
-  enqueue_graph_step(ctx, ctx->cap_stream);
+  cudaError_t e = capture_step(ctx, &g, ctx->graph_while);
+  if (e != cudaSuccess && ctx->graph_while) {  // no conditional nodes: fixed rounds
+    ctx->graph_while = false;
+    count_launch((int)-(kernel_launches() - k0));
+    e = capture_step(ctx, &g, false);
+  }
+  // kernel nodes per replay (a while-body counts once; replays add them)
   ctx->graph_kernels = kernel_launches() - k0;
-  count_launch((int)-ctx->graph_kernels);  // capture enqueues nothing; replays are counted
-  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  count_launch((int)-ctx->graph_kernels);
   ctx->capturing = false;
   if (e != cudaSuccess) return fail(ctx, MR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(&ctx->gexec, g, 0);
@@ -973,6 +1080,11 @@ mr_status mr_step_graph(mr_ctx ctx, int64_t nsteps) {
   ctx->stats.steps += nsteps;
   ctx->stats.stage_launches += 4 * nsteps;
   return MR_OK;
+}
+
+int32_t mr_graph_mode(mr_ctx ctx) {
+  if (!ctx || !ctx->gexec) return -1;
+  return ctx->graph_while ? 1 : 0;
 }
 
 mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n, int32_t reset) {
@@ -1029,6 +1141,7 @@ mr_status mr_set_refine_mode(mr_ctx ctx, int32_t mode) {
     if (s) return s;
     if (!ctx->cnn_ready) return fail(ctx, MR_EINVAL, "no trained or loaded proposal network");
   }
+  if (mode != ctx->refine_mode) drop_graph(ctx);
   ctx->refine_mode = mode;
   return MR_OK;
 }
@@ -1081,6 +1194,7 @@ mr_status mr_proposal_set(mr_ctx ctx, const float* params, float tau) {
     CK(cudaStreamSynchronize(ctx->st));
     ctx->cnn_ready = true;
   }
+  if (tau != ctx->cnn_tau) drop_graph(ctx);
   ctx->cnn_tau = tau;
   return MR_OK;
 }
@@ -1180,6 +1294,7 @@ mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32
     const int64_t miss = (int64_t)std::floor((1.0 - recall) * (double)ppos.size());
     tau = std::nextafter(ppos[miss], 0.f);
   }
+  drop_graph(ctx);
   ctx->cnn_tau = tau;
   ctx->cnn_ready = true;
   cudaFree(gfeat);
@@ -1193,6 +1308,13 @@ mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32
 
 mr_status mr_proposal_stats(mr_ctx ctx, int64_t* out, int32_t reset) {
   if (!ctx || !out) return MR_EINVAL;
+  if (ctx->gcounts) {  // fold in the counters of graph replays
+    int32_t g[5];
+    CK(cudaStreamSynchronize(ctx->st));
+    CK(cudaMemcpy(g, ctx->gcounts, sizeof(g), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->gcounts, 0, sizeof(g)));
+    for (int k = 0; k < 5; ++k) ctx->prop_stats[k] += g[k];
+  }
   for (int k = 0; k < 5; ++k) out[k] = ctx->prop_stats[k];
   if (reset) for (int k = 0; k < 5; ++k) ctx->prop_stats[k] = 0;
   return MR_OK;

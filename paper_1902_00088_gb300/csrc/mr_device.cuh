@@ -105,13 +105,25 @@ struct Geo {
   static constexpr int CLO = -(G / 2) - 1;
   static constexpr int CB = (B - 1) / 2 + G + 3;
   static constexpr int CBOX = CB * CB * (D == 3 ? CB : 1);
-  __device__ static __forceinline__ int cix(int i, int j, int k) {
-    return ((D == 3 ? k - CLO : 0) * CB + (j - CLO)) * CB + (i - CLO);
-  }
   __device__ static __forceinline__ int tix(int i, int j, int k) {
     return ((k + GZ) * T + (j + G)) * T + (i + G);
   }
   __device__ static __forceinline__ int lin(int i, int j, int k) { return (k * B + j) * B + i; }
+};
+
+// Part of the tile a consumer reads: the box of ghost width W (W <= G) and the
+// coarse nodes its prediction stencils touch, CLO..CLO+CB-1 per axis.
+template <int D, int B, int W>
+struct Box {
+  static_assert(W >= 1 && W <= kG, "ghost width");
+  static constexpr int S = B + 2 * W;
+  static constexpr int NPTS = S * S * (D == 3 ? S : 1);
+  static constexpr int CLO = -((W + 1) / 2) - 1;
+  static constexpr int CB = (B - 1) / 2 + 2 * ((W + 1) / 2) + 3;
+  static constexpr int CBOX = CB * CB * (D == 3 ? CB : 1);
+  __device__ static __forceinline__ int cix(int i, int j, int k) {
+    return ((D == 3 ? k - CLO : 0) * CB + (j - CLO)) * CB + (i - CLO);
+  }
 };
 
 struct BlockInfo {
@@ -144,13 +156,14 @@ struct Ring {
   int8_t lvl[64];
   int finer;    // some leaf one level finer touches the block
   int coarser;  // some leaf one level coarser touches the block
+  int mixed;    // some ring leaf is not at the block's level
 };
 constexpr int kRingBytes = (int)((sizeof(Ring) + 15) / 16 * 16);
 
 template <int D, int B>
 __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, Ring& R) {
   using Gm = Geo<D, B>;
-  if (threadIdx.x == 0) R.finer = R.coarser = 0;
+  if (threadIdx.x == 0) R.finer = R.coarser = R.mixed = 0;
   __syncthreads();
   for (int r = threadIdx.x; r < Gm::NR; r += blockDim.x) {
     const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
@@ -180,6 +193,7 @@ __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInf
     }
     if (m == b.lvl + 1) R.finer = 1;  // benign races: all writers store 1
     if (m == b.lvl - 1) R.coarser = 1;
+    if (m != b.lvl) R.mixed = 1;
     const int sh = b.lvl + 1 - m;
     for (int a = 0; a < 3; ++a) {
       const int oc = a < D && m >= 0 ? ((un[a] >> sh) << sh) - (int)(2 * b.c[a]) : 0;
@@ -305,9 +319,9 @@ __device__ __forceinline__ TF pool_at(const PoolView& pv, const TF* F, int slot,
 
 // Coarse-lattice prediction at half-coarse position o (relative to the block
 // origin) from the staged coarse box: x first, then y, then z.
-template <int D, int B, typename TT>
+template <int D, int B, int W, typename TT>
 __device__ __forceinline__ TT predict_box(const TT* box, const int o[3]) {
-  using Gm = Geo<D, B>;
+  using Gm = Box<D, B, W>;
   int base[3] = {0, 0, 0}, ns[3] = {1, 1, 1};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -340,33 +354,70 @@ __device__ __forceinline__ TT predict_box(const TT* box, const int o[3]) {
 // of nvar x CBOX values for the coarse lattice (used when a coarser leaf
 // touches the block): every coarse node takes its owner's value, and ghost
 // nodes between coarse nodes are predicted from it.
-template <int D, int B, typename TF, typename TT>
+template <int D, int B, typename TF, typename TT, int W = kG>
 __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, TF* Fw, TT* tile,
                           bool commit, const Ring& R, TT* cbox) {
   using Gm = Geo<D, B>;
+  using Bx = Box<D, B, W>;
   const int nv = pv.nvar;
   const int64_t own = (int64_t)b.slot * nv * pv.vs;
+  if (!R.mixed) {
+    // every ring leaf has the block's level: the owner of a point is the ring
+    // cell holding it from below (equal-level rule of owner()), no search
+    constexpr int P = Log2B<B>::value;
+    for (int q = threadIdx.x; q < Bx::NPTS; q += blockDim.x) {
+      const int i = q % Bx::S - W;
+      const int j = (q / Bx::S) % Bx::S - W;
+      const int k = D == 3 ? q / (Bx::S * Bx::S) - W : 0;
+      const int idx = Gm::tix(i, j, k);
+      const int h[3] = {2 * i, 2 * j, 2 * k};
+      int r = 0, li[3] = {0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < D; ++a) r += ((h[a] >> P) + 1) << (2 * a);
+#pragma unroll
+      for (int a = 0; a < D; ++a) li[a] = (h[a] - R.org[r][a]) >> 1;
+      const int src = R.slot[r];
+      const int64_t at = (int64_t)src * nv * pv.vs + Gm::lin(li[0], li[1], li[2]);
+      const bool mine = src == b.slot;
+      for (int v = 0; v < nv; ++v) {
+        const TF val = F[at + (int64_t)v * pv.vs];
+        tile[v * Gm::TILE + idx] = (TT)val;
+        if (commit && !mine) {
+          // block-edge node owned by the equal-level neighbour (i or j = B-1)
+          bool edge_node = true;
+#pragma unroll
+          for (int a = 0; a < D; ++a) edge_node &= (h[a] >= 0 && h[a] <= 2 * (B - 1));
+          if (edge_node) {
+            const int64_t me = own + (int64_t)v * pv.vs + Gm::lin(i, j, k);
+            if (F[me] != val) Fw[me] = val;
+          }
+        }
+      }
+    }
+    return;
+  }
   if (R.coarser) {
-    for (int idx = threadIdx.x; idx < Gm::CBOX; idx += blockDim.x) {
-      const int n[3] = {idx % Gm::CB + Gm::CLO, (idx / Gm::CB) % Gm::CB + Gm::CLO,
-                        D == 3 ? idx / (Gm::CB * Gm::CB) + Gm::CLO : 0};
+    for (int idx = threadIdx.x; idx < Bx::CBOX; idx += blockDim.x) {
+      const int n[3] = {idx % Bx::CB + Bx::CLO, (idx / Bx::CB) % Bx::CB + Bx::CLO,
+                        D == 3 ? idx / (Bx::CB * Bx::CB) + Bx::CLO : 0};
       const int h[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
       Own o;
       if (!owner<D, B>(b, h, 0, R, o) || o.m < b.lvl - 1) {
         set_err(pv, kErrGraded);
-        for (int v = 0; v < nv; ++v) cbox[v * Gm::CBOX + idx] = TT(0);
+        for (int v = 0; v < nv; ++v) cbox[v * Bx::CBOX + idx] = TT(0);
         continue;
       }
       const int sh = b.lvl + 1 - o.m;
       const int li[3] = {o.off[0] >> sh, o.off[1] >> sh, o.off[2] >> sh};
-      for (int v = 0; v < nv; ++v) cbox[v * Gm::CBOX + idx] = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
+      for (int v = 0; v < nv; ++v) cbox[v * Bx::CBOX + idx] = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x) {
-    const int i = idx % Gm::T - Gm::G;
-    const int j = (idx / Gm::T) % Gm::T - Gm::G;
-    const int k = D == 3 ? idx / (Gm::T * Gm::T) - Gm::G : 0;
+  for (int q = threadIdx.x; q < Bx::NPTS; q += blockDim.x) {
+    const int i = q % Bx::S - W;
+    const int j = (q / Bx::S) % Bx::S - W;
+    const int k = D == 3 ? q / (Bx::S * Bx::S) - W : 0;
+    const int idx = Gm::tix(i, j, k);
     const int ijk[3] = {i, j, k};
     bool ghost = false, edge = false;
 #pragma unroll
@@ -408,7 +459,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
     } else {
       if (o.m != b.lvl - 1) set_err(pv, kErrGraded);
-      for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = predict_box<D, B, TT>(cbox + v * Gm::CBOX, ijk);
+      for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = predict_box<D, B, W, TT>(cbox + v * Bx::CBOX, ijk);
     }
   }
 }

@@ -47,7 +47,9 @@ struct Counters {
   int32_t done;     // a coarsening round merged nothing: later rounds of the step skip
   unsigned long long stage_blocks;  // blocks processed by RK stage launches
   int32_t hist_n;   // entries written to the step history
-  int32_t pad2;
+  int32_t rounds;   // coarsening rounds run in the current graph step
+  int32_t round_id;     // coarsening rounds so far (monotonic); merged mothers are stamped with it
+  int32_t first_round;  // the current round is the first of an adapt: every block is evaluated
 };
 constexpr int kMaxHist = 1 << 16;  // step history: blocks of the adapted grid before each step
 
@@ -100,6 +102,7 @@ struct PoolView {
   int32_t* eoff;           // scan output [cap] x2 (int2)
   int32_t* partial;        // scan partials
   int32_t* pos_of_slot;
+  int32_t* stamp;          // per slot: round_id of the round that created the block (merges)
   Counters* cnt;
   const TreeTime* tt;      // stage coefficients from device memory (graph mode), or null
 };

@@ -15,8 +15,8 @@ namespace mr {
 //   s2: acc += dt/3 k,    Y3 = y + dt k        s3: y = acc + dt/6 k
 // Advection RHS: -(u Dx phi + v Dy phi [+ w Dz phi]),
 //   D1 f = ((f[-2] - f[2]) + 8 (f[1] - f[-1])) / (12 dx).
-template <int D, int B, int RHS, typename TS, typename TY, typename TSRC>
-__global__ void __launch_bounds__(256) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
+template <int D, int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
+__global__ void __launch_bounds__(NT) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
                             TS* __restrict__ acc, TY* __restrict__ ynext, int stage, StageArgs sa) {
   using Gm = Geo<D, B>;
   using TC = TY;  // stencil arithmetic type
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_stage_adv(PoolView pv, const TSRC* __re
     const TreeDev& td = pv.trees[b.tree];
     build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
+    fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
     __syncthreads();
     const TC c = (TC)td.cD[b.lvl];
     const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
@@ -217,8 +217,8 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
 // Sec. 2.3: the synchronised mother tile is upsampled by the 4th-order
 // interpolating prediction and split into 2^d children (one treecode digit
 // appended); children are placed in the new active list in Hilbert order.
-template <int D, int B, typename TS>
-__global__ void __launch_bounds__(256) k_refine(PoolView pv, TS* __restrict__ y) {
+template <int D, int B, typename TS, int NT>
+__global__ void __launch_bounds__(NT) k_refine(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
   Ring& R = *smem_as<Ring>(0);
   __shared__ int cslot[8];
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(256) k_refine(PoolView pv, TS* __restrict__ y)
     const TreeDev& td = pv.trees[b.tree];
     build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TS, TS>(pv, b, y, y, tile, false, R, cbox);
+    fill_tile<D, B, TS, TS, 1>(pv, b, y, y, tile, false, R, cbox);
     if (threadIdx.x == 0) {
       uint64_t key[8];
       int32_t cc[8][3];
@@ -291,8 +291,8 @@ struct DetGeo {
   static constexpr int NX = NC * B * (D == 3 ? NC : 1);
 };
 
-template <int D, int B, typename TS, typename TD>
-__global__ void __launch_bounds__(256) k_details(PoolView pv, TS* __restrict__ y) {
+template <int D, int B, typename TS, typename TD, int NT>
+__global__ void __launch_bounds__(NT) k_details(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
   using DG = DetGeo<D, B>;
   Ring& R = *smem_as<Ring>(0);
@@ -303,12 +303,28 @@ __global__ void __launch_bounds__(256) k_details(PoolView pv, TS* __restrict__ y
   X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(X) + 15) & ~(uintptr_t)15);
   const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
+  const bool all_blocks = pv.cnt->first_round != 0;
+  const int prev = pv.cnt->round_id - 1;
+  __shared__ int dirty;
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
     const TreeDev& td = pv.trees[b.tree];
     build_ring<D, B>(pv, td, b, R);
+    if (threadIdx.x == 0) dirty = all_blocks ? 1 : 0;
     __syncthreads();
-    fill_tile<D, B, TS, TS>(pv, b, y, y, tile, true, R, cbox);
+    if (!all_blocks && threadIdx.x < Gm::NR && R.slot[threadIdx.x] >= 0 &&
+        pv.stamp[R.slot[threadIdx.x]] == prev)
+      dirty = 1;
+    __syncthreads();
+    if (!dirty) {
+      // No leaf of the ring changed in the previous round: the synchronised
+      // tile, hence the details and norms stored for this block, are unchanged.
+      if (pv.norm_kind == 1 && threadIdx.x < nv)
+        atomic_max_pos(&pv.svar[b.tree * nv + threadIdx.x], pv.bmax[(int64_t)b.slot * nv + threadIdx.x]);
+      __syncthreads();
+      continue;
+    }
+    fill_tile<D, B, TS, TS, 2>(pv, b, y, y, tile, true, R, cbox);
     __syncthreads();
     for (int v = 0; v < nv; ++v) {
       const TS* tv = tile + v * Gm::TILE;
@@ -602,6 +618,7 @@ __global__ void k_refine_finalize(PoolView pv) {
   }
 }
 
+
 __device__ __forceinline__ bool same_family(const PoolView& pv, int s, int t) {
   if (pv.tree[s] != pv.tree[t] || pv.lvl[s] != pv.lvl[t]) return false;
   for (int a = 0; a < 3; ++a)
@@ -609,70 +626,82 @@ __device__ __forceinline__ bool same_family(const PoolView& pv, int s, int t) {
   return true;
 }
 
-// First flag pass: r = -1 if the block's largest normalised detail is below
-// eps (strict), it is above Jmin, all 2^d sisters are leaves, and no leaf one
-// level finer touches it (gradedness after the merge); else 0.
+// Flags of one coarsening round (Sec. 2.3), one warp per block.  A block
+// qualifies (-1) if its largest normalised detail is below eps (strict), it is
+// above Jmin, all 2^d sisters are leaves, and no leaf one level finer touches
+// it (gradedness after the merge).  A family coarsens (-2) only if all its
+// sisters qualify (completeness); this is the fixpoint of the paper's -2
+// assignment, reached here by evaluating the condition for the whole family.
+// Also emits the new-list counts (first member of a merged family hosts the
+// mother; other members free their slots).
 template <int D>
-__global__ void k_flag_a(PoolView pv) {
-  const int nact = pv.cnt->n_round;
+__device__ __forceinline__ bool qualifies(const PoolView& pv, const TreeDev& td, int s, int lane,
+                                          double* mdet_out) {
+  const BlockInfo b = load_block(pv, s);
   const int nv = pv.nvar;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
-    const BlockInfo b = load_block(pv, pv.act[p]);
-    const TreeDev& td = pv.trees[b.tree];
-    double m = 0.0;
-    bool nan = false;
-    for (int v = 0; v < nv; ++v) {
-      double sv = pv.svar[b.tree * nv + v];
-      if (sv == 0.0) sv = 1.0;
-      const double mv = pv.md[(int64_t)b.slot * nv + v];
-      nan |= isnan(mv);
-      m = fmax(m, mv / sv);
-    }
-    if (nan) {
-      m = __longlong_as_double(0x7ff8000000000000LL);
-      set_err(pv, kErrNaN);
-    }
-    pv.mdet[b.slot] = m;
-    bool ok = (m < td.eps) && b.lvl > td.Jmin;
-    for (int ch = 0; ok && ch < (1 << D); ++ch) {
+  double m = 0.0;
+  bool nan = false;
+  for (int v = 0; v < nv; ++v) {
+    double sv = pv.svar[b.tree * nv + v];
+    if (sv == 0.0) sv = 1.0;
+    const double mv = pv.md[(int64_t)s * nv + v];
+    nan |= isnan(mv);
+    m = fmax(m, mv / sv);
+  }
+  if (nan) m = __longlong_as_double(0x7ff8000000000000LL);
+  if (mdet_out) *mdet_out = m;
+  bool ok = (m < td.eps) && b.lvl > td.Jmin;
+  // lanes: 0..2^d-1 sisters, then the ring cells outside the block
+  constexpr int NR = D == 3 ? 64 : 16;
+  bool fail = false;
+  for (int r = lane; r < (1 << D) + NR; r += 32) {
+    if (r < (1 << D)) {
       int64_t c[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((ch >> a) & 1);
-      ok &= tab_get<D>(pv, td, b.lvl, c) >= 0;
-    }
-    constexpr int NR = D == 3 ? 64 : 16;
-    for (int r = 0; ok && r < NR; ++r) {
-      const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
+      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((r >> a) & 1);
+      fail |= tab_get<D>(pv, td, b.lvl, c) < 0;
+    } else {
+      const int q = r - (1 << D);
+      const int qq[3] = {q % 4 - 1, (q / 4) % 4 - 1, q / 16 - 1};
       bool inside = true;
       int64_t cell[3] = {0, 0, 0};
       for (int a = 0; a < D; ++a) {
-        inside &= (q[a] == 0 || q[a] == 1);
-        cell[a] = 2 * b.c[a] + q[a];
+        inside &= (qq[a] == 0 || qq[a] == 1);
+        cell[a] = 2 * b.c[a] + qq[a];
       }
-      if (!inside && tab_get<D>(pv, td, b.lvl + 1, cell) >= 0) ok = false;
+      if (!inside) fail |= tab_get<D>(pv, td, b.lvl + 1, cell) >= 0;
     }
-    pv.f1[b.slot] = ok ? -1 : 0;
   }
+  fail = __any_sync(0xffffffffu, fail);
+  return ok && !fail;
 }
 
-// Second flag pass: completeness — a family coarsens only if every sister kept
-// -1 (the fixpoint of the paper's -2 assignment).  Emits the new-list counts.
 template <int D>
-__global__ void k_flag_b(PoolView pv) {
+__global__ void k_flags(PoolView pv) {
   const int nact = pv.cnt->n_round;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
-    const BlockInfo b = load_block(pv, pv.act[p]);
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int p = blockIdx.x * wpb + (threadIdx.x >> 5); p < nact; p += gridDim.x * wpb) {
+    const int s = pv.act[p];
+    const BlockInfo b = load_block(pv, s);
     const TreeDev& td = pv.trees[b.tree];
-    bool all = pv.f1[b.slot] == -1;
+    double m = 0.0;
+    bool all = qualifies<D>(pv, td, s, lane, &m);
+    if (lane == 0) {
+      pv.mdet[s] = m;
+      if (isnan(m)) set_err(pv, kErrNaN);
+    }
     for (int ch = 0; all && ch < (1 << D); ++ch) {
       int64_t c[3] = {0, 0, 0};
       for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((ch >> a) & 1);
-      const int s = tab_get<D>(pv, td, b.lvl, c);
-      all &= s >= 0 && pv.f1[s] == -1;
+      const int t = tab_get<D>(pv, td, b.lvl, c);
+      if (t != s) all = t >= 0 && qualifies<D>(pv, td, t, lane, nullptr);
     }
-    pv.flag[b.slot] = all ? -2 : 0;
-    const bool first = all && (p == 0 || !same_family(pv, b.slot, pv.act[p - 1]));
-    pv.emit[2 * p] = (!all || first) ? 1 : 0;
-    pv.emit[2 * p + 1] = (all && !first) ? 1 : 0;
+    if (lane == 0) {
+      pv.flag[s] = all ? -2 : 0;
+      const bool first = all && (p == 0 || !same_family(pv, s, pv.act[p - 1]));
+      pv.emit[2 * p] = (!all || first) ? 1 : 0;
+      pv.emit[2 * p + 1] = (all && !first) ? 1 : 0;
+    }
   }
 }
 
@@ -689,6 +718,7 @@ __global__ void k_coarsen_finalize(PoolView pv) {
     if (pv.emit[2 * p]) {
       int64_t pc[3] = {b.c[0] >> 1, b.c[1] >> 1, b.c[2] >> 1};
       pv.tab[td.tab_off[b.lvl - 1] + (int64_t)morton<D>(pc, b.lvl - 1)] = s;
+      pv.stamp[s] = pv.cnt->round_id;
       pv.lvl[s] = (int8_t)(b.lvl - 1);
       int32_t c32[3] = {(int32_t)pc[0], (int32_t)pc[1], (int32_t)pc[2]};
       for (int a = 0; a < 3; ++a) pv.crd[3 * s + a] = c32[a];

@@ -1,6 +1,7 @@
 // Host-side launchers of the kernel templates, dispatched over block size and
 // precision.  Included once per dimension (mr_k2.cu, mr_k3.cu).
 #pragma once
+#include <algorithm>
 #include <cstdio>
 
 #include "mr_kernels.cuh"
@@ -28,21 +29,25 @@ static inline int flat_grid(const PoolView& pv, int threads) {
 }
 
 // ---------------------------------------------------------------- stage ------
+// 2D blocks of 17^2 nodes: 128-thread CTAs, so small grids run in one wave.
+template <int D, int B>
+struct Threads { static constexpr int value = (D == 2 && B == 17) ? 128 : 256; };
+
 template <int D, int B, int RHS, typename TS, typename TY>
 static void stage_impl(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
                        const LaunchCfg& lc, cudaStream_t st) {
-  constexpr int threads = 256;
+  constexpr int threads = Threads<D, B>::value;
   const int nv = 1;
   const size_t smem = kRingBytes + sizeof(TY) * nv * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
   TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
   if (stage == 0) {
-    auto k = k_stage_adv<D, B, RHS, TS, TY, TS>;
+    auto k = k_stage_adv<D, B, RHS, TS, TY, TS, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
     k<<<grid, threads, smem, st>>>(pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
   } else {
     const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
-    auto k = k_stage_adv<D, B, RHS, TS, TY, TY>;
+    auto k = k_stage_adv<D, B, RHS, TS, TY, TY, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
     k<<<grid, threads, smem, st>>>(pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
@@ -136,9 +141,9 @@ static void dispatch_bs(const PoolView& pv, A&&... args) {
 template <int D, int B, typename TS>
 struct RefineRun {
   static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
-    constexpr int threads = 256;
+    constexpr int threads = Threads<D, B>::value;
     const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
-    auto k = k_refine<D, B, TS>;
+    auto k = k_refine<D, B, TS, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
     k<<<grid, threads, smem, st>>>(pv, (TS*)f.y);
@@ -183,16 +188,16 @@ template <int D, int B, typename TS>
 struct DetailsRun {
   static void run(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
                   cudaStream_t st) {
-    constexpr int threads = 256;
+    constexpr int threads = Threads<D, B>::value;
     const bool d64 = fp64 || sizeof(TS) == 8;
     const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX) + 32 +
                         (d64 ? 8 : sizeof(TS)) * DetGeo<D, B>::NX;
     if (d64) {
-      auto k = k_details<D, B, TS, double>;
+      auto k = k_details<D, B, TS, double, threads>;
       prep_smem(k, smem);
       k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
     } else {
-      auto k = k_details<D, B, TS, TS>;
+      auto k = k_details<D, B, TS, TS, threads>;
       prep_smem(k, smem);
       k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
     }
@@ -218,9 +223,8 @@ void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool m
   k_round_begin<<<1, 256, 0, st>>>(pv.cnt, pv.svar, pv.ntrees * pv.nvar, pv.norm_kind == 1 ? 0.0 : 1.0);
   count_launch();
   dispatch_bs<D, DetailsRun>(pv, f, fp64, lc, st);
-  k_flag_a<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
-  k_flag_b<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
-  count_launch(2);
+  k_flags<D><<<(int)std::min<int64_t>(4096, (pv.cap + 7) / 8), 256, 0, st>>>(pv);
+  count_launch();
   if (!merge) return;
   launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st);
   dispatch_bs<D, CoarsenRun>(pv, f, lc, st);

@@ -115,6 +115,7 @@ __global__ void k_refine_counters(Counters* c, int nch) {
 }
 
 __global__ void k_coarsen_counters(Counters* c, int nch) {
+  c->first_round = 0;
   if (c->done) return;
   c->merged = (c->n_act - c->n_new) / (nch - 1);
   c->n_free = c->n_free + c->n_alloc;
@@ -125,7 +126,10 @@ __global__ void k_coarsen_counters(Counters* c, int nch) {
 // Start of a coarsening round: the round works on all blocks unless an earlier
 // round of this step merged nothing (then every kernel of the round is empty).
 __global__ void k_round_begin(Counters* c, double* svar, int n, double v) {
-  if (threadIdx.x == 0) c->n_round = c->done ? 0 : c->n_act;
+  if (threadIdx.x == 0) {
+    c->n_round = c->done ? 0 : c->n_act;
+    c->round_id += 1;
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) svar[i] = v;
 }
 
@@ -133,6 +137,8 @@ __global__ void k_round_begin(Counters* c, double* svar, int n, double v) {
 // number of blocks of the adapted grid the step starts from.
 __global__ void k_step_begin(Counters* c, int32_t* hist) {
   c->done = 0;
+  c->rounds = 0;
+  c->first_round = 1;
   if (hist && c->hist_n < kMaxHist) hist[c->hist_n++] = c->n_act;
 }
 
@@ -148,6 +154,13 @@ __global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int 
   T.cy[0] = h / 2.0; T.cy[1] = h / 2.0; T.cy[2] = h; T.cy[3] = 0.0;
   for (int s = 0; s < 4; ++s) T.ct[s] = swirl ? cos(M_PI * ts[s] / trees[k].rhs[0]) : 0.0;
 }
+// End of a coarsening round inside a graph while-node: run another round while
+// the last one merged a family and fewer than max_rounds ran.
+__global__ void k_round_continue(Counters* c, cudaGraphConditionalHandle h, int max_rounds) {
+  c->rounds += 1;
+  cudaGraphSetConditional(h, (!c->done && c->rounds < max_rounds) ? 1u : 0u);
+}
+
 __global__ void k_time_advance(TreeTime* tt, int ntrees) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < ntrees) tt[k].t = tt[k].t + tt[k].dt;

@@ -293,6 +293,7 @@ def test_graph_steps_equal_eager_steps(mr):
     assert abs(b.get_time()[0] - t) <= 1e-15
     hist = b.step_history()
     assert len(hist) == 6 and hist[0] > 0
+    assert b.graph_mode() in ("while-node", "fixed-rounds")
 
 
 def test_forest_trees_are_independent_and_match_oracle(mr, oracle_mod):

@@ -79,3 +79,29 @@ def test_learned_proposal_gain_over_refine_all(mr):
     assert ratio < 0.8, (ratio, pl)
     assert e1["l2"] <= 1.1 * e0["l2"] + 1e-5, (e0, e1)
     assert pl["network"] > 0 and pl["misses"] < pf["misses"], (pl, pf)
+
+
+def test_learned_graph_steps_equal_eager_steps(mr):
+    # The captured step runs the proposal, its closure (fixed passes) and the
+    # judge on the device: same grid, fields and counters as host-driven steps.
+    params = synthetic.cnn_init_params(cnn.SHAPES, seed=7)
+    tree = dict(Jmin=2, Jmax=6, eps=1e-4, ic="gauss", ic_params=(0.4, 0.6, 0.0, 0.04),
+                rhs_params=(1.0, 0.5, 0.0))
+    dt = 0.5 / (16 * 64) / math.hypot(1.0, 0.5)
+    runs = []
+    for graph in (False, True):
+        g = mr.Forest(dim=2, precision="fp32", detail_fp64=True, trees=[tree], capacity=40000)
+        g.init_tree()
+        g.proposal_set(params, 0.5)
+        g.set_refine_mode("learned")
+        if graph:
+            g.set_time(0.0, dt)
+            g.step_graph(12)
+        else:
+            for s in range(12):
+                g.step(s * dt, dt)
+        info, f = g.get_blocks()
+        runs.append((info, f, g.proposal_stats()))
+    (ia, fa, sa), (ib, fb, sb) = runs
+    assert np.array_equal(ia, ib) and np.array_equal(fa, fb)
+    assert sa == sb and sa["considered"] > 0, (sa, sb)
