@@ -5,7 +5,7 @@ are sum over the blocks of the adapted grid G (before the safety refinement) of
 Bs^d, times 4 stages; the time is the whole mr_step (refine-all, 4 x (ghost
 sync + RK stage), coarsening rounds, tree rebuild).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload adv3d|swirl|adv2d]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload swirl|adv3d|adv2d|forest|ns]
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
 
 Prints one JSON line on rank 0.
@@ -112,25 +112,51 @@ class Clocks:
         self.proc = None
 
     def __enter__(self):
+        # Sampling starts before the timed region; the first sample is awaited
+        # so that the sampler is running when the region begins.
+        import threading
+        self.lines = []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return self
+        first = threading.Event()
+
+        def reader():
+            for l in self.proc.stdout:
+                if l.strip():
+                    self.lines.append((time.perf_counter(), l))
+                    first.set()
+            first.set()
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        first.wait(10.0)
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.proc:
+            self.t1 = time.perf_counter()
+            time.sleep(0.05)  # one more sample after the region
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out = ""
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.thread.join(timeout=5)
+        # samples taken inside the region, else the ones bracketing it
+        inside = [l for (t, l) in self.lines if self.t0 <= t <= self.t1] if self.proc else []
+        if not inside and self.proc:
+            before = [l for (t, l) in self.lines if t < self.t0][-1:]
+            after = [l for (t, l) in self.lines if t > self.t1][:1]
+            inside = before + after
+            self.bracketed = True
+        self.lines = inside
 
     def summary(self):
         sm, mx, reasons = [], None, set()
@@ -150,8 +176,11 @@ class Clocks:
         if not sm:
             return None
         sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        if getattr(self, "bracketed", False):
+            out["note"] = "region shorter than the sampling interval: samples just before and after it"
+        return out
 
 
 def oracle_sample(w, seconds_target=15.0):
@@ -224,8 +253,8 @@ def dts_of(w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="swirl", choices=sorted(WORKLOADS))
     ap.add_argument("--capacity", type=int, default=0)
     ap.add_argument("--eps", type=float, default=0.0)
@@ -240,6 +269,7 @@ def main():
     ap.add_argument("--load-state", default="", help="start from a saved state instead of init + spin-up")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="ns: refine all instead of the learned proposal")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -271,8 +301,9 @@ def main():
     trees = trees_of(w)
     nt = len(trees)
     # Independent replicas per rank (trees never exchange data): weak scaling.
-    g = mr.Forest(dim=w["dim"], Bs=w["Bs"], precision=w["precision"], detail_fp64=w["detail_fp64"],
-                  rhs=w["rhs"], trees=trees, capacity=w["capacity"], stream=stream.cuda_stream)
+    g = mr.Forest(dim=w["dim"], Bs=w["Bs"], nvar=w.get("nvar", 1), precision=w["precision"],
+                  detail_fp64=w["detail_fp64"], rhs=w["rhs"], trees=trees, capacity=w["capacity"],
+                  norm_kind=w.get("norm_kind", 0), stream=stream.cuda_stream)
     B, d = w["Bs"], w["dim"]
     npts = B ** d
     dts = np.array(dts_of(w))
@@ -298,6 +329,34 @@ def main():
         t = z["t"].copy()
         steps_done = int(z["steps_done"])
         spin = 0
+    learned = None
+    if w.get("learned") and not args.no_learned:
+        # Train the proposal network on this run's own decisions: refine-all
+        # steps record (tile features, was the refinement needed) pairs, then
+        # the network is trained by the library's forward/backward/Adam kernels.
+        import synthetic as inputs
+        L = w["learned"]
+        t0 = time.perf_counter()
+        g.proposal_collect(True, 200_000)
+        for _ in range(L["collect_steps"]):
+            g.step(t, dts)
+            t = t + dts
+        steps_done += L["collect_steps"]
+        nsamp, npos = g.proposal_dataset()
+        init = inputs.cnn_init_params(mr.Forest.CNN_SHAPES, seed=20190201)
+        g.proposal_collect(False)
+        try:
+            tau, loss = g.proposal_train(init, epochs=L["epochs"], batch=256, lr=1e-3, w_pos=0.0,
+                                         recall=0.999, holdout=0.2)
+        except mr.MRError as e:  # e.g. no positive sample: the step stays refine-all
+            learned = {"collect_steps": L["collect_steps"], "samples": nsamp, "positives": npos,
+                       "not_trained": str(e)}
+        else:
+            g.set_refine_mode("learned")
+            g.proposal_stats(reset=True)
+            learned = {"collect_steps": L["collect_steps"], "samples": nsamp, "positives": npos,
+                       "epochs": L["epochs"], "tau": tau, "final_loss": loss,
+                       "setup_s": time.perf_counter() - t0}
     if graph:
         g.set_time(t, dts)
         autotune = args.autotune if args.autotune >= 0 else (3 if "trees" in w else 0)
@@ -359,6 +418,32 @@ def main():
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
     ms_max = float(ms_t.item())
     value = points * world / (ms_max / 1e3)
+
+    if learned is not None and "tau" in learned:
+        learned["timed_region"] = g.proposal_stats(reset=True)
+        learned["stage_blocks_per_step"] = st["stage_blocks"] / args.steps
+        if graph:
+            # The same state advanced by refine-all steps: the work and time the
+            # proposal saves (untimed for the metric).
+            k3 = 5
+            g.set_refine_mode("all")
+            g.step_graph(1)
+            g.reset_stats()
+            g.step_history(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g.step_graph(k3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms3 = e0.elapsed_time(e1)
+            h3 = g.step_history(reset=True)
+            st3 = g.stats()
+            learned["refine_all_same_state"] = {
+                "steps": k3, "ms_per_step": ms3 / k3, "stage_blocks_per_step": st3["stage_blocks"] / k3,
+                "value": int(h3.astype(np.int64).sum()) * npts * 4 / (ms3 / 1e3)}
+            g.set_refine_mode("learned")
+            steps_done += k3 + 1
 
     # Roofline of the dominant kernel (RK stage): algorithmic bytes / stage time.
     # The stage time comes from CUDA events around the RK phase in a separate
@@ -460,10 +545,12 @@ def main():
                        "l2_rel_error": None if err is None else err["l2"],
                        "linf_rel_error": None if err is None else err["linf"],
                        "error_at_t": None if err is None else (w.get("full_time") if full else float(tnow[0])),
-                       "phase_ms_eager_probe": st["ms"]},
+                       "phase_ms_eager_probe": st["ms"],
+                       "learned_proposal": learned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_stage_adv (RK stage incl. fused ghost gather)",
+                         "kernel": "%s (RK stage incl. fused ghost gather)" % (
+                             "k_stage_ns" if w["rhs"] == "ns" else "k_stage_adv"),
                          "stage_launch_us": per_launch_us,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "gpu_launches": launches,

@@ -36,6 +36,7 @@ struct mr_ctx_s {
   int8_t *lvl = nullptr, *f1 = nullptr, *flag = nullptr, *mask = nullptr;
   int16_t* tree = nullptr;
   int32_t* stamp = nullptr;
+  int32_t* plan = nullptr;  // S x 32: stage plans of the active blocks
   int32_t *crd = nullptr, *act = nullptr, *act_next = nullptr, *freelist = nullptr, *tab = nullptr,
           *cells = nullptr, *emit = nullptr, *eoff = nullptr, *partial = nullptr, *pos = nullptr;
   uint64_t* hkey = nullptr;
@@ -123,6 +124,7 @@ PoolView view(mr_ctx c) {
   v.act_next = c->act_next; v.freelist = c->freelist; v.tab = c->tab; v.lat = c->lat;
   v.svar = c->svar; v.cells = c->cells; v.emit = c->emit; v.eoff = c->eoff;
   v.partial = c->partial; v.pos_of_slot = c->pos; v.cnt = c->cnt; v.stamp = c->stamp;
+  v.plan = c->plan;
   return v;
 }
 Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb}; }
@@ -398,6 +400,7 @@ mr_status rk_step(mr_ctx ctx, const double* t, const double* dt) {
   ctx->stats.stage_launches += 4;
   PoolView pv = view(ctx);
   const Fields f = fields(ctx);
+  by_dim(ctx, [&] { launch_plan<2>(pv, ctx->lc, ctx->st); }, [&] { launch_plan<3>(pv, ctx->lc, ctx->st); });
   for (int s = 0; s < 4; ++s) {
     StageArgs sa;
     std::memset(&sa, 0, sizeof(sa));
@@ -599,6 +602,7 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if ((e = dalloc(ctx, &ctx->pos, S))) return e;
     if ((e = dalloc(ctx, &ctx->stamp, S))) return e;
     if ((e = cudaMemset(ctx->stamp, 0, S * 4))) return e;
+    if ((e = dalloc(ctx, &ctx->plan, S * 32))) return e;
     if ((e = dalloc(ctx, &ctx->tab, ctx->ntab))) return e;
     if ((e = dalloc(ctx, &ctx->cells, 2 * ctx->ncells))) return e;
     if ((e = dalloc(ctx, &ctx->emit, 2 * ctx->nscan))) return e;
@@ -949,6 +953,7 @@ void enqueue_graph_prologue(mr_ctx ctx, cudaStream_t st) {
   }
   by_dim(ctx, [&] { launch_refine<2>(pv, f, mode, ctx->mask, ctx->lc, st); },
          [&] { launch_refine<3>(pv, f, mode, ctx->mask, ctx->lc, st); });
+  by_dim(ctx, [&] { launch_plan<2>(pv, ctx->lc, st); }, [&] { launch_plan<3>(pv, ctx->lc, st); });
   StageArgs sa;
   std::memset(&sa, 0, sizeof(sa));
   for (int s = 0; s < 4; ++s)

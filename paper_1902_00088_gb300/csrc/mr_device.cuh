@@ -359,37 +359,54 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
                           bool commit, const Ring& R, TT* cbox) {
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, W>;
+  // Each thread takes U points at a time: owners and addresses first, then the
+  // U loads together, then the stores, so that the loads are in flight at once.
+  constexpr int U = 4;
   const int nv = pv.nvar;
   const int64_t own = (int64_t)b.slot * nv * pv.vs;
   if (!R.mixed) {
     // every ring leaf has the block's level: the owner of a point is the ring
     // cell holding it from below (equal-level rule of owner()), no search
     constexpr int P = Log2B<B>::value;
-    for (int q = threadIdx.x; q < Bx::NPTS; q += blockDim.x) {
-      const int i = q % Bx::S - W;
-      const int j = (q / Bx::S) % Bx::S - W;
-      const int k = D == 3 ? q / (Bx::S * Bx::S) - W : 0;
-      const int idx = Gm::tix(i, j, k);
-      const int h[3] = {2 * i, 2 * j, 2 * k};
-      int r = 0, li[3] = {0, 0, 0};
+    for (int q0 = threadIdx.x; q0 < Bx::NPTS; q0 += U * blockDim.x) {
+      int64_t at[U];
+      int idx[U], li[U];
+      bool ok[U], ed[U];
 #pragma unroll
-      for (int a = 0; a < D; ++a) r += ((h[a] >> P) + 1) << (2 * a);
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * blockDim.x;
+        ok[u] = q < Bx::NPTS;
+        const int qq = ok[u] ? q : 0;
+        const int i = qq % Bx::S - W;
+        const int j = (qq / Bx::S) % Bx::S - W;
+        const int k = D == 3 ? qq / (Bx::S * Bx::S) - W : 0;
+        idx[u] = Gm::tix(i, j, k);
+        li[u] = Gm::lin(i, j, k);
+        const int h[3] = {2 * i, 2 * j, 2 * k};
+        int r = 0, lo[3] = {0, 0, 0};
 #pragma unroll
-      for (int a = 0; a < D; ++a) li[a] = (h[a] - R.org[r][a]) >> 1;
-      const int src = R.slot[r];
-      const int64_t at = (int64_t)src * nv * pv.vs + Gm::lin(li[0], li[1], li[2]);
-      const bool mine = src == b.slot;
+        for (int a = 0; a < D; ++a) r += ((h[a] >> P) + 1) << (2 * a);
+#pragma unroll
+        for (int a = 0; a < D; ++a) lo[a] = (h[a] - R.org[r][a]) >> 1;
+        const int src = R.slot[r];
+        at[u] = (int64_t)src * nv * pv.vs + Gm::lin(lo[0], lo[1], lo[2]);
+        // block-edge node owned by the equal-level neighbour (i or j = B-1)
+        bool edge_node = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a) edge_node &= (h[a] >= 0 && h[a] <= 2 * (B - 1));
+        ed[u] = commit && src != b.slot && edge_node;
+      }
       for (int v = 0; v < nv; ++v) {
-        const TF val = F[at + (int64_t)v * pv.vs];
-        tile[v * Gm::TILE + idx] = (TT)val;
-        if (commit && !mine) {
-          // block-edge node owned by the equal-level neighbour (i or j = B-1)
-          bool edge_node = true;
+        TF val[U];
 #pragma unroll
-          for (int a = 0; a < D; ++a) edge_node &= (h[a] >= 0 && h[a] <= 2 * (B - 1));
-          if (edge_node) {
-            const int64_t me = own + (int64_t)v * pv.vs + Gm::lin(i, j, k);
-            if (F[me] != val) Fw[me] = val;
+        for (int u = 0; u < U; ++u) val[u] = ok[u] ? F[at[u] + (int64_t)v * pv.vs] : TF(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (!ok[u]) continue;
+          tile[v * Gm::TILE + idx[u]] = (TT)val[u];
+          if (ed[u]) {
+            const int64_t me = own + (int64_t)v * pv.vs + li[u];
+            if (F[me] != val[u]) Fw[me] = val[u];
           }
         }
       }
@@ -397,69 +414,207 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
     return;
   }
   if (R.coarser) {
-    for (int idx = threadIdx.x; idx < Bx::CBOX; idx += blockDim.x) {
-      const int n[3] = {idx % Bx::CB + Bx::CLO, (idx / Bx::CB) % Bx::CB + Bx::CLO,
-                        D == 3 ? idx / (Bx::CB * Bx::CB) + Bx::CLO : 0};
-      const int h[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
-      Own o;
-      if (!owner<D, B>(b, h, 0, R, o) || o.m < b.lvl - 1) {
-        set_err(pv, kErrGraded);
-        for (int v = 0; v < nv; ++v) cbox[v * Bx::CBOX + idx] = TT(0);
-        continue;
+    for (int q0 = threadIdx.x; q0 < Bx::CBOX; q0 += U * blockDim.x) {
+      int64_t at[U];
+      bool ok[U], good[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = q0 + u * blockDim.x;
+        ok[u] = idx < Bx::CBOX;
+        good[u] = false;
+        at[u] = 0;
+        if (!ok[u]) continue;
+        const int n[3] = {idx % Bx::CB + Bx::CLO, (idx / Bx::CB) % Bx::CB + Bx::CLO,
+                          D == 3 ? idx / (Bx::CB * Bx::CB) + Bx::CLO : 0};
+        const int h[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
+        Own o;
+        if (!owner<D, B>(b, h, 0, R, o) || o.m < b.lvl - 1) {
+          set_err(pv, kErrGraded);
+          continue;
+        }
+        good[u] = true;
+        const int sh = b.lvl + 1 - o.m;
+        at[u] = ((int64_t)o.slot * nv) * pv.vs +
+                Gm::lin(o.off[0] >> sh, o.off[1] >> sh, D == 3 ? o.off[2] >> sh : 0);
       }
-      const int sh = b.lvl + 1 - o.m;
-      const int li[3] = {o.off[0] >> sh, o.off[1] >> sh, o.off[2] >> sh};
-      for (int v = 0; v < nv; ++v) cbox[v * Bx::CBOX + idx] = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
+      for (int v = 0; v < nv; ++v) {
+        TF val[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) val[u] = good[u] ? F[at[u] + (int64_t)v * pv.vs] : TF(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) cbox[v * Bx::CBOX + q0 + u * blockDim.x] = good[u] ? (TT)val[u] : TT(0);
+      }
     }
     __syncthreads();
   }
-  for (int q = threadIdx.x; q < Bx::NPTS; q += blockDim.x) {
-    const int i = q % Bx::S - W;
-    const int j = (q / Bx::S) % Bx::S - W;
-    const int k = D == 3 ? q / (Bx::S * Bx::S) - W : 0;
-    const int idx = Gm::tix(i, j, k);
-    const int ijk[3] = {i, j, k};
-    bool ghost = false, edge = false;
+  // kinds of tile points: 0 own node, 1 block-edge node of another owner,
+  // 2 ghost node that is a node of its owner, 3 ghost predicted from the coarse
+  // box, 4 no owner (error, zero)
+  for (int q0 = threadIdx.x; q0 < Bx::NPTS; q0 += U * blockDim.x) {
+    int64_t at[U];
+    int idx[U], li[U], kind[U], ijk[U][3];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      if (ijk[a] < 0 || ijk[a] > B - 1) ghost = true;
-      else if (ijk[a] == 0 || ijk[a] == B - 1) edge = true;
-    }
-    const int h[3] = {2 * i, 2 * j, 2 * k};
-    if (!ghost) {
-      const int64_t at = Gm::lin(i, j, k);
-      Own o;
-      const bool over = edge && owner<D, B>(b, h, b.lvl, R, o) && o.slot != b.slot;
-      for (int v = 0; v < nv; ++v) {
-        TF val;
-        if (over) {
-          const int shv = b.lvl + 1 - o.m;
-          const int li[3] = {o.off[0] >> shv, o.off[1] >> shv, o.off[2] >> shv};
-          val = pool_at<D, B>(pv, F, o.slot, v, li);
-          if (commit && F[own + (int64_t)v * pv.vs + at] != val) Fw[own + (int64_t)v * pv.vs + at] = val;
-        } else {
-          val = F[own + (int64_t)v * pv.vs + at];
-        }
-        tile[v * Gm::TILE + idx] = (TT)val;
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * blockDim.x;
+      const int qq = q < Bx::NPTS ? q : 0;
+      const int i = qq % Bx::S - W;
+      const int j = (qq / Bx::S) % Bx::S - W;
+      const int k = D == 3 ? qq / (Bx::S * Bx::S) - W : 0;
+      ijk[u][0] = i;
+      ijk[u][1] = j;
+      ijk[u][2] = k;
+      idx[u] = Gm::tix(i, j, k);
+      li[u] = Gm::lin(i, j, k);
+      at[u] = 0;
+      kind[u] = 5;  // past the end
+      if (q >= Bx::NPTS) continue;
+      bool ghost = false, edge = false;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int x = ijk[u][a];
+        if (x < 0 || x > B - 1) ghost = true;
+        else if (x == 0 || x == B - 1) edge = true;
       }
-      continue;
-    }
-    Own o;
-    if (!owner<D, B>(b, h, 0, R, o)) {
-      set_err(pv, kErrGraded);
-      for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = TT(0);
-      continue;
-    }
-    const int sh = b.lvl + 1 - o.m;
-    bool node = true;
+      const int h[3] = {2 * i, 2 * j, 2 * k};
+      Own o;
+      if (!ghost) {
+        if (edge && owner<D, B>(b, h, b.lvl, R, o) && o.slot != b.slot) {
+          const int shv = b.lvl + 1 - o.m;
+          kind[u] = 1;
+          at[u] = ((int64_t)o.slot * nv) * pv.vs +
+                  Gm::lin(o.off[0] >> shv, o.off[1] >> shv, D == 3 ? o.off[2] >> shv : 0);
+        } else {
+          kind[u] = 0;
+          at[u] = own + li[u];
+        }
+        continue;
+      }
+      if (!owner<D, B>(b, h, 0, R, o)) {
+        set_err(pv, kErrGraded);
+        kind[u] = 4;
+        continue;
+      }
+      const int sh = b.lvl + 1 - o.m;
+      bool node = true;
 #pragma unroll
-    for (int a = 0; a < D; ++a) node &= (o.off[a] & ((1 << sh) - 1)) == 0;
-    if (o.m >= b.lvl || node) {
-      const int li[3] = {o.off[0] >> sh, o.off[1] >> sh, o.off[2] >> sh};
-      for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = (TT)pool_at<D, B>(pv, F, o.slot, v, li);
-    } else {
-      if (o.m != b.lvl - 1) set_err(pv, kErrGraded);
-      for (int v = 0; v < nv; ++v) tile[v * Gm::TILE + idx] = predict_box<D, B, W, TT>(cbox + v * Bx::CBOX, ijk);
+      for (int a = 0; a < D; ++a) node &= (o.off[a] & ((1 << sh) - 1)) == 0;
+      if (o.m >= b.lvl || node) {
+        kind[u] = 2;
+        at[u] = ((int64_t)o.slot * nv) * pv.vs +
+                Gm::lin(o.off[0] >> sh, o.off[1] >> sh, D == 3 ? o.off[2] >> sh : 0);
+      } else {
+        if (o.m != b.lvl - 1) set_err(pv, kErrGraded);
+        kind[u] = 3;
+      }
+    }
+    for (int v = 0; v < nv; ++v) {
+      TF val[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) val[u] = kind[u] <= 2 ? F[at[u] + (int64_t)v * pv.vs] : TF(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (kind[u] == 5) continue;
+        TT* t = tile + v * Gm::TILE + idx[u];
+        if (kind[u] == 3) {
+          *t = predict_box<D, B, W, TT>(cbox + v * Bx::CBOX, ijk[u]);
+        } else if (kind[u] == 4) {
+          *t = TT(0);
+        } else {
+          *t = (TT)val[u];
+          if (kind[u] == 1 && commit) {
+            const int64_t me = own + (int64_t)v * pv.vs + li[u];
+            if (F[me] != val[u]) Fw[me] = val[u];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Stage plan of one active block, valid while the tree is fixed (the four RK
+// stages of a step): INTS int32 per active position,
+//   [0] slot, [1] level | tree << 8 | uniform << 30, [2 .. 2+D) block coordinates,
+//   [2+D .. 2+D+NB) slots of the 3^d blocks at offsets (dx, dy, dz) in {-1,0,1}^d
+//   (x fastest), the centre being the block itself.
+// "uniform": every one of them is a leaf at the block's level, so each node of
+// the ghost layer and each block-edge node has an equal-level owner, the block
+// that holds it at its lower edge (Sec. 2.2, Sec. 2.5).
+template <int D>
+struct Plan {
+  static constexpr int NB = D == 3 ? 27 : 9;
+  static constexpr int INTS = D == 3 ? 32 : 16;
+  static constexpr int NBO = 2 + D;  // offset of the neighbour slots
+};
+
+template <int D>
+__device__ __forceinline__ BlockInfo plan_block(const int32_t* pl) {
+  BlockInfo b;
+  b.slot = pl[0];
+  b.lvl = pl[1] & 255;
+  b.tree = (pl[1] >> 8) & 0xffff;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) b.c[a] = a < D ? pl[2 + a] : 0;
+  return b;
+}
+
+// Ghost gather for a block with a uniform neighbourhood: node i of an axis
+// comes from the left neighbour (i < 0, local i + B - 1), the block itself
+// (0 <= i <= B - 2) or the right neighbour (i >= B - 1, local i - (B - 1));
+// the tile box of width W is filled (NV variables, TF -> TT).  Loads are issued
+// U at a time before their stores so that they are in flight together.  With
+// commit, block-edge nodes taken from a neighbour are written back into Fw
+// where they differ (the neighbour owns them).
+template <int D, int B, int W, int NV, typename TF, typename TT>
+__device__ __forceinline__ void gather_uniform(const PoolView& pv, const BlockInfo& b, const int32_t* nb,
+                                               const TF* F, TF* Fw, TT* tile, bool commit) {
+  using Gm = Geo<D, B>;
+  using Bx = Box<D, B, W>;
+  constexpr int U = 4;
+  const int64_t own = (int64_t)b.slot * NV * pv.vs;
+  for (int q0 = threadIdx.x; q0 < Bx::NPTS; q0 += U * blockDim.x) {
+    int64_t at[U];
+    int idx[U], li[U];
+    bool ok[U], ed[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * blockDim.x;
+      ok[u] = q < Bx::NPTS;
+      const int qq = ok[u] ? q : 0;
+      const int ijk[3] = {qq % Bx::S - W, (qq / Bx::S) % Bx::S - W, D == 3 ? qq / (Bx::S * Bx::S) - W : 0};
+      int n = 0, mul = 1, l3[3] = {0, 0, 0};
+      bool inner = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int x = ijk[a];
+        const int s = x < 0 ? 0 : (x <= B - 2 ? 1 : 2);
+        l3[a] = x - (s - 1) * (B - 1);
+        n += s * mul;
+        mul *= 3;
+        inner &= (x >= 0 && x <= B - 1);
+      }
+      const int slot = nb[n];
+      at[u] = (int64_t)slot * NV * pv.vs + Gm::lin(l3[0], l3[1], l3[2]);
+      idx[u] = Gm::tix(ijk[0], ijk[1], ijk[2]);
+      li[u] = Gm::lin(ijk[0], ijk[1], ijk[2]);
+      ed[u] = commit && inner && slot != b.slot;
+    }
+    TF v[U][NV];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int w = 0; w < NV; ++w) v[u][w] = ok[u] ? F[at[u] + (int64_t)w * pv.vs] : TF(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+#pragma unroll
+      for (int w = 0; w < NV; ++w) {
+        tile[w * Gm::TILE + idx[u]] = (TT)v[u][w];
+        if (ed[u]) {
+          const int64_t me = own + (int64_t)w * pv.vs + li[u];
+          if (F[me] != v[u][w]) Fw[me] = v[u][w];
+        }
+      }
     }
   }
 }

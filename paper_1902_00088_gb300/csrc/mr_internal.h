@@ -103,6 +103,7 @@ struct PoolView {
   int32_t* partial;        // scan partials
   int32_t* pos_of_slot;
   int32_t* stamp;          // per slot: round_id of the round that created the block (merges)
+  int32_t* plan;           // per active position: stage plan (slot, level/tree, coords, neighbours)
   Counters* cnt;
   const TreeTime* tt;      // stage coefficients from device memory (graph mode), or null
 };
@@ -124,6 +125,7 @@ struct LaunchCfg {
 };
 
 // Per-dimension launchers (explicitly instantiated in mr_k2.cu / mr_k3.cu).
+template <int D> void launch_plan(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_stage(const PoolView& pv, const Fields& f, int stage,
                                    const StageArgs& sa, const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_refine(const PoolView& pv, const Fields& f, int mode,

@@ -15,22 +15,41 @@ namespace mr {
 //   s2: acc += dt/3 k,    Y3 = y + dt k        s3: y = acc + dt/6 k
 // Advection RHS: -(u Dx phi + v Dy phi [+ w Dz phi]),
 //   D1 f = ((f[-2] - f[2]) + 8 (f[1] - f[-1])) / (12 dx).
+//
+// The block's plan (k_plan) is read from shared memory, the next block's plan
+// is fetched while this one is processed; blocks with a uniform neighbourhood
+// take the direct gather, the others the general one through their ring.
 template <int D, int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
-__global__ void __launch_bounds__(NT) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
+__global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
                             TS* __restrict__ acc, TY* __restrict__ ynext, int stage, StageArgs sa) {
   using Gm = Geo<D, B>;
+  using PL = Plan<D>;
   using TC = TY;  // stencil arithmetic type
+  static_assert(NT >= PL::INTS, "one thread per plan entry");
   Ring& R = *smem_as<Ring>(0);
   TC* tile = smem_as<TC>(kRingBytes);
   TC* cbox = tile + pv.nvar * Gm::TILE;
+  __shared__ int32_t splan[2][PL::INTS];
   const int nact = pv.cnt->n_act;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
-  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
-    const BlockInfo b = load_block(pv, pv.act[p]);
+  if (blockIdx.x < nact && threadIdx.x < PL::INTS)
+    splan[0][threadIdx.x] = pv.plan[(int64_t)blockIdx.x * PL::INTS + threadIdx.x];
+  __syncthreads();
+  int buf = 0;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x, buf ^= 1) {
+    const int pn = p + gridDim.x;
+    int32_t pre = 0;
+    if (pn < nact && threadIdx.x < PL::INTS) pre = pv.plan[(int64_t)pn * PL::INTS + threadIdx.x];
+    const int32_t* pl = splan[buf];
+    const BlockInfo b = plan_block<D>(pl);
     const TreeDev& td = pv.trees[b.tree];
-    build_ring<D, B>(pv, td, b, R);
-    __syncthreads();
-    fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
+    if ((pl[1] >> 30) & 1) {
+      gather_uniform<D, B, 2, 1, TSRC, TC>(pv, b, pl + PL::NBO, src, (TSRC*)src, tile, stage == 0);
+    } else {
+      build_ring<D, B>(pv, td, b, R);
+      __syncthreads();
+      fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
+    }
     __syncthreads();
     const TC c = (TC)td.cD[b.lvl];
     const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
@@ -38,46 +57,91 @@ __global__ void __launch_bounds__(NT) k_stage_adv(PoolView pv, const TSRC* __res
     const double ct = pv.tt ? pv.tt[b.tree].ct[stage] : sa.ct[b.tree];
     const int64_t base = (int64_t)b.slot * pv.vs;  // nvar == 1
     const int sh = td.Jmax - b.lvl;
-    for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
-      const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-      const TC* t0 = tile + Gm::tix(i, j, k);
-      const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
-      const TC dyv = ((t0[-2 * Gm::T] - t0[2 * Gm::T]) + TC(8) * (t0[Gm::T] - t0[-Gm::T])) * c;
-      TC dzv = TC(0);
-      if (D == 3) {
-        constexpr int P = Gm::T * Gm::T;
-        dzv = ((t0[-2 * P] - t0[2 * P]) + TC(8) * (t0[P] - t0[-P])) * c;
+    // UC points per thread at a time: their state, accumulator and velocity
+    // loads are issued together, then the stencils and the updates
+    constexpr int UC = D == 3 ? 4 : 3;
+    for (int q0 = threadIdx.x; q0 < Gm::NI; q0 += UC * NT) {
+      TS yv[UC], av[UC];
+      double u0[UC], u1[UC];
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int q = q0 + u * NT;
+        yv[u] = av[u] = TS(0);
+        u0[u] = td.rhs[0];
+        u1[u] = td.rhs[1];
+        if (q >= Gm::NI) continue;
+        if (stage <= 2) yv[u] = y[base + q];  // stage 0: committed (synchronised) y_n
+        if (stage >= 1) av[u] = acc[base + q];
+        if (RHS == MR_RHS_SWIRL) {
+          const int i = q % B, j = (q / B) % B;
+          const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
+          const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
+          const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
+          const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
+          u0[u] = ct * (A[Ux] * Bt[Uy]);
+          u1[u] = -(ct * (A[Uy] * Bt[Ux]));
+        }
       }
-      double u0, u1, u2 = 0.0;
-      if (RHS == MR_RHS_SWIRL) {
-        const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
-        const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
-        const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
-        const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
-        u0 = ct * (A[Ux] * Bt[Uy]);
-        u1 = -(ct * (A[Uy] * Bt[Ux]));
-      } else {
-        u0 = td.rhs[0];
-        u1 = td.rhs[1];
-        u2 = td.rhs[2];
-      }
-      TC s = (TC)u0 * dxv + (TC)u1 * dyv;
-      if (D == 3) s = s + (TC)u2 * dzv;
-      const TS kk = (TS)(-s);
-      const int64_t at = base + q;
-      if (stage == 0) {
-        const TS yv = y[at];  // committed (synchronised) y_n
-        acc[at] = yv + (TS)ca * kk;
-        ynext[at] = (TY)(yv + (TS)cy * kk);
-      } else if (stage == 1 || stage == 2) {
-        const TS yv = y[at];
-        acc[at] = acc[at] + (TS)ca * kk;
-        ynext[at] = (TY)(yv + (TS)cy * kk);
-      } else {
-        y[at] = acc[at] + (TS)ca * kk;
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int q = q0 + u * NT;
+        if (q >= Gm::NI) continue;
+        const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
+        const TC* t0 = tile + Gm::tix(i, j, k);
+        const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
+        const TC dyv = ((t0[-2 * Gm::T] - t0[2 * Gm::T]) + TC(8) * (t0[Gm::T] - t0[-Gm::T])) * c;
+        TC s = (TC)u0[u] * dxv + (TC)u1[u] * dyv;
+        if (D == 3) {
+          constexpr int P = Gm::T * Gm::T;
+          const TC dzv = ((t0[-2 * P] - t0[2 * P]) + TC(8) * (t0[P] - t0[-P])) * c;
+          s = s + (TC)td.rhs[2] * dzv;
+        }
+        const TS kk = (TS)(-s);
+        const int64_t at = base + q;
+        if (stage == 0) {
+          acc[at] = yv[u] + (TS)ca * kk;
+          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+        } else if (stage == 1 || stage == 2) {
+          acc[at] = av[u] + (TS)ca * kk;
+          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+        } else {
+          y[at] = av[u] + (TS)ca * kk;
+        }
       }
     }
+    if (pn < nact && threadIdx.x < PL::INTS) splan[buf ^ 1][threadIdx.x] = pre;
     __syncthreads();
+  }
+}
+
+// Stage plans of the active blocks (layout in Plan<D>): one thread per block,
+// the 3^d - 1 equal-level neighbours looked up in the dense leaf tables.
+template <int D>
+__global__ void k_plan(PoolView pv) {
+  using PL = Plan<D>;
+  const int nact = pv.cnt->n_act;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const int s = pv.act[p];
+    const int l = pv.lvl[s], t = pv.tree[s];
+    const TreeDev& td = pv.trees[t];
+    int64_t c[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) c[a] = pv.crd[3 * s + a];
+    int32_t* out = pv.plan + (int64_t)p * PL::INTS;
+    bool uni = true;
+#pragma unroll 1
+    for (int n = 0; n < PL::NB; ++n) {
+      const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
+      int q = s;
+      if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
+        const int64_t cn[3] = {c[0] + o[0], c[1] + o[1], c[2] + o[2]};
+        q = tab_get<D>(pv, td, l, cn);
+      }
+      uni &= q >= 0;
+      out[PL::NBO + n] = q;
+    }
+    out[0] = s;
+    out[1] = l | (t << 8) | (uni ? 1 << 30 : 0);
+    for (int a = 0; a < D; ++a) out[2 + a] = (int32_t)c[a];
   }
 }
 
@@ -218,7 +282,7 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
 // interpolating prediction and split into 2^d children (one treecode digit
 // appended); children are placed in the new active list in Hilbert order.
 template <int D, int B, typename TS, int NT>
-__global__ void __launch_bounds__(NT) k_refine(PoolView pv, TS* __restrict__ y) {
+__global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
   Ring& R = *smem_as<Ring>(0);
   __shared__ int cslot[8];
@@ -292,7 +356,7 @@ struct DetGeo {
 };
 
 template <int D, int B, typename TS, typename TD, int NT>
-__global__ void __launch_bounds__(NT) k_details(PoolView pv, TS* __restrict__ y) {
+__global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_details(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
   using DG = DetGeo<D, B>;
   Ring& R = *smem_as<Ring>(0);

@@ -99,6 +99,12 @@ static void stage_ns(const PoolView& pv, const Fields& f, int stage, const Stage
 }
 
 template <int D>
+void launch_plan(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st) {
+  k_plan<D><<<lc.num_sms * 4, 128, 0, st>>>(pv);
+  count_launch();
+}
+
+template <int D>
 void launch_stage(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
                   const LaunchCfg& lc, cudaStream_t st) {
   if constexpr (D == 2) {
@@ -345,6 +351,7 @@ void launch_error(const PoolView& pv, const Fields& f, int tree, const double* e
 }
 
 #define MR_INSTANTIATE(D)                                                                       \
+  template void launch_plan<D>(const PoolView&, const LaunchCfg&, cudaStream_t);                \
   template void launch_stage<D>(const PoolView&, const Fields&, int, const StageArgs&,         \
                                 const LaunchCfg&, cudaStream_t);                                \
   template void launch_refine<D>(const PoolView&, const Fields&, int, const int8_t*,            \
