@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) k_features(PoolView pv, const TS* __restr
         double dmax = 0.0;
         for (int v = 0; v < nv; ++v) {
           const int o[3] = {i, j, 0};
-          const double d = tile[v * Gm::TILE + idx] - predict_tile<2, B, double, double>(tile + v * Gm::TILE, o, 2);
+          const double d = tile[v * Gm::TILE + idx] - predict_tile<2, B, kG, double, double>(tile + v * Gm::TILE, o, 2);
           double sv = pv.norm_kind == 1 ? pv.svar[b.tree * nv + v] : 1.0;
           if (sv == 0.0) sv = 1.0;
           dmax = fmax(dmax, fabs(d) / sv);

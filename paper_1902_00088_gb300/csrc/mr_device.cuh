@@ -118,11 +118,20 @@ struct Box {
   static_assert(W >= 1 && W <= kG, "ghost width");
   static constexpr int S = B + 2 * W;
   static constexpr int NPTS = S * S * (D == 3 ? S : 1);
+  static constexpr int TILE = NPTS;  // tile of this width: S^d nodes, x fastest
   static constexpr int CLO = -((W + 1) / 2) - 1;
   static constexpr int CB = (B - 1) / 2 + 2 * ((W + 1) / 2) + 3;
   static constexpr int CBOX = CB * CB * (D == 3 ? CB : 1);
+  // scratch of the separable prediction, per variable: X[nz][ny][x] (coarse
+  // y, z; fine x) and, in 3D, Y[nz][y][x] (coarse z; fine x, y)
+  static constexpr int NXP = (D == 3 ? CB : 1) * CB * S;
+  static constexpr int NYP = D == 3 ? CB * S * S : 0;
+  static constexpr int SCR = NXP + NYP;
   __device__ static __forceinline__ int cix(int i, int j, int k) {
     return ((D == 3 ? k - CLO : 0) * CB + (j - CLO)) * CB + (i - CLO);
+  }
+  __device__ static __forceinline__ int tix(int i, int j, int k) {
+    return (((D == 3 ? k + W : 0)) * S + (j + W)) * S + (i + W);
   }
 };
 
@@ -356,7 +365,7 @@ __device__ __forceinline__ TT predict_box(const TT* box, const int o[3]) {
 // nodes between coarse nodes are predicted from it.
 template <int D, int B, typename TF, typename TT, int W = kG>
 __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, TF* Fw, TT* tile,
-                          bool commit, const Ring& R, TT* cbox) {
+                          bool commit, const Ring& R, TT* cbox, TT* scr = nullptr) {
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, W>;
   // Each thread takes U points at a time: owners and addresses first, then the
@@ -380,7 +389,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
         const int i = qq % Bx::S - W;
         const int j = (qq / Bx::S) % Bx::S - W;
         const int k = D == 3 ? qq / (Bx::S * Bx::S) - W : 0;
-        idx[u] = Gm::tix(i, j, k);
+        idx[u] = Bx::tix(i, j, k);
         li[u] = Gm::lin(i, j, k);
         const int h[3] = {2 * i, 2 * j, 2 * k};
         int r = 0, lo[3] = {0, 0, 0};
@@ -403,7 +412,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (!ok[u]) continue;
-          tile[v * Gm::TILE + idx[u]] = (TT)val[u];
+          tile[v * Bx::TILE + idx[u]] = (TT)val[u];
           if (ed[u]) {
             const int64_t me = own + (int64_t)v * pv.vs + li[u];
             if (F[me] != val[u]) Fw[me] = val[u];
@@ -447,6 +456,38 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       }
     }
     __syncthreads();
+    if (scr) {
+      // separable prediction over the coarse box, x first, then y (then z at
+      // the point): the same operations in the same order as predict_box
+      for (int v = 0; v < nv; ++v) {
+        const TT* cb = cbox + v * Bx::CBOX;
+        TT* X = scr + v * Bx::SCR;
+        for (int q = threadIdx.x; q < Bx::NXP; q += blockDim.x) {
+          const int x = q % Bx::S - W, ny = (q / Bx::S) % Bx::CB + Bx::CLO;
+          const int nz = D == 3 ? q / (Bx::S * Bx::CB) + Bx::CLO : 0;
+          const int fl = x >> 1;
+          X[q] = (x & 1) ? dd4(cb[Bx::cix(fl - 1, ny, nz)], cb[Bx::cix(fl, ny, nz)], cb[Bx::cix(fl + 1, ny, nz)],
+                               cb[Bx::cix(fl + 2, ny, nz)])
+                         : cb[Bx::cix(fl, ny, nz)];
+        }
+      }
+      if (D == 3) {
+        __syncthreads();
+        for (int v = 0; v < nv; ++v) {
+          const TT* X = scr + v * Bx::SCR;
+          TT* Y = scr + v * Bx::SCR + Bx::NXP;
+          for (int q = threadIdx.x; q < Bx::NYP; q += blockDim.x) {
+            const int x = q % Bx::S, y = (q / Bx::S) % Bx::S - W, nzi = q / (Bx::S * Bx::S);
+            const int fl = y >> 1;
+            const TT* c = X + nzi * Bx::CB * Bx::S + x;
+            Y[q] = (y & 1) ? dd4(c[(fl - 1 - Bx::CLO) * Bx::S], c[(fl - Bx::CLO) * Bx::S],
+                                 c[(fl + 1 - Bx::CLO) * Bx::S], c[(fl + 2 - Bx::CLO) * Bx::S])
+                           : c[(fl - Bx::CLO) * Bx::S];
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
   // kinds of tile points: 0 own node, 1 block-edge node of another owner,
   // 2 ghost node that is a node of its owner, 3 ghost predicted from the coarse
@@ -464,7 +505,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       ijk[u][0] = i;
       ijk[u][1] = j;
       ijk[u][2] = k;
-      idx[u] = Gm::tix(i, j, k);
+      idx[u] = Bx::tix(i, j, k);
       li[u] = Gm::lin(i, j, k);
       at[u] = 0;
       kind[u] = 5;  // past the end
@@ -515,9 +556,20 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (kind[u] == 5) continue;
-        TT* t = tile + v * Gm::TILE + idx[u];
+        TT* t = tile + v * Bx::TILE + idx[u];
         if (kind[u] == 3) {
-          *t = predict_box<D, B, W, TT>(cbox + v * Bx::CBOX, ijk[u]);
+          if (scr) {
+            // last axis from the scratch: z in 3D (Y), y in 2D (X)
+            const TT* c = scr + v * Bx::SCR + (D == 3 ? Bx::NXP : 0) + (ijk[u][0] + W) +
+                          (D == 3 ? (ijk[u][1] + W) * Bx::S : 0);
+            const int st = D == 3 ? Bx::S * Bx::S : Bx::S;
+            const int e = ijk[u][D - 1], fl = e >> 1;
+            *t = (e & 1) ? dd4(c[(fl - 1 - Bx::CLO) * st], c[(fl - Bx::CLO) * st], c[(fl + 1 - Bx::CLO) * st],
+                               c[(fl + 2 - Bx::CLO) * st])
+                         : c[(fl - Bx::CLO) * st];
+          } else {
+            *t = predict_box<D, B, W, TT>(cbox + v * Bx::CBOX, ijk[u]);
+          }
         } else if (kind[u] == 4) {
           *t = TT(0);
         } else {
@@ -595,7 +647,7 @@ __device__ __forceinline__ void gather_uniform(const PoolView& pv, const BlockIn
       }
       const int slot = nb[n];
       at[u] = (int64_t)slot * NV * pv.vs + Gm::lin(l3[0], l3[1], l3[2]);
-      idx[u] = Gm::tix(ijk[0], ijk[1], ijk[2]);
+      idx[u] = Bx::tix(ijk[0], ijk[1], ijk[2]);
       li[u] = Gm::lin(ijk[0], ijk[1], ijk[2]);
       ed[u] = commit && inner && slot != b.slot;
     }
@@ -609,7 +661,7 @@ __device__ __forceinline__ void gather_uniform(const PoolView& pv, const BlockIn
       if (!ok[u]) continue;
 #pragma unroll
       for (int w = 0; w < NV; ++w) {
-        tile[w * Gm::TILE + idx[u]] = (TT)v[u][w];
+        tile[w * Bx::TILE + idx[u]] = (TT)v[u][w];
         if (ed[u]) {
           const int64_t me = own + (int64_t)w * pv.vs + li[u];
           if (F[me] != v[u][w]) Fw[me] = v[u][w];
@@ -623,9 +675,9 @@ __device__ __forceinline__ void gather_uniform(const PoolView& pv, const BlockIn
 // coarse nodes) from a tile whose coarse node n sits at tile index n*stride.
 // x first, then y, then z.  Used by refinement (stride 1: the mother's tile) and
 // by the details (stride 2: even nodes of the block's own tile).
-template <int D, int B, typename TT, typename TA = TT>
+template <int D, int B, int W, typename TT, typename TA = TT>
 __device__ __forceinline__ TA predict_tile(const TT* tile, const int o[3], int stride) {
-  using Gm = Geo<D, B>;
+  using Gm = Box<D, B, W>;
   int base[3] = {0, 0, 0}, ns[3] = {1, 1, 1};
 #pragma unroll
   for (int a = 0; a < D; ++a) {

@@ -23,12 +23,14 @@ template <int D, int B, int RHS, typename TS, typename TY, typename TSRC, int NT
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
                             TS* __restrict__ acc, TY* __restrict__ ynext, int stage, StageArgs sa) {
   using Gm = Geo<D, B>;
+  using Bx = Box<D, B, 2>;  // the stencils reach two nodes
   using PL = Plan<D>;
   using TC = TY;  // stencil arithmetic type
   static_assert(NT >= PL::INTS, "one thread per plan entry");
   Ring& R = *smem_as<Ring>(0);
-  TC* tile = smem_as<TC>(kRingBytes);
-  TC* cbox = tile + pv.nvar * Gm::TILE;
+  TC* tile = smem_as<TC>(kRingBytes);  // nvar == 1
+  TC* cbox = tile + Bx::TILE;
+  TC* scr = cbox + Bx::CBOX;
   __shared__ int32_t splan[2][PL::INTS];
   const int nact = pv.cnt->n_act;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
     } else {
       build_ring<D, B>(pv, td, b, R);
       __syncthreads();
-      fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
+      fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
     }
     __syncthreads();
     const TC c = (TC)td.cD[b.lvl];
@@ -87,12 +89,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
         const int q = q0 + u * NT;
         if (q >= Gm::NI) continue;
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-        const TC* t0 = tile + Gm::tix(i, j, k);
+        const TC* t0 = tile + Bx::tix(i, j, k);
         const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
-        const TC dyv = ((t0[-2 * Gm::T] - t0[2 * Gm::T]) + TC(8) * (t0[Gm::T] - t0[-Gm::T])) * c;
+        const TC dyv = ((t0[-2 * Bx::S] - t0[2 * Bx::S]) + TC(8) * (t0[Bx::S] - t0[-Bx::S])) * c;
         TC s = (TC)u0[u] * dxv + (TC)u1[u] * dyv;
         if (D == 3) {
-          constexpr int P = Gm::T * Gm::T;
+          constexpr int P = Bx::S * Bx::S;
           const TC dzv = ((t0[-2 * P] - t0[2 * P]) + TC(8) * (t0[P] - t0[-P])) * c;
           s = s + (TC)td.rhs[2] * dzv;
         }
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
   TC* pth = pp + Gm::TILE;
   TC* F = pth + Gm::TILE;                 // 4 x NF
   TC* Gf = F + 4 * NG::NF;                // 4 x NG
+  static_assert(Box<2, B, kG>::SCR <= Gm::TILE, "prediction scratch fits in the primitive arrays");
   const int nact = pv.cnt->n_act;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
   auto I = [&](int i, int j) { return (j + G) * T + (i + G); };
@@ -190,7 +193,8 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
     const TreeDev& td = pv.trees[b.tree];
     build_ring<2, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox);
+    // prediction scratch: the primitive arrays, unused until the tile is complete
+    fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, pu);
     __syncthreads();
     const double gam = td.rhs[0], mud = td.rhs[1], Pr = td.rhs[2];
     const TC gm1 = (TC)(gam - 1.0);
@@ -284,10 +288,12 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
 template <int D, int B, typename TS, int NT>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
+  using Bx = Box<D, B, 1>;  // prediction of the children reaches one node
   Ring& R = *smem_as<Ring>(0);
   __shared__ int cslot[8];
   TS* tile = smem_as<TS>(kRingBytes);
-  TS* cbox = tile + pv.nvar * Gm::TILE;
+  TS* cbox = tile + pv.nvar * Bx::TILE;
+  TS* scr = cbox + pv.nvar * Bx::CBOX;
   const int nact = pv.cnt->n_act;
   const int n_alloc = pv.cnt->n_alloc, n_free = pv.cnt->n_free;
   if (n_alloc > n_free) {
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine
     const TreeDev& td = pv.trees[b.tree];
     build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TS, TS, 1>(pv, b, y, y, tile, false, R, cbox);
+    fill_tile<D, B, TS, TS, 1>(pv, b, y, y, tile, false, R, cbox, scr);
     if (threadIdx.x == 0) {
       uint64_t key[8];
       int32_t cc[8][3];
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine
       const int o[3] = {((ch >> 0) & 1) * (B - 1) + i, ((ch >> 1) & 1) * (B - 1) + j,
                         D == 3 ? ((ch >> 2) & 1) * (B - 1) + k : 0};
       for (int v = 0; v < nv; ++v)
-        y[((int64_t)cslot[ch] * nv + v) * pv.vs + q] = predict_tile<D, B, TS>(tile + v * Gm::TILE, o, 1);
+        y[((int64_t)cslot[ch] * nv + v) * pv.vs + q] = predict_tile<D, B, 1, TS>(tile + v * Bx::TILE, o, 1);
     }
     __syncthreads();
   }
@@ -358,13 +364,15 @@ struct DetGeo {
 template <int D, int B, typename TS, typename TD, int NT>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_details(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
+  using Bx = Box<D, B, 2>;  // prediction from even nodes reaches two nodes
   using DG = DetGeo<D, B>;
   Ring& R = *smem_as<Ring>(0);
   __shared__ double red[2][32];
   TS* tile = smem_as<TS>(kRingBytes);  // storage type; TD is the arithmetic type
-  TS* cbox = tile + pv.nvar * Gm::TILE;
-  TD* X = reinterpret_cast<TD*>(cbox + pv.nvar * Gm::CBOX + 2);  // 16-byte aligned below
-  X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(X) + 15) & ~(uintptr_t)15);
+  TS* cbox = tile + pv.nvar * Bx::TILE;
+  // gather scratch, reused for the x pass once the tile is complete
+  TS* scr = cbox + pv.nvar * Bx::CBOX;
+  TD* X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(scr) + 15) & ~(uintptr_t)15);
   const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
   const bool all_blocks = pv.cnt->first_round != 0;
@@ -388,21 +396,21 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       __syncthreads();
       continue;
     }
-    fill_tile<D, B, TS, TS, 2>(pv, b, y, y, tile, true, R, cbox);
+    fill_tile<D, B, TS, TS, 2>(pv, b, y, y, tile, true, R, cbox, scr);
     __syncthreads();
     for (int v = 0; v < nv; ++v) {
-      const TS* tv = tile + v * Gm::TILE;
+      const TS* tv = tile + v * Bx::TILE;
       // x pass on coarse rows (yc, zc) in [-1, NC-2]
       for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
         const int x = idx % B, yc = (idx / B) % DG::NC - 1, zc = D == 3 ? idx / (B * DG::NC) - 1 : 0;
         const int yy = 2 * yc, zz = 2 * zc;
         TD val;
         if ((x & 1) == 0) {
-          val = (TD)tv[Gm::tix(x, yy, zz)];
+          val = (TD)tv[Bx::tix(x, yy, zz)];
         } else {
           const int n0 = (x - 1) / 2;
-          val = dd4((TD)tv[Gm::tix(2 * n0 - 2, yy, zz)], (TD)tv[Gm::tix(2 * n0, yy, zz)],
-                    (TD)tv[Gm::tix(2 * n0 + 2, yy, zz)], (TD)tv[Gm::tix(2 * n0 + 4, yy, zz)]);
+          val = dd4((TD)tv[Bx::tix(2 * n0 - 2, yy, zz)], (TD)tv[Bx::tix(2 * n0, yy, zz)],
+                    (TD)tv[Bx::tix(2 * n0 + 2, yy, zz)], (TD)tv[Bx::tix(2 * n0 + 4, yy, zz)]);
         }
         X[idx] = val;
       }
@@ -413,7 +421,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       double md = 0.0, mq = 0.0;
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-        const TD val = (TD)tv[Gm::tix(i, j, k)];
+        const TD val = (TD)tv[Bx::tix(i, j, k)];
         mq = fmax(mq, fabs((double)val));
         if (((i | j | k) & 1) == 0) continue;
         auto ypass = [&](int zc) -> TD {
@@ -456,7 +464,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     for (int q = threadIdx.x; q < Gm::NI * nv; q += blockDim.x) {
       const int v = q / Gm::NI, r = q % Gm::NI;
       const int i = r % B, j = (r / B) % B, k = D == 3 ? r / (B * B) : 0;
-      bad |= !isfinite((double)tile[v * Gm::TILE + Gm::tix(i, j, k)]);
+      bad |= !isfinite((double)tile[v * Bx::TILE + Bx::tix(i, j, k)]);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0)
       pv.md[(int64_t)b.slot * nv] = __longlong_as_double(0x7ff8000000000000LL);

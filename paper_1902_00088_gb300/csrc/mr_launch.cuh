@@ -38,7 +38,8 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
                        const LaunchCfg& lc, cudaStream_t st) {
   constexpr int threads = Threads<D, B>::value;
   const int nv = 1;
-  const size_t smem = kRingBytes + sizeof(TY) * nv * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
+  using Bx = Box<D, B, 2>;
+  const size_t smem = kRingBytes + sizeof(TY) * nv * (Bx::TILE + Bx::CBOX + Bx::SCR);
   TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
   if (stage == 0) {
     auto k = k_stage_adv<D, B, RHS, TS, TY, TS, threads>;
@@ -148,7 +149,8 @@ template <int D, int B, typename TS>
 struct RefineRun {
   static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
     constexpr int threads = Threads<D, B>::value;
-    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
+    using Bx = Box<D, B, 1>;
+    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX + Bx::SCR);
     auto k = k_refine<D, B, TS, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
@@ -196,8 +198,9 @@ struct DetailsRun {
                   cudaStream_t st) {
     constexpr int threads = Threads<D, B>::value;
     const bool d64 = fp64 || sizeof(TS) == 8;
-    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX) + 32 +
-                        (d64 ? 8 : sizeof(TS)) * DetGeo<D, B>::NX;
+    using Bx = Box<D, B, 2>;
+    const size_t scr = sizeof(TS) * pv.nvar * Bx::SCR, xp = (d64 ? 8 : sizeof(TS)) * DetGeo<D, B>::NX;
+    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp);
     if (d64) {
       auto k = k_details<D, B, TS, double, threads>;
       prep_smem(k, smem);
