@@ -209,17 +209,22 @@ mr_status mr_error_noalloc(mr_ctx ctx, int32_t tree, double t, double* out);
 /* Kernel launches enqueued by this process so far (for throughput claims). */
 int64_t mr_launch_count(mr_ctx ctx);
 
-/* Phase timers and work counters (tracing).  Phases: 0 refine, 1 RK4 stages,
- * 2 details + flags, 3 merge + list rebuild, 4 synchronisation/export.
- * ms[p] is device time between CUDA events recorded on the context's stream
- * around the phase (only while timing is enabled); stage_blocks counts the
- * blocks processed by all RK stage launches, stage_launches those launches. */
+/* Phase timers and work counters (tracing).  Phases: 0 refine (with the
+ * proposal), 1 RK4 stages, 2 details of a coarsening round, 3 flags, merge and
+ * list rebuild, 4 synchronisation/export.  ms[p] is device time between CUDA
+ * events recorded on the context's stream around the phase (only while timing
+ * is enabled); stage_blocks counts the blocks processed by all RK stage
+ * launches, stage_launches those launches; det_blocks the blocks whose details
+ * were evaluated (blocks whose neighbourhood did not change since the previous
+ * round reuse theirs), det_launches the host-driven coarsening rounds. */
 typedef struct {
   double ms[5];
   int64_t phase_calls[5];
   int64_t stage_launches;
   int64_t stage_blocks;
   int64_t steps;
+  int64_t det_launches;
+  int64_t det_blocks;
 } mr_stats;
 mr_status mr_enable_timing(mr_ctx ctx, int32_t on);
 

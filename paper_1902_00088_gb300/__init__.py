@@ -48,10 +48,11 @@ class BlockInfo(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("ms", C.c_double * 5), ("phase_calls", C.c_int64 * 5),
-                ("stage_launches", C.c_int64), ("stage_blocks", C.c_int64), ("steps", C.c_int64)]
+                ("stage_launches", C.c_int64), ("stage_blocks", C.c_int64), ("steps", C.c_int64),
+                ("det_launches", C.c_int64), ("det_blocks", C.c_int64)]
 
 
-PHASES = ("refine", "stage", "details_flags", "merge", "sync_export")
+PHASES = ("refine", "stage", "details", "flags_merge", "sync_export")
 
 BLOCK_INFO_DTYPE = np.dtype([("level", np.int32), ("tree", np.int32), ("treecode", np.uint64),
                              ("coords", np.int32, 3), ("pad", np.int32),
@@ -360,4 +361,5 @@ class Forest:
         self._ck(self.lib.mr_get_stats(self.h, C.byref(s)))
         return dict(ms={PHASES[i]: s.ms[i] for i in range(5)},
                     calls={PHASES[i]: s.phase_calls[i] for i in range(5)},
-                    stage_launches=s.stage_launches, stage_blocks=s.stage_blocks, steps=s.steps)
+                    stage_launches=s.stage_launches, stage_blocks=s.stage_blocks, steps=s.steps,
+                    det_launches=s.det_launches, det_blocks=s.det_blocks)

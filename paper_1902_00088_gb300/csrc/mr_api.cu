@@ -253,11 +253,17 @@ void do_ic(mr_ctx c) {
          [&] { launch_ic<3>(pv, fields(c), c->lc, c->st); });
 }
 void do_round(mr_ctx c, bool merge) {
-  PhaseTimer tm(c, 2);
   PoolView pv = view(c);
   const bool fp64 = c->p.detail_fp64 != 0;
-  by_dim(c, [&] { launch_coarsen_round<2>(pv, fields(c), fp64, merge, c->lc, c->st); },
-         [&] { launch_coarsen_round<3>(pv, fields(c), fp64, merge, c->lc, c->st); });
+  c->stats.det_launches += 1;
+  {
+    PhaseTimer tm(c, 2);
+    by_dim(c, [&] { launch_round_details<2>(pv, fields(c), fp64, c->lc, c->st); },
+           [&] { launch_round_details<3>(pv, fields(c), fp64, c->lc, c->st); });
+  }
+  PhaseTimer tm(c, 3);
+  by_dim(c, [&] { launch_round_merge<2>(pv, fields(c), merge, c->lc, c->st); },
+         [&] { launch_round_merge<3>(pv, fields(c), merge, c->lc, c->st); });
 }
 
 int max_rounds_of(mr_ctx ctx) {
@@ -1365,6 +1371,7 @@ mr_status mr_get_stats(mr_ctx ctx, mr_stats* out) {
   flush_timers(ctx);
   Counters h = read_counters(ctx);
   ctx->stats.stage_blocks = (int64_t)h.stage_blocks;
+  ctx->stats.det_blocks = (int64_t)h.det_blocks;
   *out = ctx->stats;
   return MR_OK;
 }
@@ -1376,6 +1383,7 @@ mr_status mr_reset_stats(mr_ctx ctx) {
   ctx->stats = mr_stats{};
   unsigned long long z = 0;
   cudaMemcpy(&ctx->cnt->stage_blocks, &z, sizeof(z), cudaMemcpyHostToDevice);
+  cudaMemcpy(&ctx->cnt->det_blocks, &z, sizeof(z), cudaMemcpyHostToDevice);
   return MR_OK;
 }
 

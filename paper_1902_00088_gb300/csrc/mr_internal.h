@@ -50,6 +50,7 @@ struct Counters {
   int32_t rounds;   // coarsening rounds run in the current graph step
   int32_t round_id;     // coarsening rounds so far (monotonic); merged mothers are stamped with it
   int32_t first_round;  // the current round is the first of an adapt: every block is evaluated
+  unsigned long long det_blocks;  // blocks whose details a coarsening round evaluated
 };
 constexpr int kMaxHist = 1 << 16;  // step history: blocks of the adapted grid before each step
 
@@ -134,6 +135,10 @@ template <int D> void launch_ic(const PoolView& pv, const Fields& f, const Launc
                                 cudaStream_t st);
 template <int D> void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64,
                                            bool merge, const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_round_details(const PoolView& pv, const Fields& f, bool fp64,
+                                           const LaunchCfg& lc, cudaStream_t st);
+template <int D> void launch_round_merge(const PoolView& pv, const Fields& f, bool merge,
+                                         const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_sync(const PoolView& pv, const Fields& f, double* tiles,
                                   const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_neighbors(const PoolView& pv, const int4* rel, int R, int32_t* nbr,

@@ -116,35 +116,51 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
   }
 }
 
-// Stage plans of the active blocks (layout in Plan<D>): one thread per block,
-// the 3^d - 1 equal-level neighbours looked up in the dense leaf tables.
+// Stage plan of active position p (layout in Plan<D>): the 3^d - 1
+// equal-level neighbours looked up in the dense leaf tables.
+template <int D>
+__device__ __forceinline__ void plan_one(const PoolView& pv, int p) {
+  using PL = Plan<D>;
+  const int s = pv.act[p];
+  const int l = pv.lvl[s], t = pv.tree[s];
+  const TreeDev& td = pv.trees[t];
+  int64_t c[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) c[a] = pv.crd[3 * s + a];
+  int32_t* out = pv.plan + (int64_t)p * PL::INTS;
+  bool uni = true;
+#pragma unroll 1
+  for (int n = 0; n < PL::NB; ++n) {
+    const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
+    int q = s;
+    if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
+      const int64_t cn[3] = {c[0] + o[0], c[1] + o[1], c[2] + o[2]};
+      q = tab_get<D>(pv, td, l, cn);
+    }
+    uni &= q >= 0;
+    out[PL::NBO + n] = q;
+  }
+  out[0] = s;
+  out[1] = l | (t << 8) | (uni ? 1 << 30 : 0);
+  for (int a = 0; a < D; ++a) out[2 + a] = (int32_t)c[a];
+}
+
+// Stage plans of all active blocks, one thread per block.
 template <int D>
 __global__ void k_plan(PoolView pv) {
-  using PL = Plan<D>;
   const int nact = pv.cnt->n_act;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
-    const int s = pv.act[p];
-    const int l = pv.lvl[s], t = pv.tree[s];
-    const TreeDev& td = pv.trees[t];
-    int64_t c[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) c[a] = pv.crd[3 * s + a];
-    int32_t* out = pv.plan + (int64_t)p * PL::INTS;
-    bool uni = true;
-#pragma unroll 1
-    for (int n = 0; n < PL::NB; ++n) {
-      const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
-      int q = s;
-      if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
-        const int64_t cn[3] = {c[0] + o[0], c[1] + o[1], c[2] + o[2]};
-        q = tab_get<D>(pv, td, l, cn);
-      }
-      uni &= q >= 0;
-      out[PL::NBO + n] = q;
-    }
-    out[0] = s;
-    out[1] = l | (t << 8) | (uni ? 1 << 30 : 0);
-    for (int a = 0; a < D; ++a) out[2 + a] = (int32_t)c[a];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) plan_one<D>(pv, p);
+}
+
+// Start of a coarsening round: the blocks it works on (none once a round
+// merged nothing), its id, and the per-tree threshold scales reset to v.
+template <int D>
+__global__ void k_round_begin(PoolView pv, double v) {
+  Counters* c = pv.cnt;
+  if (threadIdx.x == 0) {
+    c->n_round = c->done ? 0 : c->n_act;
+    c->round_id += 1;
   }
+  for (int i = threadIdx.x; i < pv.ntrees * pv.nvar; i += blockDim.x) pv.svar[i] = v;
 }
 
 // ------------------------------------------------------------- NS stage ----
@@ -183,18 +199,32 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
   TC* F = pth + Gm::TILE;                 // 4 x NF
   TC* Gf = F + 4 * NG::NF;                // 4 x NG
   static_assert(Box<2, B, kG>::SCR <= Gm::TILE, "prediction scratch fits in the primitive arrays");
+  using PL = Plan<2>;
+  __shared__ int32_t splan[2][PL::INTS];
   const int nact = pv.cnt->n_act;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
   auto I = [&](int i, int j) { return (j + G) * T + (i + G); };
   auto fI = [&](int i, int j) { return j * (B + 4) + (i + 2); };
   auto gI = [&](int i, int j) { return (j + 2) * B + i; };
-  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
-    const BlockInfo b = load_block(pv, pv.act[p]);
+  if (blockIdx.x < nact && threadIdx.x < PL::INTS)
+    splan[0][threadIdx.x] = pv.plan[(int64_t)blockIdx.x * PL::INTS + threadIdx.x];
+  __syncthreads();
+  int buf = 0;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x, buf ^= 1) {
+    const int pn = p + gridDim.x;
+    int32_t pre = 0;
+    if (pn < nact && threadIdx.x < PL::INTS) pre = pv.plan[(int64_t)pn * PL::INTS + threadIdx.x];
+    const int32_t* pl = splan[buf];
+    const BlockInfo b = plan_block<2>(pl);
     const TreeDev& td = pv.trees[b.tree];
-    build_ring<2, B>(pv, td, b, R);
-    __syncthreads();
-    // prediction scratch: the primitive arrays, unused until the tile is complete
-    fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, pu);
+    if ((pl[1] >> 30) & 1) {
+      gather_uniform<2, B, kG, 4, TSRC, TC>(pv, b, pl + PL::NBO, src, (TSRC*)src, tile, stage == 0);
+    } else {
+      build_ring<2, B>(pv, td, b, R);
+      __syncthreads();
+      // prediction scratch: the primitive arrays, unused until the tile is complete
+      fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, pu);
+    }
     __syncthreads();
     const double gam = td.rhs[0], mud = td.rhs[1], Pr = td.rhs[2];
     const TC gm1 = (TC)(gam - 1.0);
@@ -256,32 +286,56 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
     const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
     const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
     const int64_t base = (int64_t)b.slot * 4 * pv.vs;
-    for (int idx = threadIdx.x; idx < 4 * Gm::NI; idx += blockDim.x) {
-      const int v = idx / Gm::NI, q = idx % Gm::NI;
-      const int i = q % B, j = q / B;
-      const TC* Fv = F + v * NG::NF;
-      const TC* Gv = Gf + v * NG::NG;
-      const TC dFx = ((Fv[fI(i - 2, j)] - Fv[fI(i + 2, j)]) + TC(8) * (Fv[fI(i + 1, j)] - Fv[fI(i - 1, j)])) * c;
-      const TC dGy = ((Gv[gI(i, j - 2)] - Gv[gI(i, j + 2)]) + TC(8) * (Gv[gI(i, j + 1)] - Gv[gI(i, j - 1)])) * c;
-      const TS kk = (TS)(-(dFx + dGy));
-      const int64_t at = base + (int64_t)v * pv.vs + q;
-      if (stage == 0) {
-        const TS yv = y[at];
-        acc[at] = yv + (TS)ca * kk;
-        ynext[at] = (TY)(yv + (TS)cy * kk);
-      } else if (stage == 1 || stage == 2) {
-        const TS yv = y[at];
-        acc[at] = acc[at] + (TS)ca * kk;
-        ynext[at] = (TY)(yv + (TS)cy * kk);
-      } else {
-        y[at] = acc[at] + (TS)ca * kk;
+    // UC points per thread at a time: state and accumulator loads first
+    constexpr int UC = 4, NT = 256;
+    for (int i0 = threadIdx.x; i0 < 4 * Gm::NI; i0 += UC * NT) {
+      TS yv[UC], av[UC];
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int idx = i0 + u * NT;
+        yv[u] = av[u] = TS(0);
+        if (idx >= 4 * Gm::NI) continue;
+        const int64_t at = base + (int64_t)(idx / Gm::NI) * pv.vs + idx % Gm::NI;
+        if (stage <= 2) yv[u] = y[at];
+        if (stage >= 1) av[u] = acc[at];
+      }
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int idx = i0 + u * NT;
+        if (idx >= 4 * Gm::NI) continue;
+        const int v = idx / Gm::NI, q = idx % Gm::NI;
+        const int i = q % B, j = q / B;
+        const TC* Fv = F + v * NG::NF;
+        const TC* Gv = Gf + v * NG::NG;
+        const TC dFx = ((Fv[fI(i - 2, j)] - Fv[fI(i + 2, j)]) + TC(8) * (Fv[fI(i + 1, j)] - Fv[fI(i - 1, j)])) * c;
+        const TC dGy = ((Gv[gI(i, j - 2)] - Gv[gI(i, j + 2)]) + TC(8) * (Gv[gI(i, j + 1)] - Gv[gI(i, j - 1)])) * c;
+        const TS kk = (TS)(-(dFx + dGy));
+        const int64_t at = base + (int64_t)v * pv.vs + q;
+        if (stage == 0) {
+          acc[at] = yv[u] + (TS)ca * kk;
+          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+        } else if (stage == 1 || stage == 2) {
+          acc[at] = av[u] + (TS)ca * kk;
+          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+        } else {
+          y[at] = av[u] + (TS)ca * kk;
+        }
       }
     }
+    if (pn < nact && threadIdx.x < PL::INTS) splan[buf ^ 1][threadIdx.x] = pre;
     __syncthreads();
   }
 }
 
 // ----------------------------------------------------------------- refine ----
+// x pass of the upsampling: fine x in [0, 2(B-1)] on mother rows y, z in [-1, B]
+template <int D, int B>
+struct RefGeo {
+  static constexpr int NF = 2 * B - 1;
+  static constexpr int NR = B + 2;
+  static constexpr int NX = NF * NR * (D == 3 ? NR : 1);
+};
+
 // Sec. 2.3: the synchronised mother tile is upsampled by the 4th-order
 // interpolating prediction and split into 2^d children (one treecode digit
 // appended); children are placed in the new active list in Hilbert order.
@@ -289,11 +343,13 @@ template <int D, int B, typename TS, int NT>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 1>;  // prediction of the children reaches one node
+  using RG = RefGeo<D, B>;
   Ring& R = *smem_as<Ring>(0);
   __shared__ int cslot[8];
   TS* tile = smem_as<TS>(kRingBytes);
   TS* cbox = tile + pv.nvar * Bx::TILE;
-  TS* scr = cbox + pv.nvar * Bx::CBOX;
+  TS* scr = cbox + pv.nvar * Bx::CBOX;  // gather scratch, then the x pass of the upsampling
+  TS* X = scr;
   const int nact = pv.cnt->n_act;
   const int n_alloc = pv.cnt->n_alloc, n_free = pv.cnt->n_free;
   if (n_alloc > n_free) {
@@ -335,15 +391,42 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine
       }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < Gm::NCH * Gm::NI; idx += blockDim.x) {
-      const int ch = idx / Gm::NI, q = idx % Gm::NI;
-      const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-      const int o[3] = {((ch >> 0) & 1) * (B - 1) + i, ((ch >> 1) & 1) * (B - 1) + j,
-                        D == 3 ? ((ch >> 2) & 1) * (B - 1) + k : 0};
-      for (int v = 0; v < nv; ++v)
-        y[((int64_t)cslot[ch] * nv + v) * pv.vs + q] = predict_tile<D, B, 1, TS>(tile + v * Bx::TILE, o, 1);
+    // Separable upsampling, per variable: X = prediction along x on the
+    // mother's rows (y, z in [-1, B]), then y (and z) per child node -- the
+    // operations of the tensor product in the same order.
+    for (int v = 0; v < nv; ++v) {
+      const TS* tv = tile + v * Bx::TILE;
+      for (int idx = threadIdx.x; idx < RG::NX; idx += blockDim.x) {
+        const int ox = idx % RG::NF, jy = (idx / RG::NF) % RG::NR - 1;
+        const int kz = D == 3 ? idx / (RG::NF * RG::NR) - 1 : 0;
+        const int fl = ox >> 1;
+        X[idx] = (ox & 1) ? dd4(tv[Bx::tix(fl - 1, jy, kz)], tv[Bx::tix(fl, jy, kz)], tv[Bx::tix(fl + 1, jy, kz)],
+                                tv[Bx::tix(fl + 2, jy, kz)])
+                          : tv[Bx::tix(fl, jy, kz)];
+      }
+      __syncthreads();
+      auto xr = [&](int ox, int jy, int kz) { return X[((D == 3 ? kz + 1 : 0) * RG::NR + (jy + 1)) * RG::NF + ox]; };
+      for (int idx = threadIdx.x; idx < Gm::NCH * Gm::NI; idx += blockDim.x) {
+        const int ch = idx / Gm::NI, q = idx % Gm::NI;
+        const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
+        const int ox = ((ch >> 0) & 1) * (B - 1) + i, oy = ((ch >> 1) & 1) * (B - 1) + j;
+        const int oz = D == 3 ? ((ch >> 2) & 1) * (B - 1) + k : 0;
+        auto ypass = [&](int kz) -> TS {
+          const int fl = oy >> 1;
+          return (oy & 1) ? dd4(xr(ox, fl - 1, kz), xr(ox, fl, kz), xr(ox, fl + 1, kz), xr(ox, fl + 2, kz))
+                          : xr(ox, fl, kz);
+        };
+        TS val;
+        if (D == 2) {
+          val = ypass(0);
+        } else {
+          const int fl = oz >> 1;
+          val = (oz & 1) ? dd4(ypass(fl - 1), ypass(fl), ypass(fl + 1), ypass(fl + 2)) : ypass(fl);
+        }
+        y[((int64_t)cslot[ch] * nv + v) * pv.vs + q] = val;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -378,15 +461,34 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   const bool all_blocks = pv.cnt->first_round != 0;
   const int prev = pv.cnt->round_id - 1;
   __shared__ int dirty;
+  using PL = Plan<D>;
+  __shared__ int32_t snb[PL::NB];
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
     const TreeDev& td = pv.trees[b.tree];
-    build_ring<D, B>(pv, td, b, R);
+    // equal-level neighbours, one lookup per thread: uniform when all exist
+    int q = b.slot;
+    if (threadIdx.x < PL::NB) {
+      const int n = threadIdx.x;
+      const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
+      if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
+        const int64_t cn[3] = {b.c[0] + o[0], b.c[1] + o[1], b.c[2] + o[2]};
+        q = tab_get<D>(pv, td, b.lvl, cn);
+      }
+      snb[n] = q;
+    }
     if (threadIdx.x == 0) dirty = all_blocks ? 1 : 0;
-    __syncthreads();
-    if (!all_blocks && threadIdx.x < Gm::NR && R.slot[threadIdx.x] >= 0 &&
-        pv.stamp[R.slot[threadIdx.x]] == prev)
-      dirty = 1;
+    const bool uni = __syncthreads_and(q >= 0);
+    if (uni) {
+      // the ring's leaves are the block and its 3^d - 1 equal-level neighbours
+      if (!all_blocks && threadIdx.x < PL::NB && pv.stamp[q] == prev) dirty = 1;
+    } else {
+      build_ring<D, B>(pv, td, b, R);
+      __syncthreads();
+      if (!all_blocks && threadIdx.x < Gm::NR && R.slot[threadIdx.x] >= 0 &&
+          pv.stamp[R.slot[threadIdx.x]] == prev)
+        dirty = 1;
+    }
     __syncthreads();
     if (!dirty) {
       // No leaf of the ring changed in the previous round: the synchronised
@@ -396,7 +498,18 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       __syncthreads();
       continue;
     }
-    fill_tile<D, B, TS, TS, 2>(pv, b, y, y, tile, true, R, cbox, scr);
+    if (threadIdx.x == 0) atomicAdd(&pv.cnt->det_blocks, 1ull);
+    if (uni && nv == 1)
+      gather_uniform<D, B, 2, 1, TS, TS>(pv, b, snb, y, y, tile, true);
+    else if (uni && nv == 4)
+      gather_uniform<D, B, 2, 4, TS, TS>(pv, b, snb, y, y, tile, true);
+    else {
+      if (uni) {
+        build_ring<D, B>(pv, td, b, R);
+        __syncthreads();
+      }
+      fill_tile<D, B, TS, TS, 2>(pv, b, y, y, tile, true, R, cbox, scr);
+    }
     __syncthreads();
     for (int v = 0; v < nv; ++v) {
       const TS* tv = tile + v * Bx::TILE;

@@ -150,7 +150,8 @@ struct RefineRun {
   static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
     constexpr int threads = Threads<D, B>::value;
     using Bx = Box<D, B, 1>;
-    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX + Bx::SCR);
+    const size_t scr = (size_t)std::max<int64_t>((int64_t)pv.nvar * Bx::SCR, RefGeo<D, B>::NX);
+    const size_t smem = kRingBytes + sizeof(TS) * (pv.nvar * (Bx::TILE + Bx::CBOX) + scr);
     auto k = k_refine<D, B, TS, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
@@ -162,7 +163,6 @@ struct RefineRun {
 __global__ void k_refine_counters(Counters* c, int nch);
 __global__ void k_coarsen_counters(Counters* c, int nch);
 __global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check_capacity);
-__global__ void k_round_begin(Counters* c, double* svar, int n, double v);
 
 template <int D>
 void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* mask,
@@ -226,12 +226,17 @@ struct CoarsenRun {
 };
 
 template <int D>
-void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool merge,
-                          const LaunchCfg& lc, cudaStream_t st) {
-  const int nch = 1 << D;
-  k_round_begin<<<1, 256, 0, st>>>(pv.cnt, pv.svar, pv.ntrees * pv.nvar, pv.norm_kind == 1 ? 0.0 : 1.0);
+void launch_round_details(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
+                          cudaStream_t st) {
+  k_round_begin<D><<<1, 256, 0, st>>>(pv, pv.norm_kind == 1 ? 0.0 : 1.0);
   count_launch();
   dispatch_bs<D, DetailsRun>(pv, f, fp64, lc, st);
+}
+
+template <int D>
+void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const LaunchCfg& lc,
+                        cudaStream_t st) {
+  const int nch = 1 << D;
   k_flags<D><<<(int)std::min<int64_t>(4096, (pv.cap + 7) / 8), 256, 0, st>>>(pv);
   count_launch();
   if (!merge) return;
@@ -241,6 +246,13 @@ void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool m
   k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 2);
   k_coarsen_counters<<<1, 1, 0, st>>>(pv.cnt, nch);
   count_launch(3);
+}
+
+template <int D>
+void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool merge,
+                          const LaunchCfg& lc, cudaStream_t st) {
+  launch_round_details<D>(pv, f, fp64, lc, st);
+  launch_round_merge<D>(pv, f, merge, lc, st);
 }
 
 // ------------------------------------------------------------------ sync -----
@@ -362,6 +374,10 @@ void launch_error(const PoolView& pv, const Fields& f, int tree, const double* e
   template void launch_ic<D>(const PoolView&, const Fields&, const LaunchCfg&, cudaStream_t);   \
   template void launch_coarsen_round<D>(const PoolView&, const Fields&, bool, bool,             \
                                         const LaunchCfg&, cudaStream_t);                        \
+  template void launch_round_details<D>(const PoolView&, const Fields&, bool, const LaunchCfg&, \
+                                        cudaStream_t);                                          \
+  template void launch_round_merge<D>(const PoolView&, const Fields&, bool, const LaunchCfg&,   \
+                                      cudaStream_t);                                            \
   template void launch_sync<D>(const PoolView&, const Fields&, double*, const LaunchCfg&,       \
                                cudaStream_t);                                                   \
   template void launch_neighbors<D>(const PoolView&, const int4*, int, int32_t*, int8_t*,       \

@@ -123,16 +123,6 @@ __global__ void k_coarsen_counters(Counters* c, int nch) {
   if (c->merged == 0) c->done = 1;
 }
 
-// Start of a coarsening round: the round works on all blocks unless an earlier
-// round of this step merged nothing (then every kernel of the round is empty).
-__global__ void k_round_begin(Counters* c, double* svar, int n, double v) {
-  if (threadIdx.x == 0) {
-    c->n_round = c->done ? 0 : c->n_act;
-    c->round_id += 1;
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) svar[i] = v;
-}
-
 // Start of a step: coarsening rounds enabled again; hist (nullable) records the
 // number of blocks of the adapted grid the step starts from.
 __global__ void k_step_begin(Counters* c, int32_t* hist) {
