@@ -268,6 +268,8 @@ def main():
     ap.add_argument("--workload", default="swirl", choices=sorted(WORKLOADS))
     ap.add_argument("--capacity", type=int, default=0)
     ap.add_argument("--eps", type=float, default=0.0)
+    ap.add_argument("--precision", default="", choices=["", "fp64", "fp32", "fp32_acc64"],
+                    help="override the workload's arithmetic form (fp64 = plain FP64 method)")
     ap.add_argument("--no-full", action="store_true",
                     help="swirl: do not run on to t = t_a for the error (timed window only)")
     ap.add_argument("--eager", action="store_true", help="host-driven steps instead of CUDA graph replays")
@@ -292,6 +294,10 @@ def main():
             w["name"] = w["name"].replace("eps %g" % WORKLOADS[args.workload]["tree"]["eps"], "eps %g" % args.eps)
     if args.capacity > 0:
         w["capacity"] = args.capacity
+    if args.precision:
+        w["precision"] = args.precision
+        w["detail_fp64"] = args.precision != "fp32" or w["detail_fp64"]
+        w["name"] += " [form: %s]" % args.precision
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return

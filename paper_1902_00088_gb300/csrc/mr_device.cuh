@@ -671,6 +671,73 @@ __device__ __forceinline__ void gather_uniform(const PoolView& pv, const BlockIn
   }
 }
 
+// Gather table of a tile box, the same for every block: entry q (tile index
+// of node (i, j, k), x fastest) = local offset of the node in the block that
+// owns it in a uniform neighbourhood | neighbour index (0 .. 3^d - 1) << 16 |
+// (node inside the block) << 21.
+template <int D, int B, int W>
+__device__ void build_gtab(int32_t* gtab) {
+  using Bx = Box<D, B, W>;
+  using Gm = Geo<D, B>;
+  for (int q = threadIdx.x; q < Bx::NPTS; q += blockDim.x) {
+    const int ijk[3] = {q % Bx::S - W, (q / Bx::S) % Bx::S - W, D == 3 ? q / (Bx::S * Bx::S) - W : 0};
+    int n = 0, mul = 1, l3[3] = {0, 0, 0};
+    bool inner = true;
+    for (int a = 0; a < D; ++a) {
+      const int x = ijk[a];
+      const int s = x < 0 ? 0 : (x <= B - 2 ? 1 : 2);
+      l3[a] = x - (s - 1) * (B - 1);
+      n += s * mul;
+      mul *= 3;
+      inner &= (x >= 0 && x <= B - 1);
+    }
+    gtab[q] = Gm::lin(l3[0], l3[1], l3[2]) | (n << 16) | ((inner ? 1 : 0) << 21);
+  }
+}
+
+// Uniform-neighbourhood gather through the gather table: nbase[n] is the pool
+// offset of neighbour n's variable 0 (slot * NV * vs), own the block's.
+// Same values as gather_uniform.
+template <int D, int B, int W, int NV, typename TF, typename TT>
+__device__ __forceinline__ void gather_table(const PoolView& pv, int64_t own, const int64_t* nbase,
+                                             const int32_t* gtab, const TF* F, TF* Fw, TT* tile, bool commit) {
+  using Bx = Box<D, B, W>;
+  using Gm = Geo<D, B>;
+  constexpr int U = 4;
+  for (int q0 = threadIdx.x; q0 < Bx::NPTS; q0 += U * blockDim.x) {
+    int64_t at[U];
+    bool ok[U], ed[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u * blockDim.x;
+      ok[u] = q < Bx::NPTS;
+      const int e = gtab[ok[u] ? q : 0];
+      const int64_t nbv = nbase[(e >> 16) & 31];
+      at[u] = nbv + (e & 0xffff);
+      ed[u] = commit && ((e >> 21) & 1) && nbv != own;
+    }
+    TF v[U][NV];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int w = 0; w < NV; ++w) v[u][w] = ok[u] ? F[at[u] + (int64_t)w * pv.vs] : TF(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      const int q = q0 + u * blockDim.x;
+#pragma unroll
+      for (int w = 0; w < NV; ++w) {
+        tile[w * Bx::TILE + q] = (TT)v[u][w];
+        if (ed[u]) {
+          const int i = q % Bx::S - W, j = (q / Bx::S) % Bx::S - W, k = D == 3 ? q / (Bx::S * Bx::S) - W : 0;
+          const int64_t me = own + (int64_t)w * pv.vs + Gm::lin(i, j, k);
+          if (F[me] != v[u][w]) Fw[me] = v[u][w];
+        }
+      }
+    }
+  }
+}
+
 // Tensor-product prediction at half-coarse position o (per axis, odd = between
 // coarse nodes) from a tile whose coarse node n sits at tile index n*stride.
 // x first, then y, then z.  Used by refinement (stride 1: the mother's tile) and

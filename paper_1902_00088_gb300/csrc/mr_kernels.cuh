@@ -31,11 +31,17 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
   TC* tile = smem_as<TC>(kRingBytes);  // nvar == 1
   TC* cbox = tile + Bx::TILE;
   TC* scr = cbox + Bx::CBOX;
+  int32_t* gtab = reinterpret_cast<int32_t*>(scr + Bx::SCR);  // 2D: gather table
   __shared__ int32_t splan[2][PL::INTS];
+  __shared__ int64_t snb[2][PL::NB];  // pool offsets of the plan's neighbours
   const int nact = pv.cnt->n_act;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
-  if (blockIdx.x < nact && threadIdx.x < PL::INTS)
-    splan[0][threadIdx.x] = pv.plan[(int64_t)blockIdx.x * PL::INTS + threadIdx.x];
+  if (D == 2) build_gtab<D, B, 2>(gtab);
+  if (blockIdx.x < nact && threadIdx.x < PL::INTS) {
+    const int32_t v = pv.plan[(int64_t)blockIdx.x * PL::INTS + threadIdx.x];
+    splan[0][threadIdx.x] = v;
+    if (threadIdx.x >= PL::NBO && threadIdx.x < PL::NBO + PL::NB) snb[0][threadIdx.x - PL::NBO] = (int64_t)v * pv.vs;
+  }
   __syncthreads();
   int buf = 0;
   for (int p = blockIdx.x; p < nact; p += gridDim.x, buf ^= 1) {
@@ -46,7 +52,11 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
     const BlockInfo b = plan_block<D>(pl);
     const TreeDev& td = pv.trees[b.tree];
     if ((pl[1] >> 30) & 1) {
-      gather_uniform<D, B, 2, 1, TSRC, TC>(pv, b, pl + PL::NBO, src, (TSRC*)src, tile, stage == 0);
+      if (D == 2)
+        gather_table<D, B, 2, 1, TSRC, TC>(pv, (int64_t)b.slot * pv.vs, snb[buf], gtab, src, (TSRC*)src, tile,
+                                           stage == 0);
+      else
+        gather_uniform<D, B, 2, 1, TSRC, TC>(pv, b, pl + PL::NBO, src, (TSRC*)src, tile, stage == 0);
     } else {
       build_ring<D, B>(pv, td, b, R);
       __syncthreads();
@@ -59,10 +69,65 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
     const double ct = pv.tt ? pv.tt[b.tree].ct[stage] : sa.ct[b.tree];
     const int64_t base = (int64_t)b.slot * pv.vs;  // nvar == 1
     const int sh = td.Jmax - b.lvl;
-    // UC points per thread at a time: their state, accumulator and velocity
-    // loads are issued together, then the stencils and the updates
-    constexpr int UC = D == 3 ? 4 : 3;
-    for (int q0 = threadIdx.x; q0 < Gm::NI; q0 += UC * NT) {
+    if constexpr (D == 2) {
+      // thread = (column i, rows j0, j0 + G, ...): the column's velocity
+      // factors are loaded once; the rows' loads are issued together
+      constexpr int G = NT / B, RU = (B + G - 1) / G;
+      const int t = threadIdx.x;
+      if (t < G * B) {
+        const int i = t % B, j0 = t / B;
+        double ax = 0.0, bx = 0.0;
+        const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
+        const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
+        if (RHS == MR_RHS_SWIRL) {
+          const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
+          ax = A[Ux];
+          bx = Bt[Ux];
+        }
+        TS yv[RU], av[RU];
+        double u0[RU], u1[RU];
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const int j = j0 + r * G;
+          yv[r] = av[r] = TS(0);
+          u0[r] = td.rhs[0];
+          u1[r] = td.rhs[1];
+          if (j >= B) continue;
+          const int q = j * B + i;
+          if (stage <= 2) yv[r] = y[base + q];  // stage 0: committed (synchronised) y_n
+          if (stage >= 1) av[r] = acc[base + q];
+          if (RHS == MR_RHS_SWIRL) {
+            const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
+            u0[r] = ct * (ax * Bt[Uy]);
+            u1[r] = -(ct * (A[Uy] * bx));
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+          const int j = j0 + r * G;
+          if (j >= B) continue;
+          const TC* t0 = tile + Bx::tix(i, j, 0);
+          const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
+          const TC dyv = ((t0[-2 * Bx::S] - t0[2 * Bx::S]) + TC(8) * (t0[Bx::S] - t0[-Bx::S])) * c;
+          const TC s = (TC)u0[r] * dxv + (TC)u1[r] * dyv;
+          const TS kk = (TS)(-s);
+          const int64_t at = base + j * B + i;
+          if (stage == 0) {
+            acc[at] = yv[r] + (TS)ca * kk;
+            ynext[at] = (TY)(yv[r] + (TS)cy * kk);
+          } else if (stage == 1 || stage == 2) {
+            acc[at] = av[r] + (TS)ca * kk;
+            ynext[at] = (TY)(yv[r] + (TS)cy * kk);
+          } else {
+            y[at] = av[r] + (TS)ca * kk;
+          }
+        }
+      }
+    }
+    // 3D: UC points per thread at a time: their state, accumulator and
+    // velocity loads are issued together, then the stencils and the updates
+    constexpr int UC = D == 3 ? 4 : 1;
+    for (int q0 = threadIdx.x; D == 3 && q0 < Gm::NI; q0 += UC * NT) {
       TS yv[UC], av[UC];
       double u0[UC], u1[UC];
 #pragma unroll
@@ -111,7 +176,10 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
         }
       }
     }
-    if (pn < nact && threadIdx.x < PL::INTS) splan[buf ^ 1][threadIdx.x] = pre;
+    if (pn < nact && threadIdx.x < PL::INTS) {
+      splan[buf ^ 1][threadIdx.x] = pre;
+      if (threadIdx.x >= PL::NBO && threadIdx.x < PL::NBO + PL::NB) snb[buf ^ 1][threadIdx.x - PL::NBO] = (int64_t)pre * pv.vs;
+    }
     __syncthreads();
   }
 }

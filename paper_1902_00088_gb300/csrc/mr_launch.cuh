@@ -39,7 +39,7 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
   constexpr int threads = Threads<D, B>::value;
   const int nv = 1;
   using Bx = Box<D, B, 2>;
-  const size_t smem = kRingBytes + sizeof(TY) * nv * (Bx::TILE + Bx::CBOX + Bx::SCR);
+  const size_t smem = kRingBytes + sizeof(TY) * nv * (Bx::TILE + Bx::CBOX + Bx::SCR) + (D == 2 ? 4 * Bx::NPTS : 0);
   TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
   if (stage == 0) {
     auto k = k_stage_adv<D, B, RHS, TS, TY, TS, threads>;
