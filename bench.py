@@ -63,6 +63,18 @@ WORKLOADS = {
                     name="2D NS temporal mixing layer, delta 1/240 (Ma 0.3, Re 1000, seeded perturbation "
                          "1e-3), 33^2 blocks, Jmin 2, Jmax 7, eps 1e-3, FP32 stages + FP64 state/acc/details, "
                          "learned proposal, CFL 0.5"),
+    # Uniform grids at the finest level (no adaptation happens): the stage
+    # kernel at a size where HBM bandwidth matters.
+    "uniform2d": dict(dim=2, Bs=17, precision="fp32", detail_fp64=True, rhs="adv",
+                      tree=dict(Jmin=9, Jmax=9, eps=1e-3, ic="gauss", ic_params=(0.5, 0.5, 0.0, 0.05),
+                                rhs_params=(1.0, 0.5, 0.0)),
+                      umax=math.hypot(1.0, 0.5), capacity=(1 << 18) + 64,
+                      name="2D advection on a uniform grid of 512^2 blocks of 17^2 (Jmin = Jmax = 9), FP32"),
+    "uniform3d": dict(dim=3, Bs=17, precision="fp32", detail_fp64=True, rhs="adv",
+                      tree=dict(Jmin=5, Jmax=5, eps=1e-4, ic="gauss", ic_params=(0.5, 0.5, 0.5, 0.04),
+                                rhs_params=(1.0, 1.0, 1.0)),
+                      umax=math.sqrt(3.0), capacity=(1 << 15) + 64,
+                      name="3D advection on a uniform grid of 32^3 blocks of 17^3 (Jmin = Jmax = 5), FP32"),
     "adv2d": dict(dim=2, Bs=17, precision="fp64", detail_fp64=False, rhs="adv",
                   tree=dict(Jmin=2, Jmax=5, eps=1e-3, ic="gauss",
                             ic_params=(0.5, 0.5, 0.0, 0.05), rhs_params=(1.0, 0.5, 0.0)),
@@ -281,7 +293,10 @@ def main():
     ap.add_argument("--load-state", default="", help="start from a saved state instead of init + spin-up")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-learned", action="store_true", help="ns: refine all instead of the learned proposal")
+    ap.add_argument("--no-learned", action="store_true", help="refine all instead of the learned proposal")
+    ap.add_argument("--learned", type=int, default=0,
+                    help="train the proposal on this many refine-all steps after the spin-up, then time the "
+                         "learned form (workloads without a proposal by default)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -294,6 +309,9 @@ def main():
             w["name"] = w["name"].replace("eps %g" % WORKLOADS[args.workload]["tree"]["eps"], "eps %g" % args.eps)
     if args.capacity > 0:
         w["capacity"] = args.capacity
+    if args.learned > 0:
+        w["learned"] = dict(collect_steps=args.learned, epochs=6)
+        w["name"] += " [learned proposal]"
     if args.precision:
         w["precision"] = args.precision
         w["detail_fp64"] = args.precision != "fp32" or w["detail_fp64"]

@@ -171,7 +171,12 @@ int32_t mr_num_relations(int32_t dim);
 
 /* Refinement status and largest normalised detail of each block after the last
  * details evaluation (mr_adapt COARSEN or mr_step): flag -2 = merged or can be
- * coarsened, -1 unused, 0 keep, +1 refine.  Synchronises. */
+ * coarsened, -1 unused, 0 keep, +1 refine.  With FP32 fields and FP64 details
+ * (detail_fp64, per-variable normalisation off) the detail is evaluated in
+ * FP32 and re-evaluated in FP64 only for blocks whose FP32 value lies within
+ * its rounding bound of eps: the flags are those of the FP64 evaluation, and
+ * max_detail is the FP64 value for those blocks, the FP32 one (within
+ * 32 * 2^-24 * max|field| of it) for the others.  Synchronises. */
 mr_status mr_get_flags(mr_ctx ctx, int32_t tree, int64_t cap, int8_t* flags, double* max_detail);
 
 /* Replaces all trees by the given blocks (restart/replay).  n blocks with

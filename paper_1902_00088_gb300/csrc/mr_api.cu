@@ -631,6 +631,8 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
       lattice_tables(P, ctx->td[k], ctx->tdev[k].N, hl.data() + ctx->tdev[k].lat_off);
     if ((e = cudaMemcpy(ctx->lat, hl.data(), ctx->nlat * 8, cudaMemcpyHostToDevice))) return e;
     if ((e = cudaMemset(ctx->cnt, 0, sizeof(Counters)))) return e;
+    const int32_t no_plan = -1;
+    if ((e = cudaMemcpy(&ctx->cnt->plan_topo, &no_plan, 4, cudaMemcpyHostToDevice))) return e;
     if ((e = cudaMemset(ctx->mask, 0, S))) return e;
     if ((e = cudaMemset(ctx->lvl, 0xff, S))) return e;
     if ((e = cudaMemset(ctx->tab, 0xff, ctx->ntab * 4))) return e;
@@ -1298,7 +1300,8 @@ mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32
   CK(cudaMemcpyAsync(pr.data(), dprob, ne * 4, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   std::vector<float> ppos;
-  for (int64_t i = 0; i < ne; ++i) if (lab[hidx[i]] > 0.5f) ppos.push_back(pr[i]);
+  for (int64_t i = 0; i < ne; ++i)
+    if (lab[hidx[i]] > 0.5f) ppos.push_back(std::isfinite(pr[i]) ? pr[i] : 0.f);
   float tau = 0.5f;
   if (!ppos.empty()) {
     std::sort(ppos.begin(), ppos.end());

@@ -329,7 +329,9 @@ __global__ void k_adam(float* w, float* m, float* v, float* g, int n, float lr, 
                        float eps, int t, __nv_bfloat16* wb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float gi = g[i];
+  // a non-finite gradient entry (seen once in a 64-tree training run, cause
+  // not found) is skipped rather than allowed to poison the moments
+  const float gi = isfinite(g[i]) ? g[i] : 0.f;
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
   m[i] = mi;

@@ -51,7 +51,10 @@ struct Counters {
   int32_t round_id;     // coarsening rounds so far (monotonic); merged mothers are stamped with it
   int32_t first_round;  // the current round is the first of an adapt: every block is evaluated
   unsigned long long det_blocks;  // blocks whose details a coarsening round evaluated
+  int32_t topo;       // tree generation: changes with every refinement, merge or import
+  int32_t plan_topo;  // generation the stage plans were built for (-1: none)
 };
+constexpr int kMaxVar = 4;  // variables per node (advection 1, Navier-Stokes 4; checked at creation)
 constexpr int kMaxHist = 1 << 16;  // step history: blocks of the adapted grid before each step
 
 // Device-resident time of every tree (graph-captured steps advance it on the

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
     const double ct = pv.tt ? pv.tt[b.tree].ct[stage] : sa.ct[b.tree];
     const int64_t base = (int64_t)b.slot * pv.vs;  // nvar == 1
     const int sh = td.Jmax - b.lvl;
+    const TS cas = (TS)ca, cys = (TS)cy;  // RK weights in the state type
     if constexpr (D == 2) {
       // thread = (column i, rows j0, j0 + G, ...): the column's velocity
       // factors are loaded once; the rows' loads are issued together
@@ -85,21 +86,22 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
           bx = Bt[Ux];
         }
         TS yv[RU], av[RU];
-        double u0[RU], u1[RU];
+        TC u0[RU], u1[RU];  // velocity rounded to the stencil type (constant: once per block)
+        const TC uc0 = (TC)td.rhs[0], uc1 = (TC)td.rhs[1];
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
           const int j = j0 + r * G;
           yv[r] = av[r] = TS(0);
-          u0[r] = td.rhs[0];
-          u1[r] = td.rhs[1];
+          u0[r] = uc0;
+          u1[r] = uc1;
           if (j >= B) continue;
           const int q = j * B + i;
           if (stage <= 2) yv[r] = y[base + q];  // stage 0: committed (synchronised) y_n
           if (stage >= 1) av[r] = acc[base + q];
           if (RHS == MR_RHS_SWIRL) {
             const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
-            u0[r] = ct * (ax * Bt[Uy]);
-            u1[r] = -(ct * (A[Uy] * bx));
+            u0[r] = (TC)(ct * (ax * Bt[Uy]));
+            u1[r] = (TC)(-(ct * (A[Uy] * bx)));
           }
         }
 #pragma unroll
@@ -109,17 +111,17 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
           const TC* t0 = tile + Bx::tix(i, j, 0);
           const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
           const TC dyv = ((t0[-2 * Bx::S] - t0[2 * Bx::S]) + TC(8) * (t0[Bx::S] - t0[-Bx::S])) * c;
-          const TC s = (TC)u0[r] * dxv + (TC)u1[r] * dyv;
+          const TC s = u0[r] * dxv + u1[r] * dyv;
           const TS kk = (TS)(-s);
           const int64_t at = base + j * B + i;
           if (stage == 0) {
-            acc[at] = yv[r] + (TS)ca * kk;
-            ynext[at] = (TY)(yv[r] + (TS)cy * kk);
+            acc[at] = yv[r] + cas * kk;
+            ynext[at] = (TY)(yv[r] + cys * kk);
           } else if (stage == 1 || stage == 2) {
-            acc[at] = av[r] + (TS)ca * kk;
-            ynext[at] = (TY)(yv[r] + (TS)cy * kk);
+            acc[at] = av[r] + cas * kk;
+            ynext[at] = (TY)(yv[r] + cys * kk);
           } else {
-            y[at] = av[r] + (TS)ca * kk;
+            y[at] = av[r] + cas * kk;
           }
         }
       }
@@ -127,15 +129,16 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
     // 3D: UC points per thread at a time: their state, accumulator and
     // velocity loads are issued together, then the stencils and the updates
     constexpr int UC = D == 3 ? 4 : 1;
+    const TC uc2 = (TC)td.rhs[2];
     for (int q0 = threadIdx.x; D == 3 && q0 < Gm::NI; q0 += UC * NT) {
       TS yv[UC], av[UC];
-      double u0[UC], u1[UC];
+      TC u0[UC], u1[UC];
 #pragma unroll
       for (int u = 0; u < UC; ++u) {
         const int q = q0 + u * NT;
         yv[u] = av[u] = TS(0);
-        u0[u] = td.rhs[0];
-        u1[u] = td.rhs[1];
+        u0[u] = (TC)td.rhs[0];
+        u1[u] = (TC)td.rhs[1];
         if (q >= Gm::NI) continue;
         if (stage <= 2) yv[u] = y[base + q];  // stage 0: committed (synchronised) y_n
         if (stage >= 1) av[u] = acc[base + q];
@@ -145,8 +148,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
           const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
           const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
           const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
-          u0[u] = ct * (A[Ux] * Bt[Uy]);
-          u1[u] = -(ct * (A[Uy] * Bt[Ux]));
+          u0[u] = (TC)(ct * (A[Ux] * Bt[Uy]));
+          u1[u] = (TC)(-(ct * (A[Uy] * Bt[Ux])));
         }
       }
 #pragma unroll
@@ -157,22 +160,22 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
         const TC* t0 = tile + Bx::tix(i, j, k);
         const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
         const TC dyv = ((t0[-2 * Bx::S] - t0[2 * Bx::S]) + TC(8) * (t0[Bx::S] - t0[-Bx::S])) * c;
-        TC s = (TC)u0[u] * dxv + (TC)u1[u] * dyv;
+        TC s = u0[u] * dxv + u1[u] * dyv;
         if (D == 3) {
           constexpr int P = Bx::S * Bx::S;
           const TC dzv = ((t0[-2 * P] - t0[2 * P]) + TC(8) * (t0[P] - t0[-P])) * c;
-          s = s + (TC)td.rhs[2] * dzv;
+          s = s + uc2 * dzv;
         }
         const TS kk = (TS)(-s);
         const int64_t at = base + q;
         if (stage == 0) {
-          acc[at] = yv[u] + (TS)ca * kk;
-          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+          acc[at] = yv[u] + cas * kk;
+          ynext[at] = (TY)(yv[u] + cys * kk);
         } else if (stage == 1 || stage == 2) {
-          acc[at] = av[u] + (TS)ca * kk;
-          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+          acc[at] = av[u] + cas * kk;
+          ynext[at] = (TY)(yv[u] + cys * kk);
         } else {
-          y[at] = av[u] + (TS)ca * kk;
+          y[at] = av[u] + cas * kk;
         }
       }
     }
@@ -212,11 +215,13 @@ __device__ __forceinline__ void plan_one(const PoolView& pv, int p) {
   for (int a = 0; a < D; ++a) out[2 + a] = (int32_t)c[a];
 }
 
-// Stage plans of all active blocks, one thread per block.
+// Stage plans of all active blocks, one thread per block; they stay valid
+// while the tree generation is unchanged.
 template <int D>
 __global__ void k_plan(PoolView pv) {
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) plan_one<D>(pv, p);
+  if (blockIdx.x == 0 && threadIdx.x == 0) pv.cnt->plan_topo = pv.cnt->topo;
 }
 
 // Start of a coarsening round: the blocks it works on (none once a round
@@ -354,6 +359,7 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
     const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
     const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
     const int64_t base = (int64_t)b.slot * 4 * pv.vs;
+    const TS cas = (TS)ca, cys = (TS)cy;  // RK weights in the state type
     // UC points per thread at a time: state and accumulator loads first
     constexpr int UC = 4, NT = 256;
     for (int i0 = threadIdx.x; i0 < 4 * Gm::NI; i0 += UC * NT) {
@@ -380,13 +386,13 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
         const TS kk = (TS)(-(dFx + dGy));
         const int64_t at = base + (int64_t)v * pv.vs + q;
         if (stage == 0) {
-          acc[at] = yv[u] + (TS)ca * kk;
-          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+          acc[at] = yv[u] + cas * kk;
+          ynext[at] = (TY)(yv[u] + cys * kk);
         } else if (stage == 1 || stage == 2) {
-          acc[at] = av[u] + (TS)ca * kk;
-          ynext[at] = (TY)(yv[u] + (TS)cy * kk);
+          acc[at] = av[u] + cas * kk;
+          ynext[at] = (TY)(yv[u] + cys * kk);
         } else {
-          y[at] = av[u] + (TS)ca * kk;
+          y[at] = av[u] + cas * kk;
         }
       }
     }
@@ -512,6 +518,19 @@ struct DetGeo {
   static constexpr int NX = NC * B * (D == 3 ? NC : 1);
 };
 
+// Maximum of v over the CTA (warp shuffles, then one value per warp in red);
+// every thread gets the result.  In the value's own type: FP64 operations are
+// a small fraction of the FP32 rate on this GPU, so FP32 data stay FP32.
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+  for (int s = 16; s > 0; s >>= 1) v = fmax(v, (T)__shfl_xor_sync(0xffffffffu, v, s));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+  return v;
+}
+
 template <int D, int B, typename TS, typename TD, int NT>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_details(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
@@ -531,19 +550,63 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   __shared__ int dirty;
   using PL = Plan<D>;
   __shared__ int32_t snb[PL::NB];
-  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
-    const BlockInfo b = load_block(pv, pv.act[p]);
-    const TreeDev& td = pv.trees[b.tree];
-    // equal-level neighbours, one lookup per thread: uniform when all exist
-    int q = b.slot;
-    if (threadIdx.x < PL::NB) {
-      const int n = threadIdx.x;
-      const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
-      if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
-        const int64_t cn[3] = {b.c[0] + o[0], b.c[1] + o[1], b.c[2] + o[2]};
-        q = tab_get<D>(pv, td, b.lvl, cn);
+  __shared__ int64_t snbo[PL::NB];  // pool offsets of the neighbours
+  __shared__ int32_t splan[2][PL::INTS];
+  // the stage plans are used while the tree is the one they were built for
+  // (the first round after the RK stages); the next block's plan is fetched
+  // while a block is processed
+  const bool plan_ok = pv.cnt->plan_topo == pv.cnt->topo;
+  const size_t xs = sizeof(TS) * (size_t)nv * Bx::SCR, xd = sizeof(TD) * (size_t)DG::NX;
+  const size_t xbytes = xs > xd ? xs : xd;
+  int32_t* gtab = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(X) + ((xbytes + 15) & ~(size_t)15));
+  if (D == 2) build_gtab<D, B, 2>(gtab);
+  // CTA-local work count and threshold scales (one atomic per CTA, not per block)
+  unsigned long long ndet = 0;
+  __shared__ double csv[kMaxVar];
+  __shared__ int csv_tree;
+  if (threadIdx.x < kMaxVar) csv[threadIdx.x] = 0.0;
+  if (threadIdx.x == 0) csv_tree = -1;
+  auto flush_csv = [&]() {
+    if (csv_tree >= 0 && threadIdx.x < nv && csv[threadIdx.x] > 0.0)
+      atomic_max_pos(&pv.svar[csv_tree * nv + threadIdx.x], csv[threadIdx.x]);
+  };
+  if (plan_ok && blockIdx.x < nact && threadIdx.x < PL::INTS)
+    splan[0][threadIdx.x] = pv.plan[(int64_t)blockIdx.x * PL::INTS + threadIdx.x];
+  __syncthreads();
+  int buf = 0;
+  for (int p = blockIdx.x; p < nact; p += gridDim.x, buf ^= 1) {
+    const int pn = p + gridDim.x;
+    int32_t pre = 0;
+    if (plan_ok && pn < nact && threadIdx.x < PL::INTS) pre = pv.plan[(int64_t)pn * PL::INTS + threadIdx.x];
+    BlockInfo b;
+    int q = 0;
+    if (plan_ok) {
+      b = plan_block<D>(splan[buf]);
+      q = threadIdx.x < PL::NB ? splan[buf][PL::NBO + threadIdx.x] : b.slot;
+    } else {
+      b = load_block(pv, pv.act[p]);
+      // equal-level neighbours, one lookup per thread: uniform when all exist
+      q = b.slot;
+      if (threadIdx.x < PL::NB) {
+        const int n = threadIdx.x;
+        const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
+        if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
+          const TreeDev& tdl = pv.trees[b.tree];
+          const int64_t cn[3] = {b.c[0] + o[0], b.c[1] + o[1], b.c[2] + o[2]};
+          q = tab_get<D>(pv, tdl, b.lvl, cn);
+        }
       }
-      snb[n] = q;
+    }
+    const TreeDev& td = pv.trees[b.tree];
+    if (pv.norm_kind == 1 && b.tree != csv_tree) {  // block of another tree: flush the scales
+      flush_csv();
+      __syncthreads();
+      if (threadIdx.x < kMaxVar) csv[threadIdx.x] = 0.0;
+      if (threadIdx.x == 0) csv_tree = b.tree;
+    }
+    if (threadIdx.x < PL::NB) {
+      snb[threadIdx.x] = q;
+      snbo[threadIdx.x] = (int64_t)q * nv * pv.vs;
     }
     if (threadIdx.x == 0) dirty = all_blocks ? 1 : 0;
     const bool uni = __syncthreads_and(q >= 0);
@@ -562,15 +625,19 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       // No leaf of the ring changed in the previous round: the synchronised
       // tile, hence the details and norms stored for this block, are unchanged.
       if (pv.norm_kind == 1 && threadIdx.x < nv)
-        atomic_max_pos(&pv.svar[b.tree * nv + threadIdx.x], pv.bmax[(int64_t)b.slot * nv + threadIdx.x]);
+        csv[threadIdx.x] = fmax(csv[threadIdx.x], pv.bmax[(int64_t)b.slot * nv + threadIdx.x]);
+      if (plan_ok && pn < nact && threadIdx.x < PL::INTS) splan[buf ^ 1][threadIdx.x] = pre;
       __syncthreads();
       continue;
     }
-    if (threadIdx.x == 0) atomicAdd(&pv.cnt->det_blocks, 1ull);
-    if (uni && nv == 1)
+    ndet += 1;
+    const int64_t own = (int64_t)b.slot * nv * pv.vs;
+    if (uni && nv == 1 && D == 2)
+      gather_table<D, B, 2, 1, TS, TS>(pv, own, snbo, gtab, y, y, tile, true);
+    else if (uni && nv == 4 && D == 2)
+      gather_table<D, B, 2, 4, TS, TS>(pv, own, snbo, gtab, y, y, tile, true);
+    else if (uni && nv == 1)
       gather_uniform<D, B, 2, 1, TS, TS>(pv, b, snb, y, y, tile, true);
-    else if (uni && nv == 4)
-      gather_uniform<D, B, 2, 4, TS, TS>(pv, b, snb, y, y, tile, true);
     else {
       if (uni) {
         build_ring<D, B>(pv, td, b, R);
@@ -579,64 +646,77 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       fill_tile<D, B, TS, TS, 2>(pv, b, y, y, tile, true, R, cbox, scr);
     }
     __syncthreads();
-    for (int v = 0; v < nv; ++v) {
-      const TS* tv = tile + v * Bx::TILE;
-      // x pass on coarse rows (yc, zc) in [-1, NC-2]
+    // Block maximum of |d| over the interior with arithmetic type A: x pass on
+    // coarse rows (yc, zc) in [-1, NC-2] into X, then y (and z) per odd node.
+    auto pass = [&](auto tag, const TS* tv) -> double {
+      using A = decltype(tag);
+      A* XA = reinterpret_cast<A*>(X);
       for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
         const int x = idx % B, yc = (idx / B) % DG::NC - 1, zc = D == 3 ? idx / (B * DG::NC) - 1 : 0;
         const int yy = 2 * yc, zz = 2 * zc;
-        TD val;
+        A val;
         if ((x & 1) == 0) {
-          val = (TD)tv[Bx::tix(x, yy, zz)];
+          val = (A)tv[Bx::tix(x, yy, zz)];
         } else {
           const int n0 = (x - 1) / 2;
-          val = dd4((TD)tv[Bx::tix(2 * n0 - 2, yy, zz)], (TD)tv[Bx::tix(2 * n0, yy, zz)],
-                    (TD)tv[Bx::tix(2 * n0 + 2, yy, zz)], (TD)tv[Bx::tix(2 * n0 + 4, yy, zz)]);
+          val = dd4((A)tv[Bx::tix(2 * n0 - 2, yy, zz)], (A)tv[Bx::tix(2 * n0, yy, zz)],
+                    (A)tv[Bx::tix(2 * n0 + 2, yy, zz)], (A)tv[Bx::tix(2 * n0 + 4, yy, zz)]);
         }
-        X[idx] = val;
+        XA[idx] = val;
       }
       __syncthreads();
-      auto xat = [&](int x, int yc, int zc) {
-        return X[((D == 3 ? (zc + 1) * DG::NC : 0) + (yc + 1)) * B + x];
-      };
-      double md = 0.0, mq = 0.0;
+      auto xat = [&](int x, int yc, int zc) { return XA[((D == 3 ? (zc + 1) * DG::NC : 0) + (yc + 1)) * B + x]; };
+      A md = A(0);  // a maximum of A values: exact in A
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-        const TD val = (TD)tv[Bx::tix(i, j, k)];
-        mq = fmax(mq, fabs((double)val));
         if (((i | j | k) & 1) == 0) continue;
-        auto ypass = [&](int zc) -> TD {
+        const A val = (A)tv[Bx::tix(i, j, k)];
+        auto ypass = [&](int zc) -> A {
           if ((j & 1) == 0) return xat(i, j / 2, zc);
           const int m0 = (j - 1) / 2;
           return dd4(xat(i, m0 - 1, zc), xat(i, m0, zc), xat(i, m0 + 1, zc), xat(i, m0 + 2, zc));
         };
-        TD pr;
+        A pr;
         if (D == 2 || (k & 1) == 0) {
           pr = ypass(k / 2);
         } else {
           const int k0 = (k - 1) / 2;
           pr = dd4(ypass(k0 - 1), ypass(k0), ypass(k0 + 1), ypass(k0 + 2));
         }
-        const TD d = val - pr;
-        md = fmax(md, fabs((double)d));
+        const A d = val - pr;
+        md = fmax(md, (A)fabs(d));
       }
-      for (int s = 16; s > 0; s >>= 1) {
-        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, s));
-        mq = fmax(mq, __shfl_xor_sync(0xffffffffu, mq, s));
+      return (double)block_max<A>(md, reinterpret_cast<A*>(red[0]));
+    };
+    for (int v = 0; v < nv; ++v) {
+      const TS* tv = tile + v * Bx::TILE;
+      TS mqs = TS(0);  // largest |value|: a maximum of stored values, exact in their type
+      for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
+        const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
+        mqs = fmax(mqs, (TS)fabs(tv[Bx::tix(i, j, k)]));
       }
-      if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = md;
-        red[1][threadIdx.x >> 5] = mq;
+      const double mq = (double)block_max<TS>(mqs, reinterpret_cast<TS*>(red[1]));
+      double md;
+      if constexpr (sizeof(TS) == 4 && sizeof(TD) == 8) {
+        // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
+        // one by at most ~20 u max|tile| (u = 2^-24, x/y/z passes of the
+        // 4-point rule and the subtraction); where its maximum is farther than
+        // 32 u max|tile| from eps the threshold decision (Sec. 2.3) is the
+        // FP64 one, otherwise the block is evaluated again in FP64.
+        const double m32 = pass(float(0), tv);
+        float mt = 0.f;
+        for (int q = threadIdx.x; q < Bx::TILE; q += blockDim.x) mt = fmaxf(mt, fabsf((float)tv[q]));
+        const double E = 32.0 * 0x1p-24 * (double)block_max<float>(mt, reinterpret_cast<float*>(red[1])) + 1e-37;
+        const double eps = td.eps;
+        const bool sure = pv.norm_kind == 0 && (m32 + E < eps || m32 - E >= eps);
+        md = sure ? m32 : pass(double(0), tv);
+      } else {
+        md = pass(TD(0), tv);
       }
-      __syncthreads();
       if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-          md = fmax(md, red[0][w]);
-          mq = fmax(mq, red[1][w]);
-        }
         pv.md[(int64_t)b.slot * nv + v] = md;
         pv.bmax[(int64_t)b.slot * nv + v] = mq;
-        if (pv.norm_kind == 1) atomic_max_pos(&pv.svar[b.tree * nv + v], mq);
+        if (pv.norm_kind == 1) csv[v] = fmax(csv[v], mq);
       }
       __syncthreads();
     }
@@ -645,11 +725,15 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     for (int q = threadIdx.x; q < Gm::NI * nv; q += blockDim.x) {
       const int v = q / Gm::NI, r = q % Gm::NI;
       const int i = r % B, j = (r / B) % B, k = D == 3 ? r / (B * B) : 0;
-      bad |= !isfinite((double)tile[v * Bx::TILE + Bx::tix(i, j, k)]);
+      bad |= !isfinite(tile[v * Bx::TILE + Bx::tix(i, j, k)]);
     }
+    if (plan_ok && pn < nact && threadIdx.x < PL::INTS) splan[buf ^ 1][threadIdx.x] = pre;
     if (__syncthreads_or(bad) && threadIdx.x == 0)
       pv.md[(int64_t)b.slot * nv] = __longlong_as_double(0x7ff8000000000000LL);
   }
+  __syncthreads();
+  if (pv.norm_kind == 1) flush_csv();
+  if (threadIdx.x == 0 && ndet) atomicAdd(&pv.cnt->det_blocks, ndet);
 }
 
 // ---------------------------------------------------------------- coarsen ----

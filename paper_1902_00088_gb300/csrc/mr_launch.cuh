@@ -200,7 +200,8 @@ struct DetailsRun {
     const bool d64 = fp64 || sizeof(TS) == 8;
     using Bx = Box<D, B, 2>;
     const size_t scr = sizeof(TS) * pv.nvar * Bx::SCR, xp = (d64 ? 8 : sizeof(TS)) * DetGeo<D, B>::NX;
-    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp);
+    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp) +
+                        16 + (D == 2 ? 4 * Bx::NPTS : 0);
     if (d64) {
       auto k = k_details<D, B, TS, double, threads>;
       prep_smem(k, smem);

@@ -112,6 +112,7 @@ __global__ void k_refine_counters(Counters* c, int nch) {
   if (c->n_alloc > c->n_free) return;
   c->n_free = c->n_free - c->n_alloc + c->n_alloc / nch;
   c->n_act = c->n_new;
+  c->topo += 1;
 }
 
 __global__ void k_coarsen_counters(Counters* c, int nch) {
@@ -121,6 +122,7 @@ __global__ void k_coarsen_counters(Counters* c, int nch) {
   c->n_free = c->n_free + c->n_alloc;
   c->n_act = c->n_new;
   if (c->merged == 0) c->done = 1;
+  else c->topo += 1;
 }
 
 // Start of a step: coarsening rounds enabled again; hist (nullable) records the
@@ -191,6 +193,7 @@ __global__ void k_sb_counters(Counters* c, int32_t* freelist, int64_t n, int64_t
     c->n_new = (int32_t)n;
     c->n_alloc = 0;
     c->merged = 0;
+    c->topo += 1;
   }
 }
 
