@@ -405,7 +405,8 @@ def main():
         g.set_time(t, dts)
         autotune = args.autotune if args.autotune >= 0 else (3 if "trees" in w else 0)
         if autotune > 0:
-            tuned = g.autotune(autotune)
+            t_ = g.autotune(autotune)
+            tuned = {"ctas_per_sm": t_ % 100 or "occupancy", "stage_form": ["cta per block", "warp per block"][t_ // 100]}
             steps_done += 7 * (autotune + 1) + 0
         g.step_graph(args.warmup)
         steps_done += args.warmup
@@ -604,7 +605,7 @@ def main():
             "config": {"workload": w["name"], "trees": nt, "blocks_at_start": nb0, "blocks_at_end": nb,
                        "Bs": B, "dim": d, "dt": float(dts[0]) if nt == 1 else "per tree",
                        "mode": "eager" if not graph else "cuda-graph step replay (%s rounds)" % g.graph_mode(),
-                       "autotuned_ctas_per_sm": tuned,
+                       "autotuned": tuned,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2_flush": "256 MiB written between timed steps (untimed)",
                        "step_ms_p50": pct(0.5), "step_ms_p99": pct(0.99),

@@ -202,6 +202,7 @@ Counters read_counters(mr_ctx ctx) {
   Counters h{};
   cudaStreamSynchronize(ctx->st);
   cudaMemcpy(&h, ctx->cnt, sizeof(h), cudaMemcpyDeviceToHost);
+  ctx->lc.n_hint = h.n_act;
   return h;
 }
 
@@ -543,6 +544,8 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     }
     ctx->lc.num_sms = prop.multiProcessorCount;
     ctx->lc.grid_mult = 0;
+    ctx->lc.stage_form = -1;
+    ctx->lc.n_hint = 0;
   }
   const int d = P.dim, B = P.Bs, nv = P.nvar;
   int64_t ni = 1;
@@ -1053,6 +1056,7 @@ void drop_graph(mr_ctx ctx) {
 
 mr_status build_graph(mr_ctx ctx) {
   drop_graph(ctx);
+  read_counters(ctx);  // block count for the choice of the stage form
   if (ctx->collect) return fail(ctx, MR_EINVAL, "training samples are collected by host-driven steps (mr_step)");
   if (ctx->refine_mode == 1) {
     mr_status s = ensure_feat(ctx, ctx->S);
@@ -1118,12 +1122,15 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
   if (!ctx || steps < 1) return MR_EINVAL;
   const int cand[] = {1, 2, 3, 4, 6, 8, 0};
   float best = 1e30f;
-  int bestm = 0;
+  int bestm = 0, bestf = 0;
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
-  for (int m : cand) {
+  const int nforms = ctx->p.dim == 2 ? 2 : 1;
+  for (int ci = 0; ci < 7 * nforms; ++ci) {
+    const int m = cand[ci % 7], form = ci / 7;
     ctx->lc.grid_mult = m;
+    ctx->lc.stage_form = form;
     mr_status s = build_graph(ctx);
     if (s) return s;
     CK(cudaGraphLaunch(ctx->gexec, ctx->st));  // warm
@@ -1135,14 +1142,15 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, a, b));
     ctx->stats.steps += steps + 1;
-    if (ms < best) { best = ms; bestm = m; }
+    if (ms < best) { best = ms; bestm = m; bestf = form; }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   ctx->lc.grid_mult = bestm;
+  ctx->lc.stage_form = bestf;
   mr_status s = build_graph(ctx);
   if (s) return s;
-  if (best_out) *best_out = bestm;
+  if (best_out) *best_out = bestm + 100 * bestf;
   return check_device(ctx);
 }
 

@@ -17,6 +17,18 @@
 
 namespace mr {
 
+// Thread groups that cooperate on one block: the whole CTA, or one warp.
+struct CtaGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ int size() const { return blockDim.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct WarpGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+  __device__ __forceinline__ int size() const { return 32; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
 __device__ __forceinline__ int64_t pmod64(int64_t a, int64_t n) {
   int64_t r = a % n;
   return r < 0 ? r + n : r;
@@ -169,12 +181,13 @@ struct Ring {
 };
 constexpr int kRingBytes = (int)((sizeof(Ring) + 15) / 16 * 16);
 
-template <int D, int B>
+template <int D, int B, typename G = CtaGroup>
 __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, Ring& R) {
+  const G g{};
   using Gm = Geo<D, B>;
-  if (threadIdx.x == 0) R.finer = R.coarser = R.mixed = 0;
-  __syncthreads();
-  for (int r = threadIdx.x; r < Gm::NR; r += blockDim.x) {
+  if (g.rank() == 0) R.finer = R.coarser = R.mixed = 0;
+  g.sync();
+  for (int r = g.rank(); r < Gm::NR; r += g.size()) {
     const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
     bool inside = true;
     for (int a = 0; a < D; ++a) inside &= (q[a] == 0 || q[a] == 1);
@@ -363,9 +376,10 @@ __device__ __forceinline__ TT predict_box(const TT* box, const int o[3]) {
 // of nvar x CBOX values for the coarse lattice (used when a coarser leaf
 // touches the block): every coarse node takes its owner's value, and ghost
 // nodes between coarse nodes are predicted from it.
-template <int D, int B, typename TF, typename TT, int W = kG>
+template <int D, int B, typename TF, typename TT, int W = kG, typename G = CtaGroup>
 __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, TF* Fw, TT* tile,
                           bool commit, const Ring& R, TT* cbox, TT* scr = nullptr) {
+  const G g{};
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, W>;
   // Each thread takes U points at a time: owners and addresses first, then the
@@ -377,13 +391,13 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
     // every ring leaf has the block's level: the owner of a point is the ring
     // cell holding it from below (equal-level rule of owner()), no search
     constexpr int P = Log2B<B>::value;
-    for (int q0 = threadIdx.x; q0 < Bx::NPTS; q0 += U * blockDim.x) {
+    for (int q0 = g.rank(); q0 < Bx::NPTS; q0 += U * g.size()) {
       int64_t at[U];
       int idx[U], li[U];
       bool ok[U], ed[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int q = q0 + u * blockDim.x;
+        const int q = q0 + u * g.size();
         ok[u] = q < Bx::NPTS;
         const int qq = ok[u] ? q : 0;
         const int i = qq % Bx::S - W;
@@ -423,12 +437,12 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
     return;
   }
   if (R.coarser) {
-    for (int q0 = threadIdx.x; q0 < Bx::CBOX; q0 += U * blockDim.x) {
+    for (int q0 = g.rank(); q0 < Bx::CBOX; q0 += U * g.size()) {
       int64_t at[U];
       bool ok[U], good[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = q0 + u * blockDim.x;
+        const int idx = q0 + u * g.size();
         ok[u] = idx < Bx::CBOX;
         good[u] = false;
         at[u] = 0;
@@ -452,17 +466,17 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
         for (int u = 0; u < U; ++u) val[u] = good[u] ? F[at[u] + (int64_t)v * pv.vs] : TF(0);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (ok[u]) cbox[v * Bx::CBOX + q0 + u * blockDim.x] = good[u] ? (TT)val[u] : TT(0);
+          if (ok[u]) cbox[v * Bx::CBOX + q0 + u * g.size()] = good[u] ? (TT)val[u] : TT(0);
       }
     }
-    __syncthreads();
+    g.sync();
     if (scr) {
       // separable prediction over the coarse box, x first, then y (then z at
       // the point): the same operations in the same order as predict_box
       for (int v = 0; v < nv; ++v) {
         const TT* cb = cbox + v * Bx::CBOX;
         TT* X = scr + v * Bx::SCR;
-        for (int q = threadIdx.x; q < Bx::NXP; q += blockDim.x) {
+        for (int q = g.rank(); q < Bx::NXP; q += g.size()) {
           const int x = q % Bx::S - W, ny = (q / Bx::S) % Bx::CB + Bx::CLO;
           const int nz = D == 3 ? q / (Bx::S * Bx::CB) + Bx::CLO : 0;
           const int fl = x >> 1;
@@ -472,11 +486,11 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
         }
       }
       if (D == 3) {
-        __syncthreads();
+        g.sync();
         for (int v = 0; v < nv; ++v) {
           const TT* X = scr + v * Bx::SCR;
           TT* Y = scr + v * Bx::SCR + Bx::NXP;
-          for (int q = threadIdx.x; q < Bx::NYP; q += blockDim.x) {
+          for (int q = g.rank(); q < Bx::NYP; q += g.size()) {
             const int x = q % Bx::S, y = (q / Bx::S) % Bx::S - W, nzi = q / (Bx::S * Bx::S);
             const int fl = y >> 1;
             const TT* c = X + nzi * Bx::CB * Bx::S + x;
@@ -486,18 +500,18 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
           }
         }
       }
-      __syncthreads();
+      g.sync();
     }
   }
   // kinds of tile points: 0 own node, 1 block-edge node of another owner,
   // 2 ghost node that is a node of its owner, 3 ghost predicted from the coarse
   // box, 4 no owner (error, zero)
-  for (int q0 = threadIdx.x; q0 < Bx::NPTS; q0 += U * blockDim.x) {
+  for (int q0 = g.rank(); q0 < Bx::NPTS; q0 += U * g.size()) {
     int64_t at[U];
     int idx[U], li[U], kind[U], ijk[U][3];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int q = q0 + u * blockDim.x;
+      const int q = q0 + u * g.size();
       const int qq = q < Bx::NPTS ? q : 0;
       const int i = qq % Bx::S - W;
       const int j = (qq / Bx::S) % Bx::S - W;
@@ -698,18 +712,19 @@ __device__ void build_gtab(int32_t* gtab) {
 // Uniform-neighbourhood gather through the gather table: nbase[n] is the pool
 // offset of neighbour n's variable 0 (slot * NV * vs), own the block's.
 // Same values as gather_uniform.
-template <int D, int B, int W, int NV, typename TF, typename TT>
+template <int D, int B, int W, int NV, typename TF, typename TT, typename G = CtaGroup>
 __device__ __forceinline__ void gather_table(const PoolView& pv, int64_t own, const int64_t* nbase,
                                              const int32_t* gtab, const TF* F, TF* Fw, TT* tile, bool commit) {
+  const G g{};
   using Bx = Box<D, B, W>;
   using Gm = Geo<D, B>;
   constexpr int U = 4;
-  for (int q0 = threadIdx.x; q0 < Bx::NPTS; q0 += U * blockDim.x) {
+  for (int q0 = g.rank(); q0 < Bx::NPTS; q0 += U * g.size()) {
     int64_t at[U];
     bool ok[U], ed[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int q = q0 + u * blockDim.x;
+      const int q = q0 + u * g.size();
       ok[u] = q < Bx::NPTS;
       const int e = gtab[ok[u] ? q : 0];
       const int64_t nbv = nbase[(e >> 16) & 31];
@@ -724,7 +739,7 @@ __device__ __forceinline__ void gather_table(const PoolView& pv, int64_t own, co
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (!ok[u]) continue;
-      const int q = q0 + u * blockDim.x;
+      const int q = q0 + u * g.size();
 #pragma unroll
       for (int w = 0; w < NV; ++w) {
         tile[w * Bx::TILE + q] = (TT)v[u][w];

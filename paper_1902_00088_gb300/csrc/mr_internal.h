@@ -126,6 +126,8 @@ struct Fields {
 struct LaunchCfg {
   int num_sms;
   int grid_mult;  // persistent CTAs per SM for the stage kernel (0 = occupancy)
+  int stage_form;  // 2D stage: 0 one CTA per block, 1 one warp per block, -1 by block count
+  int n_hint;      // block count last read by the host (chooses the form when -1)
 };
 
 // Per-dimension launchers (explicitly instantiated in mr_k2.cu / mr_k3.cu).

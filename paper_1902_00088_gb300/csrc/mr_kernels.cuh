@@ -187,6 +187,124 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
   }
 }
 
+// 2D form of k_stage_adv with one warp per block: each warp of the CTA walks
+// its own sequence of blocks (gather, stencils, update) with warp-level
+// synchronisation only, so the per-block work (plan, coefficients, barriers)
+// is done by 32 threads instead of a whole CTA.  Same values as k_stage_adv.
+template <int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
+struct StageW {
+  using Bx = Box<2, B, 2>;
+  static constexpr int NW = NT / 32;
+  static constexpr size_t GTAB = (4 * Bx::NPTS + 15) / 16 * 16;
+  static constexpr size_t WAREA = (kRingBytes + sizeof(TY) * (Bx::TILE + Bx::CBOX + Bx::SCR) + 15) / 16 * 16;
+  static constexpr size_t SMEM = GTAB + NW * WAREA;
+};
+
+template <int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
+                                                   TS* __restrict__ acc, TY* __restrict__ ynext, int stage,
+                                                   StageArgs sa) {
+  using Gm = Geo<2, B>;
+  using Bx = Box<2, B, 2>;
+  using PL = Plan<2>;
+  using SW = StageW<B, RHS, TS, TY, TSRC, NT>;
+  using TC = TY;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* sm = smem_as<unsigned char>(0);
+  int32_t* gtab = reinterpret_cast<int32_t*>(sm);
+  unsigned char* wa = sm + SW::GTAB + warp * SW::WAREA;
+  Ring& R = *reinterpret_cast<Ring*>(wa);
+  TC* tile = reinterpret_cast<TC*>(wa + kRingBytes);
+  TC* cbox = tile + Bx::TILE;
+  TC* scr = cbox + Bx::CBOX;
+  __shared__ int64_t snb[SW::NW][PL::NB];
+  build_gtab<2, B, 2>(gtab);
+  __syncthreads();
+  const int nact = pv.cnt->n_act;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
+  const int gw = blockIdx.x * SW::NW + warp, nwt = gridDim.x * SW::NW;
+  int32_t cur = (gw < nact && lane < PL::INTS) ? pv.plan[(int64_t)gw * PL::INTS + lane] : 0;
+  for (int p = gw; p < nact; p += nwt) {
+    const int pn = p + nwt;
+    const int32_t nxt = (pn < nact && lane < PL::INTS) ? pv.plan[(int64_t)pn * PL::INTS + lane] : 0;
+    BlockInfo b;
+    b.slot = __shfl_sync(0xffffffffu, cur, 0);
+    const int meta = __shfl_sync(0xffffffffu, cur, 1);
+    b.lvl = meta & 255;
+    b.tree = (meta >> 8) & 0xffff;
+    b.c[0] = __shfl_sync(0xffffffffu, cur, 2);
+    b.c[1] = __shfl_sync(0xffffffffu, cur, 3);
+    b.c[2] = 0;
+    const TreeDev& td = pv.trees[b.tree];
+    if ((meta >> 30) & 1) {
+      if (lane >= PL::NBO && lane < PL::NBO + PL::NB) snb[warp][lane - PL::NBO] = (int64_t)cur * pv.vs;
+      __syncwarp();
+      gather_table<2, B, 2, 1, TSRC, TC, WarpGroup>(pv, (int64_t)b.slot * pv.vs, snb[warp], gtab, src, (TSRC*)src,
+                                                    tile, stage == 0);
+    } else {
+      build_ring<2, B, WarpGroup>(pv, td, b, R);
+      __syncwarp();
+      fill_tile<2, B, TSRC, TC, 2, WarpGroup>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
+    }
+    __syncwarp();
+    const TC c = (TC)td.cD[b.lvl];
+    const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
+    const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
+    const double ct = pv.tt ? pv.tt[b.tree].ct[stage] : sa.ct[b.tree];
+    const TS cas = (TS)ca, cys = (TS)cy;
+    const int64_t base = (int64_t)b.slot * pv.vs;
+    const int sh = td.Jmax - b.lvl;
+    const TC uc0 = (TC)td.rhs[0], uc1 = (TC)td.rhs[1];
+    constexpr int UC = 4;
+    for (int q0 = lane; q0 < Gm::NI; q0 += UC * 32) {
+      TS yv[UC], av[UC];
+      TC u0[UC], u1[UC];
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int q = q0 + u * 32;
+        yv[u] = av[u] = TS(0);
+        u0[u] = uc0;
+        u1[u] = uc1;
+        if (q >= Gm::NI) continue;
+        if (stage <= 2) yv[u] = y[base + q];  // stage 0: committed (synchronised) y_n
+        if (stage >= 1) av[u] = acc[base + q];
+        if (RHS == MR_RHS_SWIRL) {
+          const int i = q % B, j = q / B;
+          const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
+          const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
+          const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
+          const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
+          u0[u] = (TC)(ct * (A[Ux] * Bt[Uy]));
+          u1[u] = (TC)(-(ct * (A[Uy] * Bt[Ux])));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int q = q0 + u * 32;
+        if (q >= Gm::NI) continue;
+        const int i = q % B, j = q / B;
+        const TC* t0 = tile + Bx::tix(i, j, 0);
+        const TC dxv = ((t0[-2] - t0[2]) + TC(8) * (t0[1] - t0[-1])) * c;
+        const TC dyv = ((t0[-2 * Bx::S] - t0[2 * Bx::S]) + TC(8) * (t0[Bx::S] - t0[-Bx::S])) * c;
+        const TC s = u0[u] * dxv + u1[u] * dyv;
+        const TS kk = (TS)(-s);
+        const int64_t at = base + q;
+        if (stage == 0) {
+          acc[at] = yv[u] + cas * kk;
+          ynext[at] = (TY)(yv[u] + cys * kk);
+        } else if (stage == 1 || stage == 2) {
+          acc[at] = av[u] + cas * kk;
+          ynext[at] = (TY)(yv[u] + cys * kk);
+        } else {
+          y[at] = av[u] + cas * kk;
+        }
+      }
+    }
+    __syncwarp();
+    cur = nxt;
+  }
+}
+
 // Stage plan of active position p (layout in Plan<D>): the 3^d - 1
 // equal-level neighbours looked up in the dense leaf tables.
 template <int D>

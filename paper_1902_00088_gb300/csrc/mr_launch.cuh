@@ -41,6 +41,27 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
   using Bx = Box<D, B, 2>;
   const size_t smem = kRingBytes + sizeof(TY) * nv * (Bx::TILE + Bx::CBOX + Bx::SCR) + (D == 2 ? 4 * Bx::NPTS : 0);
   TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
+  // 2D: one warp per block when the grid holds enough blocks to fill the GPU
+  // several times over (or as tuned), else one CTA per block (shorter latency)
+  const bool warp_form = lc.stage_form == 1 || (lc.stage_form < 0 && lc.n_hint >= 8 * lc.num_sms);
+  if (D == 2 && warp_form) {
+    if (stage == 0) {
+      using SW = StageW<B, RHS, TS, TY, TS, threads>;
+      auto k = k_stage_adv_w<B, RHS, TS, TY, TS, threads>;
+      prep_smem(k, SW::SMEM);
+      const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
+      k<<<grid, threads, SW::SMEM, st>>>(pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    } else {
+      using SW = StageW<B, RHS, TS, TY, TY, threads>;
+      const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
+      auto k = k_stage_adv_w<B, RHS, TS, TY, TY, threads>;
+      prep_smem(k, SW::SMEM);
+      const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
+      k<<<grid, threads, SW::SMEM, st>>>(pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    }
+    count_launch();
+    return;
+  }
   if (stage == 0) {
     auto k = k_stage_adv<D, B, RHS, TS, TY, TS, threads>;
     prep_smem(k, smem);
