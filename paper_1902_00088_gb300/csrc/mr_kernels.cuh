@@ -854,6 +854,170 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   if (threadIdx.x == 0 && ndet) atomicAdd(&pv.cnt->det_blocks, ndet);
 }
 
+// 2D details with one warp per block (single-variable fields without
+// normalisation): the same evaluation as k_details, with warp-level
+// synchronisation and reductions, for grids with many blocks.
+template <int B, typename TS, typename TD, int NT>
+struct DetW {
+  using Bx = Box<2, B, 2>;
+  using DG = DetGeo<2, B>;
+  static constexpr int NW = NT / 32;
+  static constexpr size_t GTAB = (4 * Bx::NPTS + 15) / 16 * 16;
+  static constexpr size_t XB = sizeof(TS) * Bx::SCR > sizeof(TD) * DG::NX ? sizeof(TS) * Bx::SCR : sizeof(TD) * DG::NX;
+  static constexpr size_t TB = (kRingBytes + sizeof(TS) * (Bx::TILE + Bx::CBOX) + 15) / 16 * 16;
+  static constexpr size_t WAREA = TB + (XB + 15) / 16 * 16;
+  static constexpr size_t SMEM = GTAB + NW * WAREA;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+  for (int s = 16; s > 0; s >>= 1) v = fmax(v, (T)__shfl_xor_sync(0xffffffffu, v, s));
+  return v;
+}
+
+template <int B, typename TS, typename TD, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __restrict__ y) {
+  using Gm = Geo<2, B>;
+  using Bx = Box<2, B, 2>;
+  using DG = DetGeo<2, B>;
+  using PL = Plan<2>;
+  using DW = DetW<B, TS, TD, NT>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* sm = smem_as<unsigned char>(0);
+  int32_t* gtab = reinterpret_cast<int32_t*>(sm);
+  unsigned char* wa = sm + DW::GTAB + warp * DW::WAREA;
+  Ring& R = *reinterpret_cast<Ring*>(wa);
+  TS* tile = reinterpret_cast<TS*>(wa + kRingBytes);
+  TS* cbox = tile + Bx::TILE;
+  TS* scr = reinterpret_cast<TS*>(wa + DW::TB);  // gather scratch, then the x pass
+  __shared__ int64_t snbo[DW::NW][PL::NB];
+  build_gtab<2, B, 2>(gtab);
+  __syncthreads();
+  const int nact = pv.cnt->n_round;
+  const bool all_blocks = pv.cnt->first_round != 0;
+  const int prev = pv.cnt->round_id - 1;
+  const bool plan_ok = pv.cnt->plan_topo == pv.cnt->topo;
+  const int gw = blockIdx.x * DW::NW + warp, nwt = gridDim.x * DW::NW;
+  unsigned ndet = 0;
+  int32_t cur = (plan_ok && gw < nact && lane < PL::INTS) ? pv.plan[(int64_t)gw * PL::INTS + lane] : 0;
+  for (int p = gw; p < nact; p += nwt) {
+    const int pn = p + nwt;
+    const int32_t nxt = (plan_ok && pn < nact && lane < PL::INTS) ? pv.plan[(int64_t)pn * PL::INTS + lane] : 0;
+    BlockInfo b;
+    int q;
+    if (plan_ok) {
+      b.slot = __shfl_sync(0xffffffffu, cur, 0);
+      const int meta = __shfl_sync(0xffffffffu, cur, 1);
+      b.lvl = meta & 255;
+      b.tree = (meta >> 8) & 0xffff;
+      b.c[0] = __shfl_sync(0xffffffffu, cur, 2);
+      b.c[1] = __shfl_sync(0xffffffffu, cur, 3);
+      b.c[2] = 0;
+      const int32_t qq = __shfl_sync(0xffffffffu, cur, PL::NBO + (lane < PL::NB ? lane : 0));
+      q = lane < PL::NB ? qq : b.slot;
+    } else {
+      b = load_block(pv, pv.act[p]);
+      q = b.slot;
+      if (lane < PL::NB && lane != 4) {
+        const int64_t cn[3] = {b.c[0] + lane % 3 - 1, b.c[1] + lane / 3 - 1, 0};
+        q = tab_get<2>(pv, pv.trees[b.tree], b.lvl, cn);
+      }
+    }
+    const TreeDev& td = pv.trees[b.tree];
+    const bool uni = __all_sync(0xffffffffu, q >= 0);
+    bool ring = false;
+    bool dirty = all_blocks;
+    if (!all_blocks) {
+      if (uni) {
+        dirty = __any_sync(0xffffffffu, lane < PL::NB && pv.stamp[q] == prev);
+      } else {
+        build_ring<2, B, WarpGroup>(pv, td, b, R);
+        __syncwarp();
+        ring = true;
+        dirty = __any_sync(0xffffffffu, lane < Gm::NR && R.slot[lane] >= 0 && pv.stamp[R.slot[lane]] == prev);
+      }
+    }
+    if (dirty) {
+      ++ndet;
+      const int64_t own = (int64_t)b.slot * pv.vs;
+      if (uni) {
+        if (lane < PL::NB) snbo[warp][lane] = (int64_t)q * pv.vs;
+        __syncwarp();
+        gather_table<2, B, 2, 1, TS, TS, WarpGroup>(pv, own, snbo[warp], gtab, y, y, tile, true);
+      } else {
+        if (!ring) {
+          build_ring<2, B, WarpGroup>(pv, td, b, R);
+          __syncwarp();
+        }
+        fill_tile<2, B, TS, TS, 2, WarpGroup>(pv, b, y, y, tile, true, R, cbox, scr);
+      }
+      __syncwarp();
+      auto pass = [&](auto tag) -> double {
+        using A = decltype(tag);
+        A* XA = reinterpret_cast<A*>(scr);
+        for (int idx = lane; idx < DG::NX; idx += 32) {
+          const int x = idx % B, yy = 2 * (idx / B - 1);
+          A val;
+          if ((x & 1) == 0) {
+            val = (A)tile[Bx::tix(x, yy, 0)];
+          } else {
+            const int n0 = (x - 1) / 2;
+            val = dd4((A)tile[Bx::tix(2 * n0 - 2, yy, 0)], (A)tile[Bx::tix(2 * n0, yy, 0)],
+                      (A)tile[Bx::tix(2 * n0 + 2, yy, 0)], (A)tile[Bx::tix(2 * n0 + 4, yy, 0)]);
+          }
+          XA[idx] = val;
+        }
+        __syncwarp();
+        A md = A(0);
+        for (int qn = lane; qn < Gm::NI; qn += 32) {
+          const int i = qn % B, j = qn / B;
+          if (((i | j) & 1) == 0) continue;
+          const A val = (A)tile[Bx::tix(i, j, 0)];
+          A pr;
+          if ((j & 1) == 0) {
+            pr = XA[(j / 2 + 1) * B + i];
+          } else {
+            const int m0 = (j - 1) / 2;
+            pr = dd4(XA[m0 * B + i], XA[(m0 + 1) * B + i], XA[(m0 + 2) * B + i], XA[(m0 + 3) * B + i]);
+          }
+          md = fmax(md, (A)fabs(val - pr));
+        }
+        md = warp_max(md);
+        __syncwarp();
+        return (double)md;
+      };
+      TS mqs = TS(0);
+      bool bad = false;
+      for (int qn = lane; qn < Gm::NI; qn += 32) {
+        const TS sv = tile[Bx::tix(qn % B, qn / B, 0)];
+        mqs = fmax(mqs, (TS)fabs(sv));
+        bad |= !isfinite(sv);
+      }
+      const double mq = (double)warp_max(mqs);
+      double md;
+      if constexpr (sizeof(TS) == 4 && sizeof(TD) == 8) {
+        // as in k_details: FP32 evaluation, FP64 only within the rounding bound of eps
+        const double m32 = pass(float(0));
+        float mt = 0.f;
+        for (int qn = lane; qn < Bx::TILE; qn += 32) mt = fmaxf(mt, fabsf((float)tile[qn]));
+        const double E = 32.0 * 0x1p-24 * (double)warp_max(mt) + 1e-37;
+        const bool sure = m32 + E < td.eps || m32 - E >= td.eps;
+        md = sure ? m32 : pass(double(0));
+      } else {
+        md = pass(TD(0));
+      }
+      if (__any_sync(0xffffffffu, bad)) md = __longlong_as_double(0x7ff8000000000000LL);
+      if (lane == 0) {
+        pv.md[b.slot] = md;
+        pv.bmax[b.slot] = mq;
+      }
+      __syncwarp();
+    }
+    cur = nxt;
+  }
+  if (lane == 0 && ndet) atomicAdd(&pv.cnt->det_blocks, (unsigned long long)ndet);
+}
+
 // ---------------------------------------------------------------- coarsen ----
 // Sec. 2.3: 2^d sisters with status -2 merge into their mother by restriction
 // (every second node); a mother node on a line shared by two children is read

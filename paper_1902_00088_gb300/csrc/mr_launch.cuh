@@ -219,6 +219,23 @@ struct DetailsRun {
                   cudaStream_t st) {
     constexpr int threads = Threads<D, B>::value;
     const bool d64 = fp64 || sizeof(TS) == 8;
+    const bool warp_form = pv.nvar == 1 && pv.norm_kind == 0 &&
+                           (lc.stage_form == 1 || (lc.stage_form < 0 && lc.n_hint >= 8 * lc.num_sms));
+    if (D == 2 && warp_form) {  // one warp per block
+      if (d64) {
+        auto k = k_details_w<B, TS, double, threads>;
+        using DW = DetW<B, TS, double, threads>;
+        prep_smem(k, DW::SMEM);
+        k<<<persistent_grid(k, threads, DW::SMEM, lc, lc.grid_mult), threads, DW::SMEM, st>>>(pv, (TS*)f.y);
+      } else {
+        auto k = k_details_w<B, TS, TS, threads>;
+        using DW = DetW<B, TS, TS, threads>;
+        prep_smem(k, DW::SMEM);
+        k<<<persistent_grid(k, threads, DW::SMEM, lc, lc.grid_mult), threads, DW::SMEM, st>>>(pv, (TS*)f.y);
+      }
+      count_launch();
+      return;
+    }
     using Bx = Box<D, B, 2>;
     const size_t scr = sizeof(TS) * pv.nvar * Bx::SCR, xp = (d64 ? 8 : sizeof(TS)) * DetGeo<D, B>::NX;
     const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp) +
