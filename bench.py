@@ -83,6 +83,30 @@ WORKLOADS = {
 }
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel, from one ncu capture per workload (profiles/), valid only for
+# the kernel sources it was taken on (digest below); otherwise reported as null.
+TRAFFIC_DIGEST = "ff1230fc6ca4154e"
+TRAFFIC = {
+    "swirl": ("k_stage_adv", (2.969088e6 + 2.050048e6) / 2),
+    "uniform2d": ("k_stage_adv_w", 948.168704e6 + 570.194176e6),
+    "adv3d": ("k_stage_adv", 82.727424e6 + 14.301440e6),
+    "ns_thin": ("k_stage_ns", 1.295494e9 + 723.813120e6),
+}
+
+
+def source_digest():
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1902_00088_gb300", "csrc", "*"))) + \
+            [os.path.join(ROOT, "include", "mr.h")]:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _forest_trees():
     import synthetic as inputs
     return inputs.forest_trees(64)
@@ -536,6 +560,12 @@ def main():
         v["launch_us"] = v["ms"] * 1e3 / max(1, v["launches"])
     dom = max(kern, key=lambda n: kern[n]["ms"])
     achieved = kern[dom]["achieved_gbs"]
+    traffic = None
+    tr = TRAFFIC.get(args.workload)
+    if tr and dom == "stage" and source_digest() == TRAFFIC_DIGEST and not args.precision and not args.learned:
+        traffic = {"bytes_per_launch": tr[1], "kernel": tr[0],
+                   "algorithmic_bytes_per_launch": kern[dom]["bytes"] / max(1, kern[dom]["launches"]),
+                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/"}
 
     err = None
     tnow = g.get_time() if graph else t
@@ -615,7 +645,7 @@ def main():
                        "phase_ms_eager_probe": st["ms"],
                        "learned_proposal": learned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": kern[dom]["kernel"], "launch_us": kern[dom]["launch_us"],
                          "kernels_eager_probe": kern,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
