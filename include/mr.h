@@ -211,7 +211,9 @@ mr_status mr_error(mr_ctx ctx, int32_t tree, double t, double* out);
  * Synchronises. */
 mr_status mr_error_noalloc(mr_ctx ctx, int32_t tree, double t, double* out);
 
-/* Kernel launches enqueued by this process so far (for throughput claims). */
+/* Kernel launches enqueued by this process so far (for throughput claims),
+ * including the coarsening rounds that graph-captured steps of ctx ran on the
+ * device (read from the device: synchronises once graph steps were run). */
 int64_t mr_launch_count(mr_ctx ctx);
 
 /* Phase timers and work counters (tracing).  Phases: 0 refine (with the

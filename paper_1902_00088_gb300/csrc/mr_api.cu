@@ -62,6 +62,8 @@ struct mr_ctx_s {
   bool graph_while = true;  // coarsening rounds as a conditional while-node (else fixed rounds)
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_kernels = 0;  // kernel nodes of the captured step
+  int64_t graph_body = 0;     // of which in the while-node body (run once per coarsening round)
+  int64_t graph_steps = 0;    // captured steps launched
   bool capturing = false;
   // learned refinement proposal
   int refine_mode = 0;  // 0 refine all (Sec. 2.1), 1 learned proposal + fallback + closure
@@ -498,7 +500,13 @@ extern "C" {
 
 const char* mr_last_error(mr_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 int32_t mr_num_relations(int32_t dim) { return dim == 2 ? 16 : (dim == 3 ? 74 : 0); }
-int64_t mr_launch_count(mr_ctx) { return kernel_launches(); }
+int64_t mr_launch_count(mr_ctx ctx) {
+  // the host counts one while-node body per graph step; the device counts the
+  // bodies that ran
+  if (!ctx || ctx->graph_body == 0 || ctx->graph_steps == 0) return kernel_launches();
+  const Counters h = read_counters(ctx);
+  return kernel_launches() + ((int64_t)h.graph_rounds - ctx->graph_steps) * ctx->graph_body;
+}
 
 mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) {
   if (!out) return MR_EINVAL;
@@ -1024,9 +1032,11 @@ cudaError_t capture_step(mr_ctx ctx, cudaGraph_t* out, bool use_while) {
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(ctx->body_stream, cp.conditional.phGraph_out[0], nullptr,
                                                             nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+      const int64_t b0 = kernel_launches();
       enqueue_round(ctx, ctx->body_stream);
       k_round_continue<<<1, 1, 0, ctx->body_stream>>>(ctx->cnt, h, max_rounds_of(ctx));
       count_launch();
+      ctx->graph_body = kernel_launches() - b0;
       cudaGraph_t body = nullptr;
       e = cudaStreamEndCapture(ctx->body_stream, &body);
     }
@@ -1072,6 +1082,7 @@ mr_status build_graph(mr_ctx ctx) {
   if (e != cudaSuccess && ctx->graph_while) {  // no conditional nodes: fixed rounds
     ctx->graph_while = false;
     count_launch((int)-(kernel_launches() - k0));
+    ctx->graph_body = 0;
     e = capture_step(ctx, &g, false);
   }
   // kernel nodes per replay (a while-body counts once; replays add them)
@@ -1094,6 +1105,7 @@ mr_status mr_step_graph(mr_ctx ctx, int64_t nsteps) {
   }
   for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(ctx->gexec, ctx->st));
   count_launch((int)(ctx->graph_kernels * nsteps));
+  if (ctx->graph_while) ctx->graph_steps += nsteps;
   ctx->stats.steps += nsteps;
   ctx->stats.stage_launches += 4 * nsteps;
   return MR_OK;
@@ -1137,6 +1149,7 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
     CK(cudaEventRecord(a, ctx->st));
     for (int i = 0; i < steps; ++i) CK(cudaGraphLaunch(ctx->gexec, ctx->st));
     count_launch((int)(ctx->graph_kernels * (steps + 1)));
+    if (ctx->graph_while) ctx->graph_steps += steps + 1;
     CK(cudaEventRecord(b, ctx->st));
     CK(cudaEventSynchronize(b));
     float ms = 0.f;

@@ -53,6 +53,7 @@ struct Counters {
   unsigned long long det_blocks;  // blocks whose details a coarsening round evaluated
   int32_t topo;       // tree generation: changes with every refinement, merge or import
   int32_t plan_topo;  // generation the stage plans were built for (-1: none)
+  unsigned long long graph_rounds;  // coarsening-round bodies run by graph while nodes
 };
 constexpr int kMaxVar = 4;  // variables per node (advection 1, Navier-Stokes 4; checked at creation)
 constexpr int kMaxHist = 1 << 16;  // step history: blocks of the adapted grid before each step

@@ -150,6 +150,7 @@ __global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int 
 // the last one merged a family and fewer than max_rounds ran.
 __global__ void k_round_continue(Counters* c, cudaGraphConditionalHandle h, int max_rounds) {
   c->rounds += 1;
+  c->graph_rounds += 1;
   cudaGraphSetConditional(h, (!c->done && c->rounds < max_rounds) ? 1u : 0u);
 }
 

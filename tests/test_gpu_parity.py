@@ -6,6 +6,7 @@ treecodes, Hilbert keys, neighbour tables and flags bit for bit as well.
 FP32 forms are compared within a tolerance stated per test.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -403,3 +404,95 @@ def test_ns_uniform_grid_conserves_and_preserves_free_stream(mr):
     g.rk_step(0.0, dt)
     _, f2 = g.get_blocks()
     assert np.array_equal(f2, f)
+
+
+# ---- the benchmark workloads at full size, in the launch configuration bench.py times ----
+
+def _bench():
+    import importlib
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    return importlib.import_module("bench")
+
+
+def test_forest_full_size_graph_steps_match_oracle(mr, oracle_mod):
+    # The 64-tree forest workload at full size (Jmax 4-8), FP64, advanced by
+    # graph replays (device-side time; with ~2000 blocks the stage and details
+    # run one warp per block): sampled trees equal the oracle bit for bit.
+    bench = _bench()
+    import synthetic as inputs
+    w = bench.WORKLOADS["forest"]
+    trees = w["trees"]
+    g = mr.Forest(dim=2, precision="fp64", trees=trees, capacity=w["capacity"])
+    g.init_tree()
+    dts = np.array([inputs.cfl_dt(t, 17) for t in trees])
+    g.set_time(np.zeros(len(trees)), dts)
+    nsteps = 4
+    g.step_graph(nsteps)
+    assert g.num_blocks() >= 8 * 152  # large enough for the warp-per-block forms
+    jmax = [t["Jmax"] for t in trees]
+    sample = sorted({0, 1, int(np.argmax(jmax)), 33, 40, 63})
+    for k in sample:
+        t = trees[k]
+        o = oracle_mod.Oracle(dict(dim=2, Jmin=t["Jmin"], Jmax=t["Jmax"], eps=t["eps"], rhs="adv",
+                                   rhs_params=t["rhs_params"], ic="gauss", ic_params=t["ic_params"]))
+        o.init_tree()
+        for s in range(nsteps):
+            o.step(s * dts[k], dts[k])
+        ob = o.blocks()
+        info, fl = g.get_blocks(tree=k)
+        assert np.array_equal(info["level"], ob["level"]), k
+        assert np.array_equal(info["coords"].astype(np.int64), ob["coords"]), k
+        assert np.array_equal(fl, ob["fields"]), (k, np.abs(fl - ob["fields"]).max())
+
+
+def test_swirl_full_size_matches_oracle(mr, oracle_mod):
+    # The swirl workload's tree at full size (Jmax 8, eps 1e-4), FP64 host-driven
+    # steps: bit-exact; graph replays (device cos for the time factor) agree to
+    # rounding.
+    bench = _bench()
+    w = bench.WORKLOADS["swirl"]
+    t = w["tree"]
+    c = dict(dim=2, Jmin=t["Jmin"], Jmax=t["Jmax"], eps=t["eps"], rhs="swirl", rhs_params=t["rhs_params"],
+             ic="gauss", ic_params=t["ic_params"])
+    o, g = make_pair(mr, oracle_mod, c, capacity=w["capacity"])
+    o.init_tree()
+    g.init_tree()
+    g2 = make_pair(mr, oracle_mod, c, capacity=w["capacity"])[1]
+    g2.init_tree()
+    dt = bench.dt_of(w)
+    for s in range(3):
+        o.step(s * dt, dt)
+        g.step(s * dt, dt)
+    ob, f = assert_same_tree(o, g)
+    assert np.array_equal(f, ob["fields"])
+    g2.set_time(0.0, dt)
+    g2.step_graph(3)
+    info2, f2 = g2.get_blocks()
+    assert np.array_equal(info2["level"], ob["level"])
+    assert np.abs(f2 - ob["fields"]).max() <= 1e-13
+
+
+def test_adv3d_full_size_graph_equals_eager(mr):
+    # The 3D workload as bench.py runs it (FP32 stencils, FP64 details, graph
+    # replays): identical to host-driven steps, and the tree stays graded.
+    bench = _bench()
+    w = bench.WORKLOADS["adv3d"]
+    t = w["tree"]
+    tree = dict(Jmin=t["Jmin"], Jmax=t["Jmax"], eps=t["eps"], ic="gauss", ic_params=t["ic_params"],
+                rhs_params=t["rhs_params"])
+    dt = bench.dt_of(w)
+    a = mr.Forest(dim=3, precision="fp32", detail_fp64=True, trees=[tree], capacity=w["capacity"])
+    b = mr.Forest(dim=3, precision="fp32", detail_fp64=True, trees=[tree], capacity=w["capacity"])
+    a.init_tree()
+    b.init_tree()
+    for s in range(3):
+        a.step(s * dt, dt)
+    b.set_time(0.0, dt)
+    b.step_graph(3)
+    ia, fa = a.get_blocks()
+    ib, fb = b.get_blocks()
+    assert np.array_equal(ia, ib) and np.array_equal(fa, fb)
+    assert len(ia) > 100
