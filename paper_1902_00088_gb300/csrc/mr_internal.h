@@ -165,7 +165,7 @@ template <int D> void launch_error(const PoolView& pv, const Fields& f, int tree
 // `partial` needs 2 * ceil(n_max / kScanChunk) + 2 ints.
 constexpr int kScanChunk = 2048;
 void launch_scan2(const int32_t* in, int32_t* out, int32_t* partial, const int32_t* n_dev,
-                  int64_t n_host, int32_t* tot, cudaStream_t st);
+                  int64_t n_host, int32_t* tot, cudaStream_t st, int64_t n_expect = -1);
 void count_launch(int n = 1);
 int64_t kernel_launches();
 

@@ -634,6 +634,7 @@ template <int D, int B>
 struct DetGeo {
   static constexpr int NC = (B + 1) / 2 + 2;  // coarse rows -1 .. (B+1)/2
   static constexpr int NX = NC * B * (D == 3 ? NC : 1);
+  static constexpr int NY = D == 3 ? B * B * NC : 0;  // 3D: after the y pass, coarse z rows
 };
 
 // Maximum of v over the CTA (warp shuffles, then one value per warp in red);
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   // (the first round after the RK stages); the next block's plan is fetched
   // while a block is processed
   const bool plan_ok = pv.cnt->plan_topo == pv.cnt->topo;
-  const size_t xs = sizeof(TS) * (size_t)nv * Bx::SCR, xd = sizeof(TD) * (size_t)DG::NX;
+  const size_t xs = sizeof(TS) * (size_t)nv * Bx::SCR, xd = sizeof(TD) * (size_t)(DG::NX + DG::NY);
   const size_t xbytes = xs > xd ? xs : xd;
   int32_t* gtab = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(X) + ((xbytes + 15) & ~(size_t)15));
   if (D == 2) build_gtab<D, B, 2>(gtab);
@@ -784,22 +785,32 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       }
       __syncthreads();
       auto xat = [&](int x, int yc, int zc) { return XA[((D == 3 ? (zc + 1) * DG::NC : 0) + (yc + 1)) * B + x]; };
+      auto ypass = [&](int i, int j, int zc) -> A {
+        if ((j & 1) == 0) return xat(i, j / 2, zc);
+        const int m0 = (j - 1) / 2;
+        return dd4(xat(i, m0 - 1, zc), xat(i, m0, zc), xat(i, m0 + 1, zc), xat(i, m0 + 2, zc));
+      };
+      // 3D: the y pass once per (x, y, coarse z row), kept for the z pass
+      A* YA = XA + DG::NX;
+      if (D == 3) {
+        for (int idx = threadIdx.x; idx < DG::NY; idx += blockDim.x)
+          YA[idx] = ypass(idx % B, (idx / B) % B, idx / (B * B) - 1);
+        __syncthreads();
+      }
+      auto yat = [&](int i, int j, int zc) { return YA[((zc + 1) * B + j) * B + i]; };
       A md = A(0);  // a maximum of A values: exact in A
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
         if (((i | j | k) & 1) == 0) continue;
         const A val = (A)tv[Bx::tix(i, j, k)];
-        auto ypass = [&](int zc) -> A {
-          if ((j & 1) == 0) return xat(i, j / 2, zc);
-          const int m0 = (j - 1) / 2;
-          return dd4(xat(i, m0 - 1, zc), xat(i, m0, zc), xat(i, m0 + 1, zc), xat(i, m0 + 2, zc));
-        };
         A pr;
-        if (D == 2 || (k & 1) == 0) {
-          pr = ypass(k / 2);
+        if (D == 2) {
+          pr = ypass(i, j, 0);
+        } else if ((k & 1) == 0) {
+          pr = yat(i, j, k / 2);
         } else {
           const int k0 = (k - 1) / 2;
-          pr = dd4(ypass(k0 - 1), ypass(k0), ypass(k0 + 1), ypass(k0 + 2));
+          pr = dd4(yat(i, j, k0 - 1), yat(i, j, k0), yat(i, j, k0 + 1), yat(i, j, k0 + 2));
         }
         const A d = val - pr;
         md = fmax(md, (A)fabs(d));

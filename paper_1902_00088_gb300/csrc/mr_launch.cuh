@@ -191,7 +191,7 @@ void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* 
   const int nch = 1 << D;
   k_refine_count<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv, mode, mask);
   count_launch();
-  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st);
+  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st, 2 * (int64_t)lc.n_hint);
   dispatch_bs<D, RefineRun>(pv, f, lc, st);
   k_refine_finalize<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
   k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 1);
@@ -237,7 +237,8 @@ struct DetailsRun {
       return;
     }
     using Bx = Box<D, B, 2>;
-    const size_t scr = sizeof(TS) * pv.nvar * Bx::SCR, xp = (d64 ? 8 : sizeof(TS)) * DetGeo<D, B>::NX;
+    const size_t scr = sizeof(TS) * pv.nvar * Bx::SCR,
+                 xp = (d64 ? 8 : sizeof(TS)) * (DetGeo<D, B>::NX + DetGeo<D, B>::NY);
     const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp) +
                         16 + (D == 2 ? 4 * Bx::NPTS : 0);
     if (d64) {
@@ -279,7 +280,7 @@ void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const L
   k_flags<D><<<(int)std::min<int64_t>(4096, (pv.cap + 7) / 8), 256, 0, st>>>(pv);
   count_launch();
   if (!merge) return;
-  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st);
+  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st, 4 * (int64_t)lc.n_hint);
   dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
   k_coarsen_finalize<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
   k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 2);

@@ -98,8 +98,67 @@ __global__ void k_scan_final(const int32_t* in, int32_t* out, const int32_t* n_d
   }
 }
 
+// Single-CTA exclusive scan: 1024 threads, 4 consecutive pairs per thread per
+// pass, a running carry between passes.  One launch; its cost follows the
+// device-side count, so it serves lists up to a few million entries.
+constexpr int kSingleThreads = 1024, kSinglePer = 4;
+__global__ void __launch_bounds__(kSingleThreads) k_scan_single(const int32_t* in, int32_t* out, const int32_t* n_dev,
+                                                                int64_t n_host, int32_t* tot) {
+  __shared__ int2 wt[kSingleThreads / 32];
+  const int64_t n = scan_n(n_dev, n_host);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int2 carry = make_int2(0, 0);
+  for (int64_t base = 0; base < n; base += (int64_t)kSingleThreads * kSinglePer) {
+    int2 loc[kSinglePer];
+    int2 s = make_int2(0, 0);
+#pragma unroll
+    for (int r = 0; r < kSinglePer; ++r) {
+      const int64_t i = base + (int64_t)threadIdx.x * kSinglePer + r;
+      loc[r] = i < n ? make_int2(in[2 * i], in[2 * i + 1]) : make_int2(0, 0);
+      s.x += loc[r].x;
+      s.y += loc[r].y;
+    }
+    int2 v = s;  // inclusive scan: within the warp, then over the warp totals
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, v.x, o), y = __shfl_up_sync(0xffffffffu, v.y, o);
+      if (lane >= o) { v.x += x; v.y += y; }
+    }
+    if (lane == 31) wt[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      int2 t = wt[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, t.x, o), y = __shfl_up_sync(0xffffffffu, t.y, o);
+        if (lane >= o) { t.x += x; t.y += y; }
+      }
+      wt[lane] = t;
+    }
+    __syncthreads();
+    if (w > 0) { v.x += wt[w - 1].x; v.y += wt[w - 1].y; }
+    int2 run = make_int2(carry.x + v.x - s.x, carry.y + v.y - s.y);
+#pragma unroll
+    for (int r = 0; r < kSinglePer; ++r) {
+      const int64_t i = base + (int64_t)threadIdx.x * kSinglePer + r;
+      if (i < n) { out[2 * i] = run.x; out[2 * i + 1] = run.y; }
+      run.x += loc[r].x;
+      run.y += loc[r].y;
+    }
+    carry.x += wt[kSingleThreads / 32 - 1].x;
+    carry.y += wt[kSingleThreads / 32 - 1].y;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && tot) { tot[0] = carry.x; tot[1] = carry.y; }
+}
+
 void launch_scan2(const int32_t* in, int32_t* out, int32_t* partial, const int32_t* n_dev,
-                  int64_t n_host, int32_t* tot, cudaStream_t st) {
+                  int64_t n_host, int32_t* tot, cudaStream_t st, int64_t n_expect) {
+  // one CTA while the list is expected to be short (its passes are serial)
+  const int64_t n_est = n_expect >= 0 ? n_expect : n_host;
+  if (n_est <= 32768) {
+    k_scan_single<<<1, kSingleThreads, 0, st>>>(in, out, n_dev, n_host, tot);
+    count_launch(1);
+    return;
+  }
   const int nchunks = (int)((n_host + kScanChunk - 1) / kScanChunk);
   const int g = nchunks < 1 ? 1 : nchunks;
   k_scan_reduce<<<g, kScanThreads, 0, st>>>(in, n_dev, n_host, partial);
