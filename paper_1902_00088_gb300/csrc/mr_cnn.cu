@@ -34,55 +34,93 @@ struct CnnGeo {
 };
 
 // ------------------------------------------------------------- features ------
+// Input tile of the network for every active block: channel 0 = variable 0
+// minus its centre value over its largest deviation; channel 1 =
+// log10(1e-3 + |d| / (s_v eps)) at the odd interior nodes (largest over the
+// variables), -3 elsewhere.  FP32 throughout (a feature, not a decision; FP64
+// runs at a small fraction of the FP32 rate here); the details come from the
+// separable 4-point prediction, x on coarse rows then y.
+template <int B>
+struct FeatGeo {
+  using Gm = Geo<2, B>;
+  using Bx = Box<2, B, kG>;
+  static constexpr int NC = (B + 1) / 2 + 2;  // coarse rows -1 .. (B+1)/2
+  static constexpr int NX = NC * B;
+  static size_t smem(int nv) {
+    return kRingBytes + sizeof(float) * ((size_t)nv * (Gm::TILE + Bx::CBOX + Bx::SCR) + NX + Gm::NI);
+  }
+};
+
 template <int B, typename TS>
 __global__ void __launch_bounds__(256) k_features(PoolView pv, const TS* __restrict__ y,
                                                   float* __restrict__ feat, float* __restrict__ mpre,
                                                   int64_t base) {
   using Gm = Geo<2, B>;
+  using Bx = Box<2, B, kG>;
+  using FG = FeatGeo<B>;
   constexpr int T = Gm::T;
+  const int nv = pv.nvar;
   Ring& R = *smem_as<Ring>(0);
   __shared__ float red[2][32];
-  double* tile = smem_as<double>(kRingBytes);
-  double* cbox = tile + pv.nvar * Gm::TILE;
+  float* tile = smem_as<float>(kRingBytes);
+  float* cbox = tile + nv * Gm::TILE;
+  float* scr = cbox + nv * Bx::CBOX;
+  float* X = scr + nv * Bx::SCR;
+  float* dmap = X + FG::NX;
   const int nact = pv.cnt->n_act;
-  const int nv = pv.nvar;
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);
     const TreeDev& td = pv.trees[b.tree];
     float* out = feat + (base + p) * (int64_t)(2 * T * T);
     build_ring<2, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<2, B, TS, double>(pv, b, y, (TS*)y, tile, false, R, cbox);
+    fill_tile<2, B, TS, float>(pv, b, y, (TS*)y, tile, false, R, cbox, scr);
+    for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) dmap[q] = 0.f;
     __syncthreads();
-    const double centre = tile[Gm::tix((B - 1) / 2, (B - 1) / 2, 0)];
-    float mx = 0.f, md = 0.f;
-    for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x)
-      mx = fmaxf(mx, (float)fabs(tile[idx] - centre));
+    const float centre = tile[Gm::tix((B - 1) / 2, (B - 1) / 2, 0)];
+    float mx = 0.f;
+    for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x) mx = fmaxf(mx, fabsf(tile[idx] - centre));
     for (int s = 16; s > 0; s >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, s));
     if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = mx;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[0][w]);
-      red[0][0] = mx;
-    }
-    __syncthreads();
-    mx = red[0][0];
+    mx = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[0][w]);
     const float inv = mx > 0.f ? 1.f / mx : 0.f;
+    for (int v = 0; v < nv; ++v) {
+      const float* tv = tile + v * Gm::TILE;
+      double svd = pv.norm_kind == 1 ? pv.svar[b.tree * nv + v] : 1.0;
+      const float sv = svd == 0.0 ? 1.f : (float)svd;
+      for (int idx = threadIdx.x; idx < FG::NX; idx += blockDim.x) {  // x pass on coarse rows
+        const int x = idx % B, yy = 2 * (idx / B - 1);
+        X[idx] = (x & 1) ? dd4(tv[Gm::tix(x - 3, yy, 0)], tv[Gm::tix(x - 1, yy, 0)], tv[Gm::tix(x + 1, yy, 0)],
+                               tv[Gm::tix(x + 3, yy, 0)])
+                         : tv[Gm::tix(x, yy, 0)];
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
+        const int i = q % B, j = q / B;
+        if (((i | j) & 1) == 0) continue;
+        float pr;
+        if ((j & 1) == 0) {
+          pr = X[(j / 2 + 1) * B + i];
+        } else {
+          const int m0 = (j - 1) / 2;
+          pr = dd4(X[m0 * B + i], X[(m0 + 1) * B + i], X[(m0 + 2) * B + i], X[(m0 + 3) * B + i]);
+        }
+        dmap[q] = fmaxf(dmap[q], fabsf(tv[Gm::tix(i, j, 0)] - pr) / sv);
+      }
+      __syncthreads();
+    }
+    float md = 0.f;
+    const float ieps = (float)(1.0 / td.eps);
     for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x) {
       const int i = idx % T - Gm::G, j = idx / T - Gm::G;
-      out[idx] = (float)(tile[idx] - centre) * inv;
+      out[idx] = (tile[idx] - centre) * inv;
       float dv = -3.f;
       if (i >= 0 && i < B && j >= 0 && j < B && ((i | j) & 1)) {
-        double dmax = 0.0;
-        for (int v = 0; v < nv; ++v) {
-          const int o[3] = {i, j, 0};
-          const double d = tile[v * Gm::TILE + idx] - predict_tile<2, B, kG, double, double>(tile + v * Gm::TILE, o, 2);
-          double sv = pv.norm_kind == 1 ? pv.svar[b.tree * nv + v] : 1.0;
-          if (sv == 0.0) sv = 1.0;
-          dmax = fmax(dmax, fabs(d) / sv);
-        }
-        md = fmaxf(md, (float)dmax);
-        dv = log10f(1e-3f + (float)(dmax / td.eps));
+        const float dm = dmap[j * B + i];
+        md = fmaxf(md, dm);
+        dv = log10f(1e-3f + dm * ieps);
       }
       out[T * T + idx] = dv;
     }
@@ -161,17 +199,88 @@ __device__ float cnn_forward(const float* x, const WT* w, float* h1, float* h2, 
   return logit;
 }
 
-// Inference: p for every active block below Jmax (others get 0).
+// Inference: p for every active block below Jmax (others get 0).  The
+// weights are staged once per CTA in shared memory as floats, transposed so
+// that the 16 output channels of a tap are contiguous; each thread computes
+// all 16 output channels of one pixel (one input load feeds 16 FMAs, the 16
+// weights come as four broadcast 16-byte loads).  Per output the sum runs in
+// the order of cnn_forward (bias, then input channel, row, column), so the
+// probabilities equal the training forward pass bit for bit.
+template <int T>
+struct InferGeo {
+  using CG = CnnGeo<T>;
+  // transposed weights: layer l, input channel c, tap t -> 16 floats (o)
+  static constexpr int WT1 = 0, WT2 = WT1 + 2 * 9 * kC, WT3 = WT2 + kC * 9 * kC, WTE = WT3 + kC * 9 * kC;
+  static constexpr int NW = WTE + 4 * kC + 1;  // + b1, b2, b3, wl, bl
+  static constexpr int X0 = (NW + 3) / 4 * 4;  // activations after the weights
+  static constexpr size_t SMEM = sizeof(float) * (X0 + CG::NX + CG::N1 + CG::N2 + CG::N3);
+};
+
+template <int T, int CIN, int S>
+__device__ __forceinline__ void conv_all_o(const float* __restrict__ in, int Tin, const float* __restrict__ wt,
+                                           const float* __restrict__ bias, float* __restrict__ out, int Tout) {
+  for (int pix = threadIdx.x; pix < Tout * Tout; pix += blockDim.x) {
+    const int i = pix / Tout, j = pix % Tout;
+    float acc[kC];
+#pragma unroll
+    for (int o = 0; o < kC; ++o) acc[o] = bias[o];
+    for (int c = 0; c < CIN; ++c) {
+#pragma unroll
+      for (int di = 0; di < 3; ++di) {
+        const int ii = S * i + di - 1;
+        if (ii < 0 || ii >= Tin) continue;
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj) {
+          const int jj = S * j + dj - 1;
+          if (jj < 0 || jj >= Tin) continue;
+          const float xv = in[c * Tin * Tin + ii * Tin + jj];
+          const float4* w4 = reinterpret_cast<const float4*>(wt + ((c * 3 + di) * 3 + dj) * kC);
+#pragma unroll
+          for (int o4 = 0; o4 < kC / 4; ++o4) {
+            const float4 wv = w4[o4];
+            acc[4 * o4 + 0] += wv.x * xv;
+            acc[4 * o4 + 1] += wv.y * xv;
+            acc[4 * o4 + 2] += wv.z * xv;
+            acc[4 * o4 + 3] += wv.w * xv;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < kC; ++o) out[o * Tout * Tout + pix] = fmaxf(acc[o], 0.f);
+  }
+}
+
 template <int T>
 __global__ void __launch_bounds__(256) k_cnn_infer(PoolView pv, const float* __restrict__ feat,
                                                    const __nv_bfloat16* __restrict__ wb,
                                                    float* __restrict__ prob, int64_t n_explicit) {
   using CG = CnnGeo<T>;
-  float* x = smem_as<float>(0);
+  using IG = InferGeo<T>;
+  float* ws = smem_as<float>(0);
+  float* x = ws + IG::X0;
   float* h1 = x + CG::NX;
   float* h2 = h1 + CG::N1;
   float* h3 = h2 + CG::N2;
   __shared__ float z[kC];
+  // stage the weights, transposed to [c][tap][o]
+  for (int q = threadIdx.x; q < kC * 2 * 9; q += blockDim.x) {
+    const int o = q / 18, c = (q / 9) % 2, t = q % 9;
+    ws[IG::WT1 + (c * 9 + t) * kC + o] = __bfloat162float(wb[kW1 + q]);
+  }
+  for (int q = threadIdx.x; q < kC * kC * 9; q += blockDim.x) {
+    const int o = q / (kC * 9), c = (q / 9) % kC, t = q % 9;
+    ws[IG::WT2 + (c * 9 + t) * kC + o] = __bfloat162float(wb[kW2 + q]);
+    ws[IG::WT3 + (c * 9 + t) * kC + o] = __bfloat162float(wb[kW3 + q]);
+  }
+  if (threadIdx.x < kC) {
+    ws[IG::WTE + threadIdx.x] = __bfloat162float(wb[kB1 + threadIdx.x]);
+    ws[IG::WTE + kC + threadIdx.x] = __bfloat162float(wb[kB2 + threadIdx.x]);
+    ws[IG::WTE + 2 * kC + threadIdx.x] = __bfloat162float(wb[kB3 + threadIdx.x]);
+    ws[IG::WTE + 3 * kC + threadIdx.x] = __bfloat162float(wb[kWL + threadIdx.x]);
+  }
+  if (threadIdx.x == 0) ws[IG::WTE + 4 * kC] = __bfloat162float(wb[kBL]);
+  __syncthreads();
   const int64_t n = n_explicit >= 0 ? n_explicit : (int64_t)pv.cnt->n_act;
   for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
     if (n_explicit < 0) {
@@ -183,8 +292,23 @@ __global__ void __launch_bounds__(256) k_cnn_infer(PoolView pv, const float* __r
     }
     for (int idx = threadIdx.x; idx < CG::NX; idx += blockDim.x) x[idx] = feat[p * CG::NX + idx];
     __syncthreads();
-    const float logit = cnn_forward<T>(x, wb, h1, h2, h3, z);
-    if (threadIdx.x == 0) prob[p] = 1.f / (1.f + expf(-logit));
+    conv_all_o<T, 2, 1>(x, T, ws + IG::WT1, ws + IG::WTE, h1, T);
+    __syncthreads();
+    conv_all_o<T, kC, 2>(h1, T, ws + IG::WT2, ws + IG::WTE + kC, h2, CG::T2);
+    __syncthreads();
+    conv_all_o<T, kC, 2>(h2, CG::T2, ws + IG::WT3, ws + IG::WTE + 2 * kC, h3, CG::T3);
+    __syncthreads();
+    if (threadIdx.x < kC) {
+      float m = h3[threadIdx.x * CG::T3 * CG::T3];
+      for (int q = 1; q < CG::T3 * CG::T3; ++q) m = fmaxf(m, h3[threadIdx.x * CG::T3 * CG::T3 + q]);
+      z[threadIdx.x] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float logit = ws[IG::WTE + 4 * kC];
+      for (int o = 0; o < kC; ++o) logit += ws[IG::WTE + 3 * kC + o] * z[o];
+      prob[p] = 1.f / (1.f + expf(-logit));
+    }
     __syncthreads();
   }
 }
@@ -464,11 +588,11 @@ void launch_features(const PoolView& pv, const void* y, float* feat, float* mpre
                      int num_sms, cudaStream_t st) {
   const bool d = pv.prec != MR_PREC_FP32;
   if (pv.Bs == 17) {
-    const size_t smem = kRingBytes + 8 * pv.nvar * (Geo<2, 17>::TILE + Geo<2, 17>::CBOX);
+    const size_t smem = FeatGeo<17>::smem(pv.nvar);
     if (d) { auto k = k_features<17, double>; prep(k, smem); k<<<num_sms * 2, 256, smem, st>>>(pv, (const double*)y, feat, mpre, base); }
     else { auto k = k_features<17, float>; prep(k, smem); k<<<num_sms * 2, 256, smem, st>>>(pv, (const float*)y, feat, mpre, base); }
   } else {
-    const size_t smem = kRingBytes + 8 * pv.nvar * (Geo<2, 33>::TILE + Geo<2, 33>::CBOX);
+    const size_t smem = FeatGeo<33>::smem(pv.nvar);
     if (d) { auto k = k_features<33, double>; prep(k, smem); k<<<num_sms * 2, 256, smem, st>>>(pv, (const double*)y, feat, mpre, base); }
     else { auto k = k_features<33, float>; prep(k, smem); k<<<num_sms * 2, 256, smem, st>>>(pv, (const float*)y, feat, mpre, base); }
   }
@@ -477,8 +601,7 @@ void launch_features(const PoolView& pv, const void* y, float* feat, float* mpre
 
 template <int T>
 static size_t infer_smem() {
-  using CG = CnnGeo<T>;
-  return sizeof(float) * (CG::NX + CG::N1 + CG::N2 + CG::N3);
+  return InferGeo<T>::SMEM;
 }
 template <int T>
 static size_t train_smem() {
