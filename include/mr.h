@@ -75,7 +75,9 @@ typedef struct {
   int32_t ng;           /* ghost layer width: 4 */
   int32_t nvar;         /* variables per node: 1 (advection) or 4 (NS) */
   int32_t precision;    /* MR_PREC_* */
-  int32_t detail_fp64;  /* 1: details of FP32 fields evaluated in FP64 */
+  int32_t detail_fp64;  /* 1: threshold decisions in FP64 (FP32 fields: certified FP32
+                           evaluation, FP64 where needed); 0: FP32 details, also for the
+                           FP64 state of MR_PREC_FP32_ACC64; MR_PREC_FP64 always FP64 */
   int32_t rhs_kind;     /* MR_RHS_* */
   int32_t ntrees;       /* independent trees advanced together (>= 1) */
   int64_t capacity;     /* pool slots over all trees; a refine-all needs

@@ -650,17 +650,17 @@ __device__ __forceinline__ T block_max(T v, T* red) {
   return v;
 }
 
-template <int D, int B, typename TS, typename TD, int NT>
+template <int D, int B, typename TS, typename TD, int NT, typename TT = TS>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_details(PoolView pv, TS* __restrict__ y) {
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 2>;  // prediction from even nodes reaches two nodes
   using DG = DetGeo<D, B>;
   Ring& R = *smem_as<Ring>(0);
   __shared__ double red[2][32];
-  TS* tile = smem_as<TS>(kRingBytes);  // storage type; TD is the arithmetic type
-  TS* cbox = tile + pv.nvar * Bx::TILE;
+  TT* tile = smem_as<TT>(kRingBytes);  // tile type (TS or FP32); TD is the decision type
+  TT* cbox = tile + pv.nvar * Bx::TILE;
   // gather scratch, reused for the x pass once the tile is complete
-  TS* scr = cbox + pv.nvar * Bx::CBOX;
+  TT* scr = cbox + pv.nvar * Bx::CBOX;
   TD* X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(scr) + 15) & ~(uintptr_t)15);
   const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   // (the first round after the RK stages); the next block's plan is fetched
   // while a block is processed
   const bool plan_ok = pv.cnt->plan_topo == pv.cnt->topo;
-  const size_t xs = sizeof(TS) * (size_t)nv * Bx::SCR, xd = sizeof(TD) * (size_t)(DG::NX + DG::NY);
+  const size_t xs = sizeof(TT) * (size_t)nv * Bx::SCR, xd = sizeof(TD) * (size_t)(DG::NX + DG::NY);
   const size_t xbytes = xs > xd ? xs : xd;
   int32_t* gtab = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(X) + ((xbytes + 15) & ~(size_t)15));
   if (D == 2) build_gtab<D, B, 2>(gtab);
@@ -752,22 +752,22 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     ndet += 1;
     const int64_t own = (int64_t)b.slot * nv * pv.vs;
     if (uni && nv == 1 && D == 2)
-      gather_table<D, B, 2, 1, TS, TS>(pv, own, snbo, gtab, y, y, tile, true);
+      gather_table<D, B, 2, 1, TS, TT>(pv, own, snbo, gtab, y, y, tile, true);
     else if (uni && nv == 4 && D == 2)
-      gather_table<D, B, 2, 4, TS, TS>(pv, own, snbo, gtab, y, y, tile, true);
+      gather_table<D, B, 2, 4, TS, TT>(pv, own, snbo, gtab, y, y, tile, true);
     else if (uni && nv == 1)
-      gather_uniform<D, B, 2, 1, TS, TS>(pv, b, snb, y, y, tile, true);
+      gather_uniform<D, B, 2, 1, TS, TT>(pv, b, snb, y, y, tile, true);
     else {
       if (uni) {
         build_ring<D, B>(pv, td, b, R);
         __syncthreads();
       }
-      fill_tile<D, B, TS, TS, 2>(pv, b, y, y, tile, true, R, cbox, scr);
+      fill_tile<D, B, TS, TT, 2>(pv, b, y, y, tile, true, R, cbox, scr);
     }
     __syncthreads();
     // Block maximum of |d| over the interior with arithmetic type A: x pass on
     // coarse rows (yc, zc) in [-1, NC-2] into X, then y (and z) per odd node.
-    auto pass = [&](auto tag, const TS* tv) -> double {
+    auto pass = [&](auto tag, const TT* tv) -> double {
       using A = decltype(tag);
       A* XA = reinterpret_cast<A*>(X);
       for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
@@ -818,15 +818,15 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       return (double)block_max<A>(md, reinterpret_cast<A*>(red[0]));
     };
     for (int v = 0; v < nv; ++v) {
-      const TS* tv = tile + v * Bx::TILE;
-      TS mqs = TS(0);  // largest |value|: a maximum of stored values, exact in their type
+      const TT* tv = tile + v * Bx::TILE;
+      TT mqs = TT(0);  // largest |value|: a maximum of stored values, exact in their type
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-        mqs = fmax(mqs, (TS)fabs(tv[Bx::tix(i, j, k)]));
+        mqs = fmax(mqs, (TT)fabs(tv[Bx::tix(i, j, k)]));
       }
-      const double mq = (double)block_max<TS>(mqs, reinterpret_cast<TS*>(red[1]));
+      const double mq = (double)block_max<TT>(mqs, reinterpret_cast<TT*>(red[1]));
       double md;
-      if constexpr (sizeof(TS) == 4 && sizeof(TD) == 8) {
+      if constexpr (sizeof(TT) == 4 && sizeof(TD) == 8) {
         // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
         // one by at most ~20 u max|tile| (u = 2^-24, x/y/z passes of the
         // 4-point rule and the subtraction); where its maximum is farther than

@@ -218,8 +218,10 @@ struct DetailsRun {
   static void run(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
                   cudaStream_t st) {
     constexpr int threads = Threads<D, B>::value;
-    const bool d64 = fp64 || sizeof(TS) == 8;
-    const bool warp_form = pv.nvar == 1 && pv.norm_kind == 0 &&
+    // FP64 details for the plain FP64 form or when asked for (thresholds below
+    // FP32 resolution); otherwise FP32, also for FP64 state
+    const bool d64 = fp64 || pv.prec == MR_PREC_FP64;
+    const bool warp_form = pv.nvar == 1 && pv.norm_kind == 0 && sizeof(TS) == 4 &&
                            (lc.stage_form == 1 || (lc.stage_form < 0 && lc.n_hint >= 8 * lc.num_sms));
     if (D == 2 && warp_form) {  // one warp per block
       if (d64) {
@@ -237,16 +239,16 @@ struct DetailsRun {
       return;
     }
     using Bx = Box<D, B, 2>;
-    const size_t scr = sizeof(TS) * pv.nvar * Bx::SCR,
-                 xp = (d64 ? 8 : sizeof(TS)) * (DetGeo<D, B>::NX + DetGeo<D, B>::NY);
-    const size_t smem = kRingBytes + sizeof(TS) * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp) +
-                        16 + (D == 2 ? 4 * Bx::NPTS : 0);
+    const size_t tt = d64 ? sizeof(TS) : 4;  // tile type: the state type, FP32 for FP32 details
+    const size_t scr = tt * pv.nvar * Bx::SCR, xp = (d64 ? 8 : 4) * (DetGeo<D, B>::NX + DetGeo<D, B>::NY);
+    const size_t smem = kRingBytes + tt * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp) + 16 +
+                        (D == 2 ? 4 * Bx::NPTS : 0);
     if (d64) {
       auto k = k_details<D, B, TS, double, threads>;
       prep_smem(k, smem);
       k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
     } else {
-      auto k = k_details<D, B, TS, TS, threads>;
+      auto k = k_details<D, B, TS, float, threads, float>;
       prep_smem(k, smem);
       k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
     }
