@@ -478,6 +478,7 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
     const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
     const int64_t base = (int64_t)b.slot * 4 * pv.vs;
     const TS cas = (TS)ca, cys = (TS)cy;  // RK weights in the state type
+    const TC casf = (TC)ca, cysf = (TC)cy;  // and in the stage type
     // UC points per thread at a time: state and accumulator loads first
     constexpr int UC = 4, NT = 256;
     for (int i0 = threadIdx.x; i0 < 4 * Gm::NI; i0 += UC * NT) {
@@ -501,16 +502,33 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
         const TC* Gv = Gf + v * NG::NG;
         const TC dFx = ((Fv[fI(i - 2, j)] - Fv[fI(i + 2, j)]) + TC(8) * (Fv[fI(i + 1, j)] - Fv[fI(i - 1, j)])) * c;
         const TC dGy = ((Gv[gI(i, j - 2)] - Gv[gI(i, j + 2)]) + TC(8) * (Gv[gI(i, j + 1)] - Gv[gI(i, j - 1)])) * c;
-        const TS kk = (TS)(-(dFx + dGy));
         const int64_t at = base + (int64_t)v * pv.vs + q;
-        if (stage == 0) {
-          acc[at] = yv[u] + cas * kk;
-          ynext[at] = (TY)(yv[u] + cys * kk);
-        } else if (stage == 1 || stage == 2) {
-          acc[at] = av[u] + cas * kk;
-          ynext[at] = (TY)(yv[u] + cys * kk);
+        if constexpr (sizeof(TS) == 8 && sizeof(TC) == 4) {
+          // FP64 state, FP32 stages: the increments dt k are formed in FP32 and
+          // only accumulated in FP64 (one conversion and one FP64 add per
+          // update; FP64 arithmetic is a small fraction of the FP32 rate here),
+          // the FP32 stage value from the FP32-rounded state
+          const TC kc = -(dFx + dGy);
+          if (stage == 0) {
+            acc[at] = yv[u] + (TS)(casf * kc);
+            ynext[at] = (TY)((TC)yv[u] + cysf * kc);
+          } else if (stage == 1 || stage == 2) {
+            acc[at] = av[u] + (TS)(casf * kc);
+            ynext[at] = (TY)((TC)yv[u] + cysf * kc);
+          } else {
+            y[at] = av[u] + (TS)(casf * kc);
+          }
         } else {
-          y[at] = av[u] + cas * kk;
+          const TS kk = (TS)(-(dFx + dGy));
+          if (stage == 0) {
+            acc[at] = yv[u] + cas * kk;
+            ynext[at] = (TY)(yv[u] + cys * kk);
+          } else if (stage == 1 || stage == 2) {
+            acc[at] = av[u] + cas * kk;
+            ynext[at] = (TY)(yv[u] + cys * kk);
+          } else {
+            y[at] = av[u] + cas * kk;
+          }
         }
       }
     }
