@@ -286,6 +286,22 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(ms, points, world):
+    """Whole-job figures over the ranks: the slowest rank's time (the job ends
+    with it) and the points all ranks advanced (each rank runs its own
+    replica; nothing is exchanged during the steps)."""
+    if world <= 1:
+        return float(ms), float(points)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    p = torch.tensor([float(points)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def trees_of(w):
     return w["trees"] if "trees" in w else [w["tree"]]
 
@@ -490,11 +506,8 @@ def main():
     nb = g.num_blocks()
     g.enable_timing(False)
     st = g.stats()
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = points * world / (ms_max / 1e3)
+    ms_max, points_all = reduce_over_ranks(ms, points, world)
+    value = points_all / (ms_max / 1e3)
 
     if learned is not None and "tau" in learned:
         learned["timed_region"] = g.proposal_stats(reset=True)
