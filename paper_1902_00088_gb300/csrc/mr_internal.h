@@ -54,6 +54,7 @@ struct Counters {
   int32_t topo;       // tree generation: changes with every refinement, merge or import
   int32_t plan_topo;  // generation the stage plans were built for (-1: none)
   unsigned long long graph_rounds;  // coarsening-round bodies run by graph while nodes
+  unsigned int ctas_done;  // CTAs of the running commit kernel that finished (last one resets)
 };
 constexpr int kMaxVar = 4;  // variables per node (advection 1, Navier-Stokes 4; checked at creation)
 constexpr int kMaxHist = 1 << 16;  // step history: blocks of the adapted grid before each step

@@ -1242,30 +1242,58 @@ __global__ void k_refine_count(PoolView pv, int mode, const int8_t* mask) {
   }
 }
 
-template <int D>
-__global__ void k_refine_finalize(PoolView pv) {
-  const int nact = pv.cnt->n_act;
-  const int n_alloc = pv.cnt->n_alloc, n_free = pv.cnt->n_free;
-  if (n_alloc > n_free) return;
-  const int nch = 1 << D;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
-    const int s = pv.act[p];
-    if (pv.flag[s] != 1) continue;
-    const BlockInfo b = load_block(pv, s);
-    const TreeDev& td = pv.trees[b.tree];
-    pv.tab[td.tab_off[b.lvl] + (int64_t)morton<D>(b.c, b.lvl)] = -1;
-    const int e = pv.eoff[2 * p];
-    for (int r = 0; r < nch; ++r) {
-      const int cs = pv.act_next[e + r];
-      int64_t c[3] = {pv.crd[3 * cs], pv.crd[3 * cs + 1], pv.crd[3 * cs + 2]};
-      pv.tab[td.tab_off[b.lvl + 1] + (int64_t)morton<D>(c, b.lvl + 1)] = cs;
-    }
-    pv.freelist[n_free - n_alloc + pv.eoff[2 * p + 1] / nch] = s;
-    pv.lvl[s] = -1;
-    pv.flag[s] = 0;
-  }
+// True in thread 0 of the CTA of the grid that finishes last; the writes of
+// every other CTA of the grid are visible to it.
+__device__ __forceinline__ bool last_cta(Counters* c) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&c->ctas_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last && threadIdx.x == 0;
 }
 
+// End of a refinement in one kernel: each refined mother's table entry is
+// replaced by its children's and its slot freed, the new active list is copied
+// in place (each index is read, then written, by one thread), and the counters
+// are updated by the last CTA.
+template <int D>
+__global__ void k_refine_commit(PoolView pv) {
+  Counters* c = pv.cnt;
+  const int nact = c->n_act, n_new = c->n_new, n_alloc = c->n_alloc, n_free = c->n_free;
+  const bool ok = n_alloc <= n_free;
+  const int nch = 1 << D;
+  const int nmax = ok ? (nact > n_new ? nact : n_new) : 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nmax; p += gridDim.x * blockDim.x) {
+    const int32_t nxt = p < n_new ? pv.act_next[p] : 0;
+    if (p < nact) {
+      const int s = pv.act[p];
+      if (pv.flag[s] == 1) {
+        const BlockInfo b = load_block(pv, s);
+        const TreeDev& td = pv.trees[b.tree];
+        pv.tab[td.tab_off[b.lvl] + (int64_t)morton<D>(b.c, b.lvl)] = -1;
+        const int e = pv.eoff[2 * p];
+        for (int r = 0; r < nch; ++r) {
+          const int cs = pv.act_next[e + r];
+          int64_t cc[3] = {pv.crd[3 * cs], pv.crd[3 * cs + 1], pv.crd[3 * cs + 2]};
+          pv.tab[td.tab_off[b.lvl + 1] + (int64_t)morton<D>(cc, b.lvl + 1)] = cs;
+        }
+        pv.freelist[n_free - n_alloc + pv.eoff[2 * p + 1] / nch] = s;
+        pv.lvl[s] = -1;
+        pv.flag[s] = 0;
+      }
+    }
+    if (p < n_new) pv.act[p] = nxt;
+  }
+  if (last_cta(c)) {
+    if (ok) {
+      c->n_free = n_free - n_alloc + n_alloc / nch;
+      c->n_act = n_new;
+      c->topo += 1;
+    }
+    c->ctas_done = 0;
+  }
+}
 
 __device__ __forceinline__ bool same_family(const PoolView& pv, int s, int t) {
   if (pv.tree[s] != pv.tree[t] || pv.lvl[s] != pv.lvl[t]) return false;
@@ -1353,28 +1381,53 @@ __global__ void k_flags(PoolView pv) {
   }
 }
 
+// End of a coarsening round in one kernel: a merged family's first member in
+// Hilbert order becomes the mother (level, coordinates, key, table entry, merge
+// stamp), the others are freed; the new list is copied in place, and the round
+// counters are updated by the last CTA (first_round cleared; merged families
+// counted; done once a round merged nothing).
 template <int D>
-__global__ void k_coarsen_finalize(PoolView pv) {
-  const int nact = pv.cnt->n_round;
-  const int n_free = pv.cnt->n_free;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
-    const int s = pv.act[p];
-    if (pv.flag[s] != -2) continue;
-    const BlockInfo b = load_block(pv, s);
-    const TreeDev& td = pv.trees[b.tree];
-    pv.tab[td.tab_off[b.lvl] + (int64_t)morton<D>(b.c, b.lvl)] = -1;
-    if (pv.emit[2 * p]) {
-      int64_t pc[3] = {b.c[0] >> 1, b.c[1] >> 1, b.c[2] >> 1};
-      pv.tab[td.tab_off[b.lvl - 1] + (int64_t)morton<D>(pc, b.lvl - 1)] = s;
-      pv.stamp[s] = pv.cnt->round_id;
-      pv.lvl[s] = (int8_t)(b.lvl - 1);
-      int32_t c32[3] = {(int32_t)pc[0], (int32_t)pc[1], (int32_t)pc[2]};
-      for (int a = 0; a < 3; ++a) pv.crd[3 * s + a] = c32[a];
-      pv.hkey[s] = block_key<D>(c32, b.lvl - 1, td.Jmax);
-    } else {
-      pv.lvl[s] = -1;
-      pv.freelist[n_free + pv.eoff[2 * p + 1]] = s;
+__global__ void k_coarsen_commit(PoolView pv) {
+  Counters* c = pv.cnt;
+  const int nround = c->n_round, n_free = c->n_free, n_new = c->n_new, rid = c->round_id;
+  const bool done = c->done != 0;
+  const int ncopy = done ? 0 : n_new;
+  const int nmax = nround > ncopy ? nround : ncopy;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nmax; p += gridDim.x * blockDim.x) {
+    const int32_t nxt = p < ncopy ? pv.act_next[p] : 0;
+    if (p < nround) {
+      const int s = pv.act[p];
+      if (pv.flag[s] == -2) {
+        const BlockInfo b = load_block(pv, s);
+        const TreeDev& td = pv.trees[b.tree];
+        pv.tab[td.tab_off[b.lvl] + (int64_t)morton<D>(b.c, b.lvl)] = -1;
+        if (pv.emit[2 * p]) {
+          int64_t pc[3] = {b.c[0] >> 1, b.c[1] >> 1, b.c[2] >> 1};
+          pv.tab[td.tab_off[b.lvl - 1] + (int64_t)morton<D>(pc, b.lvl - 1)] = s;
+          pv.stamp[s] = rid;
+          pv.lvl[s] = (int8_t)(b.lvl - 1);
+          int32_t c32[3] = {(int32_t)pc[0], (int32_t)pc[1], (int32_t)pc[2]};
+          for (int a = 0; a < 3; ++a) pv.crd[3 * s + a] = c32[a];
+          pv.hkey[s] = block_key<D>(c32, b.lvl - 1, td.Jmax);
+        } else {
+          pv.lvl[s] = -1;
+          pv.freelist[n_free + pv.eoff[2 * p + 1]] = s;
+        }
+      }
     }
+    if (p < ncopy) pv.act[p] = nxt;
+  }
+  if (last_cta(c)) {
+    c->first_round = 0;
+    if (!done) {
+      const int nch = 1 << D;
+      c->merged = (c->n_act - n_new) / (nch - 1);
+      c->n_free = n_free + c->n_alloc;
+      c->n_act = n_new;
+      if (c->merged == 0) c->done = 1;
+      else c->topo += 1;
+    }
+    c->ctas_done = 0;
   }
 }
 

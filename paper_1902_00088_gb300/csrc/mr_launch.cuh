@@ -181,9 +181,6 @@ struct RefineRun {
   }
 };
 
-__global__ void k_refine_counters(Counters* c, int nch);
-__global__ void k_coarsen_counters(Counters* c, int nch);
-__global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check_capacity);
 
 template <int D>
 void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* mask,
@@ -193,10 +190,9 @@ void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* 
   count_launch();
   launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st, 2 * (int64_t)lc.n_hint);
   dispatch_bs<D, RefineRun>(pv, f, lc, st);
-  k_refine_finalize<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
-  k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 1);
-  k_refine_counters<<<1, 1, 0, st>>>(pv.cnt, nch);
-  count_launch(3);
+  k_refine_commit<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  count_launch(1);
+  (void)nch;
 }
 
 // ------------------------------------------------------------------- IC ------
@@ -284,10 +280,9 @@ void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const L
   if (!merge) return;
   launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st, 4 * (int64_t)lc.n_hint);
   dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
-  k_coarsen_finalize<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
-  k_copy_act<<<flat_grid(pv, 256), 256, 0, st>>>(pv.act_next, pv.act, pv.cnt, 2);
-  k_coarsen_counters<<<1, 1, 0, st>>>(pv.cnt, nch);
-  count_launch(3);
+  k_coarsen_commit<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  count_launch(1);
+  (void)nch;
 }
 
 template <int D>

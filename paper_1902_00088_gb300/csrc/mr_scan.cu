@@ -167,23 +167,6 @@ void launch_scan2(const int32_t* in, int32_t* out, int32_t* partial, const int32
   count_launch(3);
 }
 
-__global__ void k_refine_counters(Counters* c, int nch) {
-  if (c->n_alloc > c->n_free) return;
-  c->n_free = c->n_free - c->n_alloc + c->n_alloc / nch;
-  c->n_act = c->n_new;
-  c->topo += 1;
-}
-
-__global__ void k_coarsen_counters(Counters* c, int nch) {
-  c->first_round = 0;
-  if (c->done) return;
-  c->merged = (c->n_act - c->n_new) / (nch - 1);
-  c->n_free = c->n_free + c->n_alloc;
-  c->n_act = c->n_new;
-  if (c->merged == 0) c->done = 1;
-  else c->topo += 1;
-}
-
 // Start of a step: coarsening rounds enabled again; hist (nullable) records the
 // number of blocks of the adapted grid the step starts from.
 __global__ void k_step_begin(Counters* c, int32_t* hist) {
@@ -216,17 +199,6 @@ __global__ void k_round_continue(Counters* c, cudaGraphConditionalHandle h, int 
 __global__ void k_time_advance(TreeTime* tt, int ntrees) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < ntrees) tt[k].t = tt[k].t + tt[k].dt;
-}
-
-// Copies the n_new entries of the list just built; after a refine that failed
-// for lack of free slots (check_capacity) the current list is kept.
-// check: 1 after a refine (skip on capacity failure), 2 after a coarsening
-// round (skip when the round was empty).
-__global__ void k_copy_act(const int32_t* src, int32_t* dst, const Counters* c, int check) {
-  if (check == 1 && c->n_alloc > c->n_free) return;
-  if (check == 2 && c->done) return;
-  const int n = c->n_new;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
 }
 
 
