@@ -1353,26 +1353,64 @@ __device__ __forceinline__ bool qualifies(const PoolView& pv, const TreeDev& td,
 
 template <int D>
 __global__ void k_flags(PoolView pv) {
+  // A family (the 2^d sisters of a block) merges when every sister is a leaf
+  // whose normalised detail is below eps, above Jmin, and no leaf one level
+  // finer touches any sister: the cells of level l+1 around the family,
+  // [-1, 4]^d relative to its lower corner minus the family itself (the
+  // union of the sisters' rings).  One warp per block; the sister lookups,
+  // their details and the ring lookups are spread over the lanes.
+  constexpr int NS = 1 << D;
+  constexpr int NBOX = D == 3 ? 6 * 6 * 6 : 6 * 6;  // [-1, 4]^d around a family
   const int nact = pv.cnt->n_round;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
+  const int nv = pv.nvar;
   for (int p = blockIdx.x * wpb + (threadIdx.x >> 5); p < nact; p += gridDim.x * wpb) {
     const int s = pv.act[p];
     const BlockInfo b = load_block(pv, s);
     const TreeDev& td = pv.trees[b.tree];
-    double m = 0.0;
-    bool all = qualifies<D>(pv, td, s, lane, &m);
+    int64_t fc[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) fc[a] = b.c[a] & ~(int64_t)1;
+    // sisters: exist as leaves and below eps
+    bool ok = true;
+    double mine = 0.0;
+    if (lane < NS) {
+      int64_t c[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) c[a] = fc[a] | ((lane >> a) & 1);
+      const int t = tab_get<D>(pv, td, b.lvl, c);
+      if (t < 0) {
+        ok = false;
+      } else {
+        double m = 0.0;
+        bool nan = false;
+        for (int v = 0; v < nv; ++v) {
+          double sv = pv.svar[b.tree * nv + v];
+          if (sv == 0.0) sv = 1.0;
+          const double mv = pv.md[(int64_t)t * nv + v];
+          nan |= isnan(mv);
+          m = fmax(m, mv / sv);
+        }
+        if (nan) m = __longlong_as_double(0x7ff8000000000000LL);
+        ok = m < td.eps;
+        if (t == s) mine = m;
+      }
+    }
+    // no finer leaf around the family: cells of [-1, 4]^d outside [0, 3]^d
+    for (int u = lane; u < NBOX; u += 32) {
+      const int q[3] = {u % 6 - 1, (u / 6) % 6 - 1, D == 3 ? u / 36 - 1 : 0};
+      bool in = true;
+      for (int a = 0; a < D; ++a) in &= q[a] >= 0 && q[a] <= 3;
+      if (in) continue;
+      int64_t cell[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) cell[a] = 2 * fc[a] + q[a];
+      if (tab_get<D>(pv, td, b.lvl + 1, cell) >= 0) ok = false;
+    }
+    const bool all = __all_sync(0xffffffffu, ok) && b.lvl > td.Jmin;
+    const double m = __shfl_sync(0xffffffffu, mine, (int)(((b.c[0] & 1) | (D > 1 ? (b.c[1] & 1) << 1 : 0) |
+                                                          (D > 2 ? (b.c[2] & 1) << 2 : 0))));
     if (lane == 0) {
       pv.mdet[s] = m;
       if (isnan(m)) set_err(pv, kErrNaN);
-    }
-    for (int ch = 0; all && ch < (1 << D); ++ch) {
-      int64_t c[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((ch >> a) & 1);
-      const int t = tab_get<D>(pv, td, b.lvl, c);
-      if (t != s) all = t >= 0 && qualifies<D>(pv, td, t, lane, nullptr);
-    }
-    if (lane == 0) {
       pv.flag[s] = all ? -2 : 0;
       const bool first = all && (p == 0 || !same_family(pv, s, pv.act[p - 1]));
       pv.emit[2 * p] = (!all || first) ? 1 : 0;
