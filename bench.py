@@ -327,6 +327,7 @@ def main():
                     help="swirl: do not run on to t = t_a for the error (timed window only)")
     ap.add_argument("--eager", action="store_true", help="host-driven steps instead of CUDA graph replays")
     ap.add_argument("--autotune", type=int, default=-1, help="steps per autotuner candidate (0 = off)")
+    ap.add_argument("--no-overlap", action="store_true", help="plain kernel launches (no programmatic dependent launch)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
@@ -379,6 +380,8 @@ def main():
     g = mr.Forest(dim=w["dim"], Bs=w["Bs"], nvar=w.get("nvar", 1), precision=w["precision"],
                   detail_fp64=w["detail_fp64"], rhs=w["rhs"], trees=trees, capacity=w["capacity"],
                   norm_kind=w.get("norm_kind", 0), stream=stream.cuda_stream)
+    if args.no_overlap:
+        g.set_launch_overlap(False)
     B, d = w["Bs"], w["dim"]
     npts = B ** d
     dts = np.array(dts_of(w))
@@ -650,6 +653,7 @@ def main():
                        "Bs": B, "dim": d, "dt": float(dts[0]) if nt == 1 else "per tree",
                        "mode": "eager" if not graph else "cuda-graph step replay (%s rounds)" % g.graph_mode(),
                        "autotuned": tuned,
+                       "launch_overlap": g.launch_overlap(),
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2_flush": "256 MiB written between timed steps (untimed)",
                        "step_ms_p50": pct(0.5), "step_ms_p99": pct(0.99),

@@ -259,6 +259,17 @@ mr_status mr_step_graph(mr_ctx ctx, int64_t nsteps);
  * become empty once nothing merges (used where conditional nodes are not
  * available), -1 = no graph captured yet. */
 int32_t mr_graph_mode(mr_ctx ctx);
+/* Launch overlap (off by default): the kernels of a step are launched with
+ * programmatic dependent launch, so that each one is scheduled while the
+ * previous one finishes; every kernel first waits for its predecessor's
+ * completion and memory, so results are identical with the overlap on or off.
+ * In captured steps it changed the step time by less than the run-to-run
+ * spread (the kernels' own latency dominates, not the launch gaps).
+ * Where a graph with such launches cannot be captured or instantiated the
+ * context turns the overlap off and captures plain launches.  Setting it drops
+ * the captured step.  mr_get_launch_overlap returns 1 / 0 (-1: no context). */
+mr_status mr_set_launch_overlap(mr_ctx ctx, int32_t on);
+int32_t mr_get_launch_overlap(mr_ctx ctx);
 /* Blocks of the adapted grid at the start of every graph step since the last
  * reset (up to 65536 entries); *n = entries recorded.  Synchronises. */
 mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n, int32_t reset);

@@ -86,6 +86,8 @@ SIGNATURES = {
     "mr_get_time": (_i32, [_vp, _dp]),
     "mr_step_graph": (_i32, [_vp, _i64]),
     "mr_graph_mode": (_i32, [_vp]),
+    "mr_set_launch_overlap": (_i32, [_vp, _i32]),
+    "mr_get_launch_overlap": (_i32, [_vp]),
     "mr_get_step_history": (_i32, [_vp, _i64, _vp, C.POINTER(C.c_int64), _i32]),
     "mr_autotune": (_i32, [_vp, _i32, C.POINTER(C.c_int32)]),
     "mr_set_refine_mode": (_i32, [_vp, _i32]),
@@ -285,6 +287,12 @@ class Forest:
 
     def graph_mode(self):
         return {1: "while-node", 0: "fixed-rounds", -1: None}[int(self.lib.mr_graph_mode(self.h))]
+
+    def set_launch_overlap(self, on):
+        self._ck(self.lib.mr_set_launch_overlap(self.h, 1 if on else 0))
+
+    def launch_overlap(self):
+        return bool(self.lib.mr_get_launch_overlap(self.h))
 
     def step_history(self, reset=True):
         n = C.c_int64()

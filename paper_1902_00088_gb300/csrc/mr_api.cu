@@ -41,6 +41,7 @@ struct mr_ctx_s {
           *cells = nullptr, *emit = nullptr, *eoff = nullptr, *partial = nullptr, *pos = nullptr;
   uint64_t* hkey = nullptr;
   double *md = nullptr, *mdet = nullptr, *bmax = nullptr, *lat = nullptr, *svar = nullptr;
+  float* latf = nullptr;
   Counters* cnt = nullptr;
   TreeDev* trees = nullptr;
   int4* rel = nullptr;
@@ -123,7 +124,7 @@ PoolView view(mr_ctx c) {
   v.vs = c->vs; v.cap = c->S; v.trees = c->trees;
   v.lvl = c->lvl; v.tree = c->tree; v.crd = c->crd; v.hkey = c->hkey; v.f1 = c->f1;
   v.flag = c->flag; v.md = c->md; v.mdet = c->mdet; v.bmax = c->bmax; v.act = c->act;
-  v.act_next = c->act_next; v.freelist = c->freelist; v.tab = c->tab; v.lat = c->lat;
+  v.act_next = c->act_next; v.freelist = c->freelist; v.tab = c->tab; v.lat = c->lat; v.latf = c->latf;
   v.svar = c->svar; v.cells = c->cells; v.emit = c->emit; v.eoff = c->eoff;
   v.partial = c->partial; v.pos_of_slot = c->pos; v.cnt = c->cnt; v.stamp = c->stamp;
   v.plan = c->plan;
@@ -278,7 +279,7 @@ int max_rounds_of(mr_ctx ctx) {
 
 mr_status coarsen_until_stable(mr_ctx ctx) {
   const int rounds = max_rounds_of(ctx);
-  k_step_begin<<<1, 1, 0, ctx->st>>>(ctx->cnt, nullptr);
+  launch_k(ctx->lc.pdl, k_step_begin, 1, 1, 0, ctx->st, ctx->cnt, nullptr);
   count_launch();
   for (int r = 0; r < rounds; ++r) {
     do_round(ctx, true);
@@ -421,6 +422,9 @@ mr_status rk_step(mr_ctx ctx, const double* t, const double* dt) {
       sa.ca[k] = ca[s];
       sa.cy[k] = cy[s];
       sa.ct[k] = ctx->p.rhs_kind == MR_RHS_SWIRL ? std::cos(M_PI * tsv[s] / ctx->td[k].rhs[0]) : 0.0;
+      sa.caf[k] = (float)sa.ca[k];
+      sa.cyf[k] = (float)sa.cy[k];
+      sa.ctf[k] = (float)sa.ct[k];
     }
     by_dim(ctx, [&] { launch_stage<2>(pv, f, s, sa, ctx->lc, ctx->st); },
            [&] { launch_stage<3>(pv, f, s, sa, ctx->lc, ctx->st); });
@@ -553,6 +557,7 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     ctx->lc.num_sms = prop.multiProcessorCount;
     ctx->lc.grid_mult = 0;
     ctx->lc.stage_form = -1;
+    ctx->lc.pdl = 0;
     ctx->lc.n_hint = 0;
   }
   const int d = P.dim, B = P.Bs, nv = P.nvar;
@@ -568,6 +573,11 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     const mr_tree_desc& t = ctx->td[k];
     TreeDev td{};
     td.Jmin = t.Jmin; td.Jmax = t.Jmax; td.eps = t.eps;
+    {
+      const float f = (float)t.eps;
+      td.epsf[0] = (double)f > t.eps ? std::nextafter(f, -INFINITY) : f;
+      td.epsf[1] = (double)f < t.eps ? std::nextafter(f, INFINITY) : f;
+    }
     td.N = (int64_t)(B - 1) << t.Jmax;
     for (int l = 0; l <= kMaxLevel; ++l) {
       td.tab_off[l] = tab;
@@ -575,12 +585,21 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
       const double dx = P.L / (double)((int64_t)(B - 1) << l);
       td.dx[l] = dx;
       td.cD[l] = 1.0 / (12.0 * dx);
+      td.cDf[l] = (float)td.cD[l];
     }
     td.lat_off = lat;
     lat += (int64_t)kNumLat * td.N;
     td.cell_off = cells;
     cells += (int64_t)1 << (d * t.Jmax);
     for (int a = 0; a < 8; ++a) td.rhs[a] = t.rhs[a];
+    for (int a = 0; a < 8; ++a) td.rhsf[a] = (float)t.rhs[a];
+    {
+      const double gam = t.rhs[0], mud = t.rhs[1], Pr = t.rhs[2];
+      td.nsd[0] = gam - 1.0;
+      td.nsd[1] = mud;
+      td.nsd[2] = Pr != 0.0 && gam != 1.0 ? mud * gam / ((gam - 1.0) * Pr) : 0.0;
+      for (int a = 0; a < 3; ++a) td.nsf[a] = (float)td.nsd[a];
+    }
     for (int a = 0; a < 3; ++a) td.x0[a] = t.x0[a];
     td.ic_kind = t.ic_kind;
     if (t.ic_kind == MR_IC_MIXING) {
@@ -626,6 +645,7 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if ((e = dalloc(ctx, &ctx->eoff, 2 * ctx->nscan))) return e;
     if ((e = dalloc(ctx, &ctx->partial, 2 * (ctx->nscan / kScanChunk + 2)))) return e;
     if ((e = dalloc(ctx, &ctx->lat, ctx->nlat))) return e;
+    if ((e = dalloc(ctx, &ctx->latf, ctx->nlat))) return e;
     if ((e = dalloc(ctx, &ctx->svar, (int64_t)P.ntrees * nv))) return e;
     if ((e = dalloc(ctx, &ctx->cnt, 1))) return e;
     if ((e = dalloc(ctx, &ctx->trees, P.ntrees))) return e;
@@ -641,6 +661,8 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     for (int k = 0; k < P.ntrees; ++k)
       lattice_tables(P, ctx->td[k], ctx->tdev[k].N, hl.data() + ctx->tdev[k].lat_off);
     if ((e = cudaMemcpy(ctx->lat, hl.data(), ctx->nlat * 8, cudaMemcpyHostToDevice))) return e;
+    std::vector<float> hf(hl.begin(), hl.end());
+    if ((e = cudaMemcpy(ctx->latf, hf.data(), ctx->nlat * 4, cudaMemcpyHostToDevice))) return e;
     if ((e = cudaMemset(ctx->cnt, 0, sizeof(Counters)))) return e;
     const int32_t no_plan = -1;
     if ((e = cudaMemcpy(&ctx->cnt->plan_topo, &no_plan, 4, cudaMemcpyHostToDevice))) return e;
@@ -747,7 +769,7 @@ mr_status mr_adapt(mr_ctx ctx, int32_t mode) {
   }
   if (mode == MR_ADAPT_COARSEN) return coarsen_until_stable(ctx);
   if (mode == 3) {  // details and flags only (no merge), for inspection
-    k_step_begin<<<1, 1, 0, ctx->st>>>(ctx->cnt, nullptr);
+    launch_k(ctx->lc.pdl, k_step_begin, 1, 1, 0, ctx->st, ctx->cnt, nullptr);
     do_round(ctx, false);
     return check_device(ctx);
   }
@@ -953,8 +975,8 @@ void enqueue_graph_prologue(mr_ctx ctx, cudaStream_t st) {
   pv.tt = ctx->ttime;
   const Fields f = fields(ctx);
   const int nt = ctx->p.ntrees;
-  k_step_begin<<<1, 1, 0, st>>>(ctx->cnt, ctx->hist);
-  k_time_coef<<<(nt + 127) / 128, 128, 0, st>>>(ctx->ttime, ctx->trees, nt, ctx->p.rhs_kind == MR_RHS_SWIRL);
+  launch_k(ctx->lc.pdl, k_step_begin, 1, 1, 0, st, ctx->cnt, ctx->hist);
+  launch_k(ctx->lc.pdl, k_time_coef, (nt + 127) / 128, 128, 0, st, ctx->ttime, ctx->trees, nt, ctx->p.rhs_kind == MR_RHS_SWIRL);
   count_launch(2);
   int mode = MR_ADAPT_REFINE_ALL;
   if (ctx->refine_mode == 1) {
@@ -1034,7 +1056,7 @@ cudaError_t capture_step(mr_ctx ctx, cudaGraph_t* out, bool use_while) {
     if (e == cudaSuccess) {
       const int64_t b0 = kernel_launches();
       enqueue_round(ctx, ctx->body_stream);
-      k_round_continue<<<1, 1, 0, ctx->body_stream>>>(ctx->cnt, h, max_rounds_of(ctx));
+      launch_k(ctx->lc.pdl, k_round_continue, 1, 1, 0, ctx->body_stream, ctx->cnt, h, max_rounds_of(ctx));
       count_launch();
       ctx->graph_body = kernel_launches() - b0;
       cudaGraph_t body = nullptr;
@@ -1079,7 +1101,15 @@ mr_status build_graph(mr_ctx ctx) {
   ctx->capturing = true;
   const int64_t k0 = kernel_launches();
   cudaError_t e = capture_step(ctx, &g, ctx->graph_while);
+  if (e != cudaSuccess && ctx->lc.pdl) {  // programmatic edges not capturable: plain launches
+    cudaGetLastError();
+    ctx->lc.pdl = 0;
+    count_launch((int)-(kernel_launches() - k0));
+    ctx->graph_body = 0;
+    e = capture_step(ctx, &g, ctx->graph_while);
+  }
   if (e != cudaSuccess && ctx->graph_while) {  // no conditional nodes: fixed rounds
+    cudaGetLastError();
     ctx->graph_while = false;
     count_launch((int)-(kernel_launches() - k0));
     ctx->graph_body = 0;
@@ -1092,6 +1122,12 @@ mr_status build_graph(mr_ctx ctx) {
   if (e != cudaSuccess) return fail(ctx, MR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(&ctx->gexec, g, 0);
   cudaGraphDestroy(g);
+  if (e != cudaSuccess && ctx->lc.pdl) {  // capture again with plain launches
+    cudaGetLastError();
+    ctx->gexec = nullptr;
+    ctx->lc.pdl = 0;
+    return build_graph(ctx);
+  }
   if (e != cudaSuccess) return fail(ctx, MR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   return MR_OK;
 }
@@ -1110,6 +1146,15 @@ mr_status mr_step_graph(mr_ctx ctx, int64_t nsteps) {
   ctx->stats.stage_launches += 4 * nsteps;
   return MR_OK;
 }
+
+mr_status mr_set_launch_overlap(mr_ctx ctx, int32_t on) {
+  if (!ctx) return MR_EINVAL;
+  drop_graph(ctx);
+  ctx->lc.pdl = on ? 1 : 0;
+  return MR_OK;
+}
+
+int32_t mr_get_launch_overlap(mr_ctx ctx) { return ctx ? ctx->lc.pdl : -1; }
 
 int32_t mr_graph_mode(mr_ctx ctx) {
   if (!ctx || !ctx->gexec) return -1;
@@ -1462,6 +1507,7 @@ cudaError_t noalloc_scratch(double** out) {
 __global__ void k_noalloc_tables(double* ex, int64_t N, int dim, double L, double x00, double x01,
                                  double x02, double s0, double s1, double s2, double c0, double c1,
                                  double c2, double sigma) {
+  pdl_enter();
   const double x0[3] = {x00, x01, x02}, sh[3] = {s0, s1, s2}, c[3] = {c0, c1, c2};
   const double h = L / (double)N;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 3 * N;

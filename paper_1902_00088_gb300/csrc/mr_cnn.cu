@@ -55,6 +55,7 @@ template <int B, typename TS>
 __global__ void __launch_bounds__(256) k_features(PoolView pv, const TS* __restrict__ y,
                                                   float* __restrict__ feat, float* __restrict__ mpre,
                                                   int64_t base) {
+  pdl_enter();
   using Gm = Geo<2, B>;
   using Bx = Box<2, B, kG>;
   using FG = FeatGeo<B>;
@@ -255,6 +256,7 @@ template <int T>
 __global__ void __launch_bounds__(256) k_cnn_infer(PoolView pv, const float* __restrict__ feat,
                                                    const __nv_bfloat16* __restrict__ wb,
                                                    float* __restrict__ prob, int64_t n_explicit) {
+  pdl_enter();
   using CG = CnnGeo<T>;
   using IG = InferGeo<T>;
   float* ws = smem_as<float>(0);
@@ -324,6 +326,7 @@ __global__ void __launch_bounds__(256) k_cnn_train(const float* __restrict__ fea
                                                    int nb, const float* __restrict__ w, float w_pos,
                                                    float* __restrict__ grad, float* __restrict__ loss,
                                                    float* __restrict__ prob_out) {
+  pdl_enter();
   using CG = CnnGeo<T>;
   constexpr int T2 = CG::T2, T3 = CG::T3;
   float* x = smem_as<float>(0);
@@ -451,6 +454,7 @@ __global__ void __launch_bounds__(256) k_cnn_train(const float* __restrict__ fea
 
 __global__ void k_adam(float* w, float* m, float* v, float* g, int n, float lr, float b1, float b2,
                        float eps, int t, __nv_bfloat16* wb) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   // a non-finite gradient entry (seen once in a 64-tree training run, cause
@@ -467,6 +471,7 @@ __global__ void k_adam(float* w, float* m, float* v, float* g, int n, float lr, 
 }
 
 __global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) wb[i] = __float2bfloat16(w[i]);
 }
@@ -476,6 +481,7 @@ __global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
 // normalised detail >= eps); skip marks blocks left unrefined (for the judge).
 __global__ void k_propose(PoolView pv, const float* prob, const float* mpre, float tau, int8_t* skip,
                           int32_t* counts) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];
@@ -494,6 +500,7 @@ __global__ void k_propose(PoolView pv, const float* prob, const float* mpre, flo
 // Gradedness closure of +1 flags: a refined block forces the refinement of
 // every touching leaf one level coarser (monotone 0 -> 1, order independent).
 __global__ void k_close(PoolView pv, int8_t* skip, int32_t* changed) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];
@@ -518,6 +525,7 @@ __global__ void k_close(PoolView pv, int8_t* skip, int32_t* changed) {
 
 // Judge: a block left unrefined whose details after the step are >= eps.
 __global__ void k_judge(PoolView pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];
@@ -529,6 +537,7 @@ __global__ void k_judge(PoolView pv, const int8_t* skip, const int32_t* skip_key
 }
 
 __global__ void k_skip_key(PoolView pv, const int8_t* skip, int32_t* skip_key) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];
@@ -544,6 +553,7 @@ __global__ void k_skip_key(PoolView pv, const int8_t* skip, int32_t* skip_key) {
 // Samples whose own details were >= eps (mpre) are refined by the exact
 // fallback whatever the network says; they get -1 too (not trained on).
 __global__ void k_label(PoolView pv, const int32_t* key, const float* mpre, int64_t n, float* label) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int tree = key[4 * i], l = key[4 * i + 1];
@@ -565,6 +575,7 @@ __global__ void k_label(PoolView pv, const int32_t* key, const float* mpre, int6
 }
 
 __global__ void k_sample_keys(PoolView pv, int32_t* key, int64_t base) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];

@@ -206,9 +206,12 @@ __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInf
       c1[a] = cell[a] >> 1;
       c2[a] = cell[a] >> 2;
     }
-    int s = tab_get<D>(pv, td, b.lvl + 1, cell), m = b.lvl + 1;
-    if (s < 0) { s = tab_get<D>(pv, td, b.lvl, c1); m = b.lvl; }
-    if (s < 0) { s = tab_get<D>(pv, td, b.lvl - 1, c2); m = b.lvl - 1; }
+    // the three candidate levels are looked up together (one memory round trip)
+    const int sf = tab_get<D>(pv, td, b.lvl + 1, cell), se = tab_get<D>(pv, td, b.lvl, c1),
+              sc = tab_get<D>(pv, td, b.lvl - 1, c2);
+    int s = sf, m = b.lvl + 1;
+    if (s < 0) { s = se; m = b.lvl; }
+    if (s < 0) { s = sc; m = b.lvl - 1; }
     if (s < 0) {
       set_err(pv, kErrGraded);
       m = -1;

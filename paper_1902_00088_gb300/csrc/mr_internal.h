@@ -23,13 +23,18 @@ constexpr int kErrTimeout = 16;
 struct TreeDev {
   int32_t Jmin, Jmax;
   double eps;
+  float epsf[2];                    // eps rounded down and up to FP32 (certified FP32 decisions)
   int64_t N;                        // finest-lattice intervals per axis: (Bs-1) << Jmax
   int64_t tab_off[kMaxLevel + 1];   // offset of level l's dense slot table
   int64_t lat_off;                  // offset of this tree's lattice tables (N entries each)
   int64_t cell_off;                 // offset of this tree's finest-cell array (2^(d Jmax))
   double cD[kMaxLevel + 1];         // 1 / (12 dx_l)
+  float cDf[kMaxLevel + 1];         // cD rounded to FP32 (once, on creation)
   double dx[kMaxLevel + 1];         // dx_l = L / (2^l (Bs-1))
   double rhs[8];
+  float rhsf[8];                    // rhs rounded to FP32
+  double nsd[3];                    // Navier-Stokes: gamma - 1, mu, kappa = mu gamma / ((gamma - 1) Pr)
+  float nsf[3];                     // the same rounded to FP32
   double x0[3];
   int32_t ic_kind;
   double ic_e0, ic_amp;             // mixing layer: p0/(gamma-1) and perturbation amplitude
@@ -64,6 +69,7 @@ constexpr int kMaxHist = 1 << 16;  // step history: blocks of the adapted grid b
 struct TreeTime {
   double t, dt;
   double ca[4], cy[4], ct[4];
+  float caf[4], cyf[4], ctf[4];  // the same rounded to FP32
 };
 
 // Lattice tables: per tree, kNumLat tables of N doubles, indexed by the node
@@ -80,6 +86,7 @@ struct StageArgs {
   double ca[kMaxTrees];   // accumulator coefficient: dt/6, dt/3, dt/3, dt/6
   double cy[kMaxTrees];   // next-stage coefficient: dt/2, dt/2, dt, (unused)
   double ct[kMaxTrees];   // swirl time factor cos(pi t_s / t_a)
+  float caf[kMaxTrees], cyf[kMaxTrees], ctf[kMaxTrees];  // the same rounded to FP32
 };
 
 // Everything a kernel needs to know about the pool and the tree tables.
@@ -102,6 +109,7 @@ struct PoolView {
   int32_t* freelist;
   int32_t* tab;            // dense per-tree per-level leaf tables (-1 = no leaf)
   const double* lat;       // lattice tables
+  const float* latf;       // the same rounded to FP32 (FP32 stage velocities)
   double* svar;            // per tree x nvar threshold scale
   int32_t* cells;          // finest-cell marks (set_blocks validation / ranking)
   int32_t* emit;           // scan input  [cap] x2 (int2)
@@ -130,7 +138,38 @@ struct LaunchCfg {
   int grid_mult;  // persistent CTAs per SM for the stage kernel (0 = occupancy)
   int stage_form;  // 2D stage: 0 one CTA per block, 1 one warp per block, -1 by block count
   int n_hint;      // block count last read by the host (chooses the form when -1)
+  int pdl;         // step kernels use programmatic dependent launch (launch_k)
 };
+
+#ifdef __CUDACC__
+// First statement of every kernel of the library: wait until the kernels this
+// launch depends on have completed and their writes are visible (a no-op for a
+// launch without programmatic dependency), then let the next kernel of the
+// stream be scheduled, so that its launch overlaps this kernel's execution.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+
+// Kernel launch; with pdl the launch may begin before the previous kernel of
+// the stream has finished (the kernel waits for it in pdl_enter).  Errors are
+// reported through cudaGetLastError like those of a <<< >>> launch.
+template <typename... KArgs, typename... Args>
+inline void launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // Per-dimension launchers (explicitly instantiated in mr_k2.cu / mr_k3.cu).
 template <int D> void launch_plan(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st);
@@ -166,7 +205,7 @@ template <int D> void launch_error(const PoolView& pv, const Fields& f, int tree
 // `partial` needs 2 * ceil(n_max / kScanChunk) + 2 ints.
 constexpr int kScanChunk = 2048;
 void launch_scan2(const int32_t* in, int32_t* out, int32_t* partial, const int32_t* n_dev,
-                  int64_t n_host, int32_t* tot, cudaStream_t st, int64_t n_expect = -1);
+                  int64_t n_host, int32_t* tot, cudaStream_t st, int64_t n_expect = -1, bool pdl = false);
 void count_launch(int n = 1);
 int64_t kernel_launches();
 

@@ -7,6 +7,31 @@
 
 namespace mr {
 
+// Per-tree stage constants in the arithmetic type T.  The FP32 copies hold the
+// FP64 values rounded once (on creation, or when the step's time is set), so
+// an FP32 kernel reads them without an FP64 conversion per block.
+template <typename T> struct StageCoef {
+  T ca, cy, ct;
+  __device__ __forceinline__ StageCoef(const PoolView& pv, const StageArgs& sa, int t, int s) {
+    if constexpr (sizeof(T) == 4) {
+      if (pv.tt) { ca = pv.tt[t].caf[s]; cy = pv.tt[t].cyf[s]; ct = pv.tt[t].ctf[s]; }
+      else { ca = sa.caf[t]; cy = sa.cyf[t]; ct = sa.ctf[t]; }
+    } else {
+      if (pv.tt) { ca = pv.tt[t].ca[s]; cy = pv.tt[t].cy[s]; ct = pv.tt[t].ct[s]; }
+      else { ca = sa.ca[t]; cy = sa.cy[t]; ct = sa.ct[t]; }
+    }
+  }
+};
+template <typename T> __device__ __forceinline__ T tree_cD(const TreeDev& td, int l) {
+  if constexpr (sizeof(T) == 4) return td.cDf[l]; else return td.cD[l];
+}
+template <typename T> __device__ __forceinline__ T tree_rhs(const TreeDev& td, int a) {
+  if constexpr (sizeof(T) == 4) return td.rhsf[a]; else return td.rhs[a];
+}
+template <typename T> __device__ __forceinline__ const T* lattice(const PoolView& pv) {
+  if constexpr (sizeof(T) == 4) return pv.latf; else return pv.lat;
+}
+
 
 // ------------------------------------------------------------------ stage ----
 // One RK4 stage on every block (Sec. 3: 4th-order central FD + classic RK4):
@@ -22,6 +47,7 @@ namespace mr {
 template <int D, int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
                             TS* __restrict__ acc, TY* __restrict__ ynext, int stage, StageArgs sa) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 2>;  // the stencils reach two nodes
   using PL = Plan<D>;
@@ -63,13 +89,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
       fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
     }
     __syncthreads();
-    const TC c = (TC)td.cD[b.lvl];
-    const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
-    const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
-    const double ct = pv.tt ? pv.tt[b.tree].ct[stage] : sa.ct[b.tree];
+    const TC c = tree_cD<TC>(td, b.lvl);
+    const StageCoef<TS> cs(pv, sa, b.tree, stage);  // RK weights in the state type
+    const TC ct = StageCoef<TC>(pv, sa, b.tree, stage).ct;
     const int64_t base = (int64_t)b.slot * pv.vs;  // nvar == 1
     const int sh = td.Jmax - b.lvl;
-    const TS cas = (TS)ca, cys = (TS)cy;  // RK weights in the state type
+    const TS cas = cs.ca, cys = cs.cy;
     if constexpr (D == 2) {
       // thread = (column i, rows j0, j0 + G, ...): the column's velocity
       // factors are loaded once; the rows' loads are issued together
@@ -77,17 +102,17 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
       const int t = threadIdx.x;
       if (t < G * B) {
         const int i = t % B, j0 = t / B;
-        double ax = 0.0, bx = 0.0;
-        const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
-        const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
+        TC ax = 0, bx = 0;  // swirl factors in the stencil type
+        const TC* A = lattice<TC>(pv) + td.lat_off + (int64_t)kLatSwA * td.N;
+        const TC* Bt = lattice<TC>(pv) + td.lat_off + (int64_t)kLatSwB * td.N;
         if (RHS == MR_RHS_SWIRL) {
           const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
           ax = A[Ux];
           bx = Bt[Ux];
         }
         TS yv[RU], av[RU];
-        TC u0[RU], u1[RU];  // velocity rounded to the stencil type (constant: once per block)
-        const TC uc0 = (TC)td.rhs[0], uc1 = (TC)td.rhs[1];
+        TC u0[RU], u1[RU];  // velocity in the stencil type (constant: once per block)
+        const TC uc0 = tree_rhs<TC>(td, 0), uc1 = tree_rhs<TC>(td, 1);
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
           const int j = j0 + r * G;
@@ -100,8 +125,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
           if (stage >= 1) av[r] = acc[base + q];
           if (RHS == MR_RHS_SWIRL) {
             const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
-            u0[r] = (TC)(ct * (ax * Bt[Uy]));
-            u1[r] = (TC)(-(ct * (A[Uy] * bx)));
+            u0[r] = ct * (ax * Bt[Uy]);
+            u1[r] = -(ct * (A[Uy] * bx));
           }
         }
 #pragma unroll
@@ -129,7 +154,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
     // 3D: UC points per thread at a time: their state, accumulator and
     // velocity loads are issued together, then the stencils and the updates
     constexpr int UC = D == 3 ? 4 : 1;
-    const TC uc2 = (TC)td.rhs[2];
+    const TC uc2 = tree_rhs<TC>(td, 2);
     for (int q0 = threadIdx.x; D == 3 && q0 < Gm::NI; q0 += UC * NT) {
       TS yv[UC], av[UC];
       TC u0[UC], u1[UC];
@@ -137,8 +162,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
       for (int u = 0; u < UC; ++u) {
         const int q = q0 + u * NT;
         yv[u] = av[u] = TS(0);
-        u0[u] = (TC)td.rhs[0];
-        u1[u] = (TC)td.rhs[1];
+        u0[u] = tree_rhs<TC>(td, 0);
+        u1[u] = tree_rhs<TC>(td, 1);
         if (q >= Gm::NI) continue;
         if (stage <= 2) yv[u] = y[base + q];  // stage 0: committed (synchronised) y_n
         if (stage >= 1) av[u] = acc[base + q];
@@ -146,10 +171,10 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
           const int i = q % B, j = (q / B) % B;
           const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
           const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
-          const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
-          const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
-          u0[u] = (TC)(ct * (A[Ux] * Bt[Uy]));
-          u1[u] = (TC)(-(ct * (A[Uy] * Bt[Ux])));
+          const TC* A = lattice<TC>(pv) + td.lat_off + (int64_t)kLatSwA * td.N;
+          const TC* Bt = lattice<TC>(pv) + td.lat_off + (int64_t)kLatSwB * td.N;
+          u0[u] = ct * (A[Ux] * Bt[Uy]);
+          u1[u] = -(ct * (A[Uy] * Bt[Ux]));
         }
       }
 #pragma unroll
@@ -204,6 +229,7 @@ template <int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
                                                    TS* __restrict__ acc, TY* __restrict__ ynext, int stage,
                                                    StageArgs sa) {
+  pdl_enter();
   using Gm = Geo<2, B>;
   using Bx = Box<2, B, 2>;
   using PL = Plan<2>;
@@ -247,14 +273,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
       fill_tile<2, B, TSRC, TC, 2, WarpGroup>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
     }
     __syncwarp();
-    const TC c = (TC)td.cD[b.lvl];
-    const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
-    const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
-    const double ct = pv.tt ? pv.tt[b.tree].ct[stage] : sa.ct[b.tree];
-    const TS cas = (TS)ca, cys = (TS)cy;
+    const TC c = tree_cD<TC>(td, b.lvl);
+    const StageCoef<TS> cs(pv, sa, b.tree, stage);
+    const TC ct = StageCoef<TC>(pv, sa, b.tree, stage).ct;
+    const TS cas = cs.ca, cys = cs.cy;
     const int64_t base = (int64_t)b.slot * pv.vs;
     const int sh = td.Jmax - b.lvl;
-    const TC uc0 = (TC)td.rhs[0], uc1 = (TC)td.rhs[1];
+    const TC uc0 = tree_rhs<TC>(td, 0), uc1 = tree_rhs<TC>(td, 1);
     constexpr int UC = 4;
     for (int q0 = lane; q0 < Gm::NI; q0 += UC * 32) {
       TS yv[UC], av[UC];
@@ -272,10 +297,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
           const int i = q % B, j = q / B;
           const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
           const int64_t Uy = pmod64((b.c[1] * (B - 1) + j) << sh, td.N);
-          const double* A = pv.lat + td.lat_off + (int64_t)kLatSwA * td.N;
-          const double* Bt = pv.lat + td.lat_off + (int64_t)kLatSwB * td.N;
-          u0[u] = (TC)(ct * (A[Ux] * Bt[Uy]));
-          u1[u] = (TC)(-(ct * (A[Uy] * Bt[Ux])));
+          const TC* A = lattice<TC>(pv) + td.lat_off + (int64_t)kLatSwA * td.N;
+          const TC* Bt = lattice<TC>(pv) + td.lat_off + (int64_t)kLatSwB * td.N;
+          u0[u] = ct * (A[Ux] * Bt[Uy]);
+          u1[u] = -(ct * (A[Uy] * Bt[Ux]));
         }
       }
 #pragma unroll
@@ -337,6 +362,7 @@ __device__ __forceinline__ void plan_one(const PoolView& pv, int p) {
 // while the tree generation is unchanged.
 template <int D>
 __global__ void k_plan(PoolView pv) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) plan_one<D>(pv, p);
   if (blockIdx.x == 0 && threadIdx.x == 0) pv.cnt->plan_topo = pv.cnt->topo;
@@ -346,6 +372,7 @@ __global__ void k_plan(PoolView pv) {
 // merged nothing), its id, and the per-tree threshold scales reset to v.
 template <int D>
 __global__ void k_round_begin(PoolView pv, double v) {
+  pdl_enter();
   Counters* c = pv.cnt;
   if (threadIdx.x == 0) {
     c->n_round = c->done ? 0 : c->n_act;
@@ -376,6 +403,7 @@ template <int B, typename TS, typename TY, typename TSRC>
 __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __restrict__ src,
                                                   TS* __restrict__ y, TS* __restrict__ acc,
                                                   TY* __restrict__ ynext, int stage, StageArgs sa) {
+  pdl_enter();
   using Gm = Geo<2, B>;
   using NG = NsGeo<B>;
   using TC = TY;
@@ -417,12 +445,12 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
       fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, pu);
     }
     __syncthreads();
-    const double gam = td.rhs[0], mud = td.rhs[1], Pr = td.rhs[2];
-    const TC gm1 = (TC)(gam - 1.0);
-    const TC mu = (TC)mud;
-    const TC kap = (TC)(mud * gam / ((gam - 1.0) * Pr));
+    // gamma - 1, mu and kappa = mu gamma / ((gamma - 1) Pr), formed once per tree
+    TC gm1, mu, kap;
+    if constexpr (sizeof(TC) == 4) { gm1 = td.nsf[0]; mu = td.nsf[1]; kap = td.nsf[2]; }
+    else { gm1 = td.nsd[0]; mu = td.nsd[1]; kap = td.nsd[2]; }
     const TC c23 = (TC)(2.0 / 3.0);
-    const TC c = (TC)td.cD[b.lvl];
+    const TC c = tree_cD<TC>(td, b.lvl);
     const TC* r_ = tile;
     const TC* m1_ = tile + Gm::TILE;
     const TC* m2_ = tile + 2 * Gm::TILE;
@@ -474,11 +502,11 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
       }
     }
     __syncthreads();
-    const double ca = pv.tt ? pv.tt[b.tree].ca[stage] : sa.ca[b.tree];
-    const double cy = pv.tt ? pv.tt[b.tree].cy[stage] : sa.cy[b.tree];
+    const StageCoef<TS> cs(pv, sa, b.tree, stage);
+    const StageCoef<TC> cf(pv, sa, b.tree, stage);
     const int64_t base = (int64_t)b.slot * 4 * pv.vs;
-    const TS cas = (TS)ca, cys = (TS)cy;  // RK weights in the state type
-    const TC casf = (TC)ca, cysf = (TC)cy;  // and in the stage type
+    const TS cas = cs.ca, cys = cs.cy;  // RK weights in the state type
+    const TC casf = cf.ca, cysf = cf.cy;  // and in the stage type
     // UC points per thread at a time: state and accumulator loads first
     constexpr int UC = 4, NT = 256;
     for (int i0 = threadIdx.x; i0 < 4 * Gm::NI; i0 += UC * NT) {
@@ -551,6 +579,7 @@ struct RefGeo {
 // appended); children are placed in the new active list in Hilbert order.
 template <int D, int B, typename TS, int NT>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine(PoolView pv, TS* __restrict__ y) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 1>;  // prediction of the children reaches one node
   using RG = RefGeo<D, B>;
@@ -648,6 +677,14 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine
 // over all coarse rows is stored in shared memory (X), the y and z passes run
 // per point; every output sees the same operations as the point-wise tensor
 // product.
+// The FP32 maximum m32 is within E of the FP64 one, and m32 + E < eps or
+// m32 - E >= eps holds in exact arithmetic: the sum is rounded up and compared
+// with eps rounded down, the difference rounded down and compared with eps
+// rounded up, so the threshold decision needs no FP64 evaluation.
+__device__ __forceinline__ bool certain_vs_eps(float m32, float E, const TreeDev& td) {
+  return __fadd_ru(m32, E) < td.epsf[0] || __fsub_rd(m32, E) >= td.epsf[1];
+}
+
 template <int D, int B>
 struct DetGeo {
   static constexpr int NC = (B + 1) / 2 + 2;  // coarse rows -1 .. (B+1)/2
@@ -670,6 +707,7 @@ __device__ __forceinline__ T block_max(T v, T* red) {
 
 template <int D, int B, typename TS, typename TD, int NT, typename TT = TS>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_details(PoolView pv, TS* __restrict__ y) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 2>;  // prediction from even nodes reaches two nodes
   using DG = DetGeo<D, B>;
@@ -785,7 +823,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     __syncthreads();
     // Block maximum of |d| over the interior with arithmetic type A: x pass on
     // coarse rows (yc, zc) in [-1, NC-2] into X, then y (and z) per odd node.
-    auto pass = [&](auto tag, const TT* tv) -> double {
+    auto pass = [&](auto tag, const TT* tv) -> decltype(tag) {
       using A = decltype(tag);
       A* XA = reinterpret_cast<A*>(X);
       for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
@@ -833,7 +871,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         const A d = val - pr;
         md = fmax(md, (A)fabs(d));
       }
-      return (double)block_max<A>(md, reinterpret_cast<A*>(red[0]));
+      return block_max<A>(md, reinterpret_cast<A*>(red[0]));
     };
     for (int v = 0; v < nv; ++v) {
       const TT* tv = tile + v * Bx::TILE;
@@ -842,25 +880,28 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
         mqs = fmax(mqs, (TT)fabs(tv[Bx::tix(i, j, k)]));
       }
-      const double mq = (double)block_max<TT>(mqs, reinterpret_cast<TT*>(red[1]));
-      double md;
+      const TT mqt = block_max<TT>(mqs, reinterpret_cast<TT*>(red[1]));
+      double md = 0.0;  // thread 0's value is stored
       if constexpr (sizeof(TT) == 4 && sizeof(TD) == 8) {
         // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
         // one by at most ~20 u max|tile| (u = 2^-24, x/y/z passes of the
         // 4-point rule and the subtraction); where its maximum is farther than
         // 32 u max|tile| from eps the threshold decision (Sec. 2.3) is the
         // FP64 one, otherwise the block is evaluated again in FP64.
-        const double m32 = pass(float(0), tv);
+        const float m32 = pass(float(0), tv);
         float mt = 0.f;
         for (int q = threadIdx.x; q < Bx::TILE; q += blockDim.x) mt = fmaxf(mt, fabsf((float)tv[q]));
-        const double E = 32.0 * 0x1p-24 * (double)block_max<float>(mt, reinterpret_cast<float*>(red[1])) + 1e-37;
-        const double eps = td.eps;
-        const bool sure = pv.norm_kind == 0 && (m32 + E < eps || m32 - E >= eps);
-        md = sure ? m32 : pass(double(0), tv);
+        const float E = 0x1p-19f * block_max<float>(mt, reinterpret_cast<float*>(red[1])) + 1e-37f;
+        if (pv.norm_kind == 0 && certain_vs_eps(m32, E, td)) {
+          if (threadIdx.x == 0) md = (double)m32;
+        } else {
+          md = pass(double(0), tv);
+        }
       } else {
-        md = pass(TD(0), tv);
+        md = (double)pass(TD(0), tv);
       }
       if (threadIdx.x == 0) {
+        const double mq = (double)mqt;
         pv.md[(int64_t)b.slot * nv + v] = md;
         pv.bmax[(int64_t)b.slot * nv + v] = mq;
         if (pv.norm_kind == 1) csv[v] = fmax(csv[v], mq);
@@ -906,6 +947,7 @@ __device__ __forceinline__ T warp_max(T v) {
 
 template <int B, typename TS, typename TD, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __restrict__ y) {
+  pdl_enter();
   using Gm = Geo<2, B>;
   using Bx = Box<2, B, 2>;
   using DG = DetGeo<2, B>;
@@ -981,7 +1023,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
         fill_tile<2, B, TS, TS, 2, WarpGroup>(pv, b, y, y, tile, true, R, cbox, scr);
       }
       __syncwarp();
-      auto pass = [&](auto tag) -> double {
+      auto pass = [&](auto tag) -> decltype(tag) {
         using A = decltype(tag);
         A* XA = reinterpret_cast<A*>(scr);
         for (int idx = lane; idx < DG::NX; idx += 32) {
@@ -1013,7 +1055,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
         }
         md = warp_max(md);
         __syncwarp();
-        return (double)md;
+        return md;
       };
       TS mqs = TS(0);
       bool bad = false;
@@ -1022,23 +1064,26 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
         mqs = fmax(mqs, (TS)fabs(sv));
         bad |= !isfinite(sv);
       }
-      const double mq = (double)warp_max(mqs);
-      double md;
+      mqs = warp_max(mqs);
+      double md = 0.0;  // lane 0's value is stored
       if constexpr (sizeof(TS) == 4 && sizeof(TD) == 8) {
         // as in k_details: FP32 evaluation, FP64 only within the rounding bound of eps
-        const double m32 = pass(float(0));
+        const float m32 = pass(float(0));
         float mt = 0.f;
         for (int qn = lane; qn < Bx::TILE; qn += 32) mt = fmaxf(mt, fabsf((float)tile[qn]));
-        const double E = 32.0 * 0x1p-24 * (double)warp_max(mt) + 1e-37;
-        const bool sure = m32 + E < td.eps || m32 - E >= td.eps;
-        md = sure ? m32 : pass(double(0));
+        const float E = 0x1p-19f * warp_max(mt) + 1e-37f;
+        if (certain_vs_eps(m32, E, td)) {
+          if (lane == 0) md = (double)m32;
+        } else {
+          md = pass(double(0));
+        }
       } else {
-        md = pass(TD(0));
+        md = (double)pass(TD(0));
       }
       if (__any_sync(0xffffffffu, bad)) md = __longlong_as_double(0x7ff8000000000000LL);
       if (lane == 0) {
         pv.md[b.slot] = md;
-        pv.bmax[b.slot] = mq;
+        pv.bmax[b.slot] = (double)mqs;
       }
       __syncwarp();
     }
@@ -1054,6 +1099,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
 // the family member that comes first in Hilbert order.
 template <int D, int B, typename TS>
 __global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   TS* buf = smem_as<TS>(0);
   __shared__ int cs[8];
@@ -1106,6 +1152,7 @@ __global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y
 // v = amp (s(x) e(y)), E = p0/(gamma-1) + (u u + v v)/2.
 template <int D, int B, typename TS>
 __global__ void k_ic(PoolView pv, TS* __restrict__ y) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   const int nact = pv.cnt->n_act;
   const int nv = pv.nvar;
@@ -1142,6 +1189,7 @@ __global__ void k_ic(PoolView pv, TS* __restrict__ y) {
 // at the block's list position.
 template <int D, int B, typename TS>
 __global__ void __launch_bounds__(256) k_sync(PoolView pv, TS* __restrict__ y, double* __restrict__ tiles) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   Ring& R = *smem_as<Ring>(0);
   double* tile = smem_as<double>(kRingBytes);
@@ -1165,6 +1213,7 @@ __global__ void __launch_bounds__(256) k_sync(PoolView pv, TS* __restrict__ y, d
 // ---------------------------------------------------------------- export -----
 template <int D, int B, typename TS>
 __global__ void k_export_fields(PoolView pv, const TS* __restrict__ y, double* __restrict__ out) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   const int nact = pv.cnt->n_act;
   const int nv = pv.nvar;
@@ -1180,6 +1229,7 @@ __global__ void k_export_fields(PoolView pv, const TS* __restrict__ y, double* _
 template <int D, int B, typename TS>
 __global__ void k_import_fields(PoolView pv, TS* __restrict__ y, const double* __restrict__ in,
                                 int64_t n) {
+  pdl_enter();
   using Gm = Geo<D, B>;
   const int nv = pv.nvar;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
@@ -1195,6 +1245,7 @@ __global__ void k_import_fields(PoolView pv, TS* __restrict__ y, const double* _
 template <int D, int B, typename TS>
 __global__ void k_error(PoolView pv, const TS* __restrict__ y, int tree, const double* ex,
                         double* out) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   const TreeDev& td = pv.trees[tree];
   constexpr int BZ = D == 3 ? B - 1 : 1;
@@ -1228,6 +1279,7 @@ __global__ void k_error(PoolView pv, const TS* __restrict__ y, int tree, const d
 // ------------------------------------------------------- tree maintenance ----
 template <int D>
 __global__ void k_refine_count(PoolView pv, int mode, const int8_t* mask) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   const int nch = 1 << D;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
@@ -1259,6 +1311,7 @@ __device__ __forceinline__ bool last_cta(Counters* c) {
 // are updated by the last CTA.
 template <int D>
 __global__ void k_refine_commit(PoolView pv) {
+  pdl_enter();
   Counters* c = pv.cnt;
   const int nact = c->n_act, n_new = c->n_new, n_alloc = c->n_alloc, n_free = c->n_free;
   const bool ok = n_alloc <= n_free;
@@ -1353,6 +1406,7 @@ __device__ __forceinline__ bool qualifies(const PoolView& pv, const TreeDev& td,
 
 template <int D>
 __global__ void k_flags(PoolView pv) {
+  pdl_enter();
   // A family (the 2^d sisters of a block) merges when every sister is a leaf
   // whose normalised detail is below eps, above Jmin, and no leaf one level
   // finer touches any sister: the cells of level l+1 around the family,
@@ -1382,16 +1436,31 @@ __global__ void k_flags(PoolView pv) {
         ok = false;
       } else {
         double m = 0.0;
-        bool nan = false;
-        for (int v = 0; v < nv; ++v) {
-          double sv = pv.svar[b.tree * nv + v];
-          if (sv == 0.0) sv = 1.0;
-          const double mv = pv.md[(int64_t)t * nv + v];
-          nan |= isnan(mv);
-          m = fmax(m, mv / sv);
+        if (pv.norm_kind == 0) {
+          // unnormalised: a maximum of non-negative values (or NaN), taken and
+          // compared with eps > 0 on their bit patterns, which order as the values
+          long long mb = 0;
+          bool nan = false;
+          for (int v = 0; v < nv; ++v) {
+            const long long x = __double_as_longlong(pv.md[(int64_t)t * nv + v]);
+            nan |= (x & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+            mb = x > mb ? x : mb;
+          }
+          if (nan) mb = 0x7ff8000000000000LL;
+          m = __longlong_as_double(mb);
+          ok = !nan && mb < __double_as_longlong(td.eps);
+        } else {
+          bool nan = false;
+          for (int v = 0; v < nv; ++v) {
+            double sv = pv.svar[b.tree * nv + v];
+            if (sv == 0.0) sv = 1.0;
+            const double mv = pv.md[(int64_t)t * nv + v];
+            nan |= isnan(mv);
+            m = fmax(m, mv / sv);
+          }
+          if (nan) m = __longlong_as_double(0x7ff8000000000000LL);
+          ok = m < td.eps;
         }
-        if (nan) m = __longlong_as_double(0x7ff8000000000000LL);
-        ok = m < td.eps;
         if (t == s) mine = m;
       }
     }
@@ -1426,6 +1495,7 @@ __global__ void k_flags(PoolView pv) {
 // counted; done once a round merged nothing).
 template <int D>
 __global__ void k_coarsen_commit(PoolView pv) {
+  pdl_enter();
   Counters* c = pv.cnt;
   const int nround = c->n_round, n_free = c->n_free, n_new = c->n_new, rid = c->round_id;
   const bool done = c->done != 0;
@@ -1472,6 +1542,7 @@ __global__ void k_coarsen_commit(PoolView pv) {
 // Neighbour table (Sec. 2.2): rel[r] = (sx, sy, sz, sub), see mr.h for the order.
 template <int D>
 __global__ void k_neighbors(PoolView pv, const int4* rel, int R, int32_t* nbr, int8_t* dl) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < (int64_t)nact * R;
        w += (int64_t)gridDim.x * blockDim.x) {
@@ -1524,6 +1595,7 @@ __global__ void k_neighbors(PoolView pv, const int4* rel, int R, int32_t* nbr, i
 
 template <int D>
 __global__ void k_export_info(PoolView pv, mr_block_info* info, int8_t* flags, double* mdet) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];
@@ -1547,6 +1619,7 @@ __global__ void k_export_info(PoolView pv, mr_block_info* info, int8_t* flags, d
 template <int D>
 __global__ void k_sb_place(PoolView pv, int64_t n, const int32_t* lvl, const int32_t* tree,
                            const int32_t* crd, int ntrees) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int t = tree ? tree[i] : 0;
@@ -1577,6 +1650,7 @@ __global__ void k_sb_place(PoolView pv, int64_t n, const int32_t* lvl, const int
 // Every finest cell of every block gets +1 (coverage check: all must be 1).
 template <int D>
 __global__ void k_sb_cover(PoolView pv, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const int l = pv.lvl[i];
     if (l < 0) continue;
@@ -1597,6 +1671,7 @@ __global__ void k_sb_cover(PoolView pv, int64_t n) {
 
 template <int D>
 __global__ void k_sb_mark(PoolView pv, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (pv.lvl[i] < 0) continue;
@@ -1607,6 +1682,7 @@ __global__ void k_sb_mark(PoolView pv, int64_t n) {
 
 template <int D>
 __global__ void k_sb_order(PoolView pv, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (pv.lvl[i] < 0) continue;
@@ -1618,6 +1694,7 @@ __global__ void k_sb_order(PoolView pv, int64_t n) {
 // Graded-tree check: every ring cell must be covered by a leaf at l-1..l+1.
 template <int D>
 __global__ void k_check_graded(PoolView pv) {
+  pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const BlockInfo b = load_block(pv, pv.act[p]);

@@ -50,14 +50,14 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
       auto k = k_stage_adv_w<B, RHS, TS, TY, TS, threads>;
       prep_smem(k, SW::SMEM);
       const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
-      k<<<grid, threads, SW::SMEM, st>>>(pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+      launch_k(lc.pdl, k, grid, threads, SW::SMEM, st, pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
     } else {
       using SW = StageW<B, RHS, TS, TY, TY, threads>;
       const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
       auto k = k_stage_adv_w<B, RHS, TS, TY, TY, threads>;
       prep_smem(k, SW::SMEM);
       const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
-      k<<<grid, threads, SW::SMEM, st>>>(pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+      launch_k(lc.pdl, k, grid, threads, SW::SMEM, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
     }
     count_launch();
     return;
@@ -66,13 +66,13 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
     auto k = k_stage_adv<D, B, RHS, TS, TY, TS, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
-    k<<<grid, threads, smem, st>>>(pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    launch_k(lc.pdl, k, grid, threads, smem, st, pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
   } else {
     const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
     auto k = k_stage_adv<D, B, RHS, TS, TY, TY, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
-    k<<<grid, threads, smem, st>>>(pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    launch_k(lc.pdl, k, grid, threads, smem, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
   }
   count_launch();
 }
@@ -98,14 +98,12 @@ static void stage_ns_impl(const PoolView& pv, const Fields& f, int stage, const 
   if (stage == 0) {
     auto k = k_stage_ns<B, TS, TY, TS>;
     prep_smem(k, smem);
-    k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(
-        pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
   } else {
     const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
     auto k = k_stage_ns<B, TS, TY, TY>;
     prep_smem(k, smem);
-    k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(
-        pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
   }
   count_launch();
 }
@@ -122,7 +120,7 @@ static void stage_ns(const PoolView& pv, const Fields& f, int stage, const Stage
 
 template <int D>
 void launch_plan(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st) {
-  k_plan<D><<<lc.num_sms * 4, 128, 0, st>>>(pv);
+  launch_k(lc.pdl, k_plan<D>, lc.num_sms * 4, 128, 0, st, pv);
   count_launch();
 }
 
@@ -176,7 +174,7 @@ struct RefineRun {
     auto k = k_refine<D, B, TS, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
-    k<<<grid, threads, smem, st>>>(pv, (TS*)f.y);
+    launch_k(lc.pdl, k, grid, threads, smem, st, pv, (TS*)f.y);
     count_launch();
   }
 };
@@ -186,11 +184,12 @@ template <int D>
 void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* mask,
                    const LaunchCfg& lc, cudaStream_t st) {
   const int nch = 1 << D;
-  k_refine_count<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv, mode, mask);
+  launch_k(lc.pdl, k_refine_count<D>, flat_grid(pv, 256), 256, 0, st, pv, mode, mask);
   count_launch();
-  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st, 2 * (int64_t)lc.n_hint);
+  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st, 2 * (int64_t)lc.n_hint,
+               lc.pdl != 0);
   dispatch_bs<D, RefineRun>(pv, f, lc, st);
-  k_refine_commit<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  launch_k(lc.pdl, k_refine_commit<D>, flat_grid(pv, 256), 256, 0, st, pv);
   count_launch(1);
   (void)nch;
 }
@@ -199,7 +198,7 @@ void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* 
 template <int D, int B, typename TS>
 struct IcRun {
   static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
-    k_ic<D, B, TS><<<lc.num_sms * 8, 256, 0, st>>>(pv, (TS*)f.y);
+    launch_k(lc.pdl, k_ic<D, B, TS>, lc.num_sms * 8, 256, 0, st, pv, (TS*)f.y);
     count_launch();
   }
 };
@@ -224,12 +223,12 @@ struct DetailsRun {
         auto k = k_details_w<B, TS, double, threads>;
         using DW = DetW<B, TS, double, threads>;
         prep_smem(k, DW::SMEM);
-        k<<<persistent_grid(k, threads, DW::SMEM, lc, lc.grid_mult), threads, DW::SMEM, st>>>(pv, (TS*)f.y);
+        launch_k(lc.pdl, k, persistent_grid(k, threads, DW::SMEM, lc, lc.grid_mult), threads, DW::SMEM, st, pv, (TS*)f.y);
       } else {
         auto k = k_details_w<B, TS, TS, threads>;
         using DW = DetW<B, TS, TS, threads>;
         prep_smem(k, DW::SMEM);
-        k<<<persistent_grid(k, threads, DW::SMEM, lc, lc.grid_mult), threads, DW::SMEM, st>>>(pv, (TS*)f.y);
+        launch_k(lc.pdl, k, persistent_grid(k, threads, DW::SMEM, lc, lc.grid_mult), threads, DW::SMEM, st, pv, (TS*)f.y);
       }
       count_launch();
       return;
@@ -242,11 +241,11 @@ struct DetailsRun {
     if (d64) {
       auto k = k_details<D, B, TS, double, threads>;
       prep_smem(k, smem);
-      k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
+      launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, (TS*)f.y);
     } else {
       auto k = k_details<D, B, TS, float, threads, float>;
       prep_smem(k, smem);
-      k<<<persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st>>>(pv, (TS*)f.y);
+      launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, (TS*)f.y);
     }
     count_launch();
   }
@@ -258,7 +257,7 @@ struct CoarsenRun {
     const size_t smem = sizeof(TS) * pv.nvar * Geo<D, B>::NI;
     auto k = k_coarsen<D, B, TS>;
     prep_smem(k, smem);
-    k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y);
+    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, 0), threads, smem, st, pv, (TS*)f.y);
     count_launch();
   }
 };
@@ -266,7 +265,7 @@ struct CoarsenRun {
 template <int D>
 void launch_round_details(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
                           cudaStream_t st) {
-  k_round_begin<D><<<1, 256, 0, st>>>(pv, pv.norm_kind == 1 ? 0.0 : 1.0);
+  launch_k(lc.pdl, k_round_begin<D>, 1, 256, 0, st, pv, pv.norm_kind == 1 ? 0.0 : 1.0);
   count_launch();
   dispatch_bs<D, DetailsRun>(pv, f, fp64, lc, st);
 }
@@ -275,12 +274,13 @@ template <int D>
 void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const LaunchCfg& lc,
                         cudaStream_t st) {
   const int nch = 1 << D;
-  k_flags<D><<<(int)std::min<int64_t>(4096, (pv.cap + 7) / 8), 256, 0, st>>>(pv);
+  launch_k(lc.pdl, k_flags<D>, (int)std::min<int64_t>(4096, (pv.cap + 7) / 8), 256, 0, st, pv);
   count_launch();
   if (!merge) return;
-  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st, 4 * (int64_t)lc.n_hint);
+  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st, 4 * (int64_t)lc.n_hint,
+               lc.pdl != 0);
   dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
-  k_coarsen_commit<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv);
+  launch_k(lc.pdl, k_coarsen_commit<D>, flat_grid(pv, 256), 256, 0, st, pv);
   count_launch(1);
   (void)nch;
 }
@@ -301,7 +301,7 @@ struct SyncRun {
     const size_t smem = kRingBytes + sizeof(double) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
     auto k = k_sync<D, B, TS>;
     prep_smem(k, smem);
-    k<<<persistent_grid(k, threads, smem, lc, 0), threads, smem, st>>>(pv, (TS*)f.y, tiles);
+    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, 0), threads, smem, st, pv, (TS*)f.y, tiles);
     count_launch();
   }
 };
@@ -314,7 +314,7 @@ void launch_sync(const PoolView& pv, const Fields& f, double* tiles, const Launc
 template <int D>
 void launch_neighbors(const PoolView& pv, const int4* rel, int R, int32_t* nbr, int8_t* dl,
                       const LaunchCfg& lc, cudaStream_t st) {
-  k_neighbors<D><<<lc.num_sms * 8, 256, 0, st>>>(pv, rel, R, nbr, dl);
+  launch_k(lc.pdl, k_neighbors<D>, lc.num_sms * 8, 256, 0, st, pv, rel, R, nbr, dl);
   count_launch();
 }
 
@@ -323,14 +323,14 @@ template <int D, int B, typename TS>
 struct ExportRun {
   static void run(const PoolView& pv, const Fields& f, double* fields, const LaunchCfg& lc,
                   cudaStream_t st) {
-    k_export_fields<D, B, TS><<<lc.num_sms * 8, 256, 0, st>>>(pv, (const TS*)f.y, fields);
+    launch_k(lc.pdl, k_export_fields<D, B, TS>, lc.num_sms * 8, 256, 0, st, pv, (const TS*)f.y, fields);
     count_launch();
   }
 };
 template <int D>
 void launch_export(const PoolView& pv, const Fields& f, mr_block_info* info, double* fields,
                    int8_t* flags, double* mdet, const LaunchCfg& lc, cudaStream_t st) {
-  k_export_info<D><<<flat_grid(pv, 256), 256, 0, st>>>(pv, info, flags, mdet);
+  launch_k(lc.pdl, k_export_info<D>, flat_grid(pv, 256), 256, 0, st, pv, info, flags, mdet);
   count_launch();
   if (fields) dispatch_bs<D, ExportRun>(pv, f, fields, lc, st);
 }
@@ -340,7 +340,7 @@ template <int D, int B, typename TS>
 struct ImportRun {
   static void run(const PoolView& pv, const Fields& f, const double* fields, int64_t n,
                   const LaunchCfg& lc, cudaStream_t st) {
-    k_import_fields<D, B, TS><<<lc.num_sms * 8, 256, 0, st>>>(pv, (TS*)f.y, fields, n);
+    launch_k(lc.pdl, k_import_fields<D, B, TS>, lc.num_sms * 8, 256, 0, st, pv, (TS*)f.y, fields, n);
     count_launch();
   }
 };
@@ -359,31 +359,31 @@ void launch_set_blocks(const PoolView& pv, const Fields& f, int phase, int64_t n
                        const LaunchCfg& lc, cudaStream_t st) {
   const int g = 1024;
   if (phase == 0) {  // empty pool: no active block, every slot free
-    k_fill_i32<<<g, 256, 0, st>>>(pv.tab, ntab, -1);
-    k_fill_i8<<<g, 256, 0, st>>>(pv.lvl, pv.cap, (int8_t)-1);
-    k_sb_counters<<<g, 256, 0, st>>>(pv.cnt, pv.freelist, 0, pv.cap);
+    launch_k(lc.pdl, k_fill_i32, g, 256, 0, st, pv.tab, ntab, -1);
+    launch_k(lc.pdl, k_fill_i8, g, 256, 0, st, pv.lvl, pv.cap, (int8_t)-1);
+    launch_k(lc.pdl, k_sb_counters, g, 256, 0, st, pv.cnt, pv.freelist, 0, pv.cap);
     count_launch(3);
     return;
   }
   if (phase == 1) {
-    k_fill_i32<<<g, 256, 0, st>>>(pv.tab, ntab, -1);
-    k_fill_i32<<<g, 256, 0, st>>>(pv.cells, 2 * ncells, 0);
-    k_fill_i8<<<g, 256, 0, st>>>(pv.lvl, pv.cap, (int8_t)-1);
-    k_sb_place<D><<<g, 256, 0, st>>>(pv, n, lvl, tree, crd, ntrees);
-    k_sb_cover<D><<<lc.num_sms * 4, 256, 0, st>>>(pv, n);
-    k_sb_check<<<g, 256, 0, st>>>(pv.cells, ncells, pv.cnt);
+    launch_k(lc.pdl, k_fill_i32, g, 256, 0, st, pv.tab, ntab, -1);
+    launch_k(lc.pdl, k_fill_i32, g, 256, 0, st, pv.cells, 2 * ncells, 0);
+    launch_k(lc.pdl, k_fill_i8, g, 256, 0, st, pv.lvl, pv.cap, (int8_t)-1);
+    launch_k(lc.pdl, k_sb_place<D>, g, 256, 0, st, pv, n, lvl, tree, crd, ntrees);
+    launch_k(lc.pdl, k_sb_cover<D>, lc.num_sms * 4, 256, 0, st, pv, n);
+    launch_k(lc.pdl, k_sb_check, g, 256, 0, st, pv.cells, ncells, pv.cnt);
     count_launch(6);
     return;
   }
-  k_fill_i32<<<g, 256, 0, st>>>(pv.cells, 2 * ncells, 0);
-  k_sb_mark<D><<<g, 256, 0, st>>>(pv, n);
+  launch_k(lc.pdl, k_fill_i32, g, 256, 0, st, pv.cells, 2 * ncells, 0);
+  launch_k(lc.pdl, k_sb_mark<D>, g, 256, 0, st, pv, n);
   count_launch(2);
-  launch_scan2(pv.cells, pv.eoff, pv.partial, nullptr, ncells, &pv.cnt->n_new, st);
-  k_sb_order<D><<<g, 256, 0, st>>>(pv, n);
-  k_sb_counters<<<g, 256, 0, st>>>(pv.cnt, pv.freelist, n, pv.cap);
+  launch_scan2(pv.cells, pv.eoff, pv.partial, nullptr, ncells, &pv.cnt->n_new, st, -1, lc.pdl != 0);
+  launch_k(lc.pdl, k_sb_order<D>, g, 256, 0, st, pv, n);
+  launch_k(lc.pdl, k_sb_counters, g, 256, 0, st, pv.cnt, pv.freelist, n, pv.cap);
   count_launch(2);
   if (fields) dispatch_bs<D, ImportRun>(pv, f, fields, n, lc, st);
-  k_check_graded<D><<<g, 256, 0, st>>>(pv);
+  launch_k(lc.pdl, k_check_graded<D>, g, 256, 0, st, pv);
   count_launch();
 }
 
@@ -392,7 +392,7 @@ template <int D, int B, typename TS>
 struct ErrorRun {
   static void run(const PoolView& pv, const Fields& f, int tree, const double* ex, double* out,
                   const LaunchCfg& lc, cudaStream_t st) {
-    k_error<D, B, TS><<<lc.num_sms * 4, 256, 0, st>>>(pv, (const TS*)f.y, tree, ex, out);
+    launch_k(lc.pdl, k_error<D, B, TS>, lc.num_sms * 4, 256, 0, st, pv, (const TS*)f.y, tree, ex, out);
     count_launch();
   }
 };

@@ -40,6 +40,7 @@ __device__ __forceinline__ int2 block_incl_scan(int2 v, int2* warp_tot) {
 }
 
 __global__ void k_scan_reduce(const int32_t* in, const int32_t* n_dev, int64_t n_host, int32_t* partial) {
+  pdl_enter();
   __shared__ int2 wt[kScanThreads / 32];
   const int64_t n = scan_n(n_dev, n_host);
   const int64_t start = (int64_t)blockIdx.x * kScanChunk;
@@ -56,6 +57,7 @@ __global__ void k_scan_reduce(const int32_t* in, const int32_t* n_dev, int64_t n
 }
 
 __global__ void k_scan_partials(int32_t* partial, int nchunks, int32_t* tot) {
+  pdl_enter();
   __shared__ int2 wt[kScanThreads / 32];
   __shared__ int2 carry;
   if (threadIdx.x == 0) carry = make_int2(0, 0);
@@ -78,6 +80,7 @@ __global__ void k_scan_partials(int32_t* partial, int nchunks, int32_t* tot) {
 
 __global__ void k_scan_final(const int32_t* in, int32_t* out, const int32_t* n_dev, int64_t n_host,
                              const int32_t* partial) {
+  pdl_enter();
   __shared__ int2 wt[kScanThreads / 32];
   const int64_t n = scan_n(n_dev, n_host);
   const int64_t start = (int64_t)blockIdx.x * kScanChunk;
@@ -104,6 +107,7 @@ __global__ void k_scan_final(const int32_t* in, int32_t* out, const int32_t* n_d
 constexpr int kSingleThreads = 1024, kSinglePer = 4;
 __global__ void __launch_bounds__(kSingleThreads) k_scan_single(const int32_t* in, int32_t* out, const int32_t* n_dev,
                                                                 int64_t n_host, int32_t* tot) {
+  pdl_enter();
   __shared__ int2 wt[kSingleThreads / 32];
   const int64_t n = scan_n(n_dev, n_host);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -151,25 +155,26 @@ __global__ void __launch_bounds__(kSingleThreads) k_scan_single(const int32_t* i
 }
 
 void launch_scan2(const int32_t* in, int32_t* out, int32_t* partial, const int32_t* n_dev,
-                  int64_t n_host, int32_t* tot, cudaStream_t st, int64_t n_expect) {
+                  int64_t n_host, int32_t* tot, cudaStream_t st, int64_t n_expect, bool pdl) {
   // one CTA while the list is expected to be short (its passes are serial)
   const int64_t n_est = n_expect >= 0 ? n_expect : n_host;
   if (n_est <= 32768) {
-    k_scan_single<<<1, kSingleThreads, 0, st>>>(in, out, n_dev, n_host, tot);
+    launch_k(pdl, k_scan_single, 1, kSingleThreads, 0, st, in, out, n_dev, n_host, tot);
     count_launch(1);
     return;
   }
   const int nchunks = (int)((n_host + kScanChunk - 1) / kScanChunk);
   const int g = nchunks < 1 ? 1 : nchunks;
-  k_scan_reduce<<<g, kScanThreads, 0, st>>>(in, n_dev, n_host, partial);
-  k_scan_partials<<<1, kScanThreads, 0, st>>>(partial, g, tot);
-  k_scan_final<<<g, kScanThreads, 0, st>>>(in, out, n_dev, n_host, partial);
+  launch_k(pdl, k_scan_reduce, g, kScanThreads, 0, st, in, n_dev, n_host, partial);
+  launch_k(pdl, k_scan_partials, 1, kScanThreads, 0, st, partial, g, tot);
+  launch_k(pdl, k_scan_final, g, kScanThreads, 0, st, in, out, n_dev, n_host, partial);
   count_launch(3);
 }
 
 // Start of a step: coarsening rounds enabled again; hist (nullable) records the
 // number of blocks of the adapted grid the step starts from.
 __global__ void k_step_begin(Counters* c, int32_t* hist) {
+  pdl_enter();
   c->done = 0;
   c->rounds = 0;
   c->first_round = 1;
@@ -179,6 +184,7 @@ __global__ void k_step_begin(Counters* c, int32_t* hist) {
 // Stage coefficients of every tree from its device-resident (t, dt); the swirl
 // factor uses the device cos (graph-captured steps).
 __global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int swirl) {
+  pdl_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ntrees) return;
   TreeTime& T = tt[k];
@@ -187,34 +193,45 @@ __global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int 
   T.ca[0] = h / 6.0; T.ca[1] = h / 3.0; T.ca[2] = h / 3.0; T.ca[3] = h / 6.0;
   T.cy[0] = h / 2.0; T.cy[1] = h / 2.0; T.cy[2] = h; T.cy[3] = 0.0;
   for (int s = 0; s < 4; ++s) T.ct[s] = swirl ? cos(M_PI * ts[s] / trees[k].rhs[0]) : 0.0;
+  for (int s = 0; s < 4; ++s) {
+    T.caf[s] = (float)T.ca[s];
+    T.cyf[s] = (float)T.cy[s];
+    T.ctf[s] = (float)T.ct[s];
+  }
 }
 // End of a coarsening round inside a graph while-node: run another round while
 // the last one merged a family and fewer than max_rounds ran.
 __global__ void k_round_continue(Counters* c, cudaGraphConditionalHandle h, int max_rounds) {
+  pdl_enter();
   c->rounds += 1;
   c->graph_rounds += 1;
   cudaGraphSetConditional(h, (!c->done && c->rounds < max_rounds) ? 1u : 0u);
 }
 
 __global__ void k_time_advance(TreeTime* tt, int ntrees) {
+  pdl_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < ntrees) tt[k].t = tt[k].t + tt[k].dt;
 }
 
 
 __global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;
 }
 __global__ void k_fill_i8(int8_t* a, int64_t n, int8_t v) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = v;
 }
 
 __global__ void k_sb_check(const int32_t* cells, int64_t ncells, Counters* c) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncells; i += (int64_t)gridDim.x * blockDim.x)
     if (cells[2 * i] != 1) atomicOr(&c->err, kErrLayout);
 }
 
 __global__ void k_sb_counters(Counters* c, int32_t* freelist, int64_t n, int64_t cap) {
+  pdl_enter();
   const int64_t nf = cap - n;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nf; j += (int64_t)gridDim.x * blockDim.x)
     freelist[j] = (int32_t)(cap - 1 - j);

@@ -42,3 +42,40 @@ def test_binding_signatures_cover_header(lib):
 def test_relation_counts_without_device(lib):
     # Sec. 2.2: 16 relations in 2D, 74 in 3D (pure host function)
     assert lib.mr_num_relations(2) == 16 and lib.mr_num_relations(3) == 74
+
+
+def test_every_kernel_waits_for_its_predecessor_first():
+    # Kernels may be launched with programmatic dependent launch: each one must
+    # wait for the previous kernel (pdl_enter) before it touches memory.
+    src = os.path.join(ROOT, "paper_1902_00088_gb300", "csrc")
+    n = 0
+    for f in sorted(os.listdir(src)):
+        if not f.endswith((".cu", ".cuh")):
+            continue
+        txt = open(os.path.join(src, f)).read()
+        for m in re.finditer(r"__global__", txt):
+            i = m.end()
+            # end of the parameter list: the first ')' closing the '(' after the kernel name
+            j = txt.index("(", i)
+            while txt[i:j].rstrip().endswith("__launch_bounds__"):
+                depth, k = 0, j
+                while True:
+                    depth += {"(": 1, ")": -1}.get(txt[k], 0)
+                    if depth == 0:
+                        break
+                    k += 1
+                i, j = k + 1, txt.index("(", k + 1)
+            depth, k = 0, j
+            while True:
+                depth += {"(": 1, ")": -1}.get(txt[k], 0)
+                if depth == 0:
+                    break
+                k += 1
+            rest = txt[k + 1:].lstrip()
+            if rest.startswith(";"):
+                continue  # declaration
+            assert rest.startswith("{"), (f, txt[m.start():m.start() + 80])
+            body = rest[1:].lstrip()
+            assert body.startswith("pdl_enter();"), (f, txt[m.start():m.start() + 80])
+            n += 1
+    assert n > 40

@@ -297,6 +297,29 @@ def test_graph_steps_equal_eager_steps(mr):
     assert b.graph_mode() in ("while-node", "fixed-rounds")
 
 
+def test_launch_overlap_gives_identical_steps(mr):
+    # Programmatic dependent launch changes when kernels are scheduled, not what
+    # they compute: graph and host-driven steps with the overlap on and off give
+    # the same grid and fields bit for bit (FP32 swirl, FP64 details).
+    tree = dict(Jmin=2, Jmax=7, eps=1e-4, ic="gauss", ic_params=(0.5, 0.75, 0.0, 0.05),
+                rhs_params=(5.0,))
+    dt = 0.5 / (16 * 128)
+    runs = []
+    for on in (True, False):
+        g = mr.Forest(dim=2, precision="fp32", detail_fp64=True, rhs="swirl", trees=[tree], capacity=40000)
+        g.set_launch_overlap(on)
+        g.init_tree()
+        for s in range(3):
+            g.step(s * dt, dt)
+        g.set_time(3 * dt, dt)
+        g.step_graph(20)
+        runs.append(g.get_blocks())
+        assert g.launch_overlap() == on
+    (ia, fa), (ib, fb) = runs
+    assert np.array_equal(ia, ib) and np.array_equal(fa, fb)
+    assert len(ia) > 20
+
+
 def test_forest_trees_are_independent_and_match_oracle(mr, oracle_mod):
     import synthetic as inputs
     trees = inputs.forest_trees(3, seed=11)
