@@ -135,10 +135,13 @@ struct Box {
   static constexpr int CB = (B - 1) / 2 + 2 * ((W + 1) / 2) + 3;
   static constexpr int CBOX = CB * CB * (D == 3 ? CB : 1);
   // scratch of the separable prediction, per variable: X[nz][ny][x] (coarse
-  // y, z; fine x) and, in 3D, Y[nz][y][x] (coarse z; fine x, y)
+  // y, z; fine x) and, in 3D, Y[nz][y][x] (coarse z; fine x, y).  In 3D X is
+  // kept in the variable's tile, which is written only after the y pass, so
+  // the scratch holds Y alone.
   static constexpr int NXP = (D == 3 ? CB : 1) * CB * S;
   static constexpr int NYP = D == 3 ? CB * S * S : 0;
-  static constexpr int SCR = NXP + NYP;
+  static constexpr int SCR = D == 3 ? NYP : NXP;
+  static_assert(D == 2 || NXP <= TILE, "the x pass fits in the tile");
   __device__ static __forceinline__ int cix(int i, int j, int k) {
     return ((D == 3 ? k - CLO : 0) * CB + (j - CLO)) * CB + (i - CLO);
   }
@@ -478,7 +481,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       // the point): the same operations in the same order as predict_box
       for (int v = 0; v < nv; ++v) {
         const TT* cb = cbox + v * Bx::CBOX;
-        TT* X = scr + v * Bx::SCR;
+        TT* X = D == 3 ? tile + v * Bx::TILE : scr + v * Bx::SCR;
         for (int q = g.rank(); q < Bx::NXP; q += g.size()) {
           const int x = q % Bx::S - W, ny = (q / Bx::S) % Bx::CB + Bx::CLO;
           const int nz = D == 3 ? q / (Bx::S * Bx::CB) + Bx::CLO : 0;
@@ -491,8 +494,8 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       if (D == 3) {
         g.sync();
         for (int v = 0; v < nv; ++v) {
-          const TT* X = scr + v * Bx::SCR;
-          TT* Y = scr + v * Bx::SCR + Bx::NXP;
+          const TT* X = tile + v * Bx::TILE;
+          TT* Y = scr + v * Bx::SCR;
           for (int q = g.rank(); q < Bx::NYP; q += g.size()) {
             const int x = q % Bx::S, y = (q / Bx::S) % Bx::S - W, nzi = q / (Bx::S * Bx::S);
             const int fl = y >> 1;
@@ -577,7 +580,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
         if (kind[u] == 3) {
           if (scr) {
             // last axis from the scratch: z in 3D (Y), y in 2D (X)
-            const TT* c = scr + v * Bx::SCR + (D == 3 ? Bx::NXP : 0) + (ijk[u][0] + W) +
+            const TT* c = scr + v * Bx::SCR + (ijk[u][0] + W) +
                           (D == 3 ? (ijk[u][1] + W) * Bx::S : 0);
             const int st = D == 3 ? Bx::S * Bx::S : Bx::S;
             const int e = ijk[u][D - 1], fl = e >> 1;
@@ -792,6 +795,69 @@ template <typename T>
 __device__ __forceinline__ T* smem_as(size_t offset_bytes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   return reinterpret_cast<T*>(smem_raw + offset_bytes);
+}
+
+// Exclusive scan of n int2 pairs (in -> out) by one CTA of NT threads: PER
+// consecutive pairs per thread per pass, a running carry between passes; the
+// totals go to tot[0..1].  The input is read past L1 (written by other CTAs of
+// the same grid).  Every thread of the CTA takes part.
+template <int NT, int PER>
+__device__ void cta_scan2(const int32_t* in, int32_t* out, int n, int32_t* tot) {
+  __shared__ int2 wt[NT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int2 carry = make_int2(0, 0);
+  for (int base = 0; base < n; base += NT * PER) {
+    int2 loc[PER];
+    int2 s = make_int2(0, 0);
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = base + threadIdx.x * PER + r;
+      loc[r] = i < n ? make_int2(__ldcg(in + 2 * i), __ldcg(in + 2 * i + 1)) : make_int2(0, 0);
+      s.x += loc[r].x;
+      s.y += loc[r].y;
+    }
+    int2 v = s;  // inclusive scan within the warp, then over the warp totals
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, v.x, o), y = __shfl_up_sync(0xffffffffu, v.y, o);
+      if (lane >= o) { v.x += x; v.y += y; }
+    }
+    if (lane == 31) wt[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      int2 t = lane < NT / 32 ? wt[lane] : make_int2(0, 0);
+      for (int o = 1; o < NT / 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, t.x, o), y = __shfl_up_sync(0xffffffffu, t.y, o);
+        if (lane >= o) { t.x += x; t.y += y; }
+      }
+      if (lane < NT / 32) wt[lane] = t;
+    }
+    __syncthreads();
+    if (w > 0) { v.x += wt[w - 1].x; v.y += wt[w - 1].y; }
+    int2 run = make_int2(carry.x + v.x - s.x, carry.y + v.y - s.y);
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = base + threadIdx.x * PER + r;
+      if (i < n) { out[2 * i] = run.x; out[2 * i + 1] = run.y; }
+      run.x += loc[r].x;
+      run.y += loc[r].y;
+    }
+    carry.x += wt[NT / 32 - 1].x;
+    carry.y += wt[NT / 32 - 1].y;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && tot) { tot[0] = carry.x; tot[1] = carry.y; }
+}
+
+// True in every thread of the CTA of the grid that finishes last; the writes
+// of every other CTA of the grid are visible to it.  The caller resets
+// ctas_done.
+__device__ __forceinline__ bool last_cta_all(Counters* c) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&c->ctas_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return last;
 }
 
 __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {

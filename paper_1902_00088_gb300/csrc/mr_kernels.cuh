@@ -705,6 +705,26 @@ __device__ __forceinline__ T block_max(T v, T* red) {
   return v;
 }
 
+// Shared-memory layout of k_details after the ring and the tile: the coarse
+// box and prediction scratch of the gather, reused once the tile is complete
+// for the passes of the prediction (X, and in 3D the y pass Y).  A pass in
+// type A keeps Y when it fits in that region, else (3D FP64 over an FP32 tile)
+// evaluates the y pass again per point: the same operations in the same order.
+template <int D, int B, typename TT, typename TD>
+struct DetSmem {
+  using Bx = Box<D, B, 2>;
+  using DG = DetGeo<D, B>;
+  static constexpr size_t FILL = sizeof(TT) * (Bx::CBOX + Bx::SCR);  // per variable
+  template <typename A>
+  __host__ __device__ static constexpr bool ystore() { return D == 2 || sizeof(A) * (DG::NX + DG::NY) <= FILL; }
+  template <typename A>
+  __host__ __device__ static constexpr size_t pass_bytes() {
+    return sizeof(A) * (ystore<A>() ? DG::NX + DG::NY : DG::NX);
+  }
+  static constexpr size_t PASS = pass_bytes<TD>() > pass_bytes<float>() ? pass_bytes<TD>() : pass_bytes<float>();
+  __host__ __device__ static size_t region(int nv) { return FILL * nv > PASS ? FILL * nv : PASS; }
+};
+
 template <int D, int B, typename TS, typename TD, int NT, typename TT = TS>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_details(PoolView pv, TS* __restrict__ y) {
   pdl_enter();
@@ -715,9 +735,10 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   __shared__ double red[2][32];
   TT* tile = smem_as<TT>(kRingBytes);  // tile type (TS or FP32); TD is the decision type
   TT* cbox = tile + pv.nvar * Bx::TILE;
-  // gather scratch, reused for the x pass once the tile is complete
+  // gather scratch, reused for the passes once the tile is complete
   TT* scr = cbox + pv.nvar * Bx::CBOX;
-  TD* X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(scr) + 15) & ~(uintptr_t)15);
+  using DS = DetSmem<D, B, TT, TD>;
+  TD* X = reinterpret_cast<TD*>((reinterpret_cast<uintptr_t>(cbox) + 15) & ~(uintptr_t)15);
   const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
   const bool all_blocks = pv.cnt->first_round != 0;
@@ -731,8 +752,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   // (the first round after the RK stages); the next block's plan is fetched
   // while a block is processed
   const bool plan_ok = pv.cnt->plan_topo == pv.cnt->topo;
-  const size_t xs = sizeof(TT) * (size_t)nv * Bx::SCR, xd = sizeof(TD) * (size_t)(DG::NX + DG::NY);
-  const size_t xbytes = xs > xd ? xs : xd;
+  const size_t xbytes = DS::region(nv);
   int32_t* gtab = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(X) + ((xbytes + 15) & ~(size_t)15));
   if (D == 2) build_gtab<D, B, 2>(gtab);
   // CTA-local work count and threshold scales (one atomic per CTA, not per block)
@@ -847,13 +867,18 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         return dd4(xat(i, m0 - 1, zc), xat(i, m0, zc), xat(i, m0 + 1, zc), xat(i, m0 + 2, zc));
       };
       // 3D: the y pass once per (x, y, coarse z row), kept for the z pass
+      // where it fits (else evaluated again for each use)
+      constexpr bool ys = DS::template ystore<A>();
       A* YA = XA + DG::NX;
-      if (D == 3) {
+      if (D == 3 && ys) {
         for (int idx = threadIdx.x; idx < DG::NY; idx += blockDim.x)
           YA[idx] = ypass(idx % B, (idx / B) % B, idx / (B * B) - 1);
         __syncthreads();
       }
-      auto yat = [&](int i, int j, int zc) { return YA[((zc + 1) * B + j) * B + i]; };
+      auto yat = [&](int i, int j, int zc) -> A {
+        if constexpr (ys) return YA[((zc + 1) * B + j) * B + i];
+        else return ypass(i, j, zc);
+      };
       A md = A(0);  // a maximum of A values: exact in A
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
@@ -1277,8 +1302,10 @@ __global__ void k_error(PoolView pv, const TS* __restrict__ y, int tree, const d
 }
 
 // ------------------------------------------------------- tree maintenance ----
-template <int D>
-__global__ void k_refine_count(PoolView pv, int mode, const int8_t* mask) {
+// SCAN: the CTA that finishes last also scans the counts (short lists), which
+// saves the separate scan launch.
+template <int D, bool SCAN>
+__global__ void __launch_bounds__(256) k_refine_count(PoolView pv, int mode, const int8_t* mask) {
   pdl_enter();
   const int nact = pv.cnt->n_act;
   const int nch = 1 << D;
@@ -1291,6 +1318,12 @@ __global__ void k_refine_count(PoolView pv, int mode, const int8_t* mask) {
     pv.flag[s] = r ? 1 : 0;
     pv.emit[2 * p] = r ? nch : 1;
     pv.emit[2 * p + 1] = r ? nch : 0;
+  }
+  if constexpr (SCAN) {
+    if (last_cta_all(pv.cnt)) {
+      cta_scan2<256, 8>(pv.emit, pv.eoff, nact, &pv.cnt->n_new);
+      if (threadIdx.x == 0) pv.cnt->ctas_done = 0;
+    }
   }
 }
 
@@ -1404,8 +1437,8 @@ __device__ __forceinline__ bool qualifies(const PoolView& pv, const TreeDev& td,
   return ok && !fail;
 }
 
-template <int D>
-__global__ void k_flags(PoolView pv) {
+template <int D, bool SCAN>
+__global__ void __launch_bounds__(256) k_flags(PoolView pv) {
   pdl_enter();
   // A family (the 2^d sisters of a block) merges when every sister is a leaf
   // whose normalised detail is below eps, above Jmin, and no leaf one level
@@ -1484,6 +1517,14 @@ __global__ void k_flags(PoolView pv) {
       const bool first = all && (p == 0 || !same_family(pv, s, pv.act[p - 1]));
       pv.emit[2 * p] = (!all || first) ? 1 : 0;
       pv.emit[2 * p + 1] = (all && !first) ? 1 : 0;
+    }
+  }
+  // SCAN: the CTA that finishes last scans the new-list counts (short lists),
+  // which saves the separate scan launch
+  if constexpr (SCAN) {
+    if (last_cta_all(pv.cnt)) {
+      cta_scan2<256, 8>(pv.emit, pv.eoff, nact, &pv.cnt->n_new);
+      if (threadIdx.x == 0) pv.cnt->ctas_done = 0;
     }
   }
 }

@@ -28,6 +28,10 @@ static inline int flat_grid(const PoolView& pv, int threads) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// Lists up to this length are scanned by the last CTA of the kernel that wrote
+// the counts (one CTA, a few passes) instead of a separate scan launch.
+constexpr int64_t kFusedScanMax = 8192;
+
 // ---------------------------------------------------------------- stage ------
 // 2D blocks of 17^2 nodes: 128-thread CTAs, so small grids run in one wave.
 template <int D, int B>
@@ -184,10 +188,17 @@ template <int D>
 void launch_refine(const PoolView& pv, const Fields& f, int mode, const int8_t* mask,
                    const LaunchCfg& lc, cudaStream_t st) {
   const int nch = 1 << D;
-  launch_k(lc.pdl, k_refine_count<D>, flat_grid(pv, 256), 256, 0, st, pv, mode, mask);
-  count_launch();
-  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st, 2 * (int64_t)lc.n_hint,
-               lc.pdl != 0);
+  // short lists: the counting kernel's last CTA scans them (no scan launch)
+  if (2 * (int64_t)lc.n_hint <= kFusedScanMax) {
+    const int grid = std::min(flat_grid(pv, 256), std::max(lc.num_sms, (2 * lc.n_hint + 255) / 256));
+    launch_k(lc.pdl, k_refine_count<D, true>, grid, 256, 0, st, pv, mode, mask);
+    count_launch();
+  } else {
+    launch_k(lc.pdl, k_refine_count<D, false>, flat_grid(pv, 256), 256, 0, st, pv, mode, mask);
+    count_launch();
+    launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_act, pv.cap, &pv.cnt->n_new, st, 2 * (int64_t)lc.n_hint,
+                 lc.pdl != 0);
+  }
   dispatch_bs<D, RefineRun>(pv, f, lc, st);
   launch_k(lc.pdl, k_refine_commit<D>, flat_grid(pv, 256), 256, 0, st, pv);
   count_launch(1);
@@ -235,9 +246,8 @@ struct DetailsRun {
     }
     using Bx = Box<D, B, 2>;
     const size_t tt = d64 ? sizeof(TS) : 4;  // tile type: the state type, FP32 for FP32 details
-    const size_t scr = tt * pv.nvar * Bx::SCR, xp = (d64 ? 8 : 4) * (DetGeo<D, B>::NX + DetGeo<D, B>::NY);
-    const size_t smem = kRingBytes + tt * pv.nvar * (Bx::TILE + Bx::CBOX) + 16 + (scr > xp ? scr : xp) + 16 +
-                        (D == 2 ? 4 * Bx::NPTS : 0);
+    const size_t region = d64 ? DetSmem<D, B, TS, double>::region(pv.nvar) : DetSmem<D, B, float, float>::region(pv.nvar);
+    const size_t smem = kRingBytes + tt * pv.nvar * Bx::TILE + 16 + region + 16 + (D == 2 ? 4 * Bx::NPTS : 0);
     if (d64) {
       auto k = k_details<D, B, TS, double, threads>;
       prep_smem(k, smem);
@@ -274,11 +284,21 @@ template <int D>
 void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const LaunchCfg& lc,
                         cudaStream_t st) {
   const int nch = 1 << D;
-  launch_k(lc.pdl, k_flags<D>, (int)std::min<int64_t>(4096, (pv.cap + 7) / 8), 256, 0, st, pv);
-  count_launch();
-  if (!merge) return;
-  launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st, 4 * (int64_t)lc.n_hint,
-               lc.pdl != 0);
+  // one warp per block: a grid for the expected list (after a refinement,
+  // 2^d times the blocks last seen by the host); the loop strides over more
+  const int64_t n_expect = (int64_t)nch * std::max(lc.n_hint, 1);
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>(4096, (pv.cap + 7) / 8),
+                                          std::max<int64_t>(lc.num_sms, (n_expect + 7) / 8));
+  if (merge && n_expect <= kFusedScanMax) {
+    launch_k(lc.pdl, k_flags<D, true>, grid, 256, 0, st, pv);  // the last CTA scans the counts
+    count_launch();
+  } else {
+    launch_k(lc.pdl, k_flags<D, false>, grid, 256, 0, st, pv);
+    count_launch();
+    if (!merge) return;
+    launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st, 4 * (int64_t)lc.n_hint,
+                 lc.pdl != 0);
+  }
   dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
   launch_k(lc.pdl, k_coarsen_commit<D>, flat_grid(pv, 256), 256, 0, st, pv);
   count_launch(1);
