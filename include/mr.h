@@ -275,10 +275,11 @@ int32_t mr_get_launch_overlap(mr_ctx ctx);
 mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n, int32_t reset);
 /* Times graph steps with 1, 2, 3, 4, 6, 8 and occupancy-limited CTAs per SM for
  * the block kernels and, in 2D, both forms of the RK stage (one CTA per block,
- * one warp per block) (steps steps each; the solution advances during tuning)
- * and keeps the fastest; *best = CTAs per SM (0 = occupancy) + 100 x form.
- * Without tuning the 2D stage uses one warp per block once the grid holds at
- * least 8 blocks per SM.  Synchronises. */
+ * one warp per block; the second for 17^2 blocks only) (steps steps each; the
+ * solution advances during tuning) and keeps the fastest; *best = CTAs per SM
+ * (0 = occupancy) + 100 x form.  Without tuning the 2D stage on 17^2 blocks
+ * uses one warp per block once the grid holds at least 8 blocks per SM.
+ * Synchronises. */
 mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best);
 /* Synchronises; accumulates pending timers into *out. */
 mr_status mr_get_stats(mr_ctx ctx, mr_stats* out);

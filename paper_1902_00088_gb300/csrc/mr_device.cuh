@@ -13,17 +13,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mr_internal.h"
 
 namespace mr {
 
 // Thread groups that cooperate on one block: the whole CTA, or one warp.
 struct CtaGroup {
+  static constexpr int kSize = 0;  // size known at run time only
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
   __device__ __forceinline__ int size() const { return blockDim.x; }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 struct WarpGroup {
+  static constexpr int kSize = 32;
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
   __device__ __forceinline__ int size() const { return 32; }
   __device__ __forceinline__ void sync() const { __syncwarp(); }
@@ -725,27 +729,29 @@ __device__ __forceinline__ void gather_table(const PoolView& pv, int64_t own, co
   using Bx = Box<D, B, W>;
   using Gm = Geo<D, B>;
   constexpr int U = 4;
-  for (int q0 = g.rank(); q0 < Bx::NPTS; q0 += U * g.size()) {
-    int64_t at[U];
-    bool ok[U], ed[U];
+  // points q0 + u * stride, u < UU: table entries, then the UU loads together
+  auto chunk = [&](auto uu, int q0, int stride) {
+    constexpr int UU = decltype(uu)::value;
+    int64_t at[UU];
+    bool ok[UU], ed[UU];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int q = q0 + u * g.size();
+    for (int u = 0; u < UU; ++u) {
+      const int q = q0 + u * stride;
       ok[u] = q < Bx::NPTS;
       const int e = gtab[ok[u] ? q : 0];
       const int64_t nbv = nbase[(e >> 16) & 31];
       at[u] = nbv + (e & 0xffff);
       ed[u] = commit && ((e >> 21) & 1) && nbv != own;
     }
-    TF v[U][NV];
+    TF v[UU][NV];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < UU; ++u)
 #pragma unroll
       for (int w = 0; w < NV; ++w) v[u][w] = ok[u] ? F[at[u] + (int64_t)w * pv.vs] : TF(0);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
+    for (int u = 0; u < UU; ++u) {
       if (!ok[u]) continue;
-      const int q = q0 + u * g.size();
+      const int q = q0 + u * stride;
 #pragma unroll
       for (int w = 0; w < NV; ++w) {
         tile[w * Bx::TILE + q] = (TT)v[u][w];
@@ -756,6 +762,16 @@ __device__ __forceinline__ void gather_table(const PoolView& pv, int64_t own, co
         }
       }
     }
+  };
+  if constexpr (G::kSize > 0) {
+    // group size known at compile time: full chunks of U, then one chunk just
+    // wide enough for the remaining points
+    constexpr int SZ = G::kSize, FULL = Bx::NPTS / (U * SZ) * (U * SZ);
+    constexpr int UT = (Bx::NPTS - FULL + SZ - 1) / SZ;
+    for (int q0 = g.rank(); q0 < FULL; q0 += U * SZ) chunk(std::integral_constant<int, U>{}, q0, SZ);
+    if constexpr (UT > 0) chunk(std::integral_constant<int, UT>{}, FULL + g.rank(), SZ);
+  } else {
+    for (int q0 = g.rank(); q0 < Bx::NPTS; q0 += U * g.size()) chunk(std::integral_constant<int, U>{}, q0, g.size());
   }
 }
 

@@ -171,7 +171,7 @@ inline void launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_
   cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-// Per-dimension launchers (explicitly instantiated in mr_k2.cu / mr_k3.cu).
+// Per-dimension launchers (explicitly instantiated in mr_k2*.cu / mr_k3*.cu).
 template <int D> void launch_plan(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_stage(const PoolView& pv, const Fields& f, int stage,
                                    const StageArgs& sa, const LaunchCfg& lc, cudaStream_t st);

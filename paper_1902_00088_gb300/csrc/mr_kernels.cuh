@@ -1,5 +1,5 @@
 // Kernel templates of the multiresolution step.  Instantiated per dimension in
-// mr_k2.cu / mr_k3.cu.  Every persistent kernel loops over the active list with
+// mr_k2*.cu / mr_k3*.cu.  Every persistent kernel loops over the active list with
 // a grid-stride loop bounded by the device-side block count, so no launch
 // needs a host round trip.
 #pragma once
@@ -44,10 +44,12 @@ template <typename T> __device__ __forceinline__ const T* lattice(const PoolView
 // The block's plan (k_plan) is read from shared memory, the next block's plan
 // is fetched while this one is processed; blocks with a uniform neighbourhood
 // take the direct gather, the others the general one through their ring.
-template <int D, int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
+template <int D, int B, int RHS, typename TS, typename TY, typename TSRC, int NT, int ST>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_adv(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
-                            TS* __restrict__ acc, TY* __restrict__ ynext, int stage, StageArgs sa) {
+                            TS* __restrict__ acc, TY* __restrict__ ynext, int stage_arg, StageArgs sa) {
   pdl_enter();
+  constexpr int stage = ST;  // the RK stage, fixed at compile time
+  static_assert(ST >= 0 && ST <= 3, "RK4 stage");
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 2>;  // the stencils reach two nodes
   using PL = Plan<D>;
@@ -225,11 +227,15 @@ struct StageW {
   static constexpr size_t SMEM = GTAB + NW * WAREA;
 };
 
-template <int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
+// ST: the RK stage, fixed at compile time (the per-point loads, stores and
+// updates of each stage without run-time branches).
+template <int B, int RHS, typename TS, typename TY, typename TSRC, int NT, int ST>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
-                                                   TS* __restrict__ acc, TY* __restrict__ ynext, int stage,
+                                                   TS* __restrict__ acc, TY* __restrict__ ynext, int stage_arg,
                                                    StageArgs sa) {
   pdl_enter();
+  constexpr int stage = ST;
+  static_assert(ST >= 0 && ST <= 3, "RK4 stage");
   using Gm = Geo<2, B>;
   using Bx = Box<2, B, 2>;
   using PL = Plan<2>;
@@ -280,8 +286,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
     const int64_t base = (int64_t)b.slot * pv.vs;
     const int sh = td.Jmax - b.lvl;
     const TC uc0 = tree_rhs<TC>(td, 0), uc1 = tree_rhs<TC>(td, 1);
-    constexpr int UC = 4;
-    for (int q0 = lane; q0 < Gm::NI; q0 += UC * 32) {
+    // points q0 + 32 u, u < UC: state, accumulator and velocity loads first,
+    // then the stencils and the updates
+    auto chunk = [&](auto ucc, int q0) {
+      constexpr int UC = decltype(ucc)::value;
       TS yv[UC], av[UC];
       TC u0[UC], u1[UC];
 #pragma unroll
@@ -324,7 +332,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
           y[at] = av[u] + cas * kk;
         }
       }
-    }
+    };
+    // full chunks of 4 points per lane, then one chunk for the remainder
+    constexpr int UC = 4, FULL = Gm::NI / (UC * 32) * (UC * 32), UT = (Gm::NI - FULL + 31) / 32;
+    for (int q0 = lane; q0 < FULL; q0 += UC * 32) chunk(std::integral_constant<int, UC>{}, q0);
+    if constexpr (UT > 0) chunk(std::integral_constant<int, UT>{}, FULL + lane);
     __syncwarp();
     cur = nxt;
   }
@@ -1082,21 +1094,29 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
         __syncwarp();
         return md;
       };
-      TS mqs = TS(0);
+      // largest |value| over the interior (stored, and the NaN check) and, for
+      // the certified FP32 evaluation, over the whole tile: one sweep
+      constexpr bool cert = sizeof(TS) == 4 && sizeof(TD) == 8;
+      TS mqs = TS(0), mts = TS(0);
       bool bad = false;
-      for (int qn = lane; qn < Gm::NI; qn += 32) {
-        const TS sv = tile[Bx::tix(qn % B, qn / B, 0)];
-        mqs = fmax(mqs, (TS)fabs(sv));
-        bad |= !isfinite(sv);
+      for (int qn = lane; qn < (cert ? Bx::TILE : Gm::NI); qn += 32) {
+        int i, j;
+        if (cert) { i = qn % Bx::S - 2; j = qn / Bx::S - 2; }
+        else { i = qn % B; j = qn / B; }
+        const TS sv = tile[Bx::tix(i, j, 0)];
+        const TS av = (TS)fabs(sv);
+        if (cert) mts = fmax(mts, av);
+        if (i >= 0 && i < B && j >= 0 && j < B) {
+          mqs = fmax(mqs, av);
+          bad |= !isfinite(sv);
+        }
       }
       mqs = warp_max(mqs);
       double md = 0.0;  // lane 0's value is stored
-      if constexpr (sizeof(TS) == 4 && sizeof(TD) == 8) {
+      if constexpr (cert) {
         // as in k_details: FP32 evaluation, FP64 only within the rounding bound of eps
         const float m32 = pass(float(0));
-        float mt = 0.f;
-        for (int qn = lane; qn < Bx::TILE; qn += 32) mt = fmaxf(mt, fabsf((float)tile[qn]));
-        const float E = 0x1p-19f * warp_max(mt) + 1e-37f;
+        const float E = 0x1p-19f * warp_max((float)mts) + 1e-37f;
         if (certain_vs_eps(m32, E, td)) {
           if (lane == 0) md = (double)m32;
         } else {

@@ -1,5 +1,6 @@
 // Host-side launchers of the kernel templates, dispatched over block size and
-// precision.  Included once per dimension (mr_k2.cu, mr_k3.cu).
+// precision.  Included once per translation unit of instantiations (mr_k2.cu,
+// mr_k2s.cu, mr_k2t.cu, mr_k3.cu, mr_k3s.cu).
 #pragma once
 #include <algorithm>
 #include <cstdio>
@@ -48,35 +49,44 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
   // 2D: one warp per block when the grid holds enough blocks to fill the GPU
   // several times over (or as tuned), else one CTA per block (shorter latency)
   const bool warp_form = lc.stage_form == 1 || (lc.stage_form < 0 && lc.n_hint >= 8 * lc.num_sms);
-  if (D == 2 && warp_form) {
-    if (stage == 0) {
-      using SW = StageW<B, RHS, TS, TY, TS, threads>;
-      auto k = k_stage_adv_w<B, RHS, TS, TY, TS, threads>;
-      prep_smem(k, SW::SMEM);
-      const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
-      launch_k(lc.pdl, k, grid, threads, SW::SMEM, st, pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
-    } else {
-      using SW = StageW<B, RHS, TS, TY, TY, threads>;
-      const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
-      auto k = k_stage_adv_w<B, RHS, TS, TY, TY, threads>;
-      prep_smem(k, SW::SMEM);
-      const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
-      launch_k(lc.pdl, k, grid, threads, SW::SMEM, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+  if constexpr (D == 2 && B == 17) {  // 17^2 blocks: 289 points per warp
+    if (warp_form) {
+      // one instantiation per stage: stage 0 reads the committed state, the
+      // others the previous stage value
+      auto go = [&](auto stc) {
+        constexpr int S = decltype(stc)::value;
+        using TSRC = std::conditional_t<S == 0, TS, TY>;
+        using SW = StageW<B, RHS, TS, TY, TSRC, threads>;
+        const TSRC* src = S == 0 ? (const TSRC*)f.y : (const TSRC*)(S == 2 ? f.Yb : f.Ya);
+        auto k = k_stage_adv_w<B, RHS, TS, TY, TSRC, threads, S>;
+        prep_smem(k, SW::SMEM);
+        const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
+        launch_k(lc.pdl, k, grid, threads, SW::SMEM, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+      };
+      switch (stage) {
+        case 0: go(std::integral_constant<int, 0>{}); break;
+        case 1: go(std::integral_constant<int, 1>{}); break;
+        case 2: go(std::integral_constant<int, 2>{}); break;
+        default: go(std::integral_constant<int, 3>{}); break;
+      }
+      count_launch();
+      return;
     }
-    count_launch();
-    return;
   }
-  if (stage == 0) {
-    auto k = k_stage_adv<D, B, RHS, TS, TY, TS, threads>;
-    prep_smem(k, smem);
-    const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
-    launch_k(lc.pdl, k, grid, threads, smem, st, pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
-  } else {
-    const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
-    auto k = k_stage_adv<D, B, RHS, TS, TY, TY, threads>;
+  auto go = [&](auto stc) {
+    constexpr int S = decltype(stc)::value;
+    using TSRC = std::conditional_t<S == 0, TS, TY>;
+    const TSRC* src = S == 0 ? (const TSRC*)f.y : (const TSRC*)(S == 2 ? f.Yb : f.Ya);
+    auto k = k_stage_adv<D, B, RHS, TS, TY, TSRC, threads, S>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
     launch_k(lc.pdl, k, grid, threads, smem, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+  };
+  switch (stage) {
+    case 0: go(std::integral_constant<int, 0>{}); break;
+    case 1: go(std::integral_constant<int, 1>{}); break;
+    case 2: go(std::integral_constant<int, 2>{}); break;
+    default: go(std::integral_constant<int, 3>{}); break;
   }
   count_launch();
 }
@@ -128,25 +138,25 @@ void launch_plan(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st) {
   count_launch();
 }
 
+// RK stage of every block for one block size (instantiated per block size in
+// translation units of their own).
+template <int D, int B>
+void launch_stage_bs(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
+                     const LaunchCfg& lc, cudaStream_t st) {
+  if constexpr (D == 2) {
+    if (pv.rhs_kind == MR_RHS_NS) stage_ns<B>(pv, f, stage, sa, lc, st);
+    else if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, B, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
+    else stage_prec<D, B, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
+  } else {
+    stage_prec<D, B, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
+  }
+}
+
 template <int D>
 void launch_stage(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
                   const LaunchCfg& lc, cudaStream_t st) {
-  if constexpr (D == 2) {
-    if (pv.rhs_kind == MR_RHS_NS) {
-      if (pv.Bs == 17) stage_ns<17>(pv, f, stage, sa, lc, st);
-      else stage_ns<33>(pv, f, stage, sa, lc, st);
-      return;
-    }
-    if (pv.Bs == 17) {
-      if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, 17, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
-      else stage_prec<D, 17, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
-    } else {
-      if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, 33, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
-      else stage_prec<D, 33, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
-    }
-  } else {
-    stage_prec<D, 17, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
-  }
+  if (D == 3 || pv.Bs == 17) launch_stage_bs<D, 17>(pv, f, stage, sa, lc, st);
+  else launch_stage_bs<D, (D == 2 ? 33 : 17)>(pv, f, stage, sa, lc, st);
 }
 
 // Dispatch helper over (Bs, state type): calls F<D, B, TS>::run(args...).
@@ -421,6 +431,16 @@ void launch_error(const PoolView& pv, const Fields& f, int tree, const double* e
                   const LaunchCfg& lc, cudaStream_t st) {
   dispatch_bs<D, ErrorRun>(pv, f, tree, ex, out4, lc, st);
 }
+
+// The RK stage launchers of each block size are instantiated in translation
+// units of their own (mr_k2s.cu, mr_k2t.cu, mr_k3s.cu), compiled in parallel
+// with the rest; the others see them as external (MR_EXTERN_STAGE).
+#define MR_INSTANTIATE_STAGE(D, B)                                                              \
+  template void launch_stage_bs<D, B>(const PoolView&, const Fields&, int, const StageArgs&,   \
+                                      const LaunchCfg&, cudaStream_t);
+#define MR_EXTERN_STAGE(D, B)                                                                   \
+  extern template void launch_stage_bs<D, B>(const PoolView&, const Fields&, int,              \
+                                             const StageArgs&, const LaunchCfg&, cudaStream_t);
 
 #define MR_INSTANTIATE(D)                                                                       \
   template void launch_plan<D>(const PoolView&, const LaunchCfg&, cudaStream_t);                \
