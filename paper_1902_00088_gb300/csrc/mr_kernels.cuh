@@ -970,10 +970,15 @@ struct DetW {
   using DG = DetGeo<2, B>;
   static constexpr int NW = NT / 32;
   static constexpr size_t GTAB = (4 * Bx::NPTS + 15) / 16 * 16;
+  // odd interior points (those with a detail), in row-major order
+  static constexpr int NODD = B * B - ((B + 1) / 2) * ((B + 1) / 2);
+  // per-CTA index tables: x pass sources (NX), odd points with their x-pass rows (NODD)
+  static constexpr size_t TABS = (4 * (DG::NX + NODD) + 15) / 16 * 16;
   static constexpr size_t XB = sizeof(TS) * Bx::SCR > sizeof(TD) * DG::NX ? sizeof(TS) * Bx::SCR : sizeof(TD) * DG::NX;
   static constexpr size_t TB = (kRingBytes + sizeof(TS) * (Bx::TILE + Bx::CBOX) + 15) / 16 * 16;
   static constexpr size_t WAREA = TB + (XB + 15) / 16 * 16;
-  static constexpr size_t SMEM = GTAB + NW * WAREA;
+  static constexpr size_t SMEM = GTAB + TABS + NW * WAREA;
+  static_assert(Bx::NPTS < (1 << 12) && DG::NX < (1 << 12), "table entries fit their fields");
 };
 
 template <typename T>
@@ -993,13 +998,36 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* sm = smem_as<unsigned char>(0);
   int32_t* gtab = reinterpret_cast<int32_t*>(sm);
-  unsigned char* wa = sm + DW::GTAB + warp * DW::WAREA;
+  int32_t* xtab = reinterpret_cast<int32_t*>(sm + DW::GTAB);
+  int32_t* otab = xtab + DG::NX;
+  unsigned char* wa = sm + DW::GTAB + DW::TABS + warp * DW::WAREA;
   Ring& R = *reinterpret_cast<Ring*>(wa);
   TS* tile = reinterpret_cast<TS*>(wa + kRingBytes);
   TS* cbox = tile + Bx::TILE;
   TS* scr = reinterpret_cast<TS*>(wa + DW::TB);  // gather scratch, then the x pass
   __shared__ int64_t snbo[DW::NW][PL::NB];
   build_gtab<2, B, 2>(gtab);
+  // x pass on coarse rows yc in [-1, NC - 2]: entry idx = (yc + 1) B + x holds
+  // the tile index of its first source node and whether x is odd (4 sources)
+  for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
+    const int x = idx % B, yy = 2 * (idx / B - 1);
+    const int odd = x & 1;
+    const int b0 = odd ? Bx::tix(x - 3, yy, 0) : Bx::tix(x, yy, 0);
+    xtab[idx] = b0 | (odd << 16);
+  }
+  // odd interior points: tile index, first x-pass entry of the y pass, j odd
+  for (int k = threadIdx.x; k < DW::NODD; k += blockDim.x) {
+    // k-th point (row-major) with (i | j) odd: rows j even hold (B - 1) / 2
+    // such points (odd i), rows j odd hold B
+    const int per2 = (B - 1) / 2 + B;  // points in a pair of rows (even j, odd j)
+    const int jp = k / per2, r = k % per2;
+    int i, j;
+    if (r < (B - 1) / 2) { j = 2 * jp; i = 2 * r + 1; }
+    else { j = 2 * jp + 1; i = r - (B - 1) / 2; }
+    const int jodd = j & 1;
+    const int xb = jodd ? ((j - 1) / 2) * B + i : (j / 2 + 1) * B + i;
+    otab[k] = Bx::tix(i, j, 0) | (xb << 12) | (jodd << 24);
+  }
   __syncthreads();
   const int nact = pv.cnt->n_round;
   const bool all_blocks = pv.cnt->first_round != 0;
@@ -1060,34 +1088,23 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
         fill_tile<2, B, TS, TS, 2, WarpGroup>(pv, b, y, y, tile, true, R, cbox, scr);
       }
       __syncwarp();
+      // the x pass over the coarse rows, then the y pass and the detail at
+      // each odd point, through the index tables (same operations as k_details)
       auto pass = [&](auto tag) -> decltype(tag) {
         using A = decltype(tag);
         A* XA = reinterpret_cast<A*>(scr);
         for (int idx = lane; idx < DG::NX; idx += 32) {
-          const int x = idx % B, yy = 2 * (idx / B - 1);
-          A val;
-          if ((x & 1) == 0) {
-            val = (A)tile[Bx::tix(x, yy, 0)];
-          } else {
-            const int n0 = (x - 1) / 2;
-            val = dd4((A)tile[Bx::tix(2 * n0 - 2, yy, 0)], (A)tile[Bx::tix(2 * n0, yy, 0)],
-                      (A)tile[Bx::tix(2 * n0 + 2, yy, 0)], (A)tile[Bx::tix(2 * n0 + 4, yy, 0)]);
-          }
-          XA[idx] = val;
+          const int e = xtab[idx];
+          const TS* t0 = tile + (e & 0xffff);
+          XA[idx] = (e >> 16) ? dd4((A)t0[0], (A)t0[2], (A)t0[4], (A)t0[6]) : (A)t0[0];
         }
         __syncwarp();
         A md = A(0);
-        for (int qn = lane; qn < Gm::NI; qn += 32) {
-          const int i = qn % B, j = qn / B;
-          if (((i | j) & 1) == 0) continue;
-          const A val = (A)tile[Bx::tix(i, j, 0)];
-          A pr;
-          if ((j & 1) == 0) {
-            pr = XA[(j / 2 + 1) * B + i];
-          } else {
-            const int m0 = (j - 1) / 2;
-            pr = dd4(XA[m0 * B + i], XA[(m0 + 1) * B + i], XA[(m0 + 2) * B + i], XA[(m0 + 3) * B + i]);
-          }
+        for (int k = lane; k < DW::NODD; k += 32) {
+          const int e = otab[k];
+          const A val = (A)tile[e & 0xfff];
+          const A* xa = XA + ((e >> 12) & 0xfff);
+          const A pr = (e >> 24) ? dd4(xa[0], xa[B], xa[2 * B], xa[3 * B]) : xa[0];
           md = fmax(md, (A)fabs(val - pr));
         }
         md = warp_max(md);
@@ -1095,18 +1112,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
         return md;
       };
       // largest |value| over the interior (stored, and the NaN check) and, for
-      // the certified FP32 evaluation, over the whole tile: one sweep
+      // the certified FP32 evaluation, over the whole tile: one sweep, the
+      // interior flag from the gather table
       constexpr bool cert = sizeof(TS) == 4 && sizeof(TD) == 8;
       TS mqs = TS(0), mts = TS(0);
       bool bad = false;
-      for (int qn = lane; qn < (cert ? Bx::TILE : Gm::NI); qn += 32) {
-        int i, j;
-        if (cert) { i = qn % Bx::S - 2; j = qn / Bx::S - 2; }
-        else { i = qn % B; j = qn / B; }
-        const TS sv = tile[Bx::tix(i, j, 0)];
+      for (int qn = lane; qn < Bx::TILE; qn += 32) {
+        const TS sv = tile[qn];
         const TS av = (TS)fabs(sv);
         if (cert) mts = fmax(mts, av);
-        if (i >= 0 && i < B && j >= 0 && j < B) {
+        if ((gtab[qn] >> 21) & 1) {
           mqs = fmax(mqs, av);
           bad |= !isfinite(sv);
         }
