@@ -717,6 +717,58 @@ __device__ __forceinline__ T block_max(T v, T* red) {
   return v;
 }
 
+// 2D detail index tables (per CTA, shared memory): the x pass on coarse rows
+// yc in [-1, NC - 2] (entry (yc + 1) B + x: tile index of its first source node,
+// x odd = 4 sources two nodes apart) and the odd interior points in row-major
+// order (tile index, first x-pass entry of the y pass, j odd = 4 entries B apart).
+template <int B>
+struct DetTab {
+  using Bx = Box<2, B, 2>;
+  using DG = DetGeo<2, B>;
+  static constexpr int NODD = B * B - ((B + 1) / 2) * ((B + 1) / 2);
+  static constexpr int INTS = DG::NX + NODD;
+  static_assert(Bx::NPTS < (1 << 12) && DG::NX < (1 << 12), "table entries fit their fields");
+  __device__ static void build(int32_t* xtab, int32_t* otab) {
+    for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
+      const int x = idx % B, yy = 2 * (idx / B - 1);
+      const int odd = x & 1;
+      const int b0 = odd ? Bx::tix(x - 3, yy, 0) : Bx::tix(x, yy, 0);
+      xtab[idx] = b0 | (odd << 16);
+    }
+    for (int k = threadIdx.x; k < NODD; k += blockDim.x) {
+      // rows j even hold (B - 1) / 2 odd points (odd i), rows j odd hold B
+      const int per2 = (B - 1) / 2 + B;
+      const int jp = k / per2, r = k % per2;
+      int i, j;
+      if (r < (B - 1) / 2) { j = 2 * jp; i = 2 * r + 1; }
+      else { j = 2 * jp + 1; i = r - (B - 1) / 2; }
+      const int jodd = j & 1;
+      const int xb = jodd ? ((j - 1) / 2) * B + i : (j / 2 + 1) * B + i;
+      otab[k] = Bx::tix(i, j, 0) | (xb << 12) | (jodd << 24);
+    }
+  }
+  // block maximum of |d| in type A over one variable's tile tv (G: CTA or warp;
+  // XA: NX values of scratch), the same operations as the point-wise evaluation
+  template <typename A, typename TV, typename G>
+  __device__ static A max_detail(const int32_t* xtab, const int32_t* otab, const TV* tv, A* XA, G g) {
+    for (int idx = g.rank(); idx < DG::NX; idx += g.size()) {
+      const int e = xtab[idx];
+      const TV* t0 = tv + (e & 0xffff);
+      XA[idx] = (e >> 16) ? dd4((A)t0[0], (A)t0[2], (A)t0[4], (A)t0[6]) : (A)t0[0];
+    }
+    g.sync();
+    A md = A(0);
+    for (int k = g.rank(); k < NODD; k += g.size()) {
+      const int e = otab[k];
+      const A val = (A)tv[e & 0xfff];
+      const A* xa = XA + ((e >> 12) & 0xfff);
+      const A pr = (e >> 24) ? dd4(xa[0], xa[B], xa[2 * B], xa[3 * B]) : xa[0];
+      md = fmax(md, (A)fabs(val - pr));
+    }
+    return md;
+  }
+};
+
 // Shared-memory layout of k_details after the ring and the tile: the coarse
 // box and prediction scratch of the gather, reused once the tile is complete
 // for the passes of the prediction (X, and in 3D the y pass Y).  A pass in
@@ -766,7 +818,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   const bool plan_ok = pv.cnt->plan_topo == pv.cnt->topo;
   const size_t xbytes = DS::region(nv);
   int32_t* gtab = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(X) + ((xbytes + 15) & ~(size_t)15));
-  if (D == 2) build_gtab<D, B, 2>(gtab);
+  int32_t* xtab = gtab + Bx::NPTS;  // 2D detail tables
+  int32_t* otab = xtab + DG::NX;
+  if constexpr (D == 2) {
+    build_gtab<D, B, 2>(gtab);
+    DetTab<B>::build(xtab, otab);
+  }
   // CTA-local work count and threshold scales (one atomic per CTA, not per block)
   unsigned long long ndet = 0;
   __shared__ double csv[kMaxVar];
@@ -858,6 +915,10 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     auto pass = [&](auto tag, const TT* tv) -> decltype(tag) {
       using A = decltype(tag);
       A* XA = reinterpret_cast<A*>(X);
+      if constexpr (D == 2) {
+        const A md = DetTab<B>::template max_detail<A>(xtab, otab, tv, XA, CtaGroup{});
+        return block_max<A>(md, reinterpret_cast<A*>(red[0]));
+      }
       for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
         const int x = idx % B, yc = (idx / B) % DG::NC - 1, zc = D == 3 ? idx / (B * DG::NC) - 1 : 0;
         const int yy = 2 * yc, zz = 2 * zc;
@@ -970,15 +1031,11 @@ struct DetW {
   using DG = DetGeo<2, B>;
   static constexpr int NW = NT / 32;
   static constexpr size_t GTAB = (4 * Bx::NPTS + 15) / 16 * 16;
-  // odd interior points (those with a detail), in row-major order
-  static constexpr int NODD = B * B - ((B + 1) / 2) * ((B + 1) / 2);
-  // per-CTA index tables: x pass sources (NX), odd points with their x-pass rows (NODD)
-  static constexpr size_t TABS = (4 * (DG::NX + NODD) + 15) / 16 * 16;
+  static constexpr size_t TABS = (4 * DetTab<B>::INTS + 15) / 16 * 16;  // detail index tables
   static constexpr size_t XB = sizeof(TS) * Bx::SCR > sizeof(TD) * DG::NX ? sizeof(TS) * Bx::SCR : sizeof(TD) * DG::NX;
   static constexpr size_t TB = (kRingBytes + sizeof(TS) * (Bx::TILE + Bx::CBOX) + 15) / 16 * 16;
   static constexpr size_t WAREA = TB + (XB + 15) / 16 * 16;
   static constexpr size_t SMEM = GTAB + TABS + NW * WAREA;
-  static_assert(Bx::NPTS < (1 << 12) && DG::NX < (1 << 12), "table entries fit their fields");
 };
 
 template <typename T>
@@ -1007,27 +1064,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
   TS* scr = reinterpret_cast<TS*>(wa + DW::TB);  // gather scratch, then the x pass
   __shared__ int64_t snbo[DW::NW][PL::NB];
   build_gtab<2, B, 2>(gtab);
-  // x pass on coarse rows yc in [-1, NC - 2]: entry idx = (yc + 1) B + x holds
-  // the tile index of its first source node and whether x is odd (4 sources)
-  for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
-    const int x = idx % B, yy = 2 * (idx / B - 1);
-    const int odd = x & 1;
-    const int b0 = odd ? Bx::tix(x - 3, yy, 0) : Bx::tix(x, yy, 0);
-    xtab[idx] = b0 | (odd << 16);
-  }
-  // odd interior points: tile index, first x-pass entry of the y pass, j odd
-  for (int k = threadIdx.x; k < DW::NODD; k += blockDim.x) {
-    // k-th point (row-major) with (i | j) odd: rows j even hold (B - 1) / 2
-    // such points (odd i), rows j odd hold B
-    const int per2 = (B - 1) / 2 + B;  // points in a pair of rows (even j, odd j)
-    const int jp = k / per2, r = k % per2;
-    int i, j;
-    if (r < (B - 1) / 2) { j = 2 * jp; i = 2 * r + 1; }
-    else { j = 2 * jp + 1; i = r - (B - 1) / 2; }
-    const int jodd = j & 1;
-    const int xb = jodd ? ((j - 1) / 2) * B + i : (j / 2 + 1) * B + i;
-    otab[k] = Bx::tix(i, j, 0) | (xb << 12) | (jodd << 24);
-  }
+  DetTab<B>::build(xtab, otab);
   __syncthreads();
   const int nact = pv.cnt->n_round;
   const bool all_blocks = pv.cnt->first_round != 0;
@@ -1093,20 +1130,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
       auto pass = [&](auto tag) -> decltype(tag) {
         using A = decltype(tag);
         A* XA = reinterpret_cast<A*>(scr);
-        for (int idx = lane; idx < DG::NX; idx += 32) {
-          const int e = xtab[idx];
-          const TS* t0 = tile + (e & 0xffff);
-          XA[idx] = (e >> 16) ? dd4((A)t0[0], (A)t0[2], (A)t0[4], (A)t0[6]) : (A)t0[0];
-        }
-        __syncwarp();
-        A md = A(0);
-        for (int k = lane; k < DW::NODD; k += 32) {
-          const int e = otab[k];
-          const A val = (A)tile[e & 0xfff];
-          const A* xa = XA + ((e >> 12) & 0xfff);
-          const A pr = (e >> 24) ? dd4(xa[0], xa[B], xa[2 * B], xa[3 * B]) : xa[0];
-          md = fmax(md, (A)fabs(val - pr));
-        }
+        A md = DetTab<B>::template max_detail<A>(xtab, otab, tile, XA, WarpGroup{});
         md = warp_max(md);
         __syncwarp();
         return md;

@@ -257,7 +257,8 @@ struct DetailsRun {
     using Bx = Box<D, B, 2>;
     const size_t tt = d64 ? sizeof(TS) : 4;  // tile type: the state type, FP32 for FP32 details
     const size_t region = d64 ? DetSmem<D, B, TS, double>::region(pv.nvar) : DetSmem<D, B, float, float>::region(pv.nvar);
-    const size_t smem = kRingBytes + tt * pv.nvar * Bx::TILE + 16 + region + 16 + (D == 2 ? 4 * Bx::NPTS : 0);
+    const size_t smem = kRingBytes + tt * pv.nvar * Bx::TILE + 16 + region + 16 +
+                        (D == 2 ? 4 * (Bx::NPTS + DetTab<B>::INTS) : 0);
     if (d64) {
       auto k = k_details<D, B, TS, double, threads>;
       prep_smem(k, smem);
