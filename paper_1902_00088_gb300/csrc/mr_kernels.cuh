@@ -607,6 +607,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine
     if (blockIdx.x == 0 && threadIdx.x == 0) set_err(pv, kErrCapacity);
     return;
   }
+  if (n_alloc == 0) return;  // no block refines: the list stays as it is
   const int nv = pv.nvar;
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const int slot = pv.act[p];
@@ -1189,6 +1190,7 @@ __global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y
   __shared__ int cs[8];
   const int nact = pv.cnt->n_round;
   const int nv = pv.nvar;
+  if (pv.cnt->n_new == nact) return;  // no family merges: the list stays as it is
   for (int p = blockIdx.x; p < nact; p += gridDim.x) {
     const int slot = pv.act[p];
     const int emit = pv.emit[2 * p], e = pv.eoff[2 * p];
@@ -1407,8 +1409,9 @@ __global__ void k_refine_commit(PoolView pv) {
   Counters* c = pv.cnt;
   const int nact = c->n_act, n_new = c->n_new, n_alloc = c->n_alloc, n_free = c->n_free;
   const bool ok = n_alloc <= n_free;
+  const bool any = n_alloc > 0;  // some block refines (else the tree and the list are unchanged)
   const int nch = 1 << D;
-  const int nmax = ok ? (nact > n_new ? nact : n_new) : 0;
+  const int nmax = ok && any ? (nact > n_new ? nact : n_new) : 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nmax; p += gridDim.x * blockDim.x) {
     const int32_t nxt = p < n_new ? pv.act_next[p] : 0;
     if (p < nact) {
@@ -1431,7 +1434,7 @@ __global__ void k_refine_commit(PoolView pv) {
     if (p < n_new) pv.act[p] = nxt;
   }
   if (last_cta(c)) {
-    if (ok) {
+    if (ok && any) {
       c->n_free = n_free - n_alloc + n_alloc / nch;
       c->n_act = n_new;
       c->topo += 1;
@@ -1599,8 +1602,9 @@ __global__ void k_coarsen_commit(PoolView pv) {
   Counters* c = pv.cnt;
   const int nround = c->n_round, n_free = c->n_free, n_new = c->n_new, rid = c->round_id;
   const bool done = c->done != 0;
-  const int ncopy = done ? 0 : n_new;
-  const int nmax = nround > ncopy ? nround : ncopy;
+  const bool none = n_new == nround;  // no family merges: the tree and the list are unchanged
+  const int ncopy = done || none ? 0 : n_new;
+  const int nmax = none ? 0 : (nround > ncopy ? nround : ncopy);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nmax; p += gridDim.x * blockDim.x) {
     const int32_t nxt = p < ncopy ? pv.act_next[p] : 0;
     if (p < nround) {
