@@ -87,13 +87,13 @@ WORKLOADS = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel, from one ncu capture per workload (profiles/), valid only for
 # the kernel sources it was taken on (digest below); otherwise reported as null.
-TRAFFIC_DIGEST = "31cac24c2007c68b"
+TRAFFIC_DIGEST = "9d17a105a2738a77"
 TRAFFIC = {
-    "swirl": ("k_stage_adv", (2.926080e6 + 2.003968e6) / 2),
-    "forest": ("k_stage_adv_w", 31.652608e6 + 4.096e3),
-    "uniform2d": ("k_stage_adv_w", 947.380480e6 + 569.066240e6),
-    "adv3d": ("k_stage_adv", 82.777856e6 + 14.296832e6),
-    "ns_thin": ("k_stage_ns", 1.317485e9 + 736.250880e6),
+    "swirl": ("k_stage_adv", (2.928384e6 + 2.005248e6) / 2),
+    "forest": ("k_stage_adv_w", 31.653632e6 + 11.776e3),
+    "uniform2d": ("k_stage_adv_w", 947.365888e6 + 569.117184e6),
+    "adv3d": ("k_stage_adv", 82.599168e6 + 13.831168e6),
+    "ns_thin": ("k_stage_ns", 1.317254e9 + 736.219648e6),
 }
 
 
