@@ -234,7 +234,7 @@ class Clocks:
 def oracle_sample(w, seconds_target=15.0):
     """Times the FP64 CPU oracle (single thread) on a bounded sample of the
     workload: same physics, Jmax reduced so a step takes seconds; returns
-    (points x stages / s, description)."""
+    (points x stages / s, description, steps, elapsed seconds)."""
     import oracle
     t = dict(w["tree"] if "tree" in w else w["trees"][0])
     umax = w.get("umax") or math.hypot(*t["rhs_params"][:2]) or 1.0
@@ -268,15 +268,17 @@ def run_reference(args, w, rank, world):
     import oracle
     oracle.build_oracle()
     per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
-    vals = []
+    vals, ms = [], []
     for s in range(args.warmup + args.steps):
-        v, desc, _, _ = oracle_sample(w, seconds_target=per_step)
+        v, desc, nst, el = oracle_sample(w, seconds_target=per_step)
         if s >= args.warmup:
             vals.append(v)
+            ms.append(1e3 * el / max(1, nst))
     value = sum(vals) / len(vals)
+    # ms_per_step: wall time of one oracle step of the sample (a reduced grid, stated in cpu_baseline)
     line = {"metric": "adaptive grid-points x RK-stages/sec", "value": value,
             "unit": "points*stages/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": w["name"] + " (oracle sample)", "l2_flush": "n/a (CPU)"},
