@@ -132,7 +132,6 @@ PoolView view(mr_ctx c) {
 }
 Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb}; }
 
-int64_t pmodh(int64_t a, int64_t n) { int64_t r = a % n; return r < 0 ? r + n : r; }
 
 // 1D factor tables of one tree on its finest lattice (node index U in [0, N)).
 void lattice_tables(const mr_params& p, const mr_tree_desc& t, int64_t N, double* out) {

@@ -1458,47 +1458,6 @@ __device__ __forceinline__ bool same_family(const PoolView& pv, int s, int t) {
 // assignment, reached here by evaluating the condition for the whole family.
 // Also emits the new-list counts (first member of a merged family hosts the
 // mother; other members free their slots).
-template <int D>
-__device__ __forceinline__ bool qualifies(const PoolView& pv, const TreeDev& td, int s, int lane,
-                                          double* mdet_out) {
-  const BlockInfo b = load_block(pv, s);
-  const int nv = pv.nvar;
-  double m = 0.0;
-  bool nan = false;
-  for (int v = 0; v < nv; ++v) {
-    double sv = pv.svar[b.tree * nv + v];
-    if (sv == 0.0) sv = 1.0;
-    const double mv = pv.md[(int64_t)s * nv + v];
-    nan |= isnan(mv);
-    m = fmax(m, mv / sv);
-  }
-  if (nan) m = __longlong_as_double(0x7ff8000000000000LL);
-  if (mdet_out) *mdet_out = m;
-  bool ok = (m < td.eps) && b.lvl > td.Jmin;
-  // lanes: 0..2^d-1 sisters, then the ring cells outside the block
-  constexpr int NR = D == 3 ? 64 : 16;
-  bool fail = false;
-  for (int r = lane; r < (1 << D) + NR; r += 32) {
-    if (r < (1 << D)) {
-      int64_t c[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((r >> a) & 1);
-      fail |= tab_get<D>(pv, td, b.lvl, c) < 0;
-    } else {
-      const int q = r - (1 << D);
-      const int qq[3] = {q % 4 - 1, (q / 4) % 4 - 1, q / 16 - 1};
-      bool inside = true;
-      int64_t cell[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) {
-        inside &= (qq[a] == 0 || qq[a] == 1);
-        cell[a] = 2 * b.c[a] + qq[a];
-      }
-      if (!inside) fail |= tab_get<D>(pv, td, b.lvl + 1, cell) >= 0;
-    }
-  }
-  fail = __any_sync(0xffffffffu, fail);
-  return ok && !fail;
-}
-
 template <int D, bool SCAN>
 __global__ void __launch_bounds__(256) k_flags(PoolView pv) {
   pdl_enter();
