@@ -1479,6 +1479,47 @@ __global__ void __launch_bounds__(256) k_flags(PoolView pv) {
     const TreeDev& td = pv.trees[b.tree];
     int64_t fc[3] = {0, 0, 0};
     for (int a = 0; a < D; ++a) fc[a] = b.c[a] & ~(int64_t)1;
+    // normalised detail m of leaf t (NaN if a variable's is) and m < eps
+    auto detail = [&](int t, double& m) -> bool {
+      if (pv.norm_kind == 0) {
+        // unnormalised: a maximum of non-negative values (or NaN), taken and
+        // compared with eps > 0 on their bit patterns, which order as the values
+        long long mb = 0;
+        bool nan = false;
+        for (int v = 0; v < nv; ++v) {
+          const long long x = __double_as_longlong(pv.md[(int64_t)t * nv + v]);
+          nan |= (x & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+          mb = x > mb ? x : mb;
+        }
+        if (nan) mb = 0x7ff8000000000000LL;
+        m = __longlong_as_double(mb);
+        return !nan && mb < __double_as_longlong(td.eps);
+      }
+      bool nan = false;
+      m = 0.0;
+      for (int v = 0; v < nv; ++v) {
+        double sv = pv.svar[b.tree * nv + v];
+        if (sv == 0.0) sv = 1.0;
+        const double mv = pv.md[(int64_t)t * nv + v];
+        nan |= isnan(mv);
+        m = fmax(m, mv / sv);
+      }
+      if (nan) m = __longlong_as_double(0x7ff8000000000000LL);
+      return m < td.eps;
+    };
+    if (b.lvl <= td.Jmin) {
+      // a family at Jmin never merges: only the block's own detail is recorded
+      if (lane == 0) {
+        double m;
+        detail(s, m);
+        pv.mdet[s] = m;
+        if (isnan(m)) set_err(pv, kErrNaN);
+        pv.flag[s] = 0;
+        pv.emit[2 * p] = 1;
+        pv.emit[2 * p + 1] = 0;
+      }
+      continue;
+    }
     // sisters: exist as leaves and below eps
     bool ok = true;
     double mine = 0.0;
@@ -1490,31 +1531,7 @@ __global__ void __launch_bounds__(256) k_flags(PoolView pv) {
         ok = false;
       } else {
         double m = 0.0;
-        if (pv.norm_kind == 0) {
-          // unnormalised: a maximum of non-negative values (or NaN), taken and
-          // compared with eps > 0 on their bit patterns, which order as the values
-          long long mb = 0;
-          bool nan = false;
-          for (int v = 0; v < nv; ++v) {
-            const long long x = __double_as_longlong(pv.md[(int64_t)t * nv + v]);
-            nan |= (x & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
-            mb = x > mb ? x : mb;
-          }
-          if (nan) mb = 0x7ff8000000000000LL;
-          m = __longlong_as_double(mb);
-          ok = !nan && mb < __double_as_longlong(td.eps);
-        } else {
-          bool nan = false;
-          for (int v = 0; v < nv; ++v) {
-            double sv = pv.svar[b.tree * nv + v];
-            if (sv == 0.0) sv = 1.0;
-            const double mv = pv.md[(int64_t)t * nv + v];
-            nan |= isnan(mv);
-            m = fmax(m, mv / sv);
-          }
-          if (nan) m = __longlong_as_double(0x7ff8000000000000LL);
-          ok = m < td.eps;
-        }
+        ok = detail(t, m);
         if (t == s) mine = m;
       }
     }
