@@ -87,7 +87,7 @@ WORKLOADS = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel, from one ncu capture per workload (profiles/), valid only for
 # the kernel sources it was taken on (digest below); otherwise reported as null.
-TRAFFIC_DIGEST = "978587703c6c5a46"
+TRAFFIC_DIGEST = "a8a63f3cc3ac68d3"
 TRAFFIC = {
     "swirl": ("k_stage_adv", (2.928384e6 + 2.005248e6) / 2),
     "forest": ("k_stage_adv_w", 31.653632e6 + 11.776e3),

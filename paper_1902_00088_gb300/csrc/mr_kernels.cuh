@@ -353,8 +353,9 @@ __device__ __forceinline__ void plan_one(const PoolView& pv, int p) {
   int64_t c[3] = {0, 0, 0};
   for (int a = 0; a < D; ++a) c[a] = pv.crd[3 * s + a];
   int32_t* out = pv.plan + (int64_t)p * PL::INTS;
-  bool uni = true;
-#pragma unroll 1
+  // all lookups first (independent loads, in flight together), then the stores
+  int32_t qn[PL::NB];
+#pragma unroll
   for (int n = 0; n < PL::NB; ++n) {
     const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
     int q = s;
@@ -362,8 +363,13 @@ __device__ __forceinline__ void plan_one(const PoolView& pv, int p) {
       const int64_t cn[3] = {c[0] + o[0], c[1] + o[1], c[2] + o[2]};
       q = tab_get<D>(pv, td, l, cn);
     }
-    uni &= q >= 0;
-    out[PL::NBO + n] = q;
+    qn[n] = q;
+  }
+  bool uni = true;
+#pragma unroll
+  for (int n = 0; n < PL::NB; ++n) {
+    uni &= qn[n] >= 0;
+    out[PL::NBO + n] = qn[n];
   }
   out[0] = s;
   out[1] = l | (t << 8) | (uni ? 1 << 30 : 0);
