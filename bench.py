@@ -289,6 +289,33 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6)):
+    """The swirl study of Sec. 3 (Fig. 4A-D as data): 33^2 blocks, blob beta 1e-2 at (0.5, 0.75), t_a 5,
+    Jmin 1, CFL 0.5, plain FP64, steps replayed as CUDA graphs up to t_a; per run the error against the
+    initial field, the adapted grid's size against the uniform one and the time per step."""
+    import numpy as np
+    import paper_1902_00088_gb300 as mr
+    t_a = 5.0
+    for jmax in jmaxs:
+        for eps in epss:
+            tree = dict(Jmin=1, Jmax=jmax, eps=eps, ic="gauss", ic_params=(0.5, 0.75, 0.0, math.sqrt(0.005)),
+                        rhs_params=(t_a,))
+            g = mr.Forest(dim=2, Bs=33, precision="fp64", rhs="swirl", trees=[tree], capacity=200_000)
+            g.init_tree()
+            n = int(math.ceil(t_a / (0.5 / (32 * (1 << jmax)))))
+            g.set_time(0.0, t_a / n)
+            g.step_history(reset=True)
+            t0 = time.time()
+            g.step_graph(n)
+            hist = g.step_history(reset=True)
+            el = time.time() - t0
+            err = g.error(0, 0.0)
+            print(json.dumps(dict(study="swirl33", Jmax=jmax, eps=eps, steps=n, l2=err["l2"], linf=err["linf"],
+                                  blocks_mean=float(np.mean(hist)), blocks_max=int(np.max(hist)),
+                                  uniform_blocks=4 ** jmax, ms_per_step=1e3 * el / n)), flush=True)
+            del g
+
+
 def reduce_over_ranks(ms, points, world):
     """Whole-job figures over the ranks: the slowest rank's time (the job ends
     with it) and the points all ranks advanced (each rank runs its own
@@ -330,7 +357,9 @@ def main():
                     help="swirl: do not run on to t = t_a for the error (timed window only)")
     ap.add_argument("--eager", action="store_true", help="host-driven steps instead of CUDA graph replays")
     ap.add_argument("--autotune", type=int, default=-1, help="steps per autotuner candidate (0 = off)")
-    ap.add_argument("--no-overlap", action="store_true", help="plain kernel launches (no programmatic dependent launch)")
+    ap.add_argument("--overlap", action="store_true", help="programmatic dependent launch of the step's kernels")
+    ap.add_argument("--study", default="", choices=["", "swirl33"],
+                    help="instead of the benchmark: the paper's swirl study (33^2 blocks, eps x Jmax), one JSON line per run")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
@@ -364,6 +393,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
+    if args.study:
+        if rank == 0:
+            swirl_study()
+        return
 
     import numpy as np
     import torch
@@ -383,8 +416,8 @@ def main():
     g = mr.Forest(dim=w["dim"], Bs=w["Bs"], nvar=w.get("nvar", 1), precision=w["precision"],
                   detail_fp64=w["detail_fp64"], rhs=w["rhs"], trees=trees, capacity=w["capacity"],
                   norm_kind=w.get("norm_kind", 0), stream=stream.cuda_stream)
-    if args.no_overlap:
-        g.set_launch_overlap(False)
+    if args.overlap:
+        g.set_launch_overlap(True)
     B, d = w["Bs"], w["dim"]
     npts = B ** d
     dts = np.array(dts_of(w))
