@@ -6,7 +6,9 @@
   matches it with 4th-order convergence in the grid spacing;
 * viscous and heat-flux terms: N(q) of a smooth periodic state converges at
   4th order to an FFT evaluation of the textbook equations written here
-  independently of the oracle.
+  independently of the oracle;
+* conservation: N(q) of each conserved variable sums to zero over a periodic
+  grid.
 """
 import math
 
@@ -113,3 +115,24 @@ def test_viscous_rhs_converges_to_spectral_reference(oracle_mod):
                 e = max(e, np.abs(k[q, var] - ref[var][np.ix_(iy, ix)]).max())
         errs.append(e)
     assert errs[1] < 1e-3 and math.log2(errs[0] / errs[1]) > 3.5, errs
+
+
+def test_conservative_form_sums_to_zero_on_periodic_grid(oracle_mod):
+    # The conservative flux form (r19) conserves mass, momentum and energy: on a
+    # uniform periodic grid every flux difference telescopes, so the sum of N(q)
+    # over the unique nodes vanishes for each conserved variable up to rounding,
+    # while the individual terms do not.  An asymmetric stencil or a term taken
+    # outside the flux divergence breaks this.
+    mu = 0.02
+    prim = lambda X, Y: (1.0 + 0.2 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y),
+                         0.3 + 0.1 * np.sin(2 * np.pi * Y),
+                         -0.2 + 0.1 * np.cos(2 * np.pi * X),
+                         1.0 + 0.1 * np.sin(2 * np.pi * (X + Y)))
+    lvl = 3
+    o = ns_oracle(oracle_mod, lvl, mu)
+    set_state(o, lvl, prim)
+    k = o.rhs(0.0)[:, :, :16, :16]  # unique nodes: each block's last node per axis is its neighbour's first
+    for var in range(4):
+        s, a = k[:, var].sum(), np.abs(k[:, var]).sum()
+        assert a > 1.0, (var, a)
+        assert abs(s) <= 1e-12 * a, (var, s, a)
