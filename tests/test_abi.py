@@ -79,3 +79,15 @@ def test_every_kernel_waits_for_its_predecessor_first():
             assert body.startswith("pdl_enter();"), (f, txt[m.start():m.start() + 80])
             n += 1
     assert n > 40
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # No CPU fallback: without the built library the binding raises instead of
+    # running anything else.
+    import paper_1902_00088_gb300 as m
+    saved, m._lib = m._lib, None  # the loaded library is cached per process
+    try:
+        with pytest.raises(ImportError):
+            m.load_library(str(tmp_path / "absent" / "libmr.so"))
+    finally:
+        m._lib = saved
