@@ -554,6 +554,37 @@ struct Tree {
     return n;
   }
 
+  // ------------------------------------------------- refinement status +1 ---
+  // Refinement indicators (Sec. 2.3, status +1) must keep the grid graded
+  // (Sec. 2.2: blocks that touch differ by at most one level).  Refining a
+  // block of level l creates blocks of level l + 1, so a touching leaf of level
+  // l - 1 would end up two levels coarser: it must be refined as well.  The
+  // rule is applied until no status changes; it only turns 0 into +1, so the
+  // result does not depend on the visiting order.  Blocks at Jmax are never
+  // refined and force nothing.  Returns the number of statuses raised.
+  int close_refine() {
+    int added = 0;
+    bool changed = true;
+    const std::vector<Rel> rels = relations();
+    while (changed) {
+      changed = false;
+      for (auto& kv : lv) {
+        Leaf& b = kv.second;
+        if (b.flag != 1 || b.lvl >= p.Jmax) continue;
+        for (const Rel& r : rels) {
+          int dl = 0;
+          Leaf* f = neighbour(b, r, &dl);
+          if (f && dl == -1 && f->flag != 1) {
+            f->flag = 1;
+            ++added;
+            changed = true;
+          }
+        }
+      }
+    }
+    return added;
+  }
+
   // ----------------------------------------------------------- coarsen ------
   // Coarsening (Sec. 2.3): 2^d sisters with status -2 merge into their mother by
   // the restriction R (every second node is kept); the last treecode digit is
@@ -942,6 +973,19 @@ void orc_set_blocks(void* h, int64_t n, const int32_t* lvl, const int64_t* crd, 
     T->lv[T->key(b.lvl, b.c)] = b;
   }
 }
+// Refinement statuses of the blocks, given in Hilbert order (replay of
+// externally decided flags, e.g. a proposal of refinement indicators).
+void orc_set_flags(void* h, const int8_t* flag) {
+  std::vector<Leaf*> o = ((Tree*)h)->ordered();
+  for (size_t n = 0; n < o.size(); ++n) o[n]->flag = flag[n];
+}
+// Largest details of the blocks, given in Hilbert order (replaces details()
+// when the flag rule is examined on its own).
+void orc_set_mdet(void* h, const double* mdet) {
+  std::vector<Leaf*> o = ((Tree*)h)->ordered();
+  for (size_t n = 0; n < o.size(); ++n) o[n]->mdet = mdet[n];
+}
+int orc_close_refine(void* h) { return ((Tree*)h)->close_refine(); }
 // Analytic initial field on the current blocks (advected by t for constant u).
 void orc_set_ic(void* h, double t) {
   Tree* T = (Tree*)h;

@@ -73,6 +73,9 @@ def _load():
         lib.orc_neighbors.restype = None
         lib.orc_rhs.argtypes = [vp, C.c_double, C.c_void_p]; lib.orc_rhs.restype = None
         lib.orc_error.argtypes = [vp, C.c_double, C.c_void_p]; lib.orc_error.restype = None
+        lib.orc_set_flags.argtypes = [vp, C.c_void_p]; lib.orc_set_flags.restype = None
+        lib.orc_set_mdet.argtypes = [vp, C.c_void_p]; lib.orc_set_mdet.restype = None
+        lib.orc_close_refine.argtypes = [vp]; lib.orc_close_refine.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -140,6 +143,22 @@ class Oracle:
 
     def step(self, t, dt):
         self.lib.orc_step(self.h, t, dt)
+
+    def close_refine(self):
+        """Gradedness closure of the +1 statuses (Sec. 2.2, 2.3); returns the number raised."""
+        return self.lib.orc_close_refine(self.h)
+
+    def set_flags(self, flags):
+        """Refinement statuses in Hilbert (export) order."""
+        f = np.ascontiguousarray(flags, np.int8)
+        assert len(f) == self.n
+        self.lib.orc_set_flags(self.h, _ptr(f))
+
+    def set_mdet(self, mdet):
+        """Largest block details in Hilbert (export) order."""
+        m = np.ascontiguousarray(mdet, np.float64)
+        assert len(m) == self.n
+        self.lib.orc_set_mdet(self.h, _ptr(m))
 
     def set_ic(self, t=0.0):
         self.lib.orc_set_ic(self.h, t)

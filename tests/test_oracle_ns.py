@@ -118,8 +118,9 @@ def test_viscous_rhs_converges_to_spectral_reference(oracle_mod):
 
 
 def test_conservative_form_sums_to_zero_on_periodic_grid(oracle_mod):
-    # The conservative flux form (r19) conserves mass, momentum and energy: on a
-    # uniform periodic grid every flux difference telescopes, so the sum of N(q)
+    # The right-hand side is written as a flux divergence, N(q) = -(dF/dx + dG/dy)
+    # with the compressible Navier-Stokes fluxes of Sec. 4, so it conserves mass,
+    # momentum and energy: on a uniform periodic grid every flux difference telescopes, so the sum of N(q)
     # over the unique nodes vanishes for each conserved variable up to rounding,
     # while the individual terms do not.  An asymmetric stencil or a term taken
     # outside the flux divergence breaks this.
