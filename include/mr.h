@@ -206,8 +206,10 @@ mr_status mr_error(mr_ctx ctx, int32_t tree, double t, double* out);
  * the paper.  Its scratch (three factor tables and four accumulators) lives in
  * one file-scope device array of 3 * 16384 + 4 doubles that every GPU loading
  * the library keeps until exit; (Bs-1) * 2^Jmax of the tree must be <= 16384,
- * else MR_EINVAL.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * else MR_EINVAL.  The call makes the context's device current for its
+ * duration (the caller's current device is restored); its first call on a
+ * device looks up the array's address there (cudaGetSymbolAddress, once per
+ * device even with concurrent host threads): make it before any stream
  * capture.  All calls on a device share the array; the accumulators are cleared
  * at the start of each call, and calls that overlap on the GPU race on it.
  * Synchronises. */

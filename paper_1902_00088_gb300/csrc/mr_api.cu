@@ -14,6 +14,7 @@
 #include <numeric>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1480,25 +1481,40 @@ static __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMaxN + 4];
 namespace {
 
 constexpr int kMaxDevices = 64;
+std::once_flag g_noalloc_once[kMaxDevices];
 double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+cudaError_t g_noalloc_err[kMaxDevices] = {cudaSuccess};
 
-// Device address of the scratch array for the current device.  In host code
-// the array's name is only a stand-in, so the address is looked up once per
-// device (with that device current) and cached.
-cudaError_t noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of the scratch array on device `dev`, which must be the
+// current device.  In host code the array's name is only a stand-in, so the
+// address is looked up once per device (std::call_once: concurrent first calls
+// from several host threads look it up once) and cached.
+cudaError_t noalloc_scratch(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_noalloc_ptr[dev]) {
+  std::call_once(g_noalloc_once[dev], [dev] {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = (double*)p;
-  }
+    g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (g_noalloc_err[dev] == cudaSuccess) g_noalloc_ptr[dev] = (double*)p;
+  });
+  if (g_noalloc_err[dev] != cudaSuccess) return g_noalloc_err[dev];
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;
 }
+
+// Makes the context's device current for the lifetime of the guard and
+// restores the caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    else if (err == cudaSuccess) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 // Factor tables of the exact field (Gaussian advected by constant u over t):
 // ex[a][U] = exp(-d^2 / (2 sigma^2)), d the nearest periodic image of
@@ -1532,8 +1548,12 @@ extern "C" mr_status mr_error_noalloc(mr_ctx ctx, int32_t tree, double t, double
   if (N > kNoAllocMaxN)
     return fail(ctx, MR_EINVAL, "mr_error_noalloc: (Bs-1)*2^Jmax = " + std::to_string(N) +
                                     " exceeds its scratch limit of " + std::to_string(kNoAllocMaxN));
+  // the scratch array of the context's device (not of whatever device the
+  // caller has current)
+  DeviceGuard guard(ctx->dev);
+  CK(guard.err);
   double* scratch = nullptr;
-  CK(noalloc_scratch(&scratch));
+  CK(noalloc_scratch(ctx->dev, &scratch));
   double* ex = scratch;
   double* acc = scratch + 3 * kNoAllocMaxN;
   double sh[3] = {0.0, 0.0, 0.0};
@@ -1542,6 +1562,7 @@ extern "C" mr_status mr_error_noalloc(mr_ctx ctx, int32_t tree, double t, double
   k_noalloc_tables<<<ctx->lc.num_sms * 2, 256, 0, ctx->st>>>(ex, N, ctx->p.dim, ctx->p.L, td.x0[0], td.x0[1],
                                                             td.x0[2], sh[0], sh[1], sh[2], td.ic[0], td.ic[1],
                                                             td.ic[2], td.ic[3]);
+  CK(cudaGetLastError());
   count_launch();
   PoolView pv = view(ctx);
   by_dim(ctx, [&] { launch_error<2>(pv, fields(ctx), tree, ex, acc, ctx->lc, ctx->st); },
