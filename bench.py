@@ -5,7 +5,7 @@ are sum over the blocks of the adapted grid G (before the safety refinement) of
 Bs^d, times 4 stages; the time is the whole mr_step (refine-all, 4 x (ghost
 sync + RK stage), coarsening rounds, tree rebuild).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload swirl|adv3d|adv2d|forest|ns]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload adv3d|swirl|adv2d|forest|ns|ns_thin|...]
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
 
 Prints one JSON line on rank 0.
@@ -258,7 +258,8 @@ def oracle_sample(w, seconds_target=15.0):
             break
     el = time.perf_counter() - t0
     desc = ("FP64 oracle, 1 thread, %d step(s) of the same workload with Jmin %d, Jmax %d "
-            "(%d..%d blocks)" % (steps, jmin, jmax, o.n, o.n))
+            "(%d blocks at the end) instead of the timed Jmin %d, Jmax %d; rate per adapted point and stage"
+            % (steps, jmin, jmax, o.n, t["Jmin"], t["Jmax"]))
     return pts / el, desc, steps, el
 
 
@@ -289,31 +290,43 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6)):
+def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,)):
     """The swirl study of Sec. 3 (Fig. 4A-D as data): 33^2 blocks, blob beta 1e-2 at (0.5, 0.75), t_a 5,
     Jmin 1, CFL 0.5, plain FP64, steps replayed as CUDA graphs up to t_a; per run the error against the
     initial field, the adapted grid's size against the uniform one and the time per step."""
     import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1902_00088_gb300 as mr
+    stream = torch.cuda.Stream()
     t_a = 5.0
-    for jmax in jmaxs:
-        for eps in epss:
-            tree = dict(Jmin=1, Jmax=jmax, eps=eps, ic="gauss", ic_params=(0.5, 0.75, 0.0, math.sqrt(0.005)),
-                        rhs_params=(t_a,))
-            g = mr.Forest(dim=2, Bs=33, precision="fp64", rhs="swirl", trees=[tree], capacity=200_000)
-            g.init_tree()
-            n = int(math.ceil(t_a / (0.5 / (32 * (1 << jmax)))))
-            g.set_time(0.0, t_a / n)
-            g.step_history(reset=True)
-            t0 = time.time()
-            g.step_graph(n)
-            hist = g.step_history(reset=True)
-            el = time.time() - t0
-            err = g.error(0, 0.0)
-            print(json.dumps(dict(study="swirl33", Jmax=jmax, eps=eps, steps=n, l2=err["l2"], linf=err["linf"],
-                                  blocks_mean=float(np.mean(hist)), blocks_max=int(np.max(hist)),
-                                  uniform_blocks=4 ** jmax, ms_per_step=1e3 * el / n)), flush=True)
-            del g
+    for beta, jmax, eps in ((b, j, e) for b in betas for j in jmaxs for e in epss):
+        # Sec. 3: phi_0 = exp(-r^2 / beta) = exp(-r^2 / (2 sigma^2)), sigma = sqrt(beta / 2)
+        tree = dict(Jmin=1, Jmax=jmax, eps=eps, ic="gauss", ic_params=(0.5, 0.75, 0.0, math.sqrt(beta / 2)),
+                    rhs_params=(t_a,))
+        g = mr.Forest(dim=2, Bs=33, precision="fp64", rhs="swirl", trees=[tree], capacity=200_000,
+                      stream=stream.cuda_stream)
+        g.init_tree()
+        n = int(math.ceil(t_a / (0.5 / (32 * (1 << jmax)))))
+        g.set_time(0.0, t_a / n)
+        g.step_graph(1)  # captures the step graph (untimed)
+        g.step_history(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step_graph(n - 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        el = e0.elapsed_time(e1) / 1e3
+        hist = g.step_history(reset=True)
+        err = g.error(0, 0.0)
+        print(json.dumps(dict(study="swirl33", beta=beta, Jmax=jmax, eps=eps, steps=n, l2=err["l2"], linf=err["linf"],
+                              blocks_mean=float(np.mean(hist)), blocks_max=int(np.max(hist)),
+                              uniform_blocks=4 ** jmax, ms_per_step=1e3 * el / (n - 1),
+                              timing="CUDA events around graph replays 2..n on the context's stream")),
+              flush=True)
+        del g
 
 
 def reduce_over_ranks(ms, points, world):
@@ -348,7 +361,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--workload", default="swirl", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="adv3d", choices=sorted(WORKLOADS))
     ap.add_argument("--capacity", type=int, default=0)
     ap.add_argument("--eps", type=float, default=0.0)
     ap.add_argument("--precision", default="", choices=["", "fp64", "fp32", "fp32_acc64"],
@@ -360,6 +373,9 @@ def main():
     ap.add_argument("--overlap", action="store_true", help="programmatic dependent launch of the step's kernels")
     ap.add_argument("--study", default="", choices=["", "swirl33"],
                     help="instead of the benchmark: the paper's swirl study (33^2 blocks, eps x Jmax), one JSON line per run")
+    ap.add_argument("--study-jmax", default="4,5", help="swirl33: comma-separated Jmax values")
+    ap.add_argument("--study-eps", default="1e-3,1e-4,1e-5,1e-6", help="swirl33: comma-separated eps values")
+    ap.add_argument("--study-beta", default="1e-2", help="swirl33: comma-separated pulse widths beta")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
@@ -395,7 +411,9 @@ def main():
         return
     if args.study:
         if rank == 0:
-            swirl_study()
+            swirl_study(jmaxs=[int(x) for x in args.study_jmax.split(",")],
+                        epss=[float(x) for x in args.study_eps.split(",")],
+                        betas=[float(x) for x in args.study_beta.split(",")])
         return
 
     import numpy as np

@@ -65,9 +65,18 @@ typedef int32_t mr_status;
 
 /* mr_adapt modes (Sec. 2.1 / 2.3). */
 #define MR_ADAPT_REFINE_ALL 0      /* every block below Jmax gains one level */
-#define MR_ADAPT_REFINE_FLAGGED 1  /* blocks whose refinement mask is +1 (mr_set_refine_mask) */
+#define MR_ADAPT_REFINE_FLAGGED 1  /* refinement indicators (status +1, Sec. 2.3) from the caller's
+                                      mask (mr_set_refine_mask), closed under gradedness (Sec. 2.2:
+                                      a leaf one level coarser than a refined block is refined too,
+                                      until nothing changes), then refined */
 #define MR_ADAPT_COARSEN 2         /* detail thresholding + completeness/gradedness, merge */
 #define MR_ADAPT_FLAGS_ONLY 3      /* details and flags of the current grid, no merge (inspection) */
+#define MR_ADAPT_PROPOSE 4         /* learned proposal only (needs MR_REFINE_LEARNED): flags = +1
+                                      where the network or the exact fallback asks for refinement,
+                                      before the gradedness closure; no refinement (inspection and
+                                      replay; read with mr_get_flags) */
+#define MR_ADAPT_REFINE_STEP 5     /* the refinement mr_step performs: refine all, or (learned mode)
+                                      proposal + fallback + gradedness closure + refinement */
 
 typedef struct {
   int32_t dim;          /* 2 or 3 */
@@ -189,7 +198,8 @@ mr_status mr_set_blocks(mr_ctx ctx, int64_t n, const int32_t* level, const int32
                         const int32_t* coords, const double* fields);
 
 /* Per-block refinement mask for MR_ADAPT_REFINE_FLAGGED, canonical order over
- * all trees (n = total block count): +1 refine, 0 keep. */
+ * all trees (n = total block count): +1 refine, 0 keep.  Blocks at Jmax are
+ * never refined; the gradedness closure may add blocks. */
 mr_status mr_set_refine_mask(mr_ctx ctx, int64_t n, const int8_t* mask);
 
 /* Error of tree against the analytic IC advected by constant u over time t (for
@@ -283,6 +293,14 @@ mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n,
  * uses one warp per block once the grid holds at least 8 blocks per SM.
  * Synchronises. */
 mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best);
+/* Fixes the launch configuration instead of the autotuner: ctas_per_sm
+ * persistent CTAs per SM for the block kernels (0 = as many as occupancy
+ * allows, at most 32) and the form of the 2D stage and details kernels on 17^2
+ * advection blocks (stage_form 1 = one warp per block, 0 = one CTA per block,
+ * -1 = by block count: warps once the grid holds 8 blocks per SM).  Results do
+ * not depend on either choice.  MR_EINVAL for values out of range or the warp
+ * form where it does not exist.  Drops the captured step. */
+mr_status mr_set_tuning(mr_ctx ctx, int32_t ctas_per_sm, int32_t stage_form);
 /* Synchronises; accumulates pending timers into *out. */
 mr_status mr_get_stats(mr_ctx ctx, mr_stats* out);
 mr_status mr_reset_stats(mr_ctx ctx);

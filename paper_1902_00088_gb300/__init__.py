@@ -17,7 +17,8 @@ MR_OK, MR_EINVAL, MR_ENOMEM, MR_ECAPACITY, MR_ECUDA, MR_ETIMEOUT, MR_ENAN, MR_EI
 PREC = {"fp64": 0, "fp32": 1, "fp32_acc64": 2}
 RHS = {"adv": 0, "swirl": 1, "ns": 2}
 IC = {"gauss": 0, "mixing": 1, "none": 2}
-ADAPT = {"refine_all": 0, "refine_flagged": 1, "coarsen": 2, "flags_only": 3}
+ADAPT = {"refine_all": 0, "refine_flagged": 1, "coarsen": 2, "flags_only": 3, "propose": 4,
+         "refine_step": 5}
 STATUS = {0: "MR_OK", 1: "MR_EINVAL", 2: "MR_ENOMEM", 3: "MR_ECAPACITY", 4: "MR_ECUDA",
           5: "MR_ETIMEOUT", 6: "MR_ENAN", 7: "MR_EINTERNAL"}
 
@@ -90,6 +91,7 @@ SIGNATURES = {
     "mr_get_launch_overlap": (_i32, [_vp]),
     "mr_get_step_history": (_i32, [_vp, _i64, _vp, C.POINTER(C.c_int64), _i32]),
     "mr_autotune": (_i32, [_vp, _i32, C.POINTER(C.c_int32)]),
+    "mr_set_tuning": (_i32, [_vp, _i32, _i32]),
     "mr_set_refine_mode": (_i32, [_vp, _i32]),
     "mr_proposal_collect": (_i32, [_vp, _i32, _i64]),
     "mr_proposal_dataset": (_i32, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -310,6 +312,11 @@ class Forest:
     CNN_PARAMS = 4961
     # parameter packing of the proposal network: W1, b1, W2, b2, W3, b3, wl, bl
     CNN_SHAPES = [(16, 2, 3, 3), (16,), (16, 16, 3, 3), (16,), (16, 16, 3, 3), (16,), (16,), (1,)]
+
+    def set_tuning(self, ctas_per_sm=0, stage_form=-1):
+        """Launch configuration: CTAs per SM (0 = occupancy) and the 2D stage form
+        (1 warp per block, 0 CTA per block, -1 by block count)."""
+        self._ck(self.lib.mr_set_tuning(self.h, ctas_per_sm, stage_form))
 
     def set_refine_mode(self, mode):
         self._ck(self.lib.mr_set_refine_mode(self.h, {"all": 0, "learned": 1}.get(mode, mode)))

@@ -308,7 +308,6 @@ mr_status ensure_cnn(mr_ctx ctx) {
   CK(cudaMalloc(&ctx->skip, ctx->S));
   CK(cudaMalloc(&ctx->skip_key, ctx->S * 4));
   CK(cudaMalloc(&ctx->pcounts, 4 * 4));
-  CK(cudaMalloc(&ctx->changed, 4));
   CK(cudaMalloc(&ctx->gcounts, 5 * 4));
   CK(cudaMemset(ctx->gcounts, 0, 5 * 4));
   CK(cudaMemset(ctx->cnn_w, 0, kCnnParams * 4));
@@ -318,7 +317,7 @@ mr_status ensure_cnn(mr_ctx ctx) {
   CK(cudaMemset(ctx->skip, 0, ctx->S));
   for (void* q : {(void*)ctx->cnn_w, (void*)ctx->cnn_m, (void*)ctx->cnn_v, (void*)ctx->cnn_g,
                   (void*)ctx->cnn_wb, (void*)ctx->skip, (void*)ctx->skip_key, (void*)ctx->pcounts,
-                  (void*)ctx->changed, (void*)ctx->gcounts})
+                  (void*)ctx->gcounts})
     ctx->owned.push_back(q);
   return MR_OK;
 }
@@ -333,6 +332,53 @@ mr_status ensure_feat(mr_ctx ctx, int64_t n) {
   CK(cudaMalloc(&ctx->prob, cap * 4));
   CK(cudaMalloc(&ctx->mpre, cap * 4));
   ctx->feat_cap = cap;
+  return MR_OK;
+}
+
+// Gradedness closure of the +1 flags (passes until one changes nothing; the
+// closure is monotone, so at most one pass per level plus one).
+mr_status close_flags(mr_ctx ctx, int8_t* skip, int* added) {
+  PoolView pv = view(ctx);
+  int jspan = 0;
+  for (auto& t : ctx->td) jspan = std::max(jspan, t.Jmax - t.Jmin);
+  *added = 0;
+  for (int it = 0; it <= jspan + 1; ++it) {
+    CK(cudaMemsetAsync(ctx->changed, 0, 4, ctx->st));
+    launch_close(pv, skip, ctx->changed, ctx->st);
+    int ch = 0;
+    CK(cudaMemcpyAsync(&ch, ctx->changed, 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *added += ch;
+    if (ch == 0) break;
+  }
+  return MR_OK;
+}
+
+// The learned proposal without refinement: flags = +1 where the network or the
+// exact fallback asks for refinement (before the gradedness closure).
+mr_status propose_only(mr_ctx ctx) {
+  if (ctx->refine_mode != 1 || !ctx->cnn_ready)
+    return fail(ctx, MR_EINVAL, "the proposal needs a trained network (mr_set_refine_mode learned)");
+  const Counters h = read_counters(ctx);
+  mr_status s = ensure_feat(ctx, h.n_act);
+  if (s) return s;
+  PoolView pv = view(ctx);
+  launch_features(pv, ctx->y, ctx->feat, ctx->mpre, 0, ctx->lc.num_sms, ctx->st);
+  launch_infer(pv, ctx->p.Bs, ctx->feat, ctx->cnn_wb, ctx->prob, -1, ctx->lc.num_sms, ctx->st);
+  CK(cudaMemsetAsync(ctx->pcounts, 0, 16, ctx->st));
+  launch_propose(pv, ctx->prob, ctx->mpre, ctx->cnn_tau, ctx->skip, ctx->pcounts, ctx->st);
+  return MR_OK;
+}
+
+// Refinement by the caller's indicators (mr_set_refine_mask), closed under
+// gradedness, then refined.
+mr_status refine_flagged(mr_ctx ctx) {
+  PoolView pv = view(ctx);
+  launch_mask_flags(pv, ctx->mask, ctx->st);
+  int added = 0;
+  mr_status s = close_flags(ctx, nullptr, &added);
+  if (s) return s;
+  do_refine(ctx, 2);
   return MR_OK;
 }
 
@@ -365,18 +411,9 @@ mr_status refine_for_step(mr_ctx ctx, int64_t* collected) {
   launch_infer(pv, ctx->p.Bs, fbuf ? fbuf : ctx->feat, ctx->cnn_wb, ctx->prob, -1, ctx->lc.num_sms, ctx->st);
   CK(cudaMemsetAsync(ctx->pcounts, 0, 16, ctx->st));
   launch_propose(pv, ctx->prob, ctx->mpre, ctx->cnn_tau, ctx->skip, ctx->pcounts, ctx->st);
-  int jspan = 0;
-  for (auto& t : ctx->td) jspan = std::max(jspan, t.Jmax - t.Jmin);
   int added = 0;
-  for (int it = 0; it <= jspan + 1; ++it) {
-    CK(cudaMemsetAsync(ctx->changed, 0, 4, ctx->st));
-    launch_close(pv, ctx->skip, ctx->changed, ctx->st);
-    int ch = 0;
-    CK(cudaMemcpyAsync(&ch, ctx->changed, 4, cudaMemcpyDeviceToHost, ctx->st));
-    CK(cudaStreamSynchronize(ctx->st));
-    added += ch;
-    if (ch == 0) break;
-  }
+  s = close_flags(ctx, ctx->skip, &added);
+  if (s) return s;
   launch_skip_key(pv, ctx->skip, ctx->skip_key, ctx->st);
   int32_t cnt[4];
   CK(cudaMemcpyAsync(cnt, ctx->pcounts, 16, cudaMemcpyDeviceToHost, ctx->st));
@@ -626,6 +663,7 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if ((e = dalloc(ctx, &ctx->f1, S))) return e;
     if ((e = dalloc(ctx, &ctx->flag, S))) return e;
     if ((e = dalloc(ctx, &ctx->mask, S))) return e;
+    if ((e = dalloc(ctx, &ctx->changed, 1))) return e;
     if ((e = dalloc(ctx, &ctx->tree, S))) return e;
     if ((e = dalloc(ctx, &ctx->crd, 3 * S))) return e;
     if ((e = dalloc(ctx, &ctx->hkey, S))) return e;
@@ -763,9 +801,23 @@ mr_status mr_rk_step(mr_ctx ctx, const double* t, const double* dt) {
 
 mr_status mr_adapt(mr_ctx ctx, int32_t mode) {
   if (!ctx) return MR_EINVAL;
-  if (mode == MR_ADAPT_REFINE_ALL || mode == MR_ADAPT_REFINE_FLAGGED) {
+  if (mode == MR_ADAPT_REFINE_ALL) {
     do_refine(ctx, mode);
     return check_device(ctx);
+  }
+  if (mode == MR_ADAPT_REFINE_FLAGGED) {
+    mr_status s = refine_flagged(ctx);
+    return s ? s : check_device(ctx);
+  }
+  if (mode == MR_ADAPT_PROPOSE) {
+    mr_status s = propose_only(ctx);
+    return s ? s : check_device(ctx);
+  }
+  if (mode == MR_ADAPT_REFINE_STEP) {
+    if (ctx->collect) return fail(ctx, MR_EINVAL, "MR_ADAPT_REFINE_STEP while collecting samples");
+    int64_t collected = 0;
+    mr_status s = refine_for_step(ctx, &collected);
+    return s ? s : check_device(ctx);
   }
   if (mode == MR_ADAPT_COARSEN) return coarsen_until_stable(ctx);
   if (mode == 3) {  // details and flags only (no merge), for inspection
@@ -1212,6 +1264,16 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
   return check_device(ctx);
 }
 
+
+mr_status mr_set_tuning(mr_ctx ctx, int32_t ctas_per_sm, int32_t stage_form) {
+  if (!ctx || ctas_per_sm < 0 || ctas_per_sm > 32 || stage_form < -1 || stage_form > 1) return MR_EINVAL;
+  if (stage_form == 1 && (ctx->p.dim != 2 || ctx->p.Bs != 17 || ctx->p.rhs_kind == MR_RHS_NS))
+    return fail(ctx, MR_EINVAL, "the warp-per-block form is for 2D advection on 17^2 blocks");
+  if (ctx->lc.grid_mult != ctas_per_sm || ctx->lc.stage_form != stage_form) drop_graph(ctx);
+  ctx->lc.grid_mult = ctas_per_sm;
+  ctx->lc.stage_form = stage_form;
+  return MR_OK;
+}
 
 mr_status mr_set_refine_mode(mr_ctx ctx, int32_t mode) {
   if (!ctx || (mode != 0 && mode != 1)) return MR_EINVAL;

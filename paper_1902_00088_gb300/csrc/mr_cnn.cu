@@ -499,27 +499,46 @@ __global__ void k_propose(PoolView pv, const float* prob, const float* mpre, flo
 
 // Gradedness closure of +1 flags: a refined block forces the refinement of
 // every touching leaf one level coarser (monotone 0 -> 1, order independent).
+// The touching leaves are the level-(l-1) leaves covering the ring of
+// level-(l+1) cells around the block.  skip (nullable) marks blocks left
+// unrefined by a proposal.
+template <int D>
 __global__ void k_close(PoolView pv, int8_t* skip, int32_t* changed) {
   pdl_enter();
   const int nact = pv.cnt->n_act;
+  constexpr int NR = D == 3 ? 64 : 16;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
     const int s = pv.act[p];
     if (pv.flag[s] != 1) continue;
     const BlockInfo b = load_block(pv, s);
     const TreeDev& td = pv.trees[b.tree];
-    for (int r = 0; r < 16; ++r) {
-      const int q[3] = {r % 4 - 1, r / 4 - 1, 0};
-      if ((q[0] == 0 || q[0] == 1) && (q[1] == 0 || q[1] == 1)) continue;
-      const int64_t nl1 = (int64_t)1 << (b.lvl + 1);
+    if (b.lvl >= td.Jmax || b.lvl - 1 < td.Jmin) continue;
+    const int64_t nl1 = (int64_t)1 << (b.lvl + 1);
+    for (int r = 0; r < NR; ++r) {
+      const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
+      bool inside = true;
+      for (int a = 0; a < D; ++a) inside &= (q[a] == 0 || q[a] == 1);
+      if (inside) continue;
       int64_t c2[3] = {0, 0, 0};
-      for (int a = 0; a < 2; ++a) c2[a] = ((2 * b.c[a] + q[a]) & (nl1 - 1)) >> 2;
-      const int t = tab_get<2>(pv, td, b.lvl - 1, c2);
+      for (int a = 0; a < D; ++a) c2[a] = ((2 * b.c[a] + q[a]) & (nl1 - 1)) >> 2;
+      const int t = tab_get<D>(pv, td, b.lvl - 1, c2);
       if (t >= 0 && pv.flag[t] != 1) {
         pv.flag[t] = 1;
-        skip[t] = 0;
+        if (skip) skip[t] = 0;
         atomicAdd(changed, 1);
       }
     }
+  }
+}
+
+// Refinement indicators given by the caller: flag = +1 for a block below Jmax
+// whose mask entry (canonical position) is positive, else 0.
+__global__ void k_mask_flags(PoolView pv, const int8_t* mask) {
+  pdl_enter();
+  const int nact = pv.cnt->n_act;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
+    const int s = pv.act[p];
+    pv.flag[s] = (mask[p] > 0 && pv.lvl[s] < pv.trees[pv.tree[s]].Jmax) ? 1 : 0;
   }
 }
 
@@ -664,7 +683,12 @@ void launch_propose(const PoolView& pv, const float* prob, const float* mpre, fl
   count_launch();
 }
 void launch_close(const PoolView& pv, int8_t* skip, int32_t* changed, cudaStream_t st) {
-  k_close<<<256, 256, 0, st>>>(pv, skip, changed);
+  if (pv.dim == 3) k_close<3><<<256, 256, 0, st>>>(pv, skip, changed);
+  else k_close<2><<<256, 256, 0, st>>>(pv, skip, changed);
+  count_launch();
+}
+void launch_mask_flags(const PoolView& pv, const int8_t* mask, cudaStream_t st) {
+  k_mask_flags<<<256, 256, 0, st>>>(pv, mask);
   count_launch();
 }
 void launch_judge(const PoolView& pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts,

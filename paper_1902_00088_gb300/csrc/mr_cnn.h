@@ -21,6 +21,7 @@ void launch_to_bf16(const float* w, __nv_bfloat16* wb, cudaStream_t st);
 void launch_propose(const PoolView& pv, const float* prob, const float* mpre, float tau, int8_t* skip,
                     int32_t* counts, cudaStream_t st);
 void launch_close(const PoolView& pv, int8_t* skip, int32_t* changed, cudaStream_t st);
+void launch_mask_flags(const PoolView& pv, const int8_t* mask, cudaStream_t st);
 void launch_judge(const PoolView& pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts,
                   cudaStream_t st);
 void launch_skip_key(const PoolView& pv, const int8_t* skip, int32_t* skip_key, cudaStream_t st);
