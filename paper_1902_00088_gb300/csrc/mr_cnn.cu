@@ -47,7 +47,7 @@ struct FeatGeo {
   static constexpr int NC = (B + 1) / 2 + 2;  // coarse rows -1 .. (B+1)/2
   static constexpr int NX = NC * B;
   static size_t smem(int nv) {
-    return kRingBytes + sizeof(float) * ((size_t)nv * (Gm::TILE + Bx::CBOX + Bx::SCR) + NX + Gm::NI);
+    return kRingBytesD<2> + sizeof(float) * ((size_t)nv * (Gm::TILE + Bx::CBOX + Bx::SCR) + NX + Gm::NI);
   }
 };
 
@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(256) k_features(PoolView pv, const TS* __restr
   using FG = FeatGeo<B>;
   constexpr int T = Gm::T;
   const int nv = pv.nvar;
-  Ring& R = *smem_as<Ring>(0);
+  RingD<2>& R = *smem_as<RingD<2>>(0);
   __shared__ float red[2][32];
-  float* tile = smem_as<float>(kRingBytes);
+  float* tile = smem_as<float>(kRingBytesD<2>);
   float* cbox = tile + nv * Gm::TILE;
   float* scr = cbox + nv * Bx::CBOX;
   float* X = scr + nv * Bx::SCR;

@@ -178,18 +178,33 @@ __device__ __forceinline__ void set_err(const PoolView& pv, int bits) {
 // units (periodic images resolved once here, so per-point work needs no
 // modulo).  These cells carry exactly the 16 (2D) / 74 (3D) relations of
 // Sec. 2.2.  A cell covered by no leaf in that range means a non-graded tree.
-struct Ring {
+//
+// Region table (filled when some ring leaf is not at the block's level): along
+// each axis a level-l node index x relative to the block origin falls into one
+// of 7 classes -- inside ring cell -1 (x < 0), on the face x = 0 between cells
+// -1 and 0, inside cell 0, on the face x = H, inside cell 1, on the face x = 2H,
+// inside cell 2 (H = (Bs - 1) / 2).  All nodes of one class box (7^d boxes)
+// have the same leaves containing them, in the same position (inside, or on
+// the same faces), hence the same owner: the owner is searched once per box,
+// and each node only offsets into it.
+template <int D>
+struct RingD {
+  static constexpr int NREG = D == 3 ? 343 : 49;
   int slot[64];
   int org[64][3];
   int8_t lvl[64];
   int finer;    // some leaf one level finer touches the block
   int coarser;  // some leaf one level coarser touches the block
   int mixed;    // some ring leaf is not at the block's level
+  // per class box: owner slot (-1: none), owner level, owner origin
+  // (level-(l+1) node units, relative to the block origin) x | y << 16, z
+  int4 reg[NREG];
 };
-constexpr int kRingBytes = (int)((sizeof(Ring) + 15) / 16 * 16);
+template <int D>
+constexpr int kRingBytesD = (int)((sizeof(RingD<D>) + 15) / 16 * 16);
 
 template <int D, int B, typename G = CtaGroup>
-__device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, Ring& R) {
+__device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, RingD<D>& R) {
   const G g{};
   using Gm = Geo<D, B>;
   if (g.rank() == 0) R.finer = R.coarser = R.mixed = 0;
@@ -252,7 +267,7 @@ struct Log2B {
 };
 
 template <int D, int B>
-__device__ __forceinline__ bool owner(const BlockInfo& b, const int h[3], int min_m, const Ring& R,
+__device__ __forceinline__ bool owner(const BlockInfo& b, const int h[3], int min_m, const RingD<D>& R,
                                       Own& o) {
   constexpr int P = Log2B<B>::value;
   static_assert(P > 0, "Bs - 1 must be a power of two");
@@ -378,6 +393,40 @@ __device__ __forceinline__ TT predict_box(const TT* box, const int o[3]) {
   return ns[2] == 4 ? dd4(vy[0], vy[1], vy[2], vy[3]) : vy[0];
 }
 
+// Class (0..6) of a level-l node index x relative to the block origin, for
+// -(H - 1) <= x <= 3H - 1 (H = (Bs - 1) / 2): inside ring cell -1, face 0,
+// inside cell 0, face H, inside cell 1, face 2H, inside cell 2.
+template <int B>
+__device__ __forceinline__ int reg_class(int x) {
+  constexpr int H = (B - 1) / 2;
+  return (x >= 0) + (x > 0) + (x >= H) + (x > H) + (x >= 2 * H) + (x > 2 * H);
+}
+// A node index of class c.
+template <int B>
+__device__ __forceinline__ int reg_rep(int c) {
+  constexpr int H = (B - 1) / 2;
+  return c == 0 ? -1 : c == 1 ? 0 : c == 2 ? 1 : c == 3 ? H : c == 4 ? H + 1 : c == 5 ? 2 * H : 2 * H + 1;
+}
+
+// Owner of every class box (see RingD), found with owner() at one node of the box.
+template <int D, int B, typename G>
+__device__ void build_regions(const BlockInfo& b, RingD<D>& R) {
+  const G g{};
+  for (int r = g.rank(); r < RingD<D>::NREG; r += g.size()) {
+    const int c[3] = {r % 7, (r / 7) % 7, r / 49};
+    int h[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) h[a] = 2 * reg_rep<B>(c[a]);
+    Own o;
+    int4 e = make_int4(-1, -1, 0, 0);
+    if (owner<D, B>(b, h, 0, R, o)) {
+      const int ox = h[0] - o.off[0], oy = h[1] - o.off[1], oz = h[2] - o.off[2];
+      e = make_int4(o.slot, o.m, (ox & 0xffff) | (oy << 16), oz);
+    }
+    R.reg[r] = e;
+  }
+}
+
 // Fills the synchronised tile (nvar x T^d, type TT) of block b from field F.
 // Block-edge nodes owned by another block (a finer one, Sec. 2.2 rule 2, or an
 // equal-level one that holds the node at its lower edge, which keeps redundant
@@ -388,7 +437,7 @@ __device__ __forceinline__ TT predict_box(const TT* box, const int o[3]) {
 // nodes between coarse nodes are predicted from it.
 template <int D, int B, typename TF, typename TT, int W = kG, typename G = CtaGroup>
 __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, TF* Fw, TT* tile,
-                          bool commit, const Ring& R, TT* cbox, TT* scr = nullptr) {
+                          bool commit, RingD<D>& R, TT* cbox, TT* scr = nullptr) {
   const G g{};
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, W>;
@@ -446,6 +495,21 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
     }
     return;
   }
+  // some ring leaf is at another level: one owner search per class box
+  build_regions<D, B, G>(b, R);
+  g.sync();
+  const int l1 = b.lvl + 1;
+  // owner of level-l node x (relative to the block origin) and the node's
+  // offset inside it in level-(l+1) units
+  auto region = [&](const int x[3], int& slot, int& m, int off[3]) {
+    const int r = reg_class<B>(x[0]) + 7 * reg_class<B>(x[1]) + (D == 3 ? 49 * reg_class<B>(x[2]) : 0);
+    const int4 e = R.reg[r];
+    slot = e.x;
+    m = e.y;
+    off[0] = 2 * x[0] - (int)(int16_t)(e.z & 0xffff);
+    off[1] = 2 * x[1] - (e.z >> 16);
+    off[2] = D == 3 ? 2 * x[2] - e.w : 0;
+  };
   if (R.coarser) {
     for (int q0 = g.rank(); q0 < Bx::CBOX; q0 += U * g.size()) {
       int64_t at[U];
@@ -457,18 +521,18 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
         good[u] = false;
         at[u] = 0;
         if (!ok[u]) continue;
-        const int n[3] = {idx % Bx::CB + Bx::CLO, (idx / Bx::CB) % Bx::CB + Bx::CLO,
-                          D == 3 ? idx / (Bx::CB * Bx::CB) + Bx::CLO : 0};
-        const int h[3] = {4 * n[0], 4 * n[1], 4 * n[2]};
-        Own o;
-        if (!owner<D, B>(b, h, 0, R, o) || o.m < b.lvl - 1) {
+        // coarse node n sits at level-l node 2n
+        const int x[3] = {2 * (idx % Bx::CB + Bx::CLO), 2 * ((idx / Bx::CB) % Bx::CB + Bx::CLO),
+                          D == 3 ? 2 * (idx / (Bx::CB * Bx::CB) + Bx::CLO) : 0};
+        int slot, m, off[3];
+        region(x, slot, m, off);
+        if (slot < 0 || m < b.lvl - 1) {
           set_err(pv, kErrGraded);
           continue;
         }
         good[u] = true;
-        const int sh = b.lvl + 1 - o.m;
-        at[u] = ((int64_t)o.slot * nv) * pv.vs +
-                Gm::lin(o.off[0] >> sh, o.off[1] >> sh, D == 3 ? o.off[2] >> sh : 0);
+        const int sh = l1 - m;
+        at[u] = ((int64_t)slot * nv) * pv.vs + Gm::lin(off[0] >> sh, off[1] >> sh, D == 3 ? off[2] >> sh : 0);
       }
       for (int v = 0; v < nv; ++v) {
         TF val[U];
@@ -534,42 +598,35 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       at[u] = 0;
       kind[u] = 5;  // past the end
       if (q >= Bx::NPTS) continue;
-      bool ghost = false, edge = false;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const int x = ijk[u][a];
-        if (x < 0 || x > B - 1) ghost = true;
-        else if (x == 0 || x == B - 1) edge = true;
-      }
-      const int h[3] = {2 * i, 2 * j, 2 * k};
-      Own o;
-      if (!ghost) {
-        if (edge && owner<D, B>(b, h, b.lvl, R, o) && o.slot != b.slot) {
-          const int shv = b.lvl + 1 - o.m;
-          kind[u] = 1;
-          at[u] = ((int64_t)o.slot * nv) * pv.vs +
-                  Gm::lin(o.off[0] >> shv, o.off[1] >> shv, D == 3 ? o.off[2] >> shv : 0);
-        } else {
-          kind[u] = 0;
-          at[u] = own + li[u];
-        }
-        continue;
-      }
-      if (!owner<D, B>(b, h, 0, R, o)) {
+      int slot, m, off[3];
+      region(ijk[u], slot, m, off);
+      if (slot < 0) {
         set_err(pv, kErrGraded);
         kind[u] = 4;
         continue;
       }
-      const int sh = b.lvl + 1 - o.m;
-      bool node = true;
+      bool inner = true;
 #pragma unroll
-      for (int a = 0; a < D; ++a) node &= (o.off[a] & ((1 << sh) - 1)) == 0;
-      if (o.m >= b.lvl || node) {
+      for (int a = 0; a < D; ++a) inner &= (ijk[u][a] >= 0 && ijk[u][a] <= B - 1);
+      const int sh = l1 - m;
+      if (inner) {
+        // the block's own node, or an edge node whose owner is another block
+        // (a finer one, or an equal-level one holding it at its lower edge)
+        if (slot == b.slot) {
+          kind[u] = 0;
+          at[u] = own + li[u];
+        } else {
+          kind[u] = 1;
+          at[u] = ((int64_t)slot * nv) * pv.vs + Gm::lin(off[0] >> sh, off[1] >> sh, D == 3 ? off[2] >> sh : 0);
+        }
+        continue;
+      }
+      const bool node = ((off[0] | off[1] | off[2]) & ((1 << sh) - 1)) == 0;
+      if (m >= b.lvl || node) {
         kind[u] = 2;
-        at[u] = ((int64_t)o.slot * nv) * pv.vs +
-                Gm::lin(o.off[0] >> sh, o.off[1] >> sh, D == 3 ? o.off[2] >> sh : 0);
+        at[u] = ((int64_t)slot * nv) * pv.vs + Gm::lin(off[0] >> sh, off[1] >> sh, D == 3 ? off[2] >> sh : 0);
       } else {
-        if (o.m != b.lvl - 1) set_err(pv, kErrGraded);
+        if (m != b.lvl - 1) set_err(pv, kErrGraded);
         kind[u] = 3;
       }
     }

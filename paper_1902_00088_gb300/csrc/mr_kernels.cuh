@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
   using PL = Plan<D>;
   using TC = TY;  // stencil arithmetic type
   static_assert(NT >= PL::INTS, "one thread per plan entry");
-  Ring& R = *smem_as<Ring>(0);
-  TC* tile = smem_as<TC>(kRingBytes);  // nvar == 1
+  RingD<D>& R = *smem_as<RingD<D>>(0);
+  TC* tile = smem_as<TC>(kRingBytesD<D>);  // nvar == 1
   TC* cbox = tile + Bx::TILE;
   TC* scr = cbox + Bx::CBOX;
   int32_t* gtab = reinterpret_cast<int32_t*>(scr + Bx::SCR);  // 2D: gather table
@@ -223,7 +223,7 @@ struct StageW {
   using Bx = Box<2, B, 2>;
   static constexpr int NW = NT / 32;
   static constexpr size_t GTAB = (4 * Bx::NPTS + 15) / 16 * 16;
-  static constexpr size_t WAREA = (kRingBytes + sizeof(TY) * (Bx::TILE + Bx::CBOX + Bx::SCR) + 15) / 16 * 16;
+  static constexpr size_t WAREA = (kRingBytesD<2> + sizeof(TY) * (Bx::TILE + Bx::CBOX + Bx::SCR) + 15) / 16 * 16;
   static constexpr size_t SMEM = GTAB + NW * WAREA;
 };
 
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
   unsigned char* sm = smem_as<unsigned char>(0);
   int32_t* gtab = reinterpret_cast<int32_t*>(sm);
   unsigned char* wa = sm + SW::GTAB + warp * SW::WAREA;
-  Ring& R = *reinterpret_cast<Ring*>(wa);
-  TC* tile = reinterpret_cast<TC*>(wa + kRingBytes);
+  RingD<2>& R = *reinterpret_cast<RingD<2>*>(wa);
+  TC* tile = reinterpret_cast<TC*>(wa + kRingBytesD<2>);
   TC* cbox = tile + Bx::TILE;
   TC* scr = cbox + Bx::CBOX;
   __shared__ int64_t snb[SW::NW][PL::NB];
@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
   using NG = NsGeo<B>;
   using TC = TY;
   constexpr int T = Gm::T, G = Gm::G;
-  Ring& R = *smem_as<Ring>(0);
-  TC* tile = smem_as<TC>(kRingBytes);     // 4 x TILE conserved variables
+  RingD<2>& R = *smem_as<RingD<2>>(0);
+  TC* tile = smem_as<TC>(kRingBytesD<2>);  // 4 x TILE conserved variables
   TC* cbox = tile + 4 * Gm::TILE;         // 4 x CBOX
   TC* pu = cbox + 4 * Gm::CBOX;           // primitives u, v, p, th: 4 x TILE
   TC* pvv = pu + Gm::TILE;
@@ -601,9 +601,9 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 1>;  // prediction of the children reaches one node
   using RG = RefGeo<D, B>;
-  Ring& R = *smem_as<Ring>(0);
+  RingD<D>& R = *smem_as<RingD<D>>(0);
   __shared__ int cslot[8];
-  TS* tile = smem_as<TS>(kRingBytes);
+  TS* tile = smem_as<TS>(kRingBytesD<D>);
   TS* cbox = tile + pv.nvar * Bx::TILE;
   TS* scr = cbox + pv.nvar * Bx::CBOX;  // gather scratch, then the x pass of the upsampling
   TS* X = scr;
@@ -802,9 +802,9 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, 2>;  // prediction from even nodes reaches two nodes
   using DG = DetGeo<D, B>;
-  Ring& R = *smem_as<Ring>(0);
+  RingD<D>& R = *smem_as<RingD<D>>(0);
   __shared__ double red[2][32];
-  TT* tile = smem_as<TT>(kRingBytes);  // tile type (TS or FP32); TD is the decision type
+  TT* tile = smem_as<TT>(kRingBytesD<D>);  // tile type (TS or FP32); TD is the decision type
   TT* cbox = tile + pv.nvar * Bx::TILE;
   // gather scratch, reused for the passes once the tile is complete
   TT* scr = cbox + pv.nvar * Bx::CBOX;
@@ -1040,7 +1040,7 @@ struct DetW {
   static constexpr size_t GTAB = (4 * Bx::NPTS + 15) / 16 * 16;
   static constexpr size_t TABS = (4 * DetTab<B>::INTS + 15) / 16 * 16;  // detail index tables
   static constexpr size_t XB = sizeof(TS) * Bx::SCR > sizeof(TD) * DG::NX ? sizeof(TS) * Bx::SCR : sizeof(TD) * DG::NX;
-  static constexpr size_t TB = (kRingBytes + sizeof(TS) * (Bx::TILE + Bx::CBOX) + 15) / 16 * 16;
+  static constexpr size_t TB = (kRingBytesD<2> + sizeof(TS) * (Bx::TILE + Bx::CBOX) + 15) / 16 * 16;
   static constexpr size_t WAREA = TB + (XB + 15) / 16 * 16;
   static constexpr size_t SMEM = GTAB + TABS + NW * WAREA;
 };
@@ -1065,8 +1065,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
   int32_t* xtab = reinterpret_cast<int32_t*>(sm + DW::GTAB);
   int32_t* otab = xtab + DG::NX;
   unsigned char* wa = sm + DW::GTAB + DW::TABS + warp * DW::WAREA;
-  Ring& R = *reinterpret_cast<Ring*>(wa);
-  TS* tile = reinterpret_cast<TS*>(wa + kRingBytes);
+  RingD<2>& R = *reinterpret_cast<RingD<2>*>(wa);
+  TS* tile = reinterpret_cast<TS*>(wa + kRingBytesD<2>);
   TS* cbox = tile + Bx::TILE;
   TS* scr = reinterpret_cast<TS*>(wa + DW::TB);  // gather scratch, then the x pass
   __shared__ int64_t snbo[DW::NW][PL::NB];
@@ -1283,8 +1283,8 @@ template <int D, int B, typename TS>
 __global__ void __launch_bounds__(256) k_sync(PoolView pv, TS* __restrict__ y, double* __restrict__ tiles) {
   pdl_enter();
   using Gm = Geo<D, B>;
-  Ring& R = *smem_as<Ring>(0);
-  double* tile = smem_as<double>(kRingBytes);
+  RingD<D>& R = *smem_as<RingD<D>>(0);
+  double* tile = smem_as<double>(kRingBytesD<D>);
   double* cbox = tile + pv.nvar * Gm::TILE;
   const int nact = pv.cnt->n_act;
   const int nv = pv.nvar;

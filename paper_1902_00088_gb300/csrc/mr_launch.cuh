@@ -44,7 +44,7 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
   constexpr int threads = Threads<D, B>::value;
   const int nv = 1;
   using Bx = Box<D, B, 2>;
-  const size_t smem = kRingBytes + sizeof(TY) * nv * (Bx::TILE + Bx::CBOX + Bx::SCR) + (D == 2 ? 4 * Bx::NPTS : 0);
+  const size_t smem = kRingBytesD<D> + sizeof(TY) * nv * (Bx::TILE + Bx::CBOX + Bx::SCR) + (D == 2 ? 4 * Bx::NPTS : 0);
   TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
   // 2D: one warp per block when the grid holds enough blocks to fill the GPU
   // several times over (or as tuned), else one CTA per block (shorter latency)
@@ -106,7 +106,7 @@ static void stage_ns_impl(const PoolView& pv, const Fields& f, int stage, const 
                           const LaunchCfg& lc, cudaStream_t st) {
   using Gm = Geo<2, B>;
   constexpr int threads = 256;
-  const size_t smem = kRingBytes + sizeof(TY) * (4 * Gm::TILE + 4 * Gm::CBOX + 4 * Gm::TILE +
+  const size_t smem = kRingBytesD<2> + sizeof(TY) * (4 * Gm::TILE + 4 * Gm::CBOX + 4 * Gm::TILE +
                                                  4 * NsGeo<B>::NF + 4 * NsGeo<B>::NG);
   TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
   if (stage == 0) {
@@ -184,7 +184,7 @@ struct RefineRun {
     constexpr int threads = Threads<D, B>::value;
     using Bx = Box<D, B, 1>;
     const size_t scr = (size_t)std::max<int64_t>((int64_t)pv.nvar * Bx::SCR, RefGeo<D, B>::NX);
-    const size_t smem = kRingBytes + sizeof(TS) * (pv.nvar * (Bx::TILE + Bx::CBOX) + scr);
+    const size_t smem = kRingBytesD<D> + sizeof(TS) * (pv.nvar * (Bx::TILE + Bx::CBOX) + scr);
     auto k = k_refine<D, B, TS, threads>;
     prep_smem(k, smem);
     const int grid = persistent_grid(k, threads, smem, lc, lc.grid_mult);
@@ -257,7 +257,7 @@ struct DetailsRun {
     using Bx = Box<D, B, 2>;
     const size_t tt = d64 ? sizeof(TS) : 4;  // tile type: the state type, FP32 for FP32 details
     const size_t region = d64 ? DetSmem<D, B, TS, double>::region(pv.nvar) : DetSmem<D, B, float, float>::region(pv.nvar);
-    const size_t smem = kRingBytes + tt * pv.nvar * Bx::TILE + 16 + region + 16 +
+    const size_t smem = kRingBytesD<D> + tt * pv.nvar * Bx::TILE + 16 + region + 16 +
                         (D == 2 ? 4 * (Bx::NPTS + DetTab<B>::INTS) : 0);
     if (d64) {
       auto k = k_details<D, B, TS, double, threads>;
@@ -329,7 +329,7 @@ struct SyncRun {
   static void run(const PoolView& pv, const Fields& f, double* tiles, const LaunchCfg& lc,
                   cudaStream_t st) {
     constexpr int threads = 256;
-    const size_t smem = kRingBytes + sizeof(double) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
+    const size_t smem = kRingBytesD<D> + sizeof(double) * pv.nvar * (Geo<D, B>::TILE + Geo<D, B>::CBOX);
     auto k = k_sync<D, B, TS>;
     prep_smem(k, smem);
     launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, 0), threads, smem, st, pv, (TS*)f.y, tiles);
