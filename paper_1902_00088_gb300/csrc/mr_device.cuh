@@ -19,6 +19,15 @@
 
 namespace mr {
 
+// Compile-time loop: f(std::integral_constant<int, I>) for I in [A, E).
+template <int A, int E, typename Fn>
+__device__ __forceinline__ void static_for(Fn&& f) {
+  if constexpr (A < E) {
+    f(std::integral_constant<int, A>{});
+    static_for<A + 1, E>(f);
+  }
+}
+
 // Thread groups that cooperate on one block: the whole CTA, or one warp.
 struct CtaGroup {
   static constexpr int kSize = 0;  // size known at run time only
@@ -427,6 +436,58 @@ __device__ void build_regions(const BlockInfo& b, RingD<D>& R) {
   }
 }
 
+// Separable prediction over the coarse box (values of nv variables in cbox),
+// x first, then y (then z at the point): the same operations in the same order
+// as predict_box.  2D: the x pass goes to scr (y per point from it); 3D: the x
+// pass is kept in the variable's tile (overwritten later by the gather) and
+// the y pass goes to scr (z per point).  Ends with a group barrier.
+template <int D, int B, int W, typename TT, typename G>
+__device__ void coarse_passes(int nv, const TT* cbox, TT* tile, TT* scr) {
+  const G g{};
+  using Bx = Box<D, B, W>;
+  for (int v = 0; v < nv; ++v) {
+    const TT* cb = cbox + v * Bx::CBOX;
+    TT* X = D == 3 ? tile + v * Bx::TILE : scr + v * Bx::SCR;
+    for (int q = g.rank(); q < Bx::NXP; q += g.size()) {
+      const int x = q % Bx::S - W, ny = (q / Bx::S) % Bx::CB + Bx::CLO;
+      const int nz = D == 3 ? q / (Bx::S * Bx::CB) + Bx::CLO : 0;
+      const int fl = x >> 1;
+      X[q] = (x & 1) ? dd4(cb[Bx::cix(fl - 1, ny, nz)], cb[Bx::cix(fl, ny, nz)], cb[Bx::cix(fl + 1, ny, nz)],
+                           cb[Bx::cix(fl + 2, ny, nz)])
+                     : cb[Bx::cix(fl, ny, nz)];
+    }
+  }
+  if (D == 3) {
+    g.sync();
+    for (int v = 0; v < nv; ++v) {
+      const TT* X = tile + v * Bx::TILE;
+      TT* Y = scr + v * Bx::SCR;
+      for (int q = g.rank(); q < Bx::NYP; q += g.size()) {
+        const int x = q % Bx::S, y = (q / Bx::S) % Bx::S - W, nzi = q / (Bx::S * Bx::S);
+        const int fl = y >> 1;
+        const TT* c = X + nzi * Bx::CB * Bx::S + x;
+        Y[q] = (y & 1) ? dd4(c[(fl - 1 - Bx::CLO) * Bx::S], c[(fl - Bx::CLO) * Bx::S],
+                             c[(fl + 1 - Bx::CLO) * Bx::S], c[(fl + 2 - Bx::CLO) * Bx::S])
+                       : c[(fl - Bx::CLO) * Bx::S];
+      }
+    }
+  }
+  g.sync();
+}
+
+// Value of a ghost node predicted from the coarse box after coarse_passes: the
+// last axis (z in 3D, y in 2D) from the scratch.
+template <int D, int B, int W, typename TT>
+__device__ __forceinline__ TT coarse_predicted(const TT* scr_v, int i, int j, int k) {
+  using Bx = Box<D, B, W>;
+  const TT* c = scr_v + (i + W) + (D == 3 ? (j + W) * Bx::S : 0);
+  constexpr int st = D == 3 ? Bx::S * Bx::S : Bx::S;
+  const int e = D == 3 ? k : j, fl = e >> 1;
+  return (e & 1) ? dd4(c[(fl - 1 - Bx::CLO) * st], c[(fl - Bx::CLO) * st], c[(fl + 1 - Bx::CLO) * st],
+                       c[(fl + 2 - Bx::CLO) * st])
+                 : c[(fl - Bx::CLO) * st];
+}
+
 // Fills the synchronised tile (nvar x T^d, type TT) of block b from field F.
 // Block-edge nodes owned by another block (a finer one, Sec. 2.2 rule 2, or an
 // equal-level one that holds the node at its lower edge, which keeps redundant
@@ -544,38 +605,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       }
     }
     g.sync();
-    if (scr) {
-      // separable prediction over the coarse box, x first, then y (then z at
-      // the point): the same operations in the same order as predict_box
-      for (int v = 0; v < nv; ++v) {
-        const TT* cb = cbox + v * Bx::CBOX;
-        TT* X = D == 3 ? tile + v * Bx::TILE : scr + v * Bx::SCR;
-        for (int q = g.rank(); q < Bx::NXP; q += g.size()) {
-          const int x = q % Bx::S - W, ny = (q / Bx::S) % Bx::CB + Bx::CLO;
-          const int nz = D == 3 ? q / (Bx::S * Bx::CB) + Bx::CLO : 0;
-          const int fl = x >> 1;
-          X[q] = (x & 1) ? dd4(cb[Bx::cix(fl - 1, ny, nz)], cb[Bx::cix(fl, ny, nz)], cb[Bx::cix(fl + 1, ny, nz)],
-                               cb[Bx::cix(fl + 2, ny, nz)])
-                         : cb[Bx::cix(fl, ny, nz)];
-        }
-      }
-      if (D == 3) {
-        g.sync();
-        for (int v = 0; v < nv; ++v) {
-          const TT* X = tile + v * Bx::TILE;
-          TT* Y = scr + v * Bx::SCR;
-          for (int q = g.rank(); q < Bx::NYP; q += g.size()) {
-            const int x = q % Bx::S, y = (q / Bx::S) % Bx::S - W, nzi = q / (Bx::S * Bx::S);
-            const int fl = y >> 1;
-            const TT* c = X + nzi * Bx::CB * Bx::S + x;
-            Y[q] = (y & 1) ? dd4(c[(fl - 1 - Bx::CLO) * Bx::S], c[(fl - Bx::CLO) * Bx::S],
-                                 c[(fl + 1 - Bx::CLO) * Bx::S], c[(fl + 2 - Bx::CLO) * Bx::S])
-                           : c[(fl - Bx::CLO) * Bx::S];
-          }
-        }
-      }
-      g.sync();
-    }
+    if (scr) coarse_passes<D, B, W, TT, G>(nv, cbox, tile, scr);
   }
   // kinds of tile points: 0 own node, 1 block-edge node of another owner,
   // 2 ghost node that is a node of its owner, 3 ghost predicted from the coarse
@@ -662,6 +692,143 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
         }
       }
     }
+  }
+}
+
+// Column form of the 3D tile fill for one CTA: each thread fills whole z-columns
+// (fixed x, y) of the tile, with the z loop unrolled, so every quantity that
+// depends on z alone (neighbour index, local offset, class box, inside or
+// ghost) is a compile-time constant and the per-node work is a table lookup,
+// an address and the copy.  Up to KC loads of a column are in flight together.
+// nbase (nullable): pool offsets (slot * nvar * vs) of the 27 equal-level
+// neighbours of a block with a uniform neighbourhood (x fastest, the block
+// itself in the centre); null: the owners come from the ring's class boxes
+// (build_ring must have run).  Same values, stores and commits as fill_tile.
+template <int B, typename TF, typename TT, int W>
+__device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t* nbase, const TF* F, TF* Fw,
+                          TT* tile, bool commit, RingD<3>& R, TT* cbox, TT* scr) {
+  using Gm = Geo<3, B>;
+  using Bx = Box<3, B, W>;
+  constexpr int S = Bx::S, S2 = S * S, BB = B * B;
+  constexpr int KC = 7;  // loads in flight per thread
+  const int nv = pv.nvar;
+  const int64_t own = (int64_t)b.slot * nv * pv.vs;
+  const int l1 = b.lvl + 1;
+  const bool uni = nbase != nullptr;
+  auto load_store = [&](auto kcc, const int64_t* at, const int* kind, int col, int i, int j, int kbase) {
+    constexpr int KN = decltype(kcc)::value;
+    for (int v = 0; v < nv; ++v) {
+      TF val[KN];
+#pragma unroll
+      for (int u = 0; u < KN; ++u) val[u] = kind[u] <= 2 ? F[at[u] + (int64_t)v * pv.vs] : TF(0);
+#pragma unroll
+      for (int u = 0; u < KN; ++u) {
+        const int k = kbase + u;
+        TT* t = tile + v * Bx::TILE + col + (k + W) * S2;
+        if (kind[u] == 3) {
+          *t = coarse_predicted<3, B, W, TT>(scr + v * Bx::SCR, i, j, k);
+        } else if (kind[u] == 4) {
+          *t = TT(0);
+        } else {
+          *t = (TT)val[u];
+          if (kind[u] == 1 && commit) {
+            const int64_t me = own + (int64_t)v * pv.vs + Gm::lin(i, j, k);
+            if (F[me] != val[u]) Fw[me] = val[u];
+          }
+        }
+      }
+    }
+  };
+  if (!uni) {
+    build_regions<3, B, CtaGroup>(b, R);
+    __syncthreads();
+    if (R.coarser) {
+      // coarse box: columns of CB coarse nodes (coarse node n at level-l node 2n)
+      constexpr int CB = Bx::CB;
+      for (int c = threadIdx.x; c < CB * CB; c += blockDim.x) {
+        const int nx = c % CB + Bx::CLO, ny = c / CB + Bx::CLO;
+        const int rb = reg_class<B>(2 * nx) + 7 * reg_class<B>(2 * ny);
+#pragma unroll
+        for (int z = 0; z < CB; ++z) {
+          const int nz = z + Bx::CLO;
+          const int4 e = R.reg[rb + 49 * reg_class<B>(2 * nz)];
+          bool good = true;
+          int64_t at = 0;
+          if (e.x < 0 || e.y < b.lvl - 1) {
+            set_err(pv, kErrGraded);
+            good = false;
+          } else {
+            const int sh = l1 - e.y;
+            const int ox = 4 * nx - (int)(int16_t)(e.z & 0xffff), oy = 4 * ny - (e.z >> 16), oz = 4 * nz - e.w;
+            at = ((int64_t)e.x * nv) * pv.vs + Gm::lin(ox >> sh, oy >> sh, oz >> sh);
+          }
+          for (int v = 0; v < nv; ++v)
+            cbox[v * Bx::CBOX + z * CB * CB + c] = good ? (TT)F[at + (int64_t)v * pv.vs] : TT(0);
+        }
+      }
+      __syncthreads();
+      if (scr) coarse_passes<3, B, W, TT, CtaGroup>(nv, cbox, tile, scr);
+    }
+  }
+  for (int col = threadIdx.x; col < S2; col += blockDim.x) {
+    const int i = col % S - W, j = col / S - W;
+    const bool inxy = i >= 0 && i <= B - 1 && j >= 0 && j <= B - 1;
+    // uniform form: neighbour row and local offset of the column
+    const int sx = i < 0 ? 0 : (i <= B - 2 ? 1 : 2), sy = j < 0 ? 0 : (j <= B - 2 ? 1 : 2);
+    const int lxy = (i - (sx - 1) * (B - 1)) + B * (j - (sy - 1) * (B - 1));
+    const int64_t* nrow = uni ? nbase + sx + 3 * sy : nullptr;
+    // ring form: class box row of the column
+    const int rb = reg_class<B>(i) + 7 * reg_class<B>(j);
+    auto chunk = [&](auto kcc, auto k0c) {
+      constexpr int KN = decltype(kcc)::value, K0 = decltype(k0c)::value;
+      int64_t at[KN];
+      int kind[KN];
+#pragma unroll
+      for (int u = 0; u < KN; ++u) {
+        const int k = K0 + u;
+        const int sk = k < 0 ? 0 : (k <= B - 2 ? 1 : 2);  // compile-time per u
+        const bool ink = k >= 0 && k <= B - 1;
+        const bool inner = inxy && ink;
+        if (uni) {
+          const int64_t nb = nrow[9 * sk];
+          at[u] = nb + lxy + BB * (k - (sk - 1) * (B - 1));
+          kind[u] = inner ? (nb != own ? 1 : 0) : 2;
+          continue;
+        }
+        const int4 e = R.reg[rb + 49 * reg_class<B>(k)];
+        if (e.x < 0) {
+          set_err(pv, kErrGraded);
+          kind[u] = 4;
+          at[u] = 0;
+          continue;
+        }
+        const int m = e.y, sh = l1 - m;
+        const int ox = 2 * i - (int)(int16_t)(e.z & 0xffff), oy = 2 * j - (e.z >> 16), oz = 2 * k - e.w;
+        const int64_t src = ((int64_t)e.x * nv) * pv.vs + Gm::lin(ox >> sh, oy >> sh, oz >> sh);
+        if (inner) {
+          kind[u] = e.x == b.slot ? 0 : 1;
+          at[u] = e.x == b.slot ? own + Gm::lin(i, j, k) : src;
+          continue;
+        }
+        const bool node = ((ox | oy | oz) & ((1 << sh) - 1)) == 0;
+        if (m >= b.lvl || node) {
+          kind[u] = 2;
+          at[u] = src;
+        } else {
+          if (m != b.lvl - 1) set_err(pv, kErrGraded);
+          kind[u] = 3;
+          at[u] = 0;
+        }
+      }
+      load_store(kcc, at, kind, col, i, j, K0);
+    };
+    // k = -W .. B-1+W in chunks of KC (compile-time k)
+    static_for<0, (S + KC - 1) / KC>([&](auto cc) {
+      constexpr int C = decltype(cc)::value;
+      constexpr int K0 = -W + C * KC;
+      constexpr int KN = (S - C * KC) < KC ? (S - C * KC) : KC;
+      chunk(std::integral_constant<int, KN>{}, std::integral_constant<int, K0>{});
+    });
   }
 }
 

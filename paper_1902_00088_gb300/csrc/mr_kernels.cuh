@@ -80,15 +80,18 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
     const BlockInfo b = plan_block<D>(pl);
     const TreeDev& td = pv.trees[b.tree];
     if ((pl[1] >> 30) & 1) {
-      if (D == 2)
+      if constexpr (D == 2)
         gather_table<D, B, 2, 1, TSRC, TC>(pv, (int64_t)b.slot * pv.vs, snb[buf], gtab, src, (TSRC*)src, tile,
                                            stage == 0);
       else
-        gather_uniform<D, B, 2, 1, TSRC, TC>(pv, b, pl + PL::NBO, src, (TSRC*)src, tile, stage == 0);
+        fill_cols<B, TSRC, TC, 2>(pv, b, snb[buf], src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
     } else {
       build_ring<D, B>(pv, td, b, R);
       __syncthreads();
-      fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
+      if constexpr (D == 2)
+        fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
+      else
+        fill_cols<B, TSRC, TC, 2>(pv, b, nullptr, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
     }
     __syncthreads();
     const TC c = tree_cD<TC>(td, b.lvl);
@@ -626,7 +629,10 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_refine
     const TreeDev& td = pv.trees[b.tree];
     build_ring<D, B>(pv, td, b, R);
     __syncthreads();
-    fill_tile<D, B, TS, TS, 1>(pv, b, y, y, tile, false, R, cbox, scr);
+    if constexpr (D == 2)
+      fill_tile<D, B, TS, TS, 1>(pv, b, y, y, tile, false, R, cbox, scr);
+    else
+      fill_cols<B, TS, TS, 1>(pv, b, nullptr, y, y, tile, false, R, cbox, scr);
     if (threadIdx.x == 0) {
       uint64_t key[8];
       int32_t cc[8][3];
@@ -907,14 +913,17 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       gather_table<D, B, 2, 1, TS, TT>(pv, own, snbo, gtab, y, y, tile, true);
     else if (uni && nv == 4 && D == 2)
       gather_table<D, B, 2, 4, TS, TT>(pv, own, snbo, gtab, y, y, tile, true);
-    else if (uni && nv == 1)
-      gather_uniform<D, B, 2, 1, TS, TT>(pv, b, snb, y, y, tile, true);
-    else {
+    else if (D == 3 && uni) {
+      if constexpr (D == 3) fill_cols<B, TS, TT, 2>(pv, b, snbo, y, y, tile, true, R, cbox, scr);
+    } else {
       if (uni) {
         build_ring<D, B>(pv, td, b, R);
         __syncthreads();
       }
-      fill_tile<D, B, TS, TT, 2>(pv, b, y, y, tile, true, R, cbox, scr);
+      if constexpr (D == 2)
+        fill_tile<D, B, TS, TT, 2>(pv, b, y, y, tile, true, R, cbox, scr);
+      else
+        fill_cols<B, TS, TT, 2>(pv, b, nullptr, y, y, tile, true, R, cbox, scr);
     }
     __syncthreads();
     // Block maximum of |d| over the interior with arithmetic type A: x pass on
