@@ -38,6 +38,7 @@ struct mr_ctx_s {
   int16_t* tree = nullptr;
   int32_t* stamp = nullptr;
   int32_t* plan = nullptr;  // S x 32: stage plans of the active blocks
+  int4* regs = nullptr;     // S x (NREG + 1): class-box owner tables built with the plans
   int32_t *crd = nullptr, *act = nullptr, *act_next = nullptr, *freelist = nullptr, *tab = nullptr,
           *cells = nullptr, *emit = nullptr, *eoff = nullptr, *partial = nullptr, *pos = nullptr;
   uint64_t* hkey = nullptr;
@@ -129,6 +130,7 @@ PoolView view(mr_ctx c) {
   v.svar = c->svar; v.cells = c->cells; v.emit = c->emit; v.eoff = c->eoff;
   v.partial = c->partial; v.pos_of_slot = c->pos; v.cnt = c->cnt; v.stamp = c->stamp;
   v.plan = c->plan;
+  v.regs = c->regs;
   return v;
 }
 Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb}; }
@@ -677,6 +679,7 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if ((e = dalloc(ctx, &ctx->stamp, S))) return e;
     if ((e = cudaMemset(ctx->stamp, 0, S * 4))) return e;
     if ((e = dalloc(ctx, &ctx->plan, S * 32))) return e;
+    if ((e = dalloc(ctx, &ctx->regs, S * reg_entries(d)))) return e;
     if ((e = dalloc(ctx, &ctx->tab, ctx->ntab))) return e;
     if ((e = dalloc(ctx, &ctx->cells, 2 * ctx->ncells))) return e;
     if ((e = dalloc(ctx, &ctx->emit, 2 * ctx->nscan))) return e;

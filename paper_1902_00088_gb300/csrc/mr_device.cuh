@@ -211,6 +211,7 @@ struct RingD {
 };
 template <int D>
 constexpr int kRingBytesD = (int)((sizeof(RingD<D>) + 15) / 16 * 16);
+static_assert(RingD<2>::NREG + 1 == reg_entries(2) && RingD<3>::NREG + 1 == reg_entries(3), "table size");
 
 template <int D, int B, typename G = CtaGroup>
 __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, RingD<D>& R) {
@@ -436,6 +437,34 @@ __device__ void build_regions(const BlockInfo& b, RingD<D>& R) {
   }
 }
 
+// Class-box owner table of plan position p (built with the stage plan while
+// the tree is fixed): NREG entries, then {finer, coarser, mixed}.
+template <int D>
+__device__ __forceinline__ int4* plan_regions(const PoolView& pv, int p) {
+  return pv.regs + (int64_t)p * (RingD<D>::NREG + 1);
+}
+template <int D, typename G>
+__device__ void store_regions(const PoolView& pv, int p, const RingD<D>& R) {
+  const G g{};
+  int4* dst = plan_regions<D>(pv, p);
+  for (int r = g.rank(); r < RingD<D>::NREG; r += g.size()) dst[r] = R.reg[r];
+  if (g.rank() == 0) dst[RingD<D>::NREG] = make_int4(R.finer, R.coarser, R.mixed, 0);
+}
+// Loads the table of plan position p into the ring (the caller synchronises
+// the group before use).
+template <int D, typename G>
+__device__ void load_regions(const PoolView& pv, int p, RingD<D>& R) {
+  const G g{};
+  const int4* src = plan_regions<D>(pv, p);
+  for (int r = g.rank(); r < RingD<D>::NREG; r += g.size()) R.reg[r] = src[r];
+  if (g.rank() == 0) {
+    const int4 f = src[RingD<D>::NREG];
+    R.finer = f.x;
+    R.coarser = f.y;
+    R.mixed = f.z;
+  }
+}
+
 // Separable prediction over the coarse box (values of nv variables in cbox),
 // x first, then y (then z at the point): the same operations in the same order
 // as predict_box.  2D: the x pass goes to scr (y per point from it); 3D: the x
@@ -498,7 +527,7 @@ __device__ __forceinline__ TT coarse_predicted(const TT* scr_v, int i, int j, in
 // nodes between coarse nodes are predicted from it.
 template <int D, int B, typename TF, typename TT, int W = kG, typename G = CtaGroup>
 __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, TF* Fw, TT* tile,
-                          bool commit, RingD<D>& R, TT* cbox, TT* scr = nullptr) {
+                          bool commit, RingD<D>& R, TT* cbox, TT* scr = nullptr, bool have_regions = false) {
   const G g{};
   using Gm = Geo<D, B>;
   using Bx = Box<D, B, W>;
@@ -557,8 +586,11 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
     return;
   }
   // some ring leaf is at another level: one owner search per class box
-  build_regions<D, B, G>(b, R);
-  g.sync();
+  // (unless the table was loaded from the stage plan)
+  if (!have_regions) {
+    build_regions<D, B, G>(b, R);
+    g.sync();
+  }
   const int l1 = b.lvl + 1;
   // owner of level-l node x (relative to the block origin) and the node's
   // offset inside it in level-(l+1) units
@@ -706,7 +738,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
 // (build_ring must have run).  Same values, stores and commits as fill_tile.
 template <int B, typename TF, typename TT, int W>
 __device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t* nbase, const TF* F, TF* Fw,
-                          TT* tile, bool commit, RingD<3>& R, TT* cbox, TT* scr) {
+                          TT* tile, bool commit, RingD<3>& R, TT* cbox, TT* scr, bool have_regions = false) {
   using Gm = Geo<3, B>;
   using Bx = Box<3, B, W>;
   constexpr int S = Bx::S, S2 = S * S, BB = B * B;
@@ -740,8 +772,10 @@ __device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t*
     }
   };
   if (!uni) {
-    build_regions<3, B, CtaGroup>(b, R);
-    __syncthreads();
+    if (!have_regions) {
+      build_regions<3, B, CtaGroup>(b, R);
+      __syncthreads();
+    }
     if (R.coarser) {
       // coarse box: columns of CB coarse nodes (coarse node n at level-l node 2n)
       constexpr int CB = Bx::CB;

@@ -19,6 +19,10 @@ constexpr int kErrNaN = 4;
 constexpr int kErrLayout = 8;    // set_blocks: overlap / gap / unsorted input
 constexpr int kErrTimeout = 16;
 
+// Entries (int4) of a block's class-box owner table: 7^d class boxes of the
+// ring around the block, then one entry of flags.
+constexpr int reg_entries(int d) { return (d == 3 ? 343 : 49) + 1; }
+
 // Per-tree constants (device copy).
 struct TreeDev {
   int32_t Jmin, Jmax;
@@ -118,6 +122,8 @@ struct PoolView {
   int32_t* pos_of_slot;
   int32_t* stamp;          // per slot: round_id of the round that created the block (merges)
   int32_t* plan;           // per active position: stage plan (slot, level/tree, coords, neighbours)
+  int4* regs;              // per active position: class-box owners of a block whose neighbourhood is
+                           // not uniform (RingD::NREG entries + flags), built with the stage plan
   Counters* cnt;
   const TreeTime* tt;      // stage coefficients from device memory (graph mode), or null
 };

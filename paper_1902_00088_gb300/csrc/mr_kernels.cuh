@@ -86,12 +86,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_stage_
       else
         fill_cols<B, TSRC, TC, 2>(pv, b, snb[buf], src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
     } else {
-      build_ring<D, B>(pv, td, b, R);
+      load_regions<D, CtaGroup>(pv, p, R);
       __syncthreads();
       if constexpr (D == 2)
-        fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
+        fill_tile<D, B, TSRC, TC, 2>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr, true);
       else
-        fill_cols<B, TSRC, TC, 2>(pv, b, nullptr, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
+        fill_cols<B, TSRC, TC, 2>(pv, b, nullptr, src, (TSRC*)src, tile, stage == 0, R, cbox, scr, true);
     }
     __syncthreads();
     const TC c = tree_cD<TC>(td, b.lvl);
@@ -277,9 +277,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
       gather_table<2, B, 2, 1, TSRC, TC, WarpGroup>(pv, (int64_t)b.slot * pv.vs, snb[warp], gtab, src, (TSRC*)src,
                                                     tile, stage == 0);
     } else {
-      build_ring<2, B, WarpGroup>(pv, td, b, R);
+      load_regions<2, WarpGroup>(pv, p, R);
       __syncwarp();
-      fill_tile<2, B, TSRC, TC, 2, WarpGroup>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr);
+      fill_tile<2, B, TSRC, TC, 2, WarpGroup>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr, true);
     }
     __syncwarp();
     const TC c = tree_cD<TC>(td, b.lvl);
@@ -345,47 +345,53 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
   }
 }
 
-// Stage plan of active position p (layout in Plan<D>): the 3^d - 1
-// equal-level neighbours looked up in the dense leaf tables.
-template <int D>
-__device__ __forceinline__ void plan_one(const PoolView& pv, int p) {
-  using PL = Plan<D>;
-  const int s = pv.act[p];
-  const int l = pv.lvl[s], t = pv.tree[s];
-  const TreeDev& td = pv.trees[t];
-  int64_t c[3] = {0, 0, 0};
-  for (int a = 0; a < D; ++a) c[a] = pv.crd[3 * s + a];
-  int32_t* out = pv.plan + (int64_t)p * PL::INTS;
-  // all lookups first (independent loads, in flight together), then the stores
-  int32_t qn[PL::NB];
-#pragma unroll
-  for (int n = 0; n < PL::NB; ++n) {
-    const int o[3] = {n % 3 - 1, (n / 3) % 3 - 1, D == 3 ? n / 9 - 1 : 0};
-    int q = s;
-    if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
-      const int64_t cn[3] = {c[0] + o[0], c[1] + o[1], c[2] + o[2]};
-      q = tab_get<D>(pv, td, l, cn);
-    }
-    qn[n] = q;
-  }
-  bool uni = true;
-#pragma unroll
-  for (int n = 0; n < PL::NB; ++n) {
-    uni &= qn[n] >= 0;
-    out[PL::NBO + n] = qn[n];
-  }
-  out[0] = s;
-  out[1] = l | (t << 8) | (uni ? 1 << 30 : 0);
-  for (int a = 0; a < D; ++a) out[2 + a] = (int32_t)c[a];
-}
-
-// Stage plans of all active blocks, one thread per block; they stay valid
-// while the tree generation is unchanged.
-template <int D>
-__global__ void k_plan(PoolView pv) {
+// Stage plans of all active blocks, one warp per block (layout in Plan<D>):
+// the 3^d - 1 equal-level neighbours, one lookup per lane in the dense leaf
+// tables; for a block whose neighbourhood is not uniform, also its ring and
+// class-box owner table (RingD), so that the four RK stages of the step and
+// the first coarsening round gather without searching.  Both stay valid while
+// the tree generation is unchanged.
+template <int D, int B>
+__global__ void __launch_bounds__(128) k_plan(PoolView pv) {
   pdl_enter();
+  using PL = Plan<D>;
+  static_assert(PL::NB <= 32 && PL::INTS <= 32, "one lane per neighbour");
+  constexpr int NW = 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RingD<D>& R = *smem_as<RingD<D>>((size_t)warp * kRingBytesD<D>);
   const int nact = pv.cnt->n_act;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) plan_one<D>(pv, p);
+  for (int p = blockIdx.x * NW + warp; p < nact; p += gridDim.x * NW) {
+    const int s = pv.act[p];
+    BlockInfo b;
+    b.slot = s;
+    b.lvl = pv.lvl[s];
+    b.tree = pv.tree[s];
+    for (int a = 0; a < 3; ++a) b.c[a] = a < D ? pv.crd[3 * s + a] : 0;
+    const TreeDev& td = pv.trees[b.tree];
+    int q = s;
+    if (lane < PL::NB) {
+      const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, D == 3 ? lane / 9 - 1 : 0};
+      if (o[0] != 0 || o[1] != 0 || o[2] != 0) {
+        const int64_t cn[3] = {b.c[0] + o[0], b.c[1] + o[1], b.c[2] + o[2]};
+        q = tab_get<D>(pv, td, b.lvl, cn);
+      }
+    }
+    const bool uni = __all_sync(0xffffffffu, q >= 0);
+    int32_t* out = pv.plan + (int64_t)p * PL::INTS;
+    if (lane == 0) out[0] = s;
+    if (lane == 1) out[1] = b.lvl | (b.tree << 8) | (uni ? 1 << 30 : 0);
+    if (lane >= 2 && lane < 2 + D) out[lane] = (int32_t)b.c[lane - 2];
+    const int qs = __shfl_sync(0xffffffffu, q, (lane - PL::NBO) & 31);
+    if (lane >= PL::NBO && lane < PL::NBO + PL::NB) out[lane] = qs;
+    if (!uni) {
+      build_ring<D, B, WarpGroup>(pv, td, b, R);
+      __syncwarp();
+      build_regions<D, B, WarpGroup>(b, R);
+      __syncwarp();
+      store_regions<D, WarpGroup>(pv, p, R);
+      __syncwarp();
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) pv.cnt->plan_topo = pv.cnt->topo;
 }
 
@@ -460,10 +466,10 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
     if ((pl[1] >> 30) & 1) {
       gather_uniform<2, B, kG, 4, TSRC, TC>(pv, b, pl + PL::NBO, src, (TSRC*)src, tile, stage == 0);
     } else {
-      build_ring<2, B>(pv, td, b, R);
+      load_regions<2, CtaGroup>(pv, p, R);
       __syncthreads();
       // prediction scratch: the primitive arrays, unused until the tile is complete
-      fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, pu);
+      fill_tile<2, B, TSRC, TC>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, pu, true);
     }
     __syncthreads();
     // gamma - 1, mu and kappa = mu gamma / ((gamma - 1) Pr), formed once per tree
@@ -890,6 +896,10 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     if (uni) {
       // the ring's leaves are the block and its 3^d - 1 equal-level neighbours
       if (!all_blocks && threadIdx.x < PL::NB && pv.stamp[q] == prev) dirty = 1;
+    } else if (plan_ok && all_blocks) {
+      // every block is evaluated and the tree is the stage plan's: its
+      // class-box owner table is ready
+      load_regions<D, CtaGroup>(pv, p, R);
     } else {
       build_ring<D, B>(pv, td, b, R);
       __syncthreads();
@@ -920,10 +930,11 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         build_ring<D, B>(pv, td, b, R);
         __syncthreads();
       }
+      const bool ready = !uni && plan_ok && all_blocks;
       if constexpr (D == 2)
-        fill_tile<D, B, TS, TT, 2>(pv, b, y, y, tile, true, R, cbox, scr);
+        fill_tile<D, B, TS, TT, 2>(pv, b, y, y, tile, true, R, cbox, scr, ready);
       else
-        fill_cols<B, TS, TT, 2>(pv, b, nullptr, y, y, tile, true, R, cbox, scr);
+        fill_cols<B, TS, TT, 2>(pv, b, nullptr, y, y, tile, true, R, cbox, scr, ready);
     }
     __syncthreads();
     // Block maximum of |d| over the interior with arithmetic type A: x pass on
@@ -1134,11 +1145,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
         __syncwarp();
         gather_table<2, B, 2, 1, TS, TS, WarpGroup>(pv, own, snbo[warp], gtab, y, y, tile, true);
       } else {
-        if (!ring) {
-          build_ring<2, B, WarpGroup>(pv, td, b, R);
-          __syncwarp();
-        }
-        fill_tile<2, B, TS, TS, 2, WarpGroup>(pv, b, y, y, tile, true, R, cbox, scr);
+        const bool ready = !ring && plan_ok && all_blocks;  // the stage plan's owner table
+        if (ready) load_regions<2, WarpGroup>(pv, p, R);
+        else if (!ring) build_ring<2, B, WarpGroup>(pv, td, b, R);
+        __syncwarp();
+        fill_tile<2, B, TS, TS, 2, WarpGroup>(pv, b, y, y, tile, true, R, cbox, scr, ready);
       }
       __syncwarp();
       // the x pass over the coarse rows, then the y pass and the detail at

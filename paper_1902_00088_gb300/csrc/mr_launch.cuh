@@ -134,7 +134,10 @@ static void stage_ns(const PoolView& pv, const Fields& f, int stage, const Stage
 
 template <int D>
 void launch_plan(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st) {
-  launch_k(lc.pdl, k_plan<D>, lc.num_sms * 4, 128, 0, st, pv);
+  const size_t smem = 4 * kRingBytesD<D>;  // one ring per warp
+  if constexpr (D == 3) launch_k(lc.pdl, k_plan<3, 17>, lc.num_sms * 8, 128, smem, st, pv);
+  else if (pv.Bs == 17) launch_k(lc.pdl, k_plan<2, 17>, lc.num_sms * 8, 128, smem, st, pv);
+  else launch_k(lc.pdl, k_plan<2, 33>, lc.num_sms * 8, 128, smem, st, pv);
   count_launch();
 }
 
