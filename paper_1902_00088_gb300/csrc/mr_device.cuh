@@ -28,6 +28,18 @@ __device__ __forceinline__ void static_for(Fn&& f) {
   }
 }
 
+// Asynchronous global -> shared copy of one 4- or 8-byte value (cp.async):
+// the value goes to shared memory without passing through registers, so a
+// thread can have every copy of a tile in flight at once; cp_async_wait_all
+// waits for the calling thread's copies (a barrier then publishes them).
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem_dst, const T* gmem_src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async of 4 or 8 bytes");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src), "n"(sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Thread groups that cooperate on one block: the whole CTA, or one warp.
 struct CtaGroup {
   static constexpr int kSize = 0;  // size known at run time only
@@ -205,6 +217,10 @@ struct RingD {
   int finer;    // some leaf one level finer touches the block
   int coarser;  // some leaf one level coarser touches the block
   int mixed;    // some ring leaf is not at the block's level
+  // classes (bit c of 7 per axis: x, y << 7, z << 14) of the class boxes owned
+  // by a coarser leaf: the tile nodes predicted from the coarse lattice lie
+  // in their union, so the separable prediction passes are confined to it
+  int cmask;
   // per class box: owner slot (-1: none), owner level, owner origin
   // (level-(l+1) node units, relative to the block origin) x | y << 16, z
   int4 reg[NREG];
@@ -217,7 +233,7 @@ template <int D, int B, typename G = CtaGroup>
 __device__ void build_ring(const PoolView& pv, const TreeDev& td, const BlockInfo& b, RingD<D>& R) {
   const G g{};
   using Gm = Geo<D, B>;
-  if (g.rank() == 0) R.finer = R.coarser = R.mixed = 0;
+  if (g.rank() == 0) R.finer = R.coarser = R.mixed = R.cmask = 0;
   g.sync();
   for (int r = g.rank(); r < Gm::NR; r += g.size()) {
     const int q[3] = {r % 4 - 1, (r / 4) % 4 - 1, r / 16 - 1};
@@ -432,6 +448,7 @@ __device__ void build_regions(const BlockInfo& b, RingD<D>& R) {
     if (owner<D, B>(b, h, 0, R, o)) {
       const int ox = h[0] - o.off[0], oy = h[1] - o.off[1], oz = h[2] - o.off[2];
       e = make_int4(o.slot, o.m, (ox & 0xffff) | (oy << 16), oz);
+      if (o.m < b.lvl) atomicOr(&R.cmask, (1 << c[0]) | (1 << (7 + c[1])) | (D == 3 ? 1 << (14 + c[2]) : 0));
     }
     R.reg[r] = e;
   }
@@ -448,7 +465,7 @@ __device__ void store_regions(const PoolView& pv, int p, const RingD<D>& R) {
   const G g{};
   int4* dst = plan_regions<D>(pv, p);
   for (int r = g.rank(); r < RingD<D>::NREG; r += g.size()) dst[r] = R.reg[r];
-  if (g.rank() == 0) dst[RingD<D>::NREG] = make_int4(R.finer, R.coarser, R.mixed, 0);
+  if (g.rank() == 0) dst[RingD<D>::NREG] = make_int4(R.finer, R.coarser, R.mixed, R.cmask);
 }
 // Loads the table of plan position p into the ring (the caller synchronises
 // the group before use).
@@ -462,42 +479,82 @@ __device__ void load_regions(const PoolView& pv, int p, RingD<D>& R) {
     R.finer = f.x;
     R.coarser = f.y;
     R.mixed = f.z;
+    R.cmask = f.w;
   }
 }
 
+// Tile nodes (per axis, tile coordinates) that can be predicted from the
+// coarse lattice: the span of the classes in mask7 (bit c = class c of
+// reg_class), clipped to the tile box of ghost width W; and the coarse
+// indices the separable passes read for them, clipped to the coarse box.
+template <int B, int W>
+struct PredBox {
+  int lo[3], hi[3];    // predicted tile nodes
+  int nlo[3], nhi[3];  // coarse nodes their prediction reads
+  __device__ __forceinline__ PredBox(int cmask, int D) {
+    constexpr int H = (B - 1) / 2;
+    using Bx = Box<2, B, W>;  // CLO and CB do not depend on the dimension
+    // first and last node of class c within the tile box
+    auto clo = [](int c) { return c == 0 ? -W : c == 1 ? 0 : c == 2 ? 1 : c == 3 ? H : c == 4 ? H + 1 : c == 5 ? 2 * H : 2 * H + 1; };
+    auto chi = [](int c) { return c == 0 ? -1 : c == 1 ? 0 : c == 2 ? H - 1 : c == 3 ? H : c == 4 ? 2 * H - 1 : c == 5 ? 2 * H : B - 1 + W; };
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int m = (cmask >> (7 * a)) & 127;
+      if (a >= D || m == 0) {
+        lo[a] = hi[a] = 0;
+        nlo[a] = nhi[a] = 0;
+        continue;
+      }
+      lo[a] = clo(__ffs(m) - 1);
+      hi[a] = chi(31 - __clz(m));
+      nlo[a] = max(Bx::CLO, (lo[a] >> 1) - 1);
+      nhi[a] = min(Bx::CLO + Bx::CB - 1, (hi[a] >> 1) + 2);
+    }
+  }
+};
+
 // Separable prediction over the coarse box (values of nv variables in cbox),
 // x first, then y (then z at the point): the same operations in the same order
-// as predict_box.  2D: the x pass goes to scr (y per point from it); 3D: the x
-// pass is kept in the variable's tile (overwritten later by the gather) and
-// the y pass goes to scr (z per point).  Ends with a group barrier.
+// as predict_box, evaluated only where the predicted nodes of pb need them.
+// 2D: the x pass goes to scr (y per point from it); 3D: the x pass is kept in
+// the variable's tile (overwritten later by the gather) and the y pass goes to
+// scr (z per point).  Ends with a group barrier.
 template <int D, int B, int W, typename TT, typename G>
-__device__ void coarse_passes(int nv, const TT* cbox, TT* tile, TT* scr) {
+__device__ void coarse_passes(int nv, const TT* cbox, TT* tile, TT* scr, const PredBox<B, W>& pb) {
   const G g{};
   using Bx = Box<D, B, W>;
+  // x pass: x in [lo0, hi0], coarse rows ny in [nlo1, nhi1], nz in [nlo2, nhi2]
+  const int ex = pb.hi[0] - pb.lo[0] + 1, ey = pb.nhi[1] - pb.nlo[1] + 1;
+  const int nxp = ex * ey * (D == 3 ? pb.nhi[2] - pb.nlo[2] + 1 : 1);
   for (int v = 0; v < nv; ++v) {
     const TT* cb = cbox + v * Bx::CBOX;
     TT* X = D == 3 ? tile + v * Bx::TILE : scr + v * Bx::SCR;
-    for (int q = g.rank(); q < Bx::NXP; q += g.size()) {
-      const int x = q % Bx::S - W, ny = (q / Bx::S) % Bx::CB + Bx::CLO;
-      const int nz = D == 3 ? q / (Bx::S * Bx::CB) + Bx::CLO : 0;
+    for (int q = g.rank(); q < nxp; q += g.size()) {
+      const int x = q % ex + pb.lo[0], ny = (q / ex) % ey + pb.nlo[1];
+      const int nz = D == 3 ? q / (ex * ey) + pb.nlo[2] : 0;
       const int fl = x >> 1;
-      X[q] = (x & 1) ? dd4(cb[Bx::cix(fl - 1, ny, nz)], cb[Bx::cix(fl, ny, nz)], cb[Bx::cix(fl + 1, ny, nz)],
-                           cb[Bx::cix(fl + 2, ny, nz)])
-                     : cb[Bx::cix(fl, ny, nz)];
+      const int at = ((D == 3 ? nz - Bx::CLO : 0) * Bx::CB + (ny - Bx::CLO)) * Bx::S + (x + W);
+      X[at] = (x & 1) ? dd4(cb[Bx::cix(fl - 1, ny, nz)], cb[Bx::cix(fl, ny, nz)], cb[Bx::cix(fl + 1, ny, nz)],
+                            cb[Bx::cix(fl + 2, ny, nz)])
+                      : cb[Bx::cix(fl, ny, nz)];
     }
   }
   if (D == 3) {
     g.sync();
+    // y pass: x in [lo0, hi0], y in [lo1, hi1], coarse nz in [nlo2, nhi2]
+    const int fy = pb.hi[1] - pb.lo[1] + 1;
+    const int nyp = ex * fy * (pb.nhi[2] - pb.nlo[2] + 1);
     for (int v = 0; v < nv; ++v) {
       const TT* X = tile + v * Bx::TILE;
       TT* Y = scr + v * Bx::SCR;
-      for (int q = g.rank(); q < Bx::NYP; q += g.size()) {
-        const int x = q % Bx::S, y = (q / Bx::S) % Bx::S - W, nzi = q / (Bx::S * Bx::S);
+      for (int q = g.rank(); q < nyp; q += g.size()) {
+        const int x = q % ex + pb.lo[0] + W, y = (q / ex) % fy + pb.lo[1];
+        const int nzi = q / (ex * fy) + pb.nlo[2] - Bx::CLO;
         const int fl = y >> 1;
         const TT* c = X + nzi * Bx::CB * Bx::S + x;
-        Y[q] = (y & 1) ? dd4(c[(fl - 1 - Bx::CLO) * Bx::S], c[(fl - Bx::CLO) * Bx::S],
-                             c[(fl + 1 - Bx::CLO) * Bx::S], c[(fl + 2 - Bx::CLO) * Bx::S])
-                       : c[(fl - Bx::CLO) * Bx::S];
+        Y[(nzi * Bx::S + (y + W)) * Bx::S + x] = (y & 1) ? dd4(c[(fl - 1 - Bx::CLO) * Bx::S], c[(fl - Bx::CLO) * Bx::S],
+                                                               c[(fl + 1 - Bx::CLO) * Bx::S], c[(fl + 2 - Bx::CLO) * Bx::S])
+                                                         : c[(fl - Bx::CLO) * Bx::S];
       }
     }
   }
@@ -603,7 +660,8 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
     off[1] = 2 * x[1] - (e.z >> 16);
     off[2] = D == 3 ? 2 * x[2] - e.w : 0;
   };
-  if (R.coarser) {
+  if (R.coarser && R.cmask) {
+    const PredBox<B, W> pb(R.cmask, D);
     for (int q0 = g.rank(); q0 < Bx::CBOX; q0 += U * g.size()) {
       int64_t at[U];
       bool ok[U], good[U];
@@ -614,9 +672,14 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
         good[u] = false;
         at[u] = 0;
         if (!ok[u]) continue;
+        const int n[3] = {idx % Bx::CB + Bx::CLO, (idx / Bx::CB) % Bx::CB + Bx::CLO,
+                          D == 3 ? idx / (Bx::CB * Bx::CB) + Bx::CLO : 0};
+        bool need = true;  // read by the prediction of some node of pb
+#pragma unroll
+        for (int a = 0; a < D; ++a) need &= n[a] >= pb.nlo[a] && n[a] <= pb.nhi[a];
+        if (!need) continue;
         // coarse node n sits at level-l node 2n
-        const int x[3] = {2 * (idx % Bx::CB + Bx::CLO), 2 * ((idx / Bx::CB) % Bx::CB + Bx::CLO),
-                          D == 3 ? 2 * (idx / (Bx::CB * Bx::CB) + Bx::CLO) : 0};
+        const int x[3] = {2 * n[0], 2 * n[1], 2 * n[2]};
         int slot, m, off[3];
         region(x, slot, m, off);
         if (slot < 0 || m < b.lvl - 1) {
@@ -637,7 +700,7 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       }
     }
     g.sync();
-    if (scr) coarse_passes<D, B, W, TT, G>(nv, cbox, tile, scr);
+    if (scr) coarse_passes<D, B, W, TT, G>(nv, cbox, tile, scr, pb);
   }
   // kinds of tile points: 0 own node, 1 block-edge node of another owner,
   // 2 ghost node that is a node of its owner, 3 ghost predicted from the coarse
@@ -742,13 +805,29 @@ __device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t*
   using Gm = Geo<3, B>;
   using Bx = Box<3, B, W>;
   constexpr int S = Bx::S, S2 = S * S, BB = B * B;
-  constexpr int KC = 7;  // loads in flight per thread
+  // same field and tile types: asynchronous copies, all in flight at once
+  constexpr bool ASYNC = std::is_same<TF, TT>::value;
+  constexpr int KC = ASYNC ? 11 : 7;  // nodes per chunk (register loads in flight)
   const int nv = pv.nvar;
   const int64_t own = (int64_t)b.slot * nv * pv.vs;
   const int l1 = b.lvl + 1;
   const bool uni = nbase != nullptr;
   auto load_store = [&](auto kcc, const int64_t* at, const int* kind, int col, int i, int j, int kbase) {
     constexpr int KN = decltype(kcc)::value;
+    if constexpr (ASYNC) {
+      // copies now; block-edge nodes of other owners are committed after the wait
+      for (int v = 0; v < nv; ++v) {
+#pragma unroll
+        for (int u = 0; u < KN; ++u) {
+          const int k = kbase + u;
+          TT* t = tile + v * Bx::TILE + col + (k + W) * S2;
+          if (kind[u] <= 2) cp_async(t, F + at[u] + (int64_t)v * pv.vs);
+          else if (kind[u] == 3) *t = coarse_predicted<3, B, W, TT>(scr + v * Bx::SCR, i, j, k);
+          else *t = TT(0);
+        }
+      }
+      return;
+    }
     for (int v = 0; v < nv; ++v) {
       TF val[KN];
 #pragma unroll
@@ -776,32 +855,69 @@ __device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t*
       build_regions<3, B, CtaGroup>(b, R);
       __syncthreads();
     }
-    if (R.coarser) {
-      // coarse box: columns of CB coarse nodes (coarse node n at level-l node 2n)
+    if (R.coarser && R.cmask) {
+      // coarse box: columns of CB coarse nodes (coarse node n at level-l node
+      // 2n), where the prediction of the nodes of pb reads them
+      const PredBox<B, W> pb(R.cmask, 3);
       constexpr int CB = Bx::CB;
       for (int c = threadIdx.x; c < CB * CB; c += blockDim.x) {
         const int nx = c % CB + Bx::CLO, ny = c / CB + Bx::CLO;
+        if (nx < pb.nlo[0] || nx > pb.nhi[0] || ny < pb.nlo[1] || ny > pb.nhi[1]) continue;
         const int rb = reg_class<B>(2 * nx) + 7 * reg_class<B>(2 * ny);
+        // per chunk of the column: addresses first, then the loads, then the stores
+        bool bad = false;
+        auto cchunk = [&](auto knc, auto z0c) {
+          constexpr int KN = decltype(knc)::value, Z0 = decltype(z0c)::value;
+          int64_t at[KN];
+          int good[KN];  // 1 load, 0 not needed, -1 no owner (error)
 #pragma unroll
-        for (int z = 0; z < CB; ++z) {
-          const int nz = z + Bx::CLO;
-          const int4 e = R.reg[rb + 49 * reg_class<B>(2 * nz)];
-          bool good = true;
-          int64_t at = 0;
-          if (e.x < 0 || e.y < b.lvl - 1) {
-            set_err(pv, kErrGraded);
-            good = false;
-          } else {
+          for (int u = 0; u < KN; ++u) {
+            const int nz = Z0 + u + Bx::CLO;
+            at[u] = 0;
+            good[u] = 0;
+            if (nz < pb.nlo[2] || nz > pb.nhi[2]) continue;
+            const int4 e = R.reg[rb + 49 * reg_class<B>(2 * nz)];
+            if (e.x < 0 || e.y < b.lvl - 1) {
+              good[u] = -1;
+              continue;
+            }
             const int sh = l1 - e.y;
             const int ox = 4 * nx - (int)(int16_t)(e.z & 0xffff), oy = 4 * ny - (e.z >> 16), oz = 4 * nz - e.w;
-            at = ((int64_t)e.x * nv) * pv.vs + Gm::lin(ox >> sh, oy >> sh, oz >> sh);
+            at[u] = ((int64_t)e.x * nv) * pv.vs + Gm::lin(ox >> sh, oy >> sh, oz >> sh);
+            good[u] = 1;
           }
-          for (int v = 0; v < nv; ++v)
-            cbox[v * Bx::CBOX + z * CB * CB + c] = good ? (TT)F[at + (int64_t)v * pv.vs] : TT(0);
-        }
+          for (int v = 0; v < nv; ++v) {
+            if constexpr (ASYNC) {
+#pragma unroll
+              for (int u = 0; u < KN; ++u) {
+                TT* t = cbox + v * Bx::CBOX + (Z0 + u) * CB * CB + c;
+                if (good[u] > 0) cp_async(t, F + at[u] + (int64_t)v * pv.vs);
+                else if (good[u] < 0) *t = TT(0);
+                bad |= good[u] < 0;
+              }
+            } else {
+              TF val[KN];
+#pragma unroll
+              for (int u = 0; u < KN; ++u) val[u] = good[u] > 0 ? F[at[u] + (int64_t)v * pv.vs] : TF(0);
+#pragma unroll
+              for (int u = 0; u < KN; ++u) {
+                if (good[u] != 0) cbox[v * Bx::CBOX + (Z0 + u) * CB * CB + c] = good[u] > 0 ? (TT)val[u] : TT(0);
+                bad |= good[u] < 0;
+              }
+            }
+          }
+        };
+        constexpr int ZC = 7;
+        static_for<0, (CB + ZC - 1) / ZC>([&](auto cc) {
+          constexpr int C = decltype(cc)::value;
+          constexpr int KN = (CB - C * ZC) < ZC ? (CB - C * ZC) : ZC;
+          cchunk(std::integral_constant<int, KN>{}, std::integral_constant<int, C * ZC>{});
+        });
+        if (bad) set_err(pv, kErrGraded);
       }
+      if constexpr (ASYNC) cp_async_wait_all();
       __syncthreads();
-      if (scr) coarse_passes<3, B, W, TT, CtaGroup>(nv, cbox, tile, scr);
+      if (scr) coarse_passes<3, B, W, TT, CtaGroup>(nv, cbox, tile, scr, pb);
     }
   }
   for (int col = threadIdx.x; col < S2; col += blockDim.x) {
@@ -863,6 +979,34 @@ __device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t*
       constexpr int KN = (S - C * KC) < KC ? (S - C * KC) : KC;
       chunk(std::integral_constant<int, KN>{}, std::integral_constant<int, K0>{});
     });
+  }
+  if constexpr (ASYNC) {
+    cp_async_wait_all();
+    if (commit) {
+      // block-edge nodes owned by another block: store the owner's value (now
+      // in the tile) where the block's own copy differs
+      __syncthreads();
+      for (int col = threadIdx.x; col < BB; col += blockDim.x) {
+        const int i = col % B, j = col / B;
+        const bool side = i == 0 || i == B - 1 || j == 0 || j == B - 1;
+        const int sx = i <= B - 2 ? 1 : 2, sy = j <= B - 2 ? 1 : 2;
+        const int rb = reg_class<B>(i) + 7 * reg_class<B>(j);
+        for (int k = 0; k < B; k += (side || k == B - 1) ? 1 : B - 1) {
+          bool other;
+          if (uni) {
+            other = nbase[sx + 3 * sy + 9 * (k <= B - 2 ? 1 : 2)] != own;
+          } else {
+            other = R.reg[rb + 49 * reg_class<B>(k)].x != b.slot;
+          }
+          if (!other) continue;
+          for (int v = 0; v < nv; ++v) {
+            const TT val = tile[v * Bx::TILE + Bx::tix(i, j, k)];
+            const int64_t me = own + (int64_t)v * pv.vs + Gm::lin(i, j, k);
+            if (F[me] != val) Fw[me] = val;
+          }
+        }
+      }
+    }
   }
 }
 
