@@ -93,7 +93,6 @@ TRAFFIC = {
     "forest": ("k_stage_adv_w", 31.653632e6 + 11.776e3),
     "uniform2d": ("k_stage_adv_w", 947.365888e6 + 569.117184e6),
     "adv3d": ("k_stage_adv", 82.599168e6 + 13.831168e6),
-    "ns_thin": ("k_stage_ns", 1.317254e9 + 736.219648e6),
 }
 
 
@@ -290,7 +289,7 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,)):
+def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,), bs=33):
     """The swirl study of Sec. 3 (Fig. 4A-D as data): 33^2 blocks, blob beta 1e-2 at (0.5, 0.75), t_a 5,
     Jmin 1, CFL 0.5, plain FP64, steps replayed as CUDA graphs up to t_a; per run the error against the
     initial field, the adapted grid's size against the uniform one and the time per step."""
@@ -305,10 +304,10 @@ def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,)):
         # Sec. 3: phi_0 = exp(-r^2 / beta) = exp(-r^2 / (2 sigma^2)), sigma = sqrt(beta / 2)
         tree = dict(Jmin=1, Jmax=jmax, eps=eps, ic="gauss", ic_params=(0.5, 0.75, 0.0, math.sqrt(beta / 2)),
                     rhs_params=(t_a,))
-        g = mr.Forest(dim=2, Bs=33, precision="fp64", rhs="swirl", trees=[tree], capacity=200_000,
+        g = mr.Forest(dim=2, Bs=bs, precision="fp64", rhs="swirl", trees=[tree], capacity=400_000,
                       stream=stream.cuda_stream)
         g.init_tree()
-        n = int(math.ceil(t_a / (0.5 / (32 * (1 << jmax)))))
+        n = int(math.ceil(t_a / (0.5 / ((bs - 1) * (1 << jmax)))))
         g.set_time(0.0, t_a / n)
         g.step_graph(1)  # captures the step graph (untimed)
         g.step_history(reset=True)
@@ -321,7 +320,7 @@ def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,)):
         el = e0.elapsed_time(e1) / 1e3
         hist = g.step_history(reset=True)
         err = g.error(0, 0.0)
-        print(json.dumps(dict(study="swirl33", beta=beta, Jmax=jmax, eps=eps, steps=n, l2=err["l2"], linf=err["linf"],
+        print(json.dumps(dict(study="swirl33", Bs=bs, beta=beta, Jmax=jmax, eps=eps, steps=n, l2=err["l2"], linf=err["linf"],
                               blocks_mean=float(np.mean(hist)), blocks_max=int(np.max(hist)),
                               uniform_blocks=4 ** jmax, ms_per_step=1e3 * el / (n - 1),
                               timing="CUDA events around graph replays 2..n on the context's stream")),
@@ -376,6 +375,7 @@ def main():
     ap.add_argument("--study-jmax", default="4,5", help="swirl33: comma-separated Jmax values")
     ap.add_argument("--study-eps", default="1e-3,1e-4,1e-5,1e-6", help="swirl33: comma-separated eps values")
     ap.add_argument("--study-beta", default="1e-2", help="swirl33: comma-separated pulse widths beta")
+    ap.add_argument("--study-bs", type=int, default=33, help="swirl33: block size (the paper's study uses 33)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
@@ -413,7 +413,7 @@ def main():
         if rank == 0:
             swirl_study(jmaxs=[int(x) for x in args.study_jmax.split(",")],
                         epss=[float(x) for x in args.study_eps.split(",")],
-                        betas=[float(x) for x in args.study_beta.split(",")])
+                        betas=[float(x) for x in args.study_beta.split(",")], bs=args.study_bs)
         return
 
     import numpy as np
