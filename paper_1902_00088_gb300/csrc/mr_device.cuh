@@ -723,6 +723,14 @@ __device__ void fill_tile(const PoolView& pv, const BlockInfo& b, const TF* F, T
       at[u] = 0;
       kind[u] = 5;  // past the end
       if (q >= Bx::NPTS) continue;
+      bool core = true;  // strictly inside the block: its own node
+#pragma unroll
+      for (int a = 0; a < D; ++a) core &= (ijk[u][a] >= 1 && ijk[u][a] <= B - 2);
+      if (core) {
+        kind[u] = 0;
+        at[u] = own + li[u];
+        continue;
+      }
       int slot, m, off[3];
       region(ijk[u], slot, m, off);
       if (slot < 0) {
@@ -923,6 +931,9 @@ __device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t*
   for (int col = threadIdx.x; col < S2; col += blockDim.x) {
     const int i = col % S - W, j = col / S - W;
     const bool inxy = i >= 0 && i <= B - 1 && j >= 0 && j <= B - 1;
+    // strictly inside the block in x and y: with 1 <= k <= Bs - 2 the node is
+    // the block's own (no other leaf contains it), whatever the ring holds
+    const bool core = i >= 1 && i <= B - 2 && j >= 1 && j <= B - 2;
     // uniform form: neighbour row and local offset of the column
     const int sx = i < 0 ? 0 : (i <= B - 2 ? 1 : 2), sy = j < 0 ? 0 : (j <= B - 2 ? 1 : 2);
     const int lxy = (i - (sx - 1) * (B - 1)) + B * (j - (sy - 1) * (B - 1));
@@ -943,6 +954,11 @@ __device__ void fill_cols(const PoolView& pv, const BlockInfo& b, const int64_t*
           const int64_t nb = nrow[9 * sk];
           at[u] = nb + lxy + BB * (k - (sk - 1) * (B - 1));
           kind[u] = inner ? (nb != own ? 1 : 0) : 2;
+          continue;
+        }
+        if (k >= 1 && k <= B - 2 && core) {
+          kind[u] = 0;
+          at[u] = own + Gm::lin(i, j, k);
           continue;
         }
         const int4 e = R.reg[rb + 49 * reg_class<B>(k)];

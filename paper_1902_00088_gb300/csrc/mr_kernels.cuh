@@ -736,6 +736,26 @@ __device__ __forceinline__ T block_max(T v, T* red) {
   return v;
 }
 
+// Maxima of a and b over the CTA in one reduction (warp shuffles, then one
+// value per warp in ra / rb); every thread gets the results.
+template <typename A, typename Bt>
+__device__ __forceinline__ void block_max2(A& a, Bt& b, A* ra, Bt* rb) {
+  for (int s = 16; s > 0; s >>= 1) {
+    a = fmax(a, (A)__shfl_xor_sync(0xffffffffu, a, s));
+    b = fmax(b, (Bt)__shfl_xor_sync(0xffffffffu, b, s));
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x >> 5] = a;
+    rb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    a = fmax(a, ra[w]);
+    b = fmax(b, rb[w]);
+  }
+}
+
 // 2D detail index tables (per CTA, shared memory): the x pass on coarse rows
 // yc in [-1, NC - 2] (entry (yc + 1) B + x: tile index of its first source node,
 // x odd = 4 sources two nodes apart) and the odd interior points in row-major
@@ -998,25 +1018,35 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       }
       return block_max<A>(md, reinterpret_cast<A*>(red[0]));
     };
+    bool bad = false;
     for (int v = 0; v < nv; ++v) {
       const TT* tv = tile + v * Bx::TILE;
-      TT mqs = TT(0);  // largest |value|: a maximum of stored values, exact in their type
+      // one sweep over the interior: largest |value| (a maximum of stored
+      // values, exact in their type) and non-finite values (NaN detection:
+      // any makes the block norm NaN); for the certified FP32 decision also
+      // the largest |value| over the tile, reduced together with it
+      TT mqs = TT(0);
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-        mqs = fmax(mqs, (TT)fabs(tv[Bx::tix(i, j, k)]));
+        const TT val = tv[Bx::tix(i, j, k)];
+        mqs = fmax(mqs, (TT)fabs(val));
+        bad |= !isfinite(val);
       }
-      const TT mqt = block_max<TT>(mqs, reinterpret_cast<TT*>(red[1]));
+      constexpr bool cert = sizeof(TT) == 4 && sizeof(TD) == 8;
+      float mt = 0.f;
+      if (cert)
+        for (int q = threadIdx.x; q < Bx::TILE; q += blockDim.x) mt = fmaxf(mt, fabsf((float)tv[q]));
+      TT mqt = mqs;
+      block_max2<TT, float>(mqt, mt, reinterpret_cast<TT*>(red[1]), reinterpret_cast<float*>(red[0]));
       double md = 0.0;  // thread 0's value is stored
-      if constexpr (sizeof(TT) == 4 && sizeof(TD) == 8) {
+      if constexpr (cert) {
         // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
         // one by at most ~20 u max|tile| (u = 2^-24, x/y/z passes of the
         // 4-point rule and the subtraction); where its maximum is farther than
         // 32 u max|tile| from eps the threshold decision (Sec. 2.3) is the
         // FP64 one, otherwise the block is evaluated again in FP64.
         const float m32 = pass(float(0), tv);
-        float mt = 0.f;
-        for (int q = threadIdx.x; q < Bx::TILE; q += blockDim.x) mt = fmaxf(mt, fabsf((float)tv[q]));
-        const float E = 0x1p-19f * block_max<float>(mt, reinterpret_cast<float*>(red[1])) + 1e-37f;
+        const float E = 0x1p-19f * mt + 1e-37f;
         if (pv.norm_kind == 0 && certain_vs_eps(m32, E, td)) {
           if (threadIdx.x == 0) md = (double)m32;
         } else {
@@ -1032,13 +1062,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         if (pv.norm_kind == 1) csv[v] = fmax(csv[v], mq);
       }
       __syncthreads();
-    }
-    // NaN detection: any non-finite interior value makes the block norm NaN
-    bool bad = false;
-    for (int q = threadIdx.x; q < Gm::NI * nv; q += blockDim.x) {
-      const int v = q / Gm::NI, r = q % Gm::NI;
-      const int i = r % B, j = (r / B) % B, k = D == 3 ? r / (B * B) : 0;
-      bad |= !isfinite(tile[v * Bx::TILE + Bx::tix(i, j, k)]);
     }
     if (plan_ok && pn < nact && threadIdx.x < PL::INTS) splan[buf ^ 1][threadIdx.x] = pre;
     if (__syncthreads_or(bad) && threadIdx.x == 0)
