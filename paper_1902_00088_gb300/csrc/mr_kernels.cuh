@@ -225,8 +225,19 @@ template <int B, int RHS, typename TS, typename TY, typename TSRC, int NT>
 struct StageW {
   using Bx = Box<2, B, 2>;
   static constexpr int NW = NT / 32;
+  // FP32 state: the block's state and accumulator rows are staged in shared
+  // memory by the bulk-copy (TMA) engine, one mbarrier per warp
+  static constexpr bool TMA = sizeof(TS) == 4;
+  static constexpr int VS = (B * B + 3) / 4 * 4;  // padded block: the pool's per-variable stride
+  // per warp: mbarrier; a region holding either the ring and the coarse-box
+  // scratch of a block whose neighbourhood is not uniform, or the staged rows;
+  // the tile
+  static constexpr size_t BAR = TMA ? 16 : 0;
+  static constexpr size_t RINGSCR = kRingBytesD<2> + sizeof(TY) * (Bx::CBOX + Bx::SCR);
+  static constexpr size_t ROWS = TMA ? 2 * sizeof(TS) * VS : 0;
+  static constexpr size_t UNION = ((RINGSCR > ROWS ? RINGSCR : ROWS) + 15) / 16 * 16;
   static constexpr size_t GTAB = (4 * Bx::NPTS + 15) / 16 * 16;
-  static constexpr size_t WAREA = (kRingBytesD<2> + sizeof(TY) * (Bx::TILE + Bx::CBOX + Bx::SCR) + 15) / 16 * 16;
+  static constexpr size_t WAREA = (BAR + UNION + sizeof(TY) * Bx::TILE + 15) / 16 * 16;
   static constexpr size_t SMEM = GTAB + NW * WAREA;
 };
 
@@ -248,13 +259,19 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
   unsigned char* sm = smem_as<unsigned char>(0);
   int32_t* gtab = reinterpret_cast<int32_t*>(sm);
   unsigned char* wa = sm + SW::GTAB + warp * SW::WAREA;
-  RingD<2>& R = *reinterpret_cast<RingD<2>*>(wa);
-  TC* tile = reinterpret_cast<TC*>(wa + kRingBytesD<2>);
-  TC* cbox = tile + Bx::TILE;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wa);
+  unsigned char* un = wa + SW::BAR;  // ring + coarse-box scratch, or the staged rows
+  RingD<2>& R = *reinterpret_cast<RingD<2>*>(un);
+  TC* cbox = reinterpret_cast<TC*>(un + kRingBytesD<2>);
   TC* scr = cbox + Bx::CBOX;
+  TS* ys = reinterpret_cast<TS*>(un);
+  TS* as = ys + SW::VS;
+  TC* tile = reinterpret_cast<TC*>(un + SW::UNION);
   __shared__ int64_t snb[SW::NW][PL::NB];
   build_gtab<2, B, 2>(gtab);
+  if (SW::TMA && lane == 0) mbar_init(bar, 1);
   __syncthreads();
+  unsigned phase = 0;
   const int nact = pv.cnt->n_act;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&pv.cnt->stage_blocks, (unsigned long long)nact);
   const int gw = blockIdx.x * SW::NW + warp, nwt = gridDim.x * SW::NW;
@@ -271,7 +288,21 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
     b.c[1] = __shfl_sync(0xffffffffu, cur, 3);
     b.c[2] = 0;
     const TreeDev& td = pv.trees[b.tree];
-    if ((meta >> 30) & 1) {
+    constexpr bool staged = SW::TMA && stage >= 1;  // stage 0 reads the state from the tile
+    const bool uni = (meta >> 30) & 1;
+    auto stage_rows = [&]() {
+      if (lane == 0) {
+        constexpr unsigned rows = (stage <= 2 ? 2 : 1) * sizeof(TS) * SW::VS;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, rows);
+        if (stage <= 2) bulk_g2s(ys, y + (int64_t)b.slot * pv.vs, sizeof(TS) * SW::VS, bar);
+        bulk_g2s(as, acc + (int64_t)b.slot * pv.vs, sizeof(TS) * SW::VS, bar);
+      }
+    };
+    // uniform neighbourhood: the rows travel while the ghost layer is
+    // gathered; otherwise the gather needs the shared region first
+    if (staged && uni) stage_rows();
+    if (uni) {
       if (lane >= PL::NBO && lane < PL::NBO + PL::NB) snb[warp][lane - PL::NBO] = (int64_t)cur * pv.vs;
       __syncwarp();
       gather_table<2, B, 2, 1, TSRC, TC, WarpGroup>(pv, (int64_t)b.slot * pv.vs, snb[warp], gtab, src, (TSRC*)src,
@@ -282,6 +313,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
       fill_tile<2, B, TSRC, TC, 2, WarpGroup>(pv, b, src, (TSRC*)src, tile, stage == 0, R, cbox, scr, true);
     }
     __syncwarp();
+    if (staged && !uni) stage_rows();
+    if (staged) {
+      // bounded wait: a copy that never lands is reported, not waited for
+      if (!mbar_wait(bar, phase, 1 << 20)) {
+        if (lane == 0) set_err(pv, kErrTimeout);
+        return;
+      }
+      phase ^= 1;
+    }
     const TC c = tree_cD<TC>(td, b.lvl);
     const StageCoef<TS> cs(pv, sa, b.tree, stage);
     const TC ct = StageCoef<TC>(pv, sa, b.tree, stage).ct;
@@ -302,8 +342,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
         u0[u] = uc0;
         u1[u] = uc1;
         if (q >= Gm::NI) continue;
-        if (stage <= 2) yv[u] = y[base + q];  // stage 0: committed (synchronised) y_n
-        if (stage >= 1) av[u] = acc[base + q];
+        if constexpr (SW::TMA) {
+          // stage 0: the committed (synchronised) y_n is the tile's value
+          if (stage == 0) yv[u] = (TS)tile[Bx::tix(q % B, q / B, 0)];
+          if (stage == 1 || stage == 2) yv[u] = ys[q];
+          if (stage >= 1) av[u] = as[q];
+        } else {
+          if (stage <= 2) yv[u] = y[base + q];  // stage 0: committed (synchronised) y_n
+          if (stage >= 1) av[u] = acc[base + q];
+        }
         if (RHS == MR_RHS_SWIRL) {
           const int i = q % B, j = q / B;
           const int64_t Ux = pmod64((b.c[0] * (B - 1) + i) << sh, td.N);
