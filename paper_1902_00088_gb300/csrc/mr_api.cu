@@ -91,7 +91,6 @@ namespace mr {
 __global__ void k_step_begin(Counters* c, int32_t* hist);
 __global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int swirl);
 __global__ void k_time_advance(TreeTime* tt, int ntrees);
-__global__ void k_round_continue(Counters* c, cudaGraphConditionalHandle h, int max_rounds);
 }
 
 namespace {
@@ -258,9 +257,29 @@ void do_ic(mr_ctx c) {
   by_dim(c, [&] { launch_ic<2>(pv, fields(c), c->lc, c->st); },
          [&] { launch_ic<3>(pv, fields(c), c->lc, c->st); });
 }
+int max_rounds_of(mr_ctx ctx);
+
+// Round control of host-driven rounds (no conditional node).
+RoundCtl round_ctl(mr_ctx c, cudaGraphConditionalHandle h = 0, bool has_h = false) {
+  RoundCtl rc{};
+  rc.svar_v = c->p.norm_kind == 1 ? 0.0 : 1.0;
+  rc.h = h;
+  rc.has_h = has_h ? 1 : 0;
+  rc.max_rounds = max_rounds_of(c);
+  return rc;
+}
+
+// State of the first coarsening round (later rounds are prepared by the
+// kernel that ends the previous one).
+void rounds_begin(mr_ctx c, cudaStream_t st) {
+  PoolView pv = view(c);
+  by_dim(c, [&] { launch_rounds_begin<2>(pv, c->lc, st); }, [&] { launch_rounds_begin<3>(pv, c->lc, st); });
+}
+
 void do_round(mr_ctx c, bool merge) {
   PoolView pv = view(c);
   const bool fp64 = c->p.detail_fp64 != 0;
+  const RoundCtl rc = round_ctl(c);
   c->stats.det_launches += 1;
   {
     PhaseTimer tm(c, 2);
@@ -268,8 +287,8 @@ void do_round(mr_ctx c, bool merge) {
            [&] { launch_round_details<3>(pv, fields(c), fp64, c->lc, c->st); });
   }
   PhaseTimer tm(c, 3);
-  by_dim(c, [&] { launch_round_merge<2>(pv, fields(c), merge, c->lc, c->st); },
-         [&] { launch_round_merge<3>(pv, fields(c), merge, c->lc, c->st); });
+  by_dim(c, [&] { launch_round_merge<2>(pv, fields(c), merge, rc, c->lc, c->st); },
+         [&] { launch_round_merge<3>(pv, fields(c), merge, rc, c->lc, c->st); });
 }
 
 int max_rounds_of(mr_ctx ctx) {
@@ -283,6 +302,7 @@ mr_status coarsen_until_stable(mr_ctx ctx) {
   const int rounds = max_rounds_of(ctx);
   launch_k(ctx->lc.pdl, k_step_begin, 1, 1, 0, ctx->st, ctx->cnt, nullptr);
   count_launch();
+  rounds_begin(ctx, ctx->st);
   for (int r = 0; r < rounds; ++r) {
     do_round(ctx, true);
     mr_status s = check_device(ctx);
@@ -825,6 +845,7 @@ mr_status mr_adapt(mr_ctx ctx, int32_t mode) {
   if (mode == MR_ADAPT_COARSEN) return coarsen_until_stable(ctx);
   if (mode == 3) {  // details and flags only (no merge), for inspection
     launch_k(ctx->lc.pdl, k_step_begin, 1, 1, 0, ctx->st, ctx->cnt, nullptr);
+    rounds_begin(ctx, ctx->st);
     do_round(ctx, false);
     return check_device(ctx);
   }
@@ -1057,13 +1078,13 @@ void enqueue_graph_prologue(mr_ctx ctx, cudaStream_t st) {
            [&] { launch_stage<3>(pv, f, s, sa, ctx->lc, st); });
 }
 
-void enqueue_round(mr_ctx ctx, cudaStream_t st) {
+void enqueue_round(mr_ctx ctx, cudaStream_t st, const RoundCtl& rc) {
   PoolView pv = view(ctx);
   pv.tt = ctx->ttime;
   const Fields f = fields(ctx);
   const bool fp64 = ctx->p.detail_fp64 != 0;
-  by_dim(ctx, [&] { launch_coarsen_round<2>(pv, f, fp64, true, ctx->lc, st); },
-         [&] { launch_coarsen_round<3>(pv, f, fp64, true, ctx->lc, st); });
+  by_dim(ctx, [&] { launch_coarsen_round<2>(pv, f, fp64, true, rc, ctx->lc, st); },
+         [&] { launch_coarsen_round<3>(pv, f, fp64, true, rc, ctx->lc, st); });
 }
 
 void enqueue_epilogue(mr_ctx ctx, cudaStream_t st) {
@@ -1086,6 +1107,7 @@ cudaError_t capture_step(mr_ctx ctx, cudaGraph_t* out, bool use_while) {
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   enqueue_graph_prologue(ctx, cs);
+  rounds_begin(ctx, cs);
   if (use_while) {
     cudaStreamCaptureStatus status;
     cudaGraph_t g = nullptr;
@@ -1110,9 +1132,8 @@ cudaError_t capture_step(mr_ctx ctx, cudaGraph_t* out, bool use_while) {
                                                             nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       const int64_t b0 = kernel_launches();
-      enqueue_round(ctx, ctx->body_stream);
-      launch_k(ctx->lc.pdl, k_round_continue, 1, 1, 0, ctx->body_stream, ctx->cnt, h, max_rounds_of(ctx));
-      count_launch();
+      // the round's last kernel sets the condition of the next iteration
+      enqueue_round(ctx, ctx->body_stream, round_ctl(ctx, h, true));
       ctx->graph_body = kernel_launches() - b0;
       cudaGraph_t body = nullptr;
       e = cudaStreamEndCapture(ctx->body_stream, &body);
@@ -1125,7 +1146,7 @@ cudaError_t capture_step(mr_ctx ctx, cudaGraph_t* out, bool use_while) {
       return e;
     }
   } else {
-    for (int r = 0; r < max_rounds_of(ctx); ++r) enqueue_round(ctx, cs);
+    for (int r = 0; r < max_rounds_of(ctx); ++r) enqueue_round(ctx, cs, round_ctl(ctx));
   }
   enqueue_epilogue(ctx, cs);
   return cudaStreamEndCapture(cs, out);

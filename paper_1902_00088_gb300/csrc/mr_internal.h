@@ -139,6 +139,18 @@ struct Fields {
   void* Yb;
 };
 
+// Control of the coarsening rounds, folded into the kernel that ends a round:
+// it prepares the next round (blocks to evaluate, round id, threshold scales
+// reset to svar_v) and, in a captured step (has_h), sets the conditional of
+// the while node that repeats the rounds (continue while a family merged and
+// fewer than max_rounds ran).
+struct RoundCtl {
+  double svar_v;
+  cudaGraphConditionalHandle h;
+  int has_h;
+  int max_rounds;
+};
+
 struct LaunchCfg {
   int num_sms;
   int grid_mult;  // persistent CTAs per SM for the stage kernel (0 = occupancy)
@@ -185,11 +197,12 @@ template <int D> void launch_refine(const PoolView& pv, const Fields& f, int mod
                                     const int8_t* mask, const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_ic(const PoolView& pv, const Fields& f, const LaunchCfg& lc,
                                 cudaStream_t st);
+template <int D> void launch_rounds_begin(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64,
-                                           bool merge, const LaunchCfg& lc, cudaStream_t st);
+                                           bool merge, const RoundCtl& rc, const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_round_details(const PoolView& pv, const Fields& f, bool fp64,
                                            const LaunchCfg& lc, cudaStream_t st);
-template <int D> void launch_round_merge(const PoolView& pv, const Fields& f, bool merge,
+template <int D> void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const RoundCtl& rc,
                                          const LaunchCfg& lc, cudaStream_t st);
 template <int D> void launch_sync(const PoolView& pv, const Fields& f, double* tiles,
                                   const LaunchCfg& lc, cudaStream_t st);

@@ -1669,7 +1669,7 @@ __global__ void __launch_bounds__(256) k_flags(PoolView pv) {
 // counters are updated by the last CTA (first_round cleared; merged families
 // counted; done once a round merged nothing).
 template <int D>
-__global__ void k_coarsen_commit(PoolView pv) {
+__global__ void k_coarsen_commit(PoolView pv, RoundCtl rc) {
   pdl_enter();
   Counters* c = pv.cnt;
   const int nround = c->n_round, n_free = c->n_free, n_new = c->n_new, rid = c->round_id;
@@ -1710,6 +1710,21 @@ __global__ void k_coarsen_commit(PoolView pv) {
       c->n_act = n_new;
       if (c->merged == 0) c->done = 1;
       else c->topo += 1;
+    }
+    // the next round, if one runs (a family merged and fewer than max_rounds
+    // ran): the blocks it evaluates, its id, its threshold scales (the last
+    // round's stay for the next step's proposal features); in a captured
+    // step the while node's condition
+    c->rounds += 1;
+    const bool next = !c->done && c->rounds < rc.max_rounds;
+    c->n_round = c->done ? 0 : c->n_act;
+    if (next) {
+      c->round_id += 1;
+      for (int i = 0; i < pv.ntrees * pv.nvar; ++i) pv.svar[i] = rc.svar_v;
+    }
+    if (rc.has_h) {
+      c->graph_rounds += 1;
+      cudaGraphSetConditional(rc.h, next ? 1u : 0u);
     }
     c->ctas_done = 0;
   }

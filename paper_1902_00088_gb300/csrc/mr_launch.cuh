@@ -287,15 +287,19 @@ struct CoarsenRun {
 };
 
 template <int D>
-void launch_round_details(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
-                          cudaStream_t st) {
+void launch_rounds_begin(const PoolView& pv, const LaunchCfg& lc, cudaStream_t st) {
   launch_k(lc.pdl, k_round_begin<D>, 1, 256, 0, st, pv, pv.norm_kind == 1 ? 0.0 : 1.0);
   count_launch();
+}
+
+template <int D>
+void launch_round_details(const PoolView& pv, const Fields& f, bool fp64, const LaunchCfg& lc,
+                          cudaStream_t st) {
   dispatch_bs<D, DetailsRun>(pv, f, fp64, lc, st);
 }
 
 template <int D>
-void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const LaunchCfg& lc,
+void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const RoundCtl& rc, const LaunchCfg& lc,
                         cudaStream_t st) {
   const int nch = 1 << D;
   // one warp per block: a grid for the expected list (after a refinement,
@@ -314,16 +318,16 @@ void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const L
                  lc.pdl != 0);
   }
   dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
-  launch_k(lc.pdl, k_coarsen_commit<D>, flat_grid(pv, 256), 256, 0, st, pv);
+  launch_k(lc.pdl, k_coarsen_commit<D>, flat_grid(pv, 256), 256, 0, st, pv, rc);
   count_launch(1);
   (void)nch;
 }
 
 template <int D>
-void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool merge,
+void launch_coarsen_round(const PoolView& pv, const Fields& f, bool fp64, bool merge, const RoundCtl& rc,
                           const LaunchCfg& lc, cudaStream_t st) {
   launch_round_details<D>(pv, f, fp64, lc, st);
-  launch_round_merge<D>(pv, f, merge, lc, st);
+  launch_round_merge<D>(pv, f, merge, rc, lc, st);
 }
 
 // ------------------------------------------------------------------ sync -----
@@ -453,11 +457,13 @@ void launch_error(const PoolView& pv, const Fields& f, int tree, const double* e
   template void launch_refine<D>(const PoolView&, const Fields&, int, const int8_t*,            \
                                  const LaunchCfg&, cudaStream_t);                               \
   template void launch_ic<D>(const PoolView&, const Fields&, const LaunchCfg&, cudaStream_t);   \
+  template void launch_rounds_begin<D>(const PoolView&, const LaunchCfg&, cudaStream_t);        \
   template void launch_coarsen_round<D>(const PoolView&, const Fields&, bool, bool,             \
-                                        const LaunchCfg&, cudaStream_t);                        \
+                                        const RoundCtl&, const LaunchCfg&, cudaStream_t);       \
   template void launch_round_details<D>(const PoolView&, const Fields&, bool, const LaunchCfg&, \
                                         cudaStream_t);                                          \
-  template void launch_round_merge<D>(const PoolView&, const Fields&, bool, const LaunchCfg&,   \
+  template void launch_round_merge<D>(const PoolView&, const Fields&, bool, const RoundCtl&,    \
+                                      const LaunchCfg&,                                         \
                                       cudaStream_t);                                            \
   template void launch_sync<D>(const PoolView&, const Fields&, double*, const LaunchCfg&,       \
                                cudaStream_t);                                                   \

@@ -201,13 +201,6 @@ __global__ void k_time_coef(TreeTime* tt, const TreeDev* trees, int ntrees, int 
 }
 // End of a coarsening round inside a graph while-node: run another round while
 // the last one merged a family and fewer than max_rounds ran.
-__global__ void k_round_continue(Counters* c, cudaGraphConditionalHandle h, int max_rounds) {
-  pdl_enter();
-  c->rounds += 1;
-  c->graph_rounds += 1;
-  cudaGraphSetConditional(h, (!c->done && c->rounds < max_rounds) ? 1u : 0u);
-}
-
 __global__ void k_time_advance(TreeTime* tt, int ntrees) {
   pdl_enter();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;

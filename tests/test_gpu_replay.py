@@ -291,3 +291,25 @@ def test_single_coarsening_round_matches_oracle(mr, oracle_mod, precision):
     for s in range(4):
         o2.step(s * dt, dt)
     assert o2.n <= o.n
+
+
+def test_fp64_swirl_33_long_run_bit_exact(mr, oracle_mod):
+    # The paper's swirl study case (Sec. 3: 33^2 blocks, beta 1e-2, t_a 5), Jmax 4,
+    # eps 1e-4, plain FP64: 512 host-driven steps (a tenth of the run to t_a,
+    # through the first refinements of the filament) stay bit-exact with the
+    # oracle, tree and fields, at every 128th step.
+    t_a = 5.0
+    c = dict(dim=2, Bs=33, Jmin=1, Jmax=4, eps=1e-4, rhs="swirl", rhs_params=(t_a,), ic="gauss",
+             ic_params=(0.5, 0.75, 0.0, math.sqrt(0.005)))
+    o, g = make_pair(mr, oracle_mod, c, capacity=20000)
+    o.init_tree()
+    g.init_tree()
+    n = int(math.ceil(t_a / (0.5 / (32 * 16))))
+    dt = t_a / n
+    for s in range(512):
+        o.step(s * dt, dt)
+        g.step(s * dt, dt)
+        if (s + 1) % 128 == 0:
+            ob, f = assert_same_tree(o, g)
+            assert np.array_equal(f, ob["fields"]), (s, np.abs(f - ob["fields"]).max())
+    assert o.n > 10 and o.errors == 0
