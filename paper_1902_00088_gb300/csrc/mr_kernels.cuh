@@ -1278,27 +1278,34 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_details_w(PoolView pv, TS* __
 // (every second node); a mother node on a line shared by two children is read
 // from the child in which it has local index 0.  The mother takes the slot of
 // the family member that comes first in Hilbert order.
+// One kernel per round: each CTA merges families (the mother's data, then the
+// family's table entries, light data and freed slots -- the family's 2^d
+// members sit at consecutive list positions, a Hilbert-curve property), and
+// the CTA that finishes last copies the new active list in place, updates the
+// counters and prepares the next round (RoundCtl).
 template <int D, int B, typename TS>
-__global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y, RoundCtl rc) {
   pdl_enter();
   using Gm = Geo<D, B>;
   TS* buf = smem_as<TS>(0);
   __shared__ int cs[8];
-  const int nact = pv.cnt->n_round;
+  Counters* c = pv.cnt;
+  const int nround = c->n_round, n_free = c->n_free, n_new = c->n_new, rid = c->round_id;
+  const bool done = c->done != 0;
+  const bool none = n_new == nround;  // no family merges: the tree and the list are unchanged
   const int nv = pv.nvar;
-  if (pv.cnt->n_new == nact) return;  // no family merges: the list stays as it is
-  for (int p = blockIdx.x; p < nact; p += gridDim.x) {
+  for (int p = blockIdx.x; !none && p < nround; p += gridDim.x) {
     const int slot = pv.act[p];
     const int emit = pv.emit[2 * p], e = pv.eoff[2 * p];
-    if (!emit) continue;
+    if (!emit) continue;  // a member of a family merged by the CTA of its first member
     if (threadIdx.x == 0) pv.act_next[e] = slot;
     if (pv.flag[slot] != -2) continue;
     const BlockInfo b = load_block(pv, slot);
     const TreeDev& td = pv.trees[b.tree];
     if (threadIdx.x < Gm::NCH) {
-      int64_t c[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) c[a] = (b.c[a] & ~(int64_t)1) | ((threadIdx.x >> a) & 1);
-      cs[threadIdx.x] = tab_get<D>(pv, td, b.lvl, c);
+      int64_t cc[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) cc[a] = (b.c[a] & ~(int64_t)1) | ((threadIdx.x >> a) & 1);
+      cs[threadIdx.x] = tab_get<D>(pv, td, b.lvl, cc);
     }
     __syncthreads();
     bool missing = false;
@@ -1324,7 +1331,58 @@ __global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y
       const int v = idx / Gm::NI, q = idx % Gm::NI;
       y[((int64_t)slot * nv + v) * pv.vs + q] = buf[idx];
     }
+    // the family's tables and light data (positions p .. p + 2^d - 1)
+    if (threadIdx.x < Gm::NCH) {
+      const int q = p + threadIdx.x;
+      const int s = pv.act[q];
+      const BlockInfo m = load_block(pv, s);
+      pv.tab[td.tab_off[m.lvl] + (int64_t)morton<D>(m.c, m.lvl)] = -1;
+      if (s == slot) {
+        const int64_t pc[3] = {m.c[0] >> 1, m.c[1] >> 1, m.c[2] >> 1};
+        pv.tab[td.tab_off[m.lvl - 1] + (int64_t)morton<D>(pc, m.lvl - 1)] = s;
+        pv.stamp[s] = rid;
+        pv.lvl[s] = (int8_t)(m.lvl - 1);
+        const int32_t c32[3] = {(int32_t)pc[0], (int32_t)pc[1], (int32_t)pc[2]};
+        for (int a = 0; a < 3; ++a) pv.crd[3 * s + a] = c32[a];
+        pv.hkey[s] = block_key<D>(c32, m.lvl - 1, td.Jmax);
+      } else {
+        pv.lvl[s] = -1;
+        pv.freelist[n_free + pv.eoff[2 * q + 1]] = s;
+      }
+    }
     __syncthreads();
+  }
+  if (last_cta_all(c)) {
+    // the new list in place (every entry of act_next is written by now)
+    const int ncopy = done || none ? 0 : n_new;
+    for (int p = threadIdx.x; p < ncopy; p += blockDim.x) pv.act[p] = __ldcg(pv.act_next + p);
+    if (threadIdx.x == 0) {
+      c->first_round = 0;
+      if (!done) {
+        const int nch = 1 << D;
+        c->merged = (c->n_act - n_new) / (nch - 1);
+        c->n_free = n_free + c->n_alloc;
+        c->n_act = n_new;
+        if (c->merged == 0) c->done = 1;
+        else c->topo += 1;
+      }
+      // the next round, if one runs (a family merged and fewer than max_rounds
+      // ran): the blocks it evaluates, its id, its threshold scales (the last
+      // round's stay for the next step's proposal features); in a captured
+      // step the while node's condition
+      c->rounds += 1;
+      const bool next = !c->done && c->rounds < rc.max_rounds;
+      c->n_round = c->done ? 0 : c->n_act;
+      if (next) {
+        c->round_id += 1;
+        for (int i = 0; i < pv.ntrees * pv.nvar; ++i) pv.svar[i] = rc.svar_v;
+      }
+      if (rc.has_h) {
+        c->graph_rounds += 1;
+        cudaGraphSetConditional(rc.h, next ? 1u : 0u);
+      }
+      c->ctas_done = 0;
+    }
   }
 }
 
@@ -1660,73 +1718,6 @@ __global__ void __launch_bounds__(256) k_flags(PoolView pv) {
       cta_scan2<256, 8>(pv.emit, pv.eoff, nact, &pv.cnt->n_new);
       if (threadIdx.x == 0) pv.cnt->ctas_done = 0;
     }
-  }
-}
-
-// End of a coarsening round in one kernel: a merged family's first member in
-// Hilbert order becomes the mother (level, coordinates, key, table entry, merge
-// stamp), the others are freed; the new list is copied in place, and the round
-// counters are updated by the last CTA (first_round cleared; merged families
-// counted; done once a round merged nothing).
-template <int D>
-__global__ void k_coarsen_commit(PoolView pv, RoundCtl rc) {
-  pdl_enter();
-  Counters* c = pv.cnt;
-  const int nround = c->n_round, n_free = c->n_free, n_new = c->n_new, rid = c->round_id;
-  const bool done = c->done != 0;
-  const bool none = n_new == nround;  // no family merges: the tree and the list are unchanged
-  const int ncopy = done || none ? 0 : n_new;
-  const int nmax = none ? 0 : (nround > ncopy ? nround : ncopy);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nmax; p += gridDim.x * blockDim.x) {
-    const int32_t nxt = p < ncopy ? pv.act_next[p] : 0;
-    if (p < nround) {
-      const int s = pv.act[p];
-      if (pv.flag[s] == -2) {
-        const BlockInfo b = load_block(pv, s);
-        const TreeDev& td = pv.trees[b.tree];
-        pv.tab[td.tab_off[b.lvl] + (int64_t)morton<D>(b.c, b.lvl)] = -1;
-        if (pv.emit[2 * p]) {
-          int64_t pc[3] = {b.c[0] >> 1, b.c[1] >> 1, b.c[2] >> 1};
-          pv.tab[td.tab_off[b.lvl - 1] + (int64_t)morton<D>(pc, b.lvl - 1)] = s;
-          pv.stamp[s] = rid;
-          pv.lvl[s] = (int8_t)(b.lvl - 1);
-          int32_t c32[3] = {(int32_t)pc[0], (int32_t)pc[1], (int32_t)pc[2]};
-          for (int a = 0; a < 3; ++a) pv.crd[3 * s + a] = c32[a];
-          pv.hkey[s] = block_key<D>(c32, b.lvl - 1, td.Jmax);
-        } else {
-          pv.lvl[s] = -1;
-          pv.freelist[n_free + pv.eoff[2 * p + 1]] = s;
-        }
-      }
-    }
-    if (p < ncopy) pv.act[p] = nxt;
-  }
-  if (last_cta(c)) {
-    c->first_round = 0;
-    if (!done) {
-      const int nch = 1 << D;
-      c->merged = (c->n_act - n_new) / (nch - 1);
-      c->n_free = n_free + c->n_alloc;
-      c->n_act = n_new;
-      if (c->merged == 0) c->done = 1;
-      else c->topo += 1;
-    }
-    // the next round, if one runs (a family merged and fewer than max_rounds
-    // ran): the blocks it evaluates, its id, its threshold scales (the last
-    // round's stay for the next step's proposal features); in a captured
-    // step the while node's condition
-    c->rounds += 1;
-    const bool next = !c->done && c->rounds < rc.max_rounds;
-    c->n_round = c->done ? 0 : c->n_act;
-    if (next) {
-      c->round_id += 1;
-      for (int i = 0; i < pv.ntrees * pv.nvar; ++i) pv.svar[i] = rc.svar_v;
-    }
-    if (rc.has_h) {
-      c->graph_rounds += 1;
-      cudaGraphSetConditional(rc.h, next ? 1u : 0u);
-    }
-    c->ctas_done = 0;
   }
 }
 

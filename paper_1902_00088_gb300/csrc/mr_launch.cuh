@@ -276,12 +276,12 @@ struct DetailsRun {
 };
 template <int D, int B, typename TS>
 struct CoarsenRun {
-  static void run(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+  static void run(const PoolView& pv, const Fields& f, const RoundCtl& rc, const LaunchCfg& lc, cudaStream_t st) {
     constexpr int threads = 256;
     const size_t smem = sizeof(TS) * pv.nvar * Geo<D, B>::NI;
     auto k = k_coarsen<D, B, TS>;
     prep_smem(k, smem);
-    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, 0), threads, smem, st, pv, (TS*)f.y);
+    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, 0), threads, smem, st, pv, (TS*)f.y, rc);
     count_launch();
   }
 };
@@ -317,9 +317,7 @@ void launch_round_merge(const PoolView& pv, const Fields& f, bool merge, const R
     launch_scan2(pv.emit, pv.eoff, pv.partial, &pv.cnt->n_round, pv.cap, &pv.cnt->n_new, st, 4 * (int64_t)lc.n_hint,
                  lc.pdl != 0);
   }
-  dispatch_bs<D, CoarsenRun>(pv, f, lc, st);
-  launch_k(lc.pdl, k_coarsen_commit<D>, flat_grid(pv, 256), 256, 0, st, pv, rc);
-  count_launch(1);
+  dispatch_bs<D, CoarsenRun>(pv, f, rc, lc, st);
   (void)nch;
 }
 
