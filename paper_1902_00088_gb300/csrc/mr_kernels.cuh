@@ -1080,11 +1080,21 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         bad |= !isfinite(val);
       }
       constexpr bool cert = sizeof(TT) == 4 && sizeof(TD) == 8;
+      // the values the evaluation reads: the interior (mqs) and the coarse
+      // lattice (even nodes) of the ghost layer
       float mt = 0.f;
-      if (cert)
-        for (int q = threadIdx.x; q < Bx::TILE; q += blockDim.x) mt = fmaxf(mt, fabsf((float)tv[q]));
+      if (cert) {
+        constexpr int NCO = (B + 1) / 2 + 2;  // coarse nodes -1 .. (B + 1) / 2 per axis
+        constexpr int NCT = NCO * NCO * (D == 3 ? NCO : 1);
+        for (int q = threadIdx.x; q < NCT; q += blockDim.x) {
+          const int x = 2 * (q % NCO) - 2, yy = 2 * ((q / NCO) % NCO) - 2, zz = D == 3 ? 2 * (q / (NCO * NCO)) - 2 : 0;
+          const bool in = x >= 0 && x <= B - 1 && yy >= 0 && yy <= B - 1 && zz >= 0 && zz <= B - 1;
+          if (!in) mt = fmaxf(mt, fabsf((float)tv[Bx::tix(x, yy, zz)]));
+        }
+      }
       TT mqt = mqs;
       block_max2<TT, float>(mqt, mt, reinterpret_cast<TT*>(red[1]), reinterpret_cast<float*>(red[0]));
+      mt = fmaxf(mt, (float)mqt);
       double md = 0.0;  // thread 0's value is stored
       if constexpr (cert) {
         // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
@@ -1690,7 +1700,9 @@ __global__ void __launch_bounds__(256) k_flags(PoolView pv) {
       }
     }
     // no finer leaf around the family: cells of [-1, 4]^d outside [0, 3]^d
-    for (int u = lane; u < NBOX; u += 32) {
+    // (looked up only for a family whose members are all candidates)
+    const bool sisters = __all_sync(0xffffffffu, ok);
+    for (int u = lane; sisters && u < NBOX; u += 32) {
       const int q[3] = {u % 6 - 1, (u / 6) % 6 - 1, D == 3 ? u / 36 - 1 : 0};
       bool in = true;
       for (int a = 0; a < D; ++a) in &= q[a] >= 0 && q[a] <= 3;
