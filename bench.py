@@ -504,7 +504,10 @@ def main():
         autotune = args.autotune if args.autotune >= 0 else (3 if "trees" in w else 0)
         if autotune > 0:
             t_ = g.autotune(autotune)
-            tuned = {"ctas_per_sm": t_ % 100 or "occupancy", "stage_form": ["cta per block", "warp per block"][t_ // 100]}
+            form = (t_ // 100) % 10
+            tuned = {"ctas_per_sm": t_ % 100 or "occupancy", "stage_form": ["cta per block", "warp per block"][form]}
+            if form == 1:
+                tuned.update(blocks_per_cta=(t_ // 1000) % 10, staging="bulk copies" if t_ // 10000 else "loads")
             steps_done += 7 * (autotune + 1) + 0
         g.step_graph(args.warmup)
         steps_done += args.warmup

@@ -287,10 +287,13 @@ int32_t mr_get_launch_overlap(mr_ctx ctx);
 mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n, int32_t reset);
 /* Times graph steps with 1, 2, 3, 4, 6, 8 and occupancy-limited CTAs per SM for
  * the block kernels and, in 2D, both forms of the RK stage (one CTA per block,
- * one warp per block; the second for 17^2 blocks only) (steps steps each; the
+ * one warp per block; the second for 17^2 advection blocks only), and for the
+ * warp form on FP32 fields 2, 4 or 8 blocks per CTA with the state and
+ * accumulator rows staged by bulk copies or loaded (steps steps each; the
  * solution advances during tuning) and keeps the fastest; *best = CTAs per SM
- * (0 = occupancy) + 100 x form.  Without tuning the 2D stage on 17^2 blocks
- * uses one warp per block once the grid holds at least 8 blocks per SM.
+ * (0 = occupancy) + 100 x form + 1000 x blocks per CTA + 10000 x staging.
+ * Without tuning the 2D stage on 17^2 blocks uses one warp per block once the
+ * grid holds at least 8 blocks per SM, 4 blocks per CTA, rows staged.
  * Synchronises. */
 mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best);
 /* Fixes the launch configuration instead of the autotuner: ctas_per_sm
@@ -301,6 +304,12 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best);
  * not depend on either choice.  MR_EINVAL for values out of range or the warp
  * form where it does not exist.  Drops the captured step. */
 mr_status mr_set_tuning(mr_ctx ctx, int32_t ctas_per_sm, int32_t stage_form);
+/* Warp-per-block form of the 2D stage on FP32 fields: blocks_per_cta (2, 4 or
+ * 8 warps per CTA, one block each) and staging (1: the state and accumulator
+ * rows of a block are copied to shared memory by the bulk-copy engine while
+ * its ghost layer is gathered; 0: loaded by the threads).  Results do not
+ * depend on either.  MR_EINVAL for other values.  Drops the captured step. */
+mr_status mr_set_warp_form(mr_ctx ctx, int32_t blocks_per_cta, int32_t staging);
 /* Synchronises; accumulates pending timers into *out. */
 mr_status mr_get_stats(mr_ctx ctx, mr_stats* out);
 mr_status mr_reset_stats(mr_ctx ctx);

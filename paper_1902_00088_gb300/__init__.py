@@ -92,6 +92,7 @@ SIGNATURES = {
     "mr_get_step_history": (_i32, [_vp, _i64, _vp, C.POINTER(C.c_int64), _i32]),
     "mr_autotune": (_i32, [_vp, _i32, C.POINTER(C.c_int32)]),
     "mr_set_tuning": (_i32, [_vp, _i32, _i32]),
+    "mr_set_warp_form": (_i32, [_vp, _i32, _i32]),
     "mr_set_refine_mode": (_i32, [_vp, _i32]),
     "mr_proposal_collect": (_i32, [_vp, _i32, _i64]),
     "mr_proposal_dataset": (_i32, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -317,6 +318,10 @@ class Forest:
         """Launch configuration: CTAs per SM (0 = occupancy) and the 2D stage form
         (1 warp per block, 0 CTA per block, -1 by block count)."""
         self._ck(self.lib.mr_set_tuning(self.h, ctas_per_sm, stage_form))
+
+    def set_warp_form(self, blocks_per_cta=4, staging=1):
+        """2D FP32 warp-per-block stage: warps (blocks) per CTA and bulk-copy staging of the rows."""
+        self._ck(self.lib.mr_set_warp_form(self.h, blocks_per_cta, staging))
 
     def set_refine_mode(self, mode):
         self._ck(self.lib.mr_set_refine_mode(self.h, {"all": 0, "learned": 1}.get(mode, mode)))

@@ -616,6 +616,8 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     ctx->lc.num_sms = prop.multiProcessorCount;
     ctx->lc.grid_mult = 0;
     ctx->lc.stage_form = -1;
+    ctx->lc.warp_blocks = 4;
+    ctx->lc.staging = 1;
     ctx->lc.pdl = 0;
     ctx->lc.n_hint = 0;
   }
@@ -1253,17 +1255,32 @@ mr_status mr_get_step_history(mr_ctx ctx, int64_t cap, int32_t* out, int64_t* n,
 
 mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
   if (!ctx || steps < 1) return MR_EINVAL;
-  const int cand[] = {1, 2, 3, 4, 6, 8, 0};
+  // candidates: CTAs per SM x form of the 2D stage (one CTA per block, one warp
+  // per block); for the warp form on FP32 fields also blocks per CTA and the
+  // staging of the rows (bulk copies or loads)
+  struct Cand { int mult, form, wb, stg; };
+  std::vector<Cand> cands;
+  const int mults[] = {1, 2, 3, 4, 6, 8, 0};
+  for (int m : mults) cands.push_back({m, 0, 4, 1});
+  const bool warp_ok = ctx->p.dim == 2 && ctx->p.Bs == 17 && ctx->p.rhs_kind != MR_RHS_NS;
+  if (warp_ok) {
+    for (int m : mults) cands.push_back({m, 1, 4, 1});
+    if (ctx->p.precision == MR_PREC_FP32) {
+      for (int wb : {2, 8})
+        for (int stg : {0, 1}) cands.push_back({0, 1, wb, stg});
+      cands.push_back({0, 1, 4, 0});
+    }
+  }
   float best = 1e30f;
-  int bestm = 0, bestf = 0;
+  Cand bc = cands[0];
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
-  const int nforms = ctx->p.dim == 2 ? 2 : 1;
-  for (int ci = 0; ci < 7 * nforms; ++ci) {
-    const int m = cand[ci % 7], form = ci / 7;
-    ctx->lc.grid_mult = m;
-    ctx->lc.stage_form = form;
+  for (const Cand& c : cands) {
+    ctx->lc.grid_mult = c.mult;
+    ctx->lc.stage_form = c.form;
+    ctx->lc.warp_blocks = c.wb;
+    ctx->lc.staging = c.stg;
     mr_status s = build_graph(ctx);
     if (s) return s;
     CK(cudaGraphLaunch(ctx->gexec, ctx->st));  // warm
@@ -1276,18 +1293,29 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, a, b));
     ctx->stats.steps += steps + 1;
-    if (ms < best) { best = ms; bestm = m; bestf = form; }
+    if (ms < best) { best = ms; bc = c; }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  ctx->lc.grid_mult = bestm;
-  ctx->lc.stage_form = bestf;
+  ctx->lc.grid_mult = bc.mult;
+  ctx->lc.stage_form = bc.form;
+  ctx->lc.warp_blocks = bc.wb;
+  ctx->lc.staging = bc.stg;
   mr_status s = build_graph(ctx);
   if (s) return s;
-  if (best_out) *best_out = bestm + 100 * bestf;
+  if (best_out) *best_out = bc.mult + 100 * bc.form + 1000 * bc.wb + 10000 * bc.stg;
   return check_device(ctx);
 }
 
+
+mr_status mr_set_warp_form(mr_ctx ctx, int32_t blocks_per_cta, int32_t staging) {
+  if (!ctx || (blocks_per_cta != 2 && blocks_per_cta != 4 && blocks_per_cta != 8) || (staging != 0 && staging != 1))
+    return MR_EINVAL;
+  if (ctx->lc.warp_blocks != blocks_per_cta || ctx->lc.staging != staging) drop_graph(ctx);
+  ctx->lc.warp_blocks = blocks_per_cta;
+  ctx->lc.staging = staging;
+  return MR_OK;
+}
 
 mr_status mr_set_tuning(mr_ctx ctx, int32_t ctas_per_sm, int32_t stage_form) {
   if (!ctx || ctas_per_sm < 0 || ctas_per_sm > 32 || stage_form < -1 || stage_form > 1) return MR_EINVAL;

@@ -157,6 +157,8 @@ struct LaunchCfg {
   int stage_form;  // 2D stage: 0 one CTA per block, 1 one warp per block, -1 by block count
   int n_hint;      // block count last read by the host (chooses the form when -1)
   int pdl;         // step kernels use programmatic dependent launch (launch_k)
+  int warp_blocks; // 2D warp-per-block stage on FP32 fields: blocks (warps) per CTA, 2, 4 or 8
+  int staging;     // ... and whether its state/accumulator rows are staged by bulk copies (1) or loaded (0)
 };
 
 #ifdef __CUDACC__

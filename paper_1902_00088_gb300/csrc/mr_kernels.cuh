@@ -245,7 +245,7 @@ struct StageW {
 // updates of each stage without run-time branches).
 template <int B, int RHS, typename TS, typename TY, typename TSRC, int NT, int ST>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, const TSRC* __restrict__ src, TS* __restrict__ y,
-                                                   TS* __restrict__ acc, TY* __restrict__ ynext, int stage_arg,
+                                                   TS* __restrict__ acc, TY* __restrict__ ynext, int staging,
                                                    StageArgs sa) {
   pdl_enter();
   constexpr int stage = ST;
@@ -288,7 +288,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
     b.c[1] = __shfl_sync(0xffffffffu, cur, 3);
     b.c[2] = 0;
     const TreeDev& td = pv.trees[b.tree];
-    constexpr bool staged = SW::TMA && stage >= 1;  // stage 0 reads the state from the tile
+    // stage 0 reads the state from the tile; the other stages stage the rows
+    // (FP32, unless switched off) or load them
+    const bool staged = SW::TMA && stage >= 1 && staging != 0;
     const bool uni = (meta >> 30) & 1;
     auto stage_rows = [&]() {
       if (lane == 0) {
@@ -345,8 +347,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_stage_adv_w(PoolView pv, cons
         if constexpr (SW::TMA) {
           // stage 0: the committed (synchronised) y_n is the tile's value
           if (stage == 0) yv[u] = (TS)tile[Bx::tix(q % B, q / B, 0)];
-          if (stage == 1 || stage == 2) yv[u] = ys[q];
-          if (stage >= 1) av[u] = as[q];
+          if (stage == 1 || stage == 2) yv[u] = staged ? ys[q] : y[base + q];
+          if (stage >= 1) av[u] = staged ? as[q] : acc[base + q];
         } else {
           if (stage <= 2) yv[u] = y[base + q];  // stage 0: committed (synchronised) y_n
           if (stage >= 1) av[u] = acc[base + q];

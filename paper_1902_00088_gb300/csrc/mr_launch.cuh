@@ -53,15 +53,23 @@ static void stage_impl(const PoolView& pv, const Fields& f, int stage, const Sta
     if (warp_form) {
       // one instantiation per stage: stage 0 reads the committed state, the
       // others the previous stage value
-      auto go = [&](auto stc) {
-        constexpr int S = decltype(stc)::value;
+      auto go_nt = [&](auto stc, auto ntc) {
+        constexpr int S = decltype(stc)::value, NT = decltype(ntc)::value;
         using TSRC = std::conditional_t<S == 0, TS, TY>;
-        using SW = StageW<B, RHS, TS, TY, TSRC, threads>;
+        using SW = StageW<B, RHS, TS, TY, TSRC, NT>;
         const TSRC* src = S == 0 ? (const TSRC*)f.y : (const TSRC*)(S == 2 ? f.Yb : f.Ya);
-        auto k = k_stage_adv_w<B, RHS, TS, TY, TSRC, threads, S>;
+        auto k = k_stage_adv_w<B, RHS, TS, TY, TSRC, NT, S>;
         prep_smem(k, SW::SMEM);
-        const int grid = persistent_grid(k, threads, SW::SMEM, lc, lc.grid_mult);
-        launch_k(lc.pdl, k, grid, threads, SW::SMEM, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+        const int grid = persistent_grid(k, NT, SW::SMEM, lc, lc.grid_mult);
+        launch_k(lc.pdl, k, grid, NT, SW::SMEM, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, lc.staging, sa);
+      };
+      // blocks (warps) per CTA: tuned for the FP32 forms, 4 otherwise
+      auto go = [&](auto stc) {
+        if constexpr (sizeof(TS) == 4) {
+          if (lc.warp_blocks == 2) return go_nt(stc, std::integral_constant<int, 64>{});
+          if (lc.warp_blocks == 8) return go_nt(stc, std::integral_constant<int, 256>{});
+        }
+        go_nt(stc, std::integral_constant<int, threads>{});
       };
       switch (stage) {
         case 0: go(std::integral_constant<int, 0>{}); break;

@@ -313,3 +313,27 @@ def test_fp64_swirl_33_long_run_bit_exact(mr, oracle_mod):
             ob, f = assert_same_tree(o, g)
             assert np.array_equal(f, ob["fields"]), (s, np.abs(f - ob["fields"]).max())
     assert o.n > 10 and o.errors == 0
+
+
+def test_warp_form_variants_give_identical_steps(mr):
+    # The tuning axes of the FP32 warp-per-block stage (blocks per CTA, rows
+    # staged by bulk copies or loaded) and the CTA form change the launch, not
+    # the arithmetic: the same grid and fields bit for bit.
+    tree = dict(Jmin=2, Jmax=7, eps=1e-4, ic="gauss", ic_params=(0.5, 0.75, 0.0, 0.05), rhs_params=(5.0,))
+    dt = 0.5 / (16 * 128)
+    runs = []
+    for form, wb, stg in ((0, 4, 1), (1, 4, 1), (1, 2, 0), (1, 8, 1), (1, 2, 1), (1, 8, 0)):
+        g = mr.Forest(dim=2, precision="fp32", detail_fp64=True, rhs="swirl", trees=[tree], capacity=40000)
+        g.set_tuning(0, form)
+        g.set_warp_form(wb, stg)
+        g.init_tree()
+        for s in range(3):
+            g.step(s * dt, dt)
+        g.set_time(3 * dt, dt)
+        g.step_graph(10)
+        runs.append(g.get_blocks())
+    for info, f in runs[1:]:
+        assert np.array_equal(info, runs[0][0]) and np.array_equal(f, runs[0][1])
+    assert len(runs[0][0]) > 20
+    with pytest.raises(mr.MRError):
+        mr.Forest(dim=2, trees=[dict(Jmin=2, Jmax=4)]).set_warp_form(3, 1)
