@@ -87,21 +87,20 @@ WORKLOADS = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # dominant kernel, from one ncu capture per workload (profiles/), valid only for
 # the kernel sources it was taken on (digest below); otherwise reported as null.
-TRAFFIC_DIGEST = "a8a63f3cc3ac68d3"
+TRAFFIC_DIGEST = "2578dcc4b4eec205"
 TRAFFIC = {
-    "swirl": ("k_stage_adv", (2.928384e6 + 2.005248e6) / 2),
-    "forest": ("k_stage_adv_w", 31.653632e6 + 11.776e3),
-    "uniform2d": ("k_stage_adv_w", 947.365888e6 + 569.117184e6),
-    "adv3d": ("k_stage_adv", 82.599168e6 + 13.831168e6),
+    "adv3d": ("k_stage_adv", 87.485696e6 + 14.678016e6),
+    "uniform2d": ("k_stage_adv_w", 957.044736e6 + 569.822976e6),
+    "forest": ("k_stage_adv_w", 34.798592e6 + 9.728e3),
 }
 
 
 def source_digest():
-    import glob
+    """Digest of the device code (kernels, device helpers, launch configuration)."""
     import hashlib
     h = hashlib.sha1()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1902_00088_gb300", "csrc", "*"))) + \
-            [os.path.join(ROOT, "include", "mr.h")]:
+    csrc = os.path.join(ROOT, "paper_1902_00088_gb300", "csrc")
+    for f in [os.path.join(csrc, n) for n in ("mr_device.cuh", "mr_internal.h", "mr_kernels.cuh", "mr_launch.cuh")]:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -634,12 +633,15 @@ def main():
         v["launch_us"] = v["ms"] * 1e3 / max(1, v["launches"])
     dom = max(kern, key=lambda n: kern[n]["ms"])
     achieved = kern[dom]["achieved_gbs"]
-    traffic = None
+    # DRAM bytes per launch of the dominant kernel from an ncu capture of the
+    # same device code (stage 2 launch), else null
+    traffic, traffic_note = None, None
     tr = TRAFFIC.get(args.workload)
     if tr and dom == "stage" and source_digest() == TRAFFIC_DIGEST and not args.precision and not args.learned:
-        traffic = {"bytes_per_launch": tr[1], "kernel": tr[0],
-                   "algorithmic_bytes_per_launch": kern[dom]["bytes"] / max(1, kern[dom]["launches"]),
-                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/"}
+        traffic = tr[1]
+        traffic_note = {"kernel": tr[0],
+                        "algorithmic_bytes_per_launch": kern[dom]["bytes"] / max(1, kern[dom]["launches"]),
+                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one stage-2 launch, profiles/"}
 
     err = None
     tnow = g.get_time() if graph else t
@@ -720,7 +722,7 @@ def main():
                        "phase_ms_eager_probe": st["ms"],
                        "learned_proposal": learned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "kernel": kern[dom]["kernel"], "launch_us": kern[dom]["launch_us"],
                          "kernels_eager_probe": kern,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
