@@ -34,8 +34,11 @@
 
 extern "C" {
 // Parameters of one tree.  rhs_kind: 0 constant-velocity advection,
-// 1 swirl (Sec. 3), 2 compressible Navier-Stokes (Sec. 4, 2D).  ic_kind:
-// 0 separable Gaussian blob, 1 temporal mixing layer, 2 none (set_blocks).
+// 1 swirl (Sec. 3), 2 compressible Navier-Stokes (Sec. 4, 2D) in flux form,
+// 3 the same in the skew-symmetric form on square-root variables; for 2 and 3
+// rhs = {gamma, mu, Pr, r_th}, r_th > 0 enabling the shock filter after each
+// step.  ic_kind: 0 separable Gaussian blob, 1 temporal mixing layer, 2 none
+// (set_blocks), 3 the double shear layer of Sec. 4.
 typedef struct {
   int32_t dim, Bs, ng, nvar, Jmin, Jmax;
   int32_t rhs_kind, ic_kind, norm_kind, max_rounds;
@@ -668,6 +671,31 @@ struct Tree {
     double e0 = p0 / (gam - 1.0);
     q[0] = 1.0; q[1] = u; q[2] = v; q[3] = e0 + 0.5 * (u * u + v * v);
   }
+  // Double shear layer of Sec. 4 (reading of its garbled axes: the layers are
+  // the lines x = xc -+ hw, across which rho and the y-velocity v jump; the
+  // x-velocity u is perturbed along the layers):
+  //   s(x) = (tanh((x - (xc - hw)) / lw) - tanh((x - (xc + hw)) / lw)) / 2,
+  //   rho = rho0 + (rho1 - rho0) s, v = v0 + (v1 - v0) s,
+  //   u = amp sin(2 pi (y - yc)), p = p0.
+  // ic = {rho1, rho0, v1, v0, lw, p0, amp, hw, xc, yc}.  The state is
+  // (rho, rho u, rho v, E) for the flux form and (sqrt(rho), sqrt(rho) u,
+  // sqrt(rho) v, p) for the skew-symmetric form.
+  void shear_layer(double x, double y, double q[4]) const {
+    double rho1 = p.ic[0], rho0 = p.ic[1], v1 = p.ic[2], v0 = p.ic[3], lw = p.ic[4], p0 = p.ic[5];
+    double amp = p.ic[6], hw = p.ic[7], xc = p.ic[8], yc = p.ic[9];
+    double sprof = 0.5 * (std::tanh((x - (xc - hw)) / lw) - std::tanh((x - (xc + hw)) / lw));
+    double rho = rho0 + (rho1 - rho0) * sprof;
+    double v = v0 + (v1 - v0) * sprof;
+    double u = amp * std::sin(2.0 * M_PI * (y - yc));
+    if (p.rhs_kind == 3) {
+      double f = std::sqrt(rho);
+      q[0] = f; q[1] = f * u; q[2] = f * v; q[3] = p0;
+    } else {
+      double gam = p.rhs[0];
+      double m1 = rho * u, m2 = rho * v;
+      q[0] = rho; q[1] = m1; q[2] = m2; q[3] = p0 / (gam - 1.0) + 0.5 * (m1 * u + m2 * v);
+    }
+  }
   void set_ic(Leaf& b, double t_shift) {
     b.t.assign(tsize(), 0.0);
     for (int k = 0; k < (d == 3 ? B : 1); ++k)
@@ -686,6 +714,10 @@ struct Tree {
           } else if (p.ic_kind == 1) {
             double q[4];
             mixing_layer(coord(0, U[0]), coord(1, U[1]), q);
+            for (int v = 0; v < 4; ++v) b.t[ix(v, i, j, k)] = q[v];
+          } else if (p.ic_kind == 3) {
+            double q[4];
+            shear_layer(coord(0, U[0]), coord(1, U[1]), q);
             for (int v = 0; v < 4; ++v) b.t[ix(v, i, j, k)] = q[v];
           }
         }
@@ -816,9 +848,189 @@ struct Tree {
         for (int i = 0; i < B; ++i)
           kk[((size_t)q * B + j) * B + i] = -(dx(F[q], i, j) + dy(G[q], i, j));
   }
+  // Compressible Navier-Stokes in the skew-symmetric form of Reiss & Sesterhenn
+  // (2014), the formulation Sec. 4 names, on the square-root variables
+  // q = (phi, psi_x, psi_y, p) with phi = sqrt(rho), psi = phi u:
+  //   d phi/dt   = -1/2 sum_j (D_j psi_j + u_j D_j phi)
+  //   d psi_i/dt = -1/2 sum_j (D_j(psi_i u_j) + u_j D_j psi_i) - (D_i p - sum_j D_j tau_ij) / phi
+  //   d p/dt     = -gamma sum_j D_j(p u_j) + (gamma - 1) sum_j u_j D_j p
+  //                + (gamma - 1) (Phi + sum_j D_j(kap D_j th)),
+  // tau as in the flux form, Phi = sum_ij tau_ij D_j u_i, th = p / rho,
+  // kap = mu gamma / ((gamma - 1) Pr).  Each convective term is the mean of its
+  // divergence and advective forms, so with the antisymmetric central D on a
+  // periodic grid sum(phi^2), sum(phi psi), sum(p/(gamma-1) + psi.psi/2) are
+  // conserved by the semi-discrete equations.  D is the 4th-order D1 throughout;
+  // tau and kap D th are formed on nodes -2..B+1 and differentiated again.
+  void rhs_ns_skew(const Leaf& b, std::vector<double>& kk) const {
+    double gam = p.rhs[0], mu = p.rhs[1], Pr = p.rhs[2];
+    double gm1 = gam - 1.0;
+    double kap = mu * gam / ((gam - 1.0) * Pr);
+    double c23 = 2.0 / 3.0;
+    double c = cD(b.lvl);
+    int R = B + 2 * g;
+    auto I = [&](int i, int j) { return (size_t)(j + g) * R + (i + g); };
+    std::vector<double> ph(R * R), sx(R * R), sy(R * R), pr(R * R), u(R * R), v(R * R), th(R * R);
+    for (int j = -g; j < B + g; ++j)
+      for (int i = -g; i < B + g; ++i) {
+        double f = b.t[ix(0, i, j, 0)];
+        ph[I(i, j)] = f;
+        sx[I(i, j)] = b.t[ix(1, i, j, 0)];
+        sy[I(i, j)] = b.t[ix(2, i, j, 0)];
+        pr[I(i, j)] = b.t[ix(3, i, j, 0)];
+        u[I(i, j)] = sx[I(i, j)] / f;
+        v[I(i, j)] = sy[I(i, j)] / f;
+        th[I(i, j)] = pr[I(i, j)] / (f * f);
+      }
+    auto dx = [&](const std::vector<double>& f, int i, int j) {
+      return ((f[I(i - 2, j)] - f[I(i + 2, j)]) + 8.0 * (f[I(i + 1, j)] - f[I(i - 1, j)])) * c;
+    };
+    auto dy = [&](const std::vector<double>& f, int i, int j) {
+      return ((f[I(i, j - 2)] - f[I(i, j + 2)]) + 8.0 * (f[I(i, j + 1)] - f[I(i, j - 1)])) * c;
+    };
+    // D1 of a product a*b of two tile arrays
+    auto dxm = [&](const std::vector<double>& a, const std::vector<double>& bb, int i, int j) {
+      auto m = [&](int s) { return a[I(i + s, j)] * bb[I(i + s, j)]; };
+      return ((m(-2) - m(2)) + 8.0 * (m(1) - m(-1))) * c;
+    };
+    auto dym = [&](const std::vector<double>& a, const std::vector<double>& bb, int i, int j) {
+      auto m = [&](int s) { return a[I(i, j + s)] * bb[I(i, j + s)]; };
+      return ((m(-2) - m(2)) + 8.0 * (m(1) - m(-1))) * c;
+    };
+    // viscous stresses and heat flux on nodes -2..B+1 (only the cross of the
+    // interior is used: x-derivatives on rows 0..B-1, y-derivatives on columns 0..B-1)
+    std::vector<double> txx(R * R, 0.0), txy(R * R, 0.0), tyy(R * R, 0.0), qx(R * R, 0.0), qy(R * R, 0.0);
+    for (int j = -2; j < B + 2; ++j)
+      for (int i = -2; i < B + 2; ++i) {
+        double ux = dx(u, i, j), vx = dx(v, i, j), uy = dy(u, i, j), vy = dy(v, i, j);
+        double div = ux + vy;
+        txx[I(i, j)] = mu * (2.0 * ux - c23 * div);
+        tyy[I(i, j)] = mu * (2.0 * vy - c23 * div);
+        txy[I(i, j)] = mu * (uy + vx);
+        qx[I(i, j)] = kap * dx(th, i, j);
+        qy[I(i, j)] = kap * dy(th, i, j);
+      }
+    size_t nb = (size_t)B * B;
+    for (int j = 0; j < B; ++j)
+      for (int i = 0; i < B; ++i) {
+        double uu = u[I(i, j)], vv = v[I(i, j)], f = ph[I(i, j)];
+        double phx = dx(ph, i, j), phy = dy(ph, i, j);
+        double sxx = dx(sx, i, j), sxy_ = dy(sx, i, j), syx = dx(sy, i, j), syy = dy(sy, i, j);
+        double px = dx(pr, i, j), py = dy(pr, i, j);
+        double ux = dx(u, i, j), vx = dx(v, i, j), uy = dy(u, i, j), vy = dy(v, i, j);
+        // mass
+        double rphi = -0.5 * ((sxx + uu * phx) + (syy + vv * phy));
+        // momentum
+        double cx = (dxm(sx, u, i, j) + uu * sxx) + (dym(sx, v, i, j) + vv * sxy_);
+        double cy = (dxm(sy, u, i, j) + uu * syx) + (dym(sy, v, i, j) + vv * syy);
+        double fx = px - (dx(txx, i, j) + dy(txy, i, j));
+        double fy = py - (dx(txy, i, j) + dy(tyy, i, j));
+        double rsx = -0.5 * cx - fx / f;
+        double rsy = -0.5 * cy - fy / f;
+        // pressure
+        double phi_v = (txx[I(i, j)] * ux + txy[I(i, j)] * (uy + vx)) + tyy[I(i, j)] * vy;
+        double heat = dx(qx, i, j) + dy(qy, i, j);
+        double rp = (-gam * (dxm(pr, u, i, j) + dym(pr, v, i, j)) + gm1 * (uu * px + vv * py)) +
+                    gm1 * (phi_v + heat);
+        size_t n = (size_t)j * B + i;
+        kk[n] = rphi;
+        kk[nb + n] = rsx;
+        kk[2 * nb + n] = rsy;
+        kk[3 * nb + n] = rp;
+      }
+  }
   void rhs(const Leaf& b, double ts, std::vector<double>& kk) const {
     if (p.rhs_kind == 2) rhs_ns(b, kk);
+    else if (p.rhs_kind == 3) rhs_ns_skew(b, kk);
     else rhs_advection(b, ts, kk);
+  }
+
+  // ------------------------------------------------------- shock filter -----
+  // Shock-capturing filter of Bogey, de Cacqueray & Bailly (2009), applied
+  // after every time step (Sec. 4, threshold r_th = rhs[3]) to each evolved
+  // variable q of a Navier-Stokes state, on the synchronised tile.  Per
+  // direction a and node n along a:
+  //   dilatation  th_n = (u_{n+1} - u_{n-1}) / (2 dx) + (v_{n+1} - v_{n-1}) / (2 dx)
+  //               (2nd-order central differences, each along its own axis)
+  //   high-pass   Dth_n = (-th_{n+1} + 2 th_n - th_{n-1}) / 4
+  //   magnitude   M_n = ((Dth_n - Dth_{n+1})^2 + (Dth_n - Dth_{n-1})^2) / 2
+  //   sensor      r_n = M_n / (c_n^2 / dx^2) + 1e-16,  c^2 = gamma p / rho
+  //   strength    s_n = (1 - r_th / r_n + |1 - r_th / r_n|) / 2
+  //   flux        F_{n+1/2} = -(q_{n+1} - q_n) / 4  (standard 2nd-order filter)
+  //   update      q_n <- q_n - sum_a (s_{n+1/2} F_{n+1/2} - s_{n-1/2} F_{n-1/2}),
+  //               s_{n+1/2} = (s_n + s_{n+1}) / 2,
+  // both directions evaluated from the unfiltered state.  The stencil reaches
+  // four nodes along a and one across, inside the ghost layer.
+  void filter() {
+    double rth = p.rhs[3];
+    if (!(rth > 0.0) || (p.rhs_kind != 2 && p.rhs_kind != 3)) return;
+    sync();
+    double gam = p.rhs[0];
+    int R = B + 2 * g;
+    auto I = [&](int i, int j) { return (size_t)(j + g) * R + (i + g); };
+    std::map<Key, std::vector<double>> out;
+    for (auto& kv : lv) {
+      const Leaf& b = kv.second;
+      double dxl = p.L / (double)((int64_t)(B - 1) << b.lvl);
+      std::vector<double> u(R * R), v(R * R), cc(R * R);
+      for (int j = -g; j < B + g; ++j)
+        for (int i = -g; i < B + g; ++i) {
+          double q0 = b.t[ix(0, i, j, 0)], q1 = b.t[ix(1, i, j, 0)], q2 = b.t[ix(2, i, j, 0)],
+                 q3 = b.t[ix(3, i, j, 0)];
+          double rho, pp;
+          if (p.rhs_kind == 2) {
+            rho = q0;
+            u[I(i, j)] = q1 / q0;
+            v[I(i, j)] = q2 / q0;
+            pp = (gam - 1.0) * (q3 - 0.5 * (q1 * u[I(i, j)] + q2 * v[I(i, j)]));
+          } else {
+            rho = q0 * q0;
+            u[I(i, j)] = q1 / q0;
+            v[I(i, j)] = q2 / q0;
+            pp = q3;
+          }
+          cc[I(i, j)] = gam * pp / rho;
+        }
+      double h2 = 0.5 / dxl;
+      auto theta = [&](int i, int j) {
+        return (u[I(i + 1, j)] - u[I(i - 1, j)]) * h2 + (v[I(i, j + 1)] - v[I(i, j - 1)]) * h2;
+      };
+      // strength at node (i, j) for direction a (0: x, 1: y)
+      auto strength = [&](int a, int i, int j) {
+        int ox = a == 0 ? 1 : 0, oy = a == 1 ? 1 : 0;
+        auto Dth = [&](int s) {
+          int ii = i + s * ox, jj = j + s * oy;
+          return (-theta(ii + ox, jj + oy) + 2.0 * theta(ii, jj) - theta(ii - ox, jj - oy)) / 4.0;
+        };
+        double d0 = Dth(0), dp = Dth(1), dm = Dth(-1);
+        double M = 0.5 * ((d0 - dp) * (d0 - dp) + (d0 - dm) * (d0 - dm));
+        double r = M / (cc[I(i, j)] / (dxl * dxl)) + 1e-16;
+        double z = 1.0 - rth / r;
+        return 0.5 * (z + std::fabs(z));
+      };
+      std::vector<double> sgx(R * R, 0.0), sgy(R * R, 0.0);
+      for (int j = -1; j <= B; ++j)
+        for (int i = -1; i <= B; ++i) {
+          if (j >= 0 && j < B) sgx[I(i, j)] = strength(0, i, j);
+          if (i >= 0 && i < B) sgy[I(i, j)] = strength(1, i, j);
+        }
+      std::vector<double> nt = b.t;
+      for (int var = 0; var < nv; ++var)
+        for (int j = 0; j < B; ++j)
+          for (int i = 0; i < B; ++i) {
+            auto q = [&](int ii, int jj) { return b.t[ix(var, ii, jj, 0)]; };
+            double sxp = 0.5 * (sgx[I(i, j)] + sgx[I(i + 1, j)]);
+            double sxm = 0.5 * (sgx[I(i - 1, j)] + sgx[I(i, j)]);
+            double syp = 0.5 * (sgy[I(i, j)] + sgy[I(i, j + 1)]);
+            double sym = 0.5 * (sgy[I(i, j - 1)] + sgy[I(i, j)]);
+            double fxp = -0.25 * (q(i + 1, j) - q(i, j)), fxm = -0.25 * (q(i, j) - q(i - 1, j));
+            double fyp = -0.25 * (q(i, j + 1) - q(i, j)), fym = -0.25 * (q(i, j) - q(i, j - 1));
+            double ddx = sxp * fxp - sxm * fxm;
+            double ddy = syp * fyp - sym * fym;
+            nt[ix(var, i, j, 0)] = q(i, j) - (ddx + ddy);
+          }
+      out[kv.first] = nt;
+    }
+    for (auto& kv : lv) kv.second.t = out[kv.first];
   }
 
   // ------------------------------------------------------------------ RK4 ---
@@ -879,6 +1091,7 @@ struct Tree {
   void step(double t, double dt) {
     refine(0);
     rk4(t, dt);
+    filter();
     coarsen_until_stable();
   }
 
@@ -1006,6 +1219,8 @@ void orc_neighbors(void* h, int32_t* nbr, int8_t* dl) {
       dl[n * rel.size() + r] = f ? (int8_t)l : 0;
     }
 }
+// Shock-capturing filter of the Navier-Stokes state (no-op unless r_th > 0).
+void orc_filter(void* h) { ((Tree*)h)->filter(); }
 // Right-hand side N(q) on the interior of every block after a sync, Hilbert order.
 void orc_rhs(void* h, double t, double* out) {
   Tree* T = (Tree*)h;

@@ -48,7 +48,7 @@ def _load():
         vp = C.c_void_p
         lib.orc_create.restype = vp
         lib.orc_create.argtypes = [C.POINTER(OracleParams)]
-        for name in ("orc_destroy", "orc_init_tree", "orc_sync", "orc_details"):
+        for name in ("orc_destroy", "orc_init_tree", "orc_sync", "orc_details", "orc_filter"):
             getattr(lib, name).argtypes = [vp]
             getattr(lib, name).restype = None
         lib.orc_nblocks.argtypes = [vp]; lib.orc_nblocks.restype = C.c_int64
@@ -87,8 +87,8 @@ def _ptr(a):
 class Oracle:
     """One tree of the FP64 oracle.  ``cfg`` is a dict with the OracleParams fields."""
 
-    RHS = {"adv": 0, "swirl": 1, "ns": 2}
-    IC = {"gauss": 0, "mixing": 1, "none": 2}
+    RHS = {"adv": 0, "swirl": 1, "ns": 2, "ns_skew": 3}
+    IC = {"gauss": 0, "mixing": 1, "none": 2, "shear_layer": 3}
 
     def __init__(self, cfg):
         lib = _load()
@@ -131,6 +131,10 @@ class Oracle:
 
     def details(self):
         self.lib.orc_details(self.h)
+
+    def filter(self):
+        """Shock-capturing filter of a Navier-Stokes state (Sec. 4); no-op unless r_th > 0."""
+        self.lib.orc_filter(self.h)
 
     def flags(self, seed=0):
         return self.lib.orc_flags(self.h, seed)
