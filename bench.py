@@ -5,7 +5,7 @@ are sum over the blocks of the adapted grid G (before the safety refinement) of
 Bs^d, times 4 stages; the time is the whole mr_step (refine-all, 4 x (ghost
 sync + RK stage), coarsening rounds, tree rebuild).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload adv3d|swirl|adv2d|forest|ns|ns_thin|...]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload adv3d|swirl|adv2d|forest|ns|ns_thin|dsl|...]
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
 
 Prints one JSON line on rank 0.
@@ -64,6 +64,20 @@ WORKLOADS = {
                     name="2D NS temporal mixing layer, delta 1/240 (Ma 0.3, Re 1000, seeded perturbation "
                          "1e-3), 33^2 blocks, Jmin 2, Jmax 7, eps 1e-3, FP32 stages and details + FP64 state/acc, "
                          "learned proposal, CFL 0.5"),
+    # The double shear layer of Sec. 4 as the paper runs it: L = 8, layers at
+    # x = L/2 -+ 0.25 (rho 2/1, v 1/-1, width L/240), p = 2.5, u = 0.1 sin(2 pi
+    # (y - L/2)), mu 1e-6, gamma 1.4, Pr 0.71, skew-symmetric form, shock filter
+    # r_th 1e-5 after every step, eps 1e-3; 33^2 blocks, Jmax 7; FP32 stages and
+    # details with FP64 state/accumulator.
+    "dsl": dict(dim=2, Bs=33, nvar=4, norm_kind=1, precision="fp32_acc64", detail_fp64=False,
+                rhs="ns_skew", L=8.0, capacity=60_000, oracle_jmax=4, spinup=1500,
+                tree=dict(Jmin=2, Jmax=7, eps=1e-3, ic="shear_layer",
+                          ic_params=(2.0, 1.0, 1.0, -1.0, 8.0 / 240.0, 2.5, 0.1, 0.25, 4.0, 4.0),
+                          rhs_params=(1.4, 1e-6, 0.71, 1e-5)),
+                umax=1.0 + math.sqrt(1.4 * 2.5 / 1.0),  # |v| + c in the light layer
+                name="2D NS double shear layer of Sec. 4 (L 8, rho 2/1, v +-1, lw L/240, p 2.5, mu 1e-6), "
+                     "skew-symmetric form + shock filter r_th 1e-5, 33^2 blocks, Jmin 2, Jmax 7, eps 1e-3, "
+                     "FP32 stages and details + FP64 state/acc, CFL 0.5"),
     # Uniform grids at the finest level (no adaptation happens): the stage
     # kernel at a size where HBM bandwidth matters.
     "uniform2d": dict(dim=2, Bs=17, precision="fp32", detail_fp64=True, rhs="adv",
@@ -131,7 +145,7 @@ WORKLOADS["ns"]["umax"] = WORKLOADS["ns_thin"]["umax"] = 0.5 + 0.5 / 0.3  # |u| 
 
 def dt_of(w):
     t = w["tree"]
-    dx = 1.0 / ((w["Bs"] - 1) * (1 << t["Jmax"]))
+    dx = w.get("L", 1.0) / ((w["Bs"] - 1) * (1 << t["Jmax"]))
     return 0.5 * dx / w["umax"]
 
 
@@ -240,12 +254,12 @@ def oracle_sample(w, seconds_target=15.0):
     jmin = min(t["Jmin"], jmax - 1)
     cfg = dict(dim=w["dim"], Bs=w["Bs"], nvar=w.get("nvar", 1), Jmin=jmin, Jmax=jmax, eps=t["eps"],
                rhs=w["rhs"], rhs_params=t["rhs_params"], ic=t.get("ic", "gauss"), ic_params=t["ic_params"],
-               norm_kind=w.get("norm_kind", 0))
+               norm_kind=w.get("norm_kind", 0), L=w.get("L", 1.0))
     if "x0" in t:
         cfg["x0"] = t["x0"]
     o = oracle.Oracle(cfg)
     o.init_tree()
-    dx = 1.0 / ((w["Bs"] - 1) * (1 << jmax))
+    dx = w.get("L", 1.0) / ((w["Bs"] - 1) * (1 << jmax))
     dt = 0.5 * dx / umax
     pts, steps, t0 = 0, 0, time.perf_counter()
     while True:
@@ -327,6 +341,93 @@ def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,), bs=3
         del g
 
 
+def uniform_field(info, f, Bs, J):
+    """Blocks all at level J -> the periodic node grid (n_var, N, N), N = (Bs-1) 2^J
+    (each block's last node per axis is its neighbour's first and is dropped)."""
+    import numpy as np
+    N = (Bs - 1) << J
+    out = np.zeros((f.shape[1], N, N))
+    for q in range(len(info)):
+        cx, cy = int(info["coords"][q][0]), int(info["coords"][q][1])
+        out[:, cy * (Bs - 1):(cy + 1) * (Bs - 1), cx * (Bs - 1):(cx + 1) * (Bs - 1)] = f[q, :, :Bs - 1, :Bs - 1]
+    return out
+
+
+def kinetic_energy_spectrum(psi_x, psi_y, L):
+    """Shell-summed spectrum of the kinetic energy density |psi|^2 / 2 (psi = sqrt(rho) u):
+    E(k) = sum over |k'| in [k - 1/2, k + 1/2) of |psi_hat(k')|^2 / 2, wavenumbers in units of
+    2 pi / L, normalised so that sum_k E(k) is the mean kinetic energy density (Parseval)."""
+    import numpy as np
+    N = psi_x.shape[0]
+    ex = np.fft.fft2(psi_x) / (N * N)
+    ey = np.fft.fft2(psi_y) / (N * N)
+    e = 0.5 * (np.abs(ex) ** 2 + np.abs(ey) ** 2)
+    k1 = np.fft.fftfreq(N, 1.0 / N)
+    kk = np.sqrt(k1[None, :] ** 2 + k1[:, None] ** 2)
+    shell = np.rint(kk).astype(np.int64)
+    return np.bincount(shell.ravel(), weights=e.ravel())[: N // 2 + 1]
+
+
+def dsl_study(jmaxs=(7, 8), fixed=(7,), eps=1e-3, bs=17, t_end=4.0, form="fp32_acc64"):
+    """The double shear layer of Sec. 4 (Fig. 6 as data): adaptive runs (Jmin 2, eps) at each Jmax and
+    fixed grids at each level of `fixed`, advanced by graph replays to t_end; per run the compression
+    rate (blocks / 4^J) over time and the kinetic energy spectrum at t_end after refining the grid to
+    its finest level."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_00088_gb300 as mr
+    w = WORKLOADS["dsl"]
+    stream = torch.cuda.Stream()
+    runs = [("adaptive", j) for j in jmaxs] + [("fixed", j) for j in fixed]
+    for kind, J in runs:
+        tree = dict(w["tree"])
+        tree.update(Jmin=2 if kind == "adaptive" else J, Jmax=J, eps=eps)
+        cap = int(1.3 * 4 ** J) + 20_000
+        g = mr.Forest(dim=2, Bs=bs, nvar=4, precision=form, detail_fp64=False, rhs="ns_skew", trees=[tree],
+                      capacity=cap, norm_kind=1, L=w["L"], stream=stream.cuda_stream)
+        g.init_tree()
+        dx = w["L"] / ((bs - 1) << J)
+        n = int(math.ceil(t_end / (0.5 * dx / w["umax"])))
+        dt = t_end / n
+        g.set_time(0.0, dt)
+        chunk = max(1, n // 40)
+        comp, done, ms = [], 0, 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        status = "ok"
+        try:
+            while done < n:
+                k = min(chunk, n - done)
+                e0.record(stream)
+                g.step_graph(k)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                done += k
+                comp.append((round(done * dt, 4), g.num_blocks() / 4 ** J))
+            for _ in range(J):  # refine to the finest level for the spectrum
+                info, _ = g.get_blocks(fields=False)
+                lv = info["level"]
+                if (lv == J).all():
+                    break
+                g.set_refine_mask((lv < J).astype(np.int8))
+                g.adapt("refine_flagged")
+            info, f = g.get_blocks()
+            u = uniform_field(info, f, bs, J)
+            spec = kinetic_energy_spectrum(u[1], u[2], w["L"])
+            ks = [k for k in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048) if k < len(spec)]
+            extra = dict(spectrum={str(k): float(spec[k]) for k in ks},
+                         spectrum_sum=float(spec.sum()), rho_min=float((u[0] ** 2).min()),
+                         rho_max=float((u[0] ** 2).max()))
+        except mr.MRError as ex:
+            status, extra = "failed: %s" % ex, {}
+        print(json.dumps(dict(study="dsl", kind=kind, J=J, Jmin=tree["Jmin"], eps=eps, Bs=bs, form=form,
+                              steps=done, t=done * dt, status=status, ms_per_step=ms / max(1, done),
+                              compression=comp[:: max(1, len(comp) // 20)] + comp[-1:], **extra)), flush=True)
+        del g
+
+
 def reduce_over_ranks(ms, points, world):
     """Whole-job figures over the ranks: the slowest rank's time (the job ends
     with it) and the points all ranks advanced (each rank runs its own
@@ -369,8 +470,11 @@ def main():
     ap.add_argument("--eager", action="store_true", help="host-driven steps instead of CUDA graph replays")
     ap.add_argument("--autotune", type=int, default=-1, help="steps per autotuner candidate (0 = off)")
     ap.add_argument("--overlap", action="store_true", help="programmatic dependent launch of the step's kernels")
-    ap.add_argument("--study", default="", choices=["", "swirl33"],
-                    help="instead of the benchmark: the paper's swirl study (33^2 blocks, eps x Jmax), one JSON line per run")
+    ap.add_argument("--study", default="", choices=["", "swirl33", "dsl"],
+                    help="instead of the benchmark: the paper's swirl study (33^2 blocks, eps x Jmax) or its double "
+                         "shear layer (compression over time, energy spectra at t = 4), one JSON line per run")
+    ap.add_argument("--study-t", type=float, default=4.0, help="dsl: end time")
+    ap.add_argument("--study-fixed", default="7", help="dsl: comma-separated levels of the fixed-grid runs")
     ap.add_argument("--study-jmax", default="4,5", help="swirl33: comma-separated Jmax values")
     ap.add_argument("--study-eps", default="1e-3,1e-4,1e-5,1e-6", help="swirl33: comma-separated eps values")
     ap.add_argument("--study-beta", default="1e-2", help="swirl33: comma-separated pulse widths beta")
@@ -408,6 +512,13 @@ def main():
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
+    if args.study == "dsl":
+        if rank == 0:
+            jm = [int(x) for x in args.study_jmax.split(",")] if args.study_jmax != "4,5" else [7, 8]
+            dsl_study(jmaxs=jm, fixed=[int(x) for x in args.study_fixed.split(",") if x],
+                      eps=float(args.study_eps.split(",")[0]) if args.study_eps != "1e-3,1e-4,1e-5,1e-6" else 1e-3,
+                      bs=args.study_bs if args.study_bs != 33 else 17, t_end=args.study_t)
+        return
     if args.study:
         if rank == 0:
             swirl_study(jmaxs=[int(x) for x in args.study_jmax.split(",")],
@@ -432,7 +543,7 @@ def main():
     # Independent replicas per rank (trees never exchange data): weak scaling.
     g = mr.Forest(dim=w["dim"], Bs=w["Bs"], nvar=w.get("nvar", 1), precision=w["precision"],
                   detail_fp64=w["detail_fp64"], rhs=w["rhs"], trees=trees, capacity=w["capacity"],
-                  norm_kind=w.get("norm_kind", 0), stream=stream.cuda_stream)
+                  norm_kind=w.get("norm_kind", 0), L=w.get("L", 1.0), stream=stream.cuda_stream)
     if args.overlap:
         g.set_launch_overlap(True)
     B, d = w["Bs"], w["dim"]
@@ -620,7 +731,8 @@ def main():
     kern = {}
     stage_ms = st["ms"]["stage"]
     kern["stage"] = dict(
-        kernel="%s (RK stage incl. fused ghost gather)" % ("k_stage_ns" if w["rhs"] == "ns" else "k_stage_adv"),
+        kernel="%s (RK stage incl. fused ghost gather)" % {"ns": "k_stage_ns", "ns_skew": "k_stage_nss"}.get(
+            w["rhs"], "k_stage_adv"),
         ms=stage_ms, launches=st["stage_launches"], blocks=st["stage_blocks"],
         bytes=st["stage_blocks"] * bytes_per_stage_block(w))
     det_s = 4 if w["precision"] == "fp32" else 8
@@ -628,6 +740,16 @@ def main():
         kernel="k_details (ghost gather + wavelet details + block norms)", ms=st["ms"]["details"],
         launches=st["det_launches"], blocks=st["det_blocks"],
         bytes=st["det_blocks"] * (w["Bs"] ** w["dim"]) * w.get("nvar", 1) * det_s)
+    if st["ms"].get("filter", 0.0) > 0:
+        # shock filter: one read and one write of the state per block (the copy
+        # back into the state array is not algorithmic); it runs once per step on
+        # the list the four stages saw
+        fst = 4 if w["precision"] == "fp32" else 8
+        fblocks = st["stage_blocks"] // 4
+        kern["filter"] = dict(
+            kernel="k_filter + k_copy_active (shock filter incl. fused ghost gather)", ms=st["ms"]["filter"],
+            launches=st["calls"]["filter"], blocks=fblocks,
+            bytes=fblocks * 2 * (w["Bs"] ** w["dim"]) * w.get("nvar", 1) * fst)
     for v in kern.values():
         v["achieved_gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else 0.0
         v["launch_us"] = v["ms"] * 1e3 / max(1, v["launches"])

@@ -54,7 +54,13 @@ typedef int32_t mr_status;
 /* Right-hand sides N(phi) (one kind per context). */
 #define MR_RHS_ADV 0    /* -u . grad phi, constant u = rhs[0..2] (Sec. 3 advection equation) */
 #define MR_RHS_SWIRL 1  /* -u . grad phi, u of Sec. 3 Eq. (1), t_a = rhs[0]; 2D only */
-#define MR_RHS_NS 2     /* compressible Navier-Stokes (Sec. 4), rhs = {gamma, mu, Pr}; 2D, nvar 4 */
+#define MR_RHS_NS 2     /* compressible Navier-Stokes (Sec. 4) in flux form on q = (rho, rho u,
+                           rho v, E); rhs = {gamma, mu, Pr, r_th}; 2D, nvar 4.  r_th > 0: the
+                           shock-capturing filter (mr_filter) runs after the RK step of every
+                           mr_step and graph step */
+#define MR_RHS_NS_SKEW 3  /* the same equations in the skew-symmetric form Sec. 4 uses (Reiss &
+                           Sesterhenn 2014) on the square-root variables q = (sqrt(rho),
+                           sqrt(rho) u, sqrt(rho) v, p); rhs as for MR_RHS_NS */
 
 /* Initial conditions (evaluated on the device from per-lattice factor tables). */
 #define MR_IC_GAUSS 0   /* prod_a exp(-d_a^2/(2 sigma^2)), nearest periodic image:
@@ -62,6 +68,12 @@ typedef int32_t mr_status;
 #define MR_IC_MIXING 1  /* temporal mixing layer: ic = {delta, U0, Mach, gamma, amp,
                            a_1..a_8, phi_1..phi_8}; rho = 1 */
 #define MR_IC_NONE 2    /* no analytic field; blocks come from mr_set_blocks */
+#define MR_IC_SHEAR_LAYER 3  /* double shear layer of Sec. 4: layers at x = xc -+ hw, profile
+                           s(x) = (tanh((x - xc + hw)/lw) - tanh((x - xc - hw)/lw)) / 2,
+                           rho = rho0 + (rho1 - rho0) s, v = v0 + (v1 - v0) s,
+                           u = amp sin(2 pi (y - yc)), p = p0;
+                           ic = {rho1, rho0, v1, v0, lw, p0, amp, hw, xc, yc}; NS kinds only,
+                           stored in the kind's variables (gamma = rhs[0]) */
 
 /* mr_adapt modes (Sec. 2.1 / 2.3). */
 #define MR_ADAPT_REFINE_ALL 0      /* every block below Jmax gains one level */
@@ -152,9 +164,25 @@ mr_status mr_rk_step(mr_ctx ctx, const double* t, const double* dt);
  * flags + merge until no family merges (or max_rounds) and synchronises. */
 mr_status mr_adapt(mr_ctx ctx, int32_t mode);
 
-/* One full multiresolution step (Sec. 2.1): refine all, RK4, coarsen.
+/* One full multiresolution step (Sec. 2.1): refine all, RK4, the shock filter
+ * (Navier-Stokes trees with r_th > 0, Sec. 4), coarsen.
  * Synchronises once per coarsening round when max_rounds = 0. */
 mr_status mr_step(mr_ctx ctx, const double* t, const double* dt);
+
+/* Shock-capturing filter of Bogey, de Cacqueray & Bailly (2009), which Sec. 4
+ * applies after every time step with threshold r_th = rhs[3], on every
+ * Navier-Stokes tree with r_th > 0 (others are unchanged).  On the synchronised
+ * field, per direction a and node n: dilatation th (2nd-order central
+ * differences of u and v), Dth_n = (-th_{n+1} + 2 th_n - th_{n-1}) / 4,
+ * M_n = ((Dth_n - Dth_{n+1})^2 + (Dth_n - Dth_{n-1})^2) / 2,
+ * r_n = M_n dx^2 / c_n^2 + 1e-16 (c^2 = gamma p / rho),
+ * s_n = max(0, 1 - r_th / r_n); every stored variable q becomes
+ * q_n - sum_a (s_{n+1/2} F_{n+1/2} - s_{n-1/2} F_{n-1/2}) with
+ * F_{n+1/2} = -(q_{n+1} - q_n) / 4 and s_{n+1/2} = (s_n + s_{n+1}) / 2, both
+ * directions from the unfiltered field.  MR_EINVAL unless rhs_kind is
+ * MR_RHS_NS or MR_RHS_NS_SKEW.  Asynchronous (errors at the next synchronising
+ * call). */
+mr_status mr_filter(mr_ctx ctx);
 
 /* Number of blocks of a tree (tree = -1: all trees).  Synchronises. */
 mr_status mr_num_blocks(mr_ctx ctx, int32_t tree, int64_t* n);
@@ -232,15 +260,16 @@ int64_t mr_launch_count(mr_ctx ctx);
 
 /* Phase timers and work counters (tracing).  Phases: 0 refine (with the
  * proposal), 1 RK4 stages, 2 details of a coarsening round, 3 flags, merge and
- * list rebuild, 4 synchronisation/export.  ms[p] is device time between CUDA
+ * list rebuild, 4 synchronisation/export, 5 shock filter (with its copy back
+ * into the state).  ms[p] is device time between CUDA
  * events recorded on the context's stream around the phase (only while timing
  * is enabled); stage_blocks counts the blocks processed by all RK stage
  * launches, stage_launches those launches; det_blocks the blocks whose details
  * were evaluated (blocks whose neighbourhood did not change since the previous
  * round reuse theirs), det_launches the host-driven coarsening rounds. */
 typedef struct {
-  double ms[5];
-  int64_t phase_calls[5];
+  double ms[6];
+  int64_t phase_calls[6];
   int64_t stage_launches;
   int64_t stage_blocks;
   int64_t steps;

@@ -15,8 +15,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmr.so")
 
 MR_OK, MR_EINVAL, MR_ENOMEM, MR_ECAPACITY, MR_ECUDA, MR_ETIMEOUT, MR_ENAN, MR_EINTERNAL = range(8)
 PREC = {"fp64": 0, "fp32": 1, "fp32_acc64": 2}
-RHS = {"adv": 0, "swirl": 1, "ns": 2}
-IC = {"gauss": 0, "mixing": 1, "none": 2}
+RHS = {"adv": 0, "swirl": 1, "ns": 2, "ns_skew": 3}
+IC = {"gauss": 0, "mixing": 1, "none": 2, "shear_layer": 3}
 ADAPT = {"refine_all": 0, "refine_flagged": 1, "coarsen": 2, "flags_only": 3, "propose": 4,
          "refine_step": 5}
 STATUS = {0: "MR_OK", 1: "MR_EINVAL", 2: "MR_ENOMEM", 3: "MR_ECAPACITY", 4: "MR_ECUDA",
@@ -48,12 +48,12 @@ class BlockInfo(C.Structure):
 
 
 class Stats(C.Structure):
-    _fields_ = [("ms", C.c_double * 5), ("phase_calls", C.c_int64 * 5),
+    _fields_ = [("ms", C.c_double * 6), ("phase_calls", C.c_int64 * 6),
                 ("stage_launches", C.c_int64), ("stage_blocks", C.c_int64), ("steps", C.c_int64),
                 ("det_launches", C.c_int64), ("det_blocks", C.c_int64)]
 
 
-PHASES = ("refine", "stage", "details", "flags_merge", "sync_export")
+PHASES = ("refine", "stage", "details", "flags_merge", "sync_export", "filter")
 
 BLOCK_INFO_DTYPE = np.dtype([("level", np.int32), ("tree", np.int32), ("treecode", np.uint64),
                              ("coords", np.int32, 3), ("pad", np.int32),
@@ -68,6 +68,7 @@ SIGNATURES = {
     "mr_init_tree": (_i32, [_vp]),
     "mr_set_rhs": (_i32, [_vp, _i32, _i32, _dp]),
     "mr_sync_ghosts": (_i32, [_vp]),
+    "mr_filter": (_i32, [_vp]),
     "mr_rk_step": (_i32, [_vp, _dp, _dp]),
     "mr_adapt": (_i32, [_vp, _i32]),
     "mr_step": (_i32, [_vp, _dp, _dp]),
@@ -197,6 +198,10 @@ class Forest:
 
     def sync_ghosts(self):
         self._ck(self.lib.mr_sync_ghosts(self.h))
+
+    def filter(self):
+        """Shock-capturing filter of the Navier-Stokes state (trees with r_th > 0)."""
+        self._ck(self.lib.mr_filter(self.h))
 
     def _td(self, t, dt):
         t = np.ascontiguousarray(np.broadcast_to(np.asarray(t, np.float64), (self.ntrees,)))
@@ -379,7 +384,7 @@ class Forest:
     def stats(self):
         s = Stats()
         self._ck(self.lib.mr_get_stats(self.h, C.byref(s)))
-        return dict(ms={PHASES[i]: s.ms[i] for i in range(5)},
-                    calls={PHASES[i]: s.phase_calls[i] for i in range(5)},
+        return dict(ms={PHASES[i]: s.ms[i] for i in range(6)},
+                    calls={PHASES[i]: s.phase_calls[i] for i in range(6)},
                     stage_launches=s.stage_launches, stage_blocks=s.stage_blocks, steps=s.steps,
                     det_launches=s.det_launches, det_blocks=s.det_blocks)

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmr.so")
-UNITS = ["mr_api.cu", "mr_scan.cu", "mr_k2.cu", "mr_k2s.cu", "mr_k2t.cu", "mr_k3.cu", "mr_k3s.cu", "mr_cnn.cu"]
+UNITS = ["mr_api.cu", "mr_scan.cu", "mr_k2.cu", "mr_k2s.cu", "mr_k2t.cu", "mr_k3.cu", "mr_k3s.cu", "mr_cnn.cu",
+         "mr_ns.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-fmad=false", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-ffp-contract=off", "-Xptxas", "-warn-spills"]

@@ -135,6 +135,19 @@ PoolView view(mr_ctx c) {
 Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb}; }
 
 
+// RHS-derived per-tree constants (creation and mr_set_rhs).
+void rhs_consts(int kind, const double* rhs, TreeDev& td) {
+  for (int a = 0; a < 8; ++a) td.rhs[a] = rhs[a];
+  for (int a = 0; a < 8; ++a) td.rhsf[a] = (float)rhs[a];
+  const double gam = rhs[0], mud = rhs[1], Pr = rhs[2];
+  td.nsd[0] = gam - 1.0;
+  td.nsd[1] = mud;
+  td.nsd[2] = Pr != 0.0 && gam != 1.0 ? mud * gam / ((gam - 1.0) * Pr) : 0.0;
+  td.nsd[3] = gam;
+  for (int a = 0; a < 4; ++a) td.nsf[a] = (float)td.nsd[a];
+  td.rth = is_ns(kind) ? rhs[3] : 0.0;
+}
+
 // 1D factor tables of one tree on its finest lattice (node index U in [0, N)).
 void lattice_tables(const mr_params& p, const mr_tree_desc& t, int64_t N, double* out) {
   const double h = p.L / (double)N;
@@ -154,6 +167,11 @@ void lattice_tables(const mr_params& p, const mr_tree_desc& t, int64_t N, double
       const double sv = std::sin(M_PI * x[0]);
       out[kLatSwA * N + U] = sv * sv;
       out[kLatSwB * N + U] = std::sin(2.0 * M_PI * x[0]);
+    }
+    if (t.ic_kind == MR_IC_SHEAR_LAYER) {
+      const double lw = t.ic[4], amp = t.ic[6], hw = t.ic[7], xc = t.ic[8], yc = t.ic[9];
+      out[kLatSlS * N + U] = 0.5 * (std::tanh((x[0] - (xc - hw)) / lw) - std::tanh((x[0] - (xc + hw)) / lw));
+      out[kLatSlU * N + U] = amp * std::sin(2.0 * M_PI * (x[1] - yc));
     }
     if (t.ic_kind == MR_IC_MIXING) {
       const double delta = t.ic[0], U0 = t.ic[1];
@@ -492,6 +510,18 @@ mr_status rk_step(mr_ctx ctx, const double* t, const double* dt) {
   return MR_OK;
 }
 
+// The shock filter of Sec. 4 runs after the RK step when a Navier-Stokes tree
+// has r_th > 0 (needs the stage plan of the current grid).
+bool filter_on(mr_ctx ctx) {
+  if (!is_ns(ctx->p.rhs_kind)) return false;
+  for (auto& t : ctx->tdev)
+    if (t.rth > 0.0) return true;
+  return false;
+}
+void do_filter(mr_ctx ctx, cudaStream_t st) {
+  launch_filter(view(ctx), fields(ctx), ctx->lc, st);
+}
+
 mr_status set_blocks_dev(mr_ctx ctx, int64_t n, const int32_t* lvl, const int32_t* tree,
                          const int32_t* crd, const double* fld) {
   // Host arrays -> device staging, then the device builds the pool.
@@ -585,22 +615,26 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
   if (P.ntrees < 1 || P.ntrees > kMaxTrees) return bad("ntrees out of range");
   if (P.precision < 0 || P.precision > 2) return bad("unknown precision");
   if (P.rhs_kind == MR_RHS_SWIRL && P.dim != 2) return bad("swirl is 2D");
-  if (P.rhs_kind == MR_RHS_NS && (P.dim != 2 || P.nvar != 4)) return bad("Navier-Stokes is 2D with nvar 4");
-  if (P.rhs_kind != MR_RHS_ADV && P.rhs_kind != MR_RHS_SWIRL && P.rhs_kind != MR_RHS_NS)
-    return bad("unknown rhs_kind");
-  if (P.rhs_kind != MR_RHS_NS && P.nvar != 1) return bad("advection has nvar 1");
+  const bool ns = is_ns(P.rhs_kind);
+  if (ns && (P.dim != 2 || P.nvar != 4)) return bad("Navier-Stokes is 2D with nvar 4");
+  if (P.rhs_kind != MR_RHS_ADV && P.rhs_kind != MR_RHS_SWIRL && !ns) return bad("unknown rhs_kind");
+  if (!ns && P.nvar != 1) return bad("advection has nvar 1");
   if (P.capacity < 1 || P.capacity > (1LL << 30)) return bad("capacity out of range");
   if (!(P.L > 0)) return bad("L must be positive");
   const int maxJ = P.dim == 2 ? 10 : 7;
   for (int k = 0; k < P.ntrees; ++k) {
     const mr_tree_desc& t = trees[k];
     if (t.Jmin < 1 || t.Jmax < t.Jmin || t.Jmax > maxJ) return bad("need 1 <= Jmin <= Jmax <= 10 (2D) / 7 (3D)");
-    if (t.ic_kind < 0 || t.ic_kind > 2) return bad("unknown ic_kind");
+    if (t.ic_kind < 0 || t.ic_kind > 3) return bad("unknown ic_kind");
     if (t.ic_kind == MR_IC_GAUSS && !(t.ic[3] > 0)) return bad("Gaussian sigma must be positive");
     if (P.rhs_kind == MR_RHS_SWIRL && !(t.rhs[0] > 0)) return bad("swirl period must be positive");
-    if (P.rhs_kind == MR_RHS_NS && !(t.rhs[0] > 1.0 && t.rhs[1] >= 0.0 && t.rhs[2] > 0.0))
+    if (ns && !(t.rhs[0] > 1.0 && t.rhs[1] >= 0.0 && t.rhs[2] > 0.0))
       return bad("Navier-Stokes needs gamma > 1, mu >= 0, Pr > 0");
-    if (P.rhs_kind == MR_RHS_NS && t.ic_kind == MR_IC_GAUSS) return bad("Navier-Stokes needs the mixing-layer IC or set_blocks");
+    if (ns && t.ic_kind == MR_IC_GAUSS) return bad("Navier-Stokes needs a flow IC or set_blocks");
+    if (!ns && (t.ic_kind == MR_IC_MIXING || t.ic_kind == MR_IC_SHEAR_LAYER)) return bad("flow ICs need a Navier-Stokes RHS");
+    if (t.ic_kind == MR_IC_MIXING && P.rhs_kind != MR_RHS_NS) return bad("the mixing-layer IC is in flux-form variables");
+    if (t.ic_kind == MR_IC_SHEAR_LAYER && !(t.ic[0] > 0 && t.ic[1] > 0 && t.ic[4] > 0 && t.ic[5] > 0))
+      return bad("shear layer needs rho1, rho0, lw, p0 > 0");
     ctx->td.push_back(t);
   }
   mr_status st = MR_OK;
@@ -652,15 +686,7 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     lat += (int64_t)kNumLat * td.N;
     td.cell_off = cells;
     cells += (int64_t)1 << (d * t.Jmax);
-    for (int a = 0; a < 8; ++a) td.rhs[a] = t.rhs[a];
-    for (int a = 0; a < 8; ++a) td.rhsf[a] = (float)t.rhs[a];
-    {
-      const double gam = t.rhs[0], mud = t.rhs[1], Pr = t.rhs[2];
-      td.nsd[0] = gam - 1.0;
-      td.nsd[1] = mud;
-      td.nsd[2] = Pr != 0.0 && gam != 1.0 ? mud * gam / ((gam - 1.0) * Pr) : 0.0;
-      for (int a = 0; a < 3; ++a) td.nsf[a] = (float)td.nsd[a];
-    }
+    rhs_consts(P.rhs_kind, t.rhs, td);
     for (int a = 0; a < 3; ++a) td.x0[a] = t.x0[a];
     td.ic_kind = t.ic_kind;
     if (t.ic_kind == MR_IC_MIXING) {
@@ -669,6 +695,10 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
       const double p0 = c0 * c0 / gam;
       td.ic_e0 = p0 / (gam - 1.0);
       td.ic_amp = t.ic[4];
+    }
+    if (t.ic_kind == MR_IC_SHEAR_LAYER) {
+      td.ic_sl[0] = t.ic[0]; td.ic_sl[1] = t.ic[1]; td.ic_sl[2] = t.ic[2]; td.ic_sl[3] = t.ic[3];
+      td.ic_sl[4] = t.ic[5];
     }
     ctx->tdev.push_back(td);
   }
@@ -794,14 +824,23 @@ mr_status mr_init_tree(mr_ctx ctx) {
   return check_device(ctx);
 }
 
+namespace {
+void drop_graph(mr_ctx ctx);
+}
+
 mr_status mr_set_rhs(mr_ctx ctx, int32_t rhs_kind, int32_t tree, const double* rp) {
   if (!ctx || !rp) return MR_EINVAL;
   if (rhs_kind != ctx->p.rhs_kind) return fail(ctx, MR_EINVAL, "rhs kind differs from the context's");
   if (tree < -1 || tree >= ctx->p.ntrees) return fail(ctx, MR_EINVAL, "tree out of range");
+  if (is_ns(rhs_kind) && !(rp[0] > 1.0 && rp[1] >= 0.0 && rp[2] > 0.0))
+    return fail(ctx, MR_EINVAL, "Navier-Stokes needs gamma > 1, mu >= 0, Pr > 0");
+  const bool filtered = filter_on(ctx);
   for (int k = 0; k < ctx->p.ntrees; ++k) {
     if (tree >= 0 && k != tree) continue;
-    for (int a = 0; a < 8; ++a) { ctx->td[k].rhs[a] = rp[a]; ctx->tdev[k].rhs[a] = rp[a]; }
+    for (int a = 0; a < 8; ++a) ctx->td[k].rhs[a] = rp[a];
+    rhs_consts(rhs_kind, rp, ctx->tdev[k]);
   }
+  if (filter_on(ctx) != filtered) drop_graph(ctx);  // a captured step has the filter launch or not
   cudaError_t e = cudaMemcpyAsync(ctx->trees, ctx->tdev.data(), ctx->p.ntrees * sizeof(TreeDev),
                                   cudaMemcpyHostToDevice, ctx->st);
   if (e != cudaSuccess) return fail(ctx, MR_ECUDA, cudaGetErrorString(e));
@@ -862,9 +901,23 @@ mr_status mr_step(mr_ctx ctx, const double* t, const double* dt) {
   if (s) return s;
   s = rk_step(ctx, t, dt);
   if (s) return s;
+  if (filter_on(ctx)) {
+    PhaseTimer tm(ctx, 5);
+    do_filter(ctx, ctx->st);
+  }
   s = coarsen_until_stable(ctx);
   if (s) return s;
   return after_step(ctx, collected);
+}
+
+mr_status mr_filter(mr_ctx ctx) {
+  if (!ctx) return MR_EINVAL;
+  if (!is_ns(ctx->p.rhs_kind)) return fail(ctx, MR_EINVAL, "the shock filter needs a Navier-Stokes RHS");
+  PoolView pv = view(ctx);
+  launch_plan<2>(pv, ctx->lc, ctx->st);
+  do_filter(ctx, ctx->st);
+  CK(cudaGetLastError());
+  return MR_OK;
 }
 
 mr_status mr_num_blocks(mr_ctx ctx, int32_t tree, int64_t* n) {
@@ -1078,6 +1131,7 @@ void enqueue_graph_prologue(mr_ctx ctx, cudaStream_t st) {
   for (int s = 0; s < 4; ++s)
     by_dim(ctx, [&] { launch_stage<2>(pv, f, s, sa, ctx->lc, st); },
            [&] { launch_stage<3>(pv, f, s, sa, ctx->lc, st); });
+  if (filter_on(ctx)) launch_filter(pv, f, ctx->lc, st);
 }
 
 void enqueue_round(mr_ctx ctx, cudaStream_t st, const RoundCtl& rc) {
@@ -1262,7 +1316,7 @@ mr_status mr_autotune(mr_ctx ctx, int32_t steps, int32_t* best_out) {
   std::vector<Cand> cands;
   const int mults[] = {1, 2, 3, 4, 6, 8, 0};
   for (int m : mults) cands.push_back({m, 0, 4, 1});
-  const bool warp_ok = ctx->p.dim == 2 && ctx->p.Bs == 17 && ctx->p.rhs_kind != MR_RHS_NS;
+  const bool warp_ok = ctx->p.dim == 2 && ctx->p.Bs == 17 && !is_ns(ctx->p.rhs_kind);
   if (warp_ok) {
     for (int m : mults) cands.push_back({m, 1, 4, 1});
     if (ctx->p.precision == MR_PREC_FP32) {
@@ -1319,7 +1373,7 @@ mr_status mr_set_warp_form(mr_ctx ctx, int32_t blocks_per_cta, int32_t staging) 
 
 mr_status mr_set_tuning(mr_ctx ctx, int32_t ctas_per_sm, int32_t stage_form) {
   if (!ctx || ctas_per_sm < 0 || ctas_per_sm > 32 || stage_form < -1 || stage_form > 1) return MR_EINVAL;
-  if (stage_form == 1 && (ctx->p.dim != 2 || ctx->p.Bs != 17 || ctx->p.rhs_kind == MR_RHS_NS))
+  if (stage_form == 1 && (ctx->p.dim != 2 || ctx->p.Bs != 17 || is_ns(ctx->p.rhs_kind)))
     return fail(ctx, MR_EINVAL, "the warp-per-block form is for 2D advection on 17^2 blocks");
   if (ctx->lc.grid_mult != ctas_per_sm || ctx->lc.stage_form != stage_form) drop_graph(ctx);
   ctx->lc.grid_mult = ctas_per_sm;

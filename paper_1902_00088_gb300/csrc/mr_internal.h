@@ -23,6 +23,9 @@ constexpr int kErrTimeout = 16;
 // ring around the block, then one entry of flags.
 constexpr int reg_entries(int d) { return (d == 3 ? 343 : 49) + 1; }
 
+// Navier-Stokes right-hand sides (flux form or skew-symmetric form, Sec. 4).
+__host__ __device__ constexpr bool is_ns(int kind) { return kind == MR_RHS_NS || kind == MR_RHS_NS_SKEW; }
+
 // Per-tree constants (device copy).
 struct TreeDev {
   int32_t Jmin, Jmax;
@@ -37,11 +40,13 @@ struct TreeDev {
   double dx[kMaxLevel + 1];         // dx_l = L / (2^l (Bs-1))
   double rhs[8];
   float rhsf[8];                    // rhs rounded to FP32
-  double nsd[3];                    // Navier-Stokes: gamma - 1, mu, kappa = mu gamma / ((gamma - 1) Pr)
-  float nsf[3];                     // the same rounded to FP32
+  double nsd[4];                    // Navier-Stokes: gamma - 1, mu, kappa = mu gamma / ((gamma - 1) Pr), gamma
+  float nsf[4];                     // the same rounded to FP32
+  double rth;                       // shock-filter threshold r_th (rhs[3]); <= 0: no filter
   double x0[3];
   int32_t ic_kind;
   double ic_e0, ic_amp;             // mixing layer: p0/(gamma-1) and perturbation amplitude
+  double ic_sl[5];                  // double shear layer: rho1, rho0, v1, v0, p0
 };
 
 // Device counters (one instance per context).
@@ -82,6 +87,7 @@ enum LatTable {
   kLatGx = 0, kLatGy, kLatGz,   // Gaussian factors (IC)
   kLatSwA, kLatSwB,             // swirl factors sin^2(pi x), sin(2 pi x)
   kLatNsU, kLatNsE, kLatNsS,    // mixing layer: u(y), exp(-(y/delta)^2), sum_k a_k sin(2 pi k x + phi_k)
+  kLatSlS, kLatSlU,             // double shear layer: layer profile s(x), u(y) = amp sin(2 pi (y - yc))
   kNumLat
 };
 
@@ -220,6 +226,12 @@ template <int D> void launch_set_blocks(const PoolView& pv, const Fields& f, int
                                         cudaStream_t st);
 template <int D> void launch_error(const PoolView& pv, const Fields& f, int tree, const double* ex,
                                    double* out4, const LaunchCfg& lc, cudaStream_t st);
+// Navier-Stokes of Sec. 4 (mr_ns.cu): RK stage in the skew-symmetric form
+// (2D, B = 17 or 33), and the shock-capturing filter of the state (y -> acc,
+// then copied back), which needs the stage plan of the current grid.
+template <int B> void launch_stage_nss(const PoolView& pv, const Fields& f, int stage,
+                                       const StageArgs& sa, const LaunchCfg& lc, cudaStream_t st);
+void launch_filter(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st);
 
 // Exclusive scan of n int2 pairs (emit -> eoff); totals written to tot[0..1].
 // n_dev: device count (nullable), else n_host.

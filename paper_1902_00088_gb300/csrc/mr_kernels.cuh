@@ -1401,7 +1401,8 @@ __global__ void __launch_bounds__(256) k_coarsen(PoolView pv, TS* __restrict__ y
 // --------------------------------------------------------------------- IC ----
 // Analytic fields from per-lattice factor tables: Gaussian as the product of
 // its 1D factors (x, then y, then z); mixing layer q = (1, u(y), v, E) with
-// v = amp (s(x) e(y)), E = p0/(gamma-1) + (u u + v v)/2.
+// v = amp (s(x) e(y)), E = p0/(gamma-1) + (u u + v v)/2; double shear layer
+// (Sec. 4) from its layer profile s(x) and u(y), in the RHS kind's variables.
 template <int D, int B, typename TS>
 __global__ void k_ic(PoolView pv, TS* __restrict__ y) {
   pdl_enter();
@@ -1430,6 +1431,20 @@ __global__ void k_ic(PoolView pv, TS* __restrict__ y) {
         y[at + pv.vs] = (TS)u;
         y[at + 2 * pv.vs] = (TS)v;
         y[at + 3 * pv.vs] = (TS)E;
+      } else if (td.ic_kind == MR_IC_SHEAR_LAYER) {
+        const double s = lat[kLatSlS * td.N + U[0]];
+        const double rho = td.ic_sl[1] + (td.ic_sl[0] - td.ic_sl[1]) * s;
+        const double v = td.ic_sl[3] + (td.ic_sl[2] - td.ic_sl[3]) * s;
+        const double u = lat[kLatSlU * td.N + U[1]];
+        double q[4];
+        if (pv.rhs_kind == MR_RHS_NS_SKEW) {
+          const double f = sqrt(rho);
+          q[0] = f; q[1] = f * u; q[2] = f * v; q[3] = td.ic_sl[4];
+        } else {
+          const double m1 = rho * u, m2 = rho * v;
+          q[0] = rho; q[1] = m1; q[2] = m2; q[3] = td.ic_sl[4] / td.nsd[0] + 0.5 * (m1 * u + m2 * v);
+        }
+        for (int w = 0; w < 4; ++w) y[at + w * pv.vs] = (TS)q[w];
       }
     }
   }

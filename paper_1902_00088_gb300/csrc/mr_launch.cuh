@@ -156,6 +156,7 @@ void launch_stage_bs(const PoolView& pv, const Fields& f, int stage, const Stage
                      const LaunchCfg& lc, cudaStream_t st) {
   if constexpr (D == 2) {
     if (pv.rhs_kind == MR_RHS_NS) stage_ns<B>(pv, f, stage, sa, lc, st);
+    else if (pv.rhs_kind == MR_RHS_NS_SKEW) launch_stage_nss<B>(pv, f, stage, sa, lc, st);
     else if (pv.rhs_kind == MR_RHS_SWIRL) stage_prec<D, B, MR_RHS_SWIRL>(pv, f, stage, sa, lc, st);
     else stage_prec<D, B, MR_RHS_ADV>(pv, f, stage, sa, lc, st);
   } else {

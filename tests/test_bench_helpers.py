@@ -1,0 +1,42 @@
+"""Host-side analysis helpers of bench.py (no GPU): the kinetic energy
+spectrum of the double shear layer study and the assembly of a uniform grid
+from exported blocks."""
+import numpy as np
+
+import bench
+
+
+def test_spectrum_of_single_modes_and_parseval():
+    # cos(2 pi 3 x) in psi_x and sin(2 pi 4 x) in psi_y: all energy in shells 3
+    # and 4, 1/4 each (mean of cos^2 / 2), and the shells sum to the mean
+    # kinetic energy density
+    N = 64
+    x = np.arange(N) / N
+    X, Y = np.meshgrid(x, x)
+    px, py = np.cos(2 * np.pi * 3 * X), np.sin(2 * np.pi * (4 * Y))
+    s = bench.kinetic_energy_spectrum(px, py, 8.0)
+    assert np.allclose(s[[3, 4]], 0.25) and np.allclose(np.delete(s, [3, 4]), 0.0, atol=1e-14)
+    rng = np.random.default_rng(0)
+    px, py = rng.standard_normal((N, N)), rng.standard_normal((N, N))
+    s = bench.kinetic_energy_spectrum(px, py, 8.0)
+    # shells beyond N/2 (the corners of the square) are cut off
+    k1 = np.fft.fftfreq(N, 1.0 / N)
+    inside = np.rint(np.sqrt(k1[None, :] ** 2 + k1[:, None] ** 2)) <= N // 2
+    e = 0.5 * (np.abs(np.fft.fft2(px)) ** 2 + np.abs(np.fft.fft2(py)) ** 2) / N ** 4
+    assert np.isclose(s.sum(), e[inside].sum())
+
+
+def test_uniform_field_places_blocks():
+    Bs, J = 5, 2
+    n = 1 << J
+    info = np.zeros(n * n, dtype=[("coords", np.int32, 3)])
+    f = np.zeros((n * n, 1, Bs, Bs))
+    for q in range(n * n):
+        cx, cy = q % n, q // n
+        info["coords"][q] = (cx, cy, 0)
+        i = cx * (Bs - 1) + np.arange(Bs)
+        j = cy * (Bs - 1) + np.arange(Bs)
+        f[q, 0] = 1000 * j[:, None] + i[None, :]
+    u = bench.uniform_field(info, f, Bs, J)
+    N = (Bs - 1) * n
+    assert np.array_equal(u[0], 1000 * np.arange(N)[:, None] + np.arange(N)[None, :])

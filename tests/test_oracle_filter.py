@@ -102,11 +102,13 @@ def test_sensor_strength_and_transfer_function(oracle_mod, form, s_target, axis)
         assert np.all(f[:, 0] == 1.0) and np.all(f[:, 3] == p0)
 
 
-def shock_like(n, m, N):
-    """Periodic state with jumps about two nodes wide: rho, u across x = 0.4, 0.9;
-    v, p across y = 0.45, 0.95 (where the sensor fires), smooth elsewhere."""
+def shock_like(n, m, N, w=None):
+    """Periodic state with jumps about two nodes wide (w = 1.28 / N): rho, u
+    across x = 0.4, 0.9; v, p across y = 0.45, 0.95 (where the sensor fires),
+    smooth elsewhere."""
     x, y = n / N, m / N
-    sx, sy = np.tanh(np.sin(2 * np.pi * (x + 0.1)) / 0.01), np.tanh(np.cos(2 * np.pi * (y - 0.2)) / 0.01)
+    w = 1.28 / N if w is None else w
+    sx, sy = np.tanh(np.sin(2 * np.pi * (x + 0.1)) / w), np.tanh(np.cos(2 * np.pi * (y - 0.2)) / w)
     r = 1.0 + 0.3 * sx + 0.05 * np.sin(2 * np.pi * y)
     u = 0.5 * sx + 0.1 * np.cos(2 * np.pi * y)
     v = 0.4 * sy * (1.0 + 0.2 * np.sin(2 * np.pi * x))
