@@ -146,6 +146,7 @@ void rhs_consts(int kind, const double* rhs, TreeDev& td) {
   td.nsd[3] = gam;
   for (int a = 0; a < 4; ++a) td.nsf[a] = (float)td.nsd[a];
   td.rth = is_ns(kind) ? rhs[3] : 0.0;
+  td.rthf = (float)td.rth;
 }
 
 // 1D factor tables of one tree on its finest lattice (node index U in [0, N)).
@@ -482,15 +483,29 @@ mr_status after_step(mr_ctx ctx, int64_t collected) {
   return MR_OK;
 }
 
+// The shock filter of Sec. 4 runs after the RK step when a Navier-Stokes tree
+// has r_th > 0 (needs the stage plan of the current grid).
+bool filter_on(mr_ctx ctx) {
+  if (!is_ns(ctx->p.rhs_kind)) return false;
+  for (auto& t : ctx->tdev)
+    if (t.rth > 0.0) return true;
+  return false;
+}
+void do_filter(mr_ctx ctx, cudaStream_t st, bool copy) {
+  launch_filter(view(ctx), fields(ctx), copy, ctx->lc, st);
+}
+
 mr_status rk_step(mr_ctx ctx, const double* t, const double* dt) {
   PoolView pv = view(ctx);
   const Fields f = fields(ctx);
   by_dim(ctx, [&] { launch_plan<2>(pv, ctx->lc, ctx->st); }, [&] { launch_plan<3>(pv, ctx->lc, ctx->st); });
   PhaseTimer tm(ctx, 1);  // the four stage launches
   ctx->stats.stage_launches += 4;
+  const bool filt = filter_on(ctx);
   for (int s = 0; s < 4; ++s) {
     StageArgs sa;
     std::memset(&sa, 0, sizeof(sa));
+    sa.copy_state = filt ? 1 : 0;
     for (int k = 0; k < ctx->p.ntrees; ++k) {
       const double h = dt[k];
       const double ca[4] = {h / 6.0, h / 3.0, h / 3.0, h / 6.0};
@@ -508,18 +523,6 @@ mr_status rk_step(mr_ctx ctx, const double* t, const double* dt) {
   }
   CK(cudaGetLastError());
   return MR_OK;
-}
-
-// The shock filter of Sec. 4 runs after the RK step when a Navier-Stokes tree
-// has r_th > 0 (needs the stage plan of the current grid).
-bool filter_on(mr_ctx ctx) {
-  if (!is_ns(ctx->p.rhs_kind)) return false;
-  for (auto& t : ctx->tdev)
-    if (t.rth > 0.0) return true;
-  return false;
-}
-void do_filter(mr_ctx ctx, cudaStream_t st) {
-  launch_filter(view(ctx), fields(ctx), ctx->lc, st);
 }
 
 mr_status set_blocks_dev(mr_ctx ctx, int64_t n, const int32_t* lvl, const int32_t* tree,
@@ -681,6 +684,8 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
       td.dx[l] = dx;
       td.cD[l] = 1.0 / (12.0 * dx);
       td.cDf[l] = (float)td.cD[l];
+      td.fh2[l] = (float)(0.5 / dx);
+      td.fdx2[l] = (float)(dx * dx);
     }
     td.lat_off = lat;
     lat += (int64_t)kNumLat * td.N;
@@ -903,7 +908,7 @@ mr_status mr_step(mr_ctx ctx, const double* t, const double* dt) {
   if (s) return s;
   if (filter_on(ctx)) {
     PhaseTimer tm(ctx, 5);
-    do_filter(ctx, ctx->st);
+    do_filter(ctx, ctx->st, false);  // the last RK stage left the state's copy
   }
   s = coarsen_until_stable(ctx);
   if (s) return s;
@@ -915,7 +920,7 @@ mr_status mr_filter(mr_ctx ctx) {
   if (!is_ns(ctx->p.rhs_kind)) return fail(ctx, MR_EINVAL, "the shock filter needs a Navier-Stokes RHS");
   PoolView pv = view(ctx);
   launch_plan<2>(pv, ctx->lc, ctx->st);
-  do_filter(ctx, ctx->st);
+  do_filter(ctx, ctx->st, true);
   CK(cudaGetLastError());
   return MR_OK;
 }
@@ -1128,10 +1133,11 @@ void enqueue_graph_prologue(mr_ctx ctx, cudaStream_t st) {
   by_dim(ctx, [&] { launch_plan<2>(pv, ctx->lc, st); }, [&] { launch_plan<3>(pv, ctx->lc, st); });
   StageArgs sa;
   std::memset(&sa, 0, sizeof(sa));
+  sa.copy_state = filter_on(ctx) ? 1 : 0;
   for (int s = 0; s < 4; ++s)
     by_dim(ctx, [&] { launch_stage<2>(pv, f, s, sa, ctx->lc, st); },
            [&] { launch_stage<3>(pv, f, s, sa, ctx->lc, st); });
-  if (filter_on(ctx)) launch_filter(pv, f, ctx->lc, st);
+  if (filter_on(ctx)) launch_filter(pv, f, false, ctx->lc, st);
 }
 
 void enqueue_round(mr_ctx ctx, cudaStream_t st, const RoundCtl& rc) {

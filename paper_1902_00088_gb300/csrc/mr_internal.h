@@ -43,6 +43,9 @@ struct TreeDev {
   double nsd[4];                    // Navier-Stokes: gamma - 1, mu, kappa = mu gamma / ((gamma - 1) Pr), gamma
   float nsf[4];                     // the same rounded to FP32
   double rth;                       // shock-filter threshold r_th (rhs[3]); <= 0: no filter
+  float rthf;                       // r_th rounded to FP32
+  float fh2[kMaxLevel + 1];         // FP32 roundings of 1 / (2 dx_l) and dx_l^2 (filter sensor)
+  float fdx2[kMaxLevel + 1];
   double x0[3];
   int32_t ic_kind;
   double ic_e0, ic_amp;             // mixing layer: p0/(gamma-1) and perturbation amplitude
@@ -97,6 +100,8 @@ struct StageArgs {
   double cy[kMaxTrees];   // next-stage coefficient: dt/2, dt/2, dt, (unused)
   double ct[kMaxTrees];   // swirl time factor cos(pi t_s / t_a)
   float caf[kMaxTrees], cyf[kMaxTrees], ctf[kMaxTrees];  // the same rounded to FP32
+  int32_t copy_state;     // Navier-Stokes stage 3: also store the new state in the stage
+                          // type into Yb (the shock filter's source)
 };
 
 // Everything a kernel needs to know about the pool and the tree tables.
@@ -227,11 +232,13 @@ template <int D> void launch_set_blocks(const PoolView& pv, const Fields& f, int
 template <int D> void launch_error(const PoolView& pv, const Fields& f, int tree, const double* ex,
                                    double* out4, const LaunchCfg& lc, cudaStream_t st);
 // Navier-Stokes of Sec. 4 (mr_ns.cu): RK stage in the skew-symmetric form
-// (2D, B = 17 or 33), and the shock-capturing filter of the state (y -> acc,
-// then copied back), which needs the stage plan of the current grid.
+// (2D, B = 17 or 33), and the shock-capturing filter of the state, in place,
+// from the copy of the state in the stage type in Yb (written by the last RK
+// stage with StageArgs::copy_state, or first by the filter itself with copy);
+// it needs the stage plan of the current grid.
 template <int B> void launch_stage_nss(const PoolView& pv, const Fields& f, int stage,
                                        const StageArgs& sa, const LaunchCfg& lc, cudaStream_t st);
-void launch_filter(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st);
+void launch_filter(const PoolView& pv, const Fields& f, bool copy, const LaunchCfg& lc, cudaStream_t st);
 
 // Exclusive scan of n int2 pairs (emit -> eoff); totals written to tot[0..1].
 // n_dev: device count (nullable), else n_host.

@@ -620,7 +620,9 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
             acc[at] = av[u] + (TS)(casf * kc);
             ynext[at] = (TY)((TC)yv[u] + cysf * kc);
           } else {
-            y[at] = av[u] + (TS)(casf * kc);
+            const TS yn = av[u] + (TS)(casf * kc);
+            y[at] = yn;
+            if (sa.copy_state) ynext[at] = (TY)yn;
           }
         } else {
           const TS kk = (TS)(-(dFx + dGy));
@@ -631,7 +633,9 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
             acc[at] = av[u] + cas * kk;
             ynext[at] = (TY)(yv[u] + cys * kk);
           } else {
-            y[at] = av[u] + cas * kk;
+            const TS yn = av[u] + cas * kk;
+            y[at] = yn;
+            if (sa.copy_state) ynext[at] = (TY)yn;
           }
         }
       }

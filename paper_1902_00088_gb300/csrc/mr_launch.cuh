@@ -116,7 +116,8 @@ static void stage_ns_impl(const PoolView& pv, const Fields& f, int stage, const 
   constexpr int threads = 256;
   const size_t smem = kRingBytesD<2> + sizeof(TY) * (4 * Gm::TILE + 4 * Gm::CBOX + 4 * Gm::TILE +
                                                  4 * NsGeo<B>::NF + 4 * NsGeo<B>::NG);
-  TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
+  // stage s reads y, Ya, Yb, Ya and writes Ya, Yb, Ya, (Yb: the new state's copy for the filter)
+  TY* ynext = (TY*)(stage == 1 || stage == 3 ? f.Yb : f.Ya);
   if (stage == 0) {
     auto k = k_stage_ns<B, TS, TY, TS>;
     prep_smem(k, smem);

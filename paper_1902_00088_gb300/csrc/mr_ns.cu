@@ -10,7 +10,8 @@ static void stage_nss_impl(const PoolView& pv, const Fields& f, int stage, const
                            const LaunchCfg& lc, cudaStream_t st) {
   constexpr int threads = 256;
   constexpr size_t smem = nss_smem<B, TY>();
-  TY* ynext = (TY*)(stage == 1 ? f.Yb : f.Ya);
+  // stage s reads y, Ya, Yb, Ya and writes Ya, Yb, Ya, (Yb: the new state's copy for the filter)
+  TY* ynext = (TY*)(stage == 1 || stage == 3 ? f.Yb : f.Ya);
   if (stage == 0) {
     auto k = k_stage_nss<B, TS, TY, TS>;
     prep_smem(k, smem);
@@ -41,34 +42,37 @@ template void launch_stage_nss<33>(const PoolView&, const Fields&, int, const St
                                    cudaStream_t);
 
 template <int B, typename TS, typename TC, int KIND>
-static void filter_impl(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+static void filter_impl(const PoolView& pv, const Fields& f, bool copy, const LaunchCfg& lc, cudaStream_t st) {
   constexpr int threads = 256;
   constexpr size_t smem = filter_smem<B, TC>();
+  if (copy) {
+    launch_k(lc.pdl, k_state_copy<TS, TC>, lc.num_sms * 8, 256, 0, st, pv, (const TS*)f.y, (TC*)f.Yb);
+    count_launch();
+  }
   auto k = k_filter<B, TS, TC, KIND>;
   prep_smem(k, smem);
   launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv,
-           (const TS*)f.y, (TS*)f.acc);
-  launch_k(lc.pdl, k_copy_active<TS>, lc.num_sms * 8, 256, 0, st, pv, (const TS*)f.acc, (TS*)f.y);
-  count_launch(2);
+           (const TC*)f.Yb, (TS*)f.y);
+  count_launch();
 }
 
 template <int B, int KIND>
-static void filter_prec(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+static void filter_prec(const PoolView& pv, const Fields& f, bool copy, const LaunchCfg& lc, cudaStream_t st) {
   switch (pv.prec) {
-    case MR_PREC_FP64: filter_impl<B, double, double, KIND>(pv, f, lc, st); break;
-    case MR_PREC_FP32: filter_impl<B, float, float, KIND>(pv, f, lc, st); break;
-    default: filter_impl<B, double, float, KIND>(pv, f, lc, st); break;
+    case MR_PREC_FP64: filter_impl<B, double, double, KIND>(pv, f, copy, lc, st); break;
+    case MR_PREC_FP32: filter_impl<B, float, float, KIND>(pv, f, copy, lc, st); break;
+    default: filter_impl<B, double, float, KIND>(pv, f, copy, lc, st); break;
   }
 }
 
-void launch_filter(const PoolView& pv, const Fields& f, const LaunchCfg& lc, cudaStream_t st) {
+void launch_filter(const PoolView& pv, const Fields& f, bool copy, const LaunchCfg& lc, cudaStream_t st) {
   const bool skew = pv.rhs_kind == MR_RHS_NS_SKEW;
   if (pv.Bs == 17) {
-    if (skew) filter_prec<17, MR_RHS_NS_SKEW>(pv, f, lc, st);
-    else filter_prec<17, MR_RHS_NS>(pv, f, lc, st);
+    if (skew) filter_prec<17, MR_RHS_NS_SKEW>(pv, f, copy, lc, st);
+    else filter_prec<17, MR_RHS_NS>(pv, f, copy, lc, st);
   } else {
-    if (skew) filter_prec<33, MR_RHS_NS_SKEW>(pv, f, lc, st);
-    else filter_prec<33, MR_RHS_NS>(pv, f, lc, st);
+    if (skew) filter_prec<33, MR_RHS_NS_SKEW>(pv, f, copy, lc, st);
+    else filter_prec<33, MR_RHS_NS>(pv, f, copy, lc, st);
   }
 }
 

@@ -35,7 +35,7 @@ constexpr size_t nss_smem() {
 }
 
 template <int B, typename TS, typename TY, typename TSRC>
-__global__ void __launch_bounds__(256) k_stage_nss(PoolView pv, const TSRC* __restrict__ src,
+__global__ void __launch_bounds__(256, 3) k_stage_nss(PoolView pv, const TSRC* __restrict__ src,
                                                    TS* __restrict__ y, TS* __restrict__ acc,
                                                    TY* __restrict__ ynext, int stage, StageArgs sa) {
   pdl_enter();
@@ -182,7 +182,9 @@ __global__ void __launch_bounds__(256) k_stage_nss(PoolView pv, const TSRC* __re
             acc[at] = av[v] + (TS)(cf.ca * kc);
             ynext[at] = (TY)((TC)yv[v] + cf.cy * kc);
           } else {
-            y[at] = av[v] + (TS)(cf.ca * kc);
+            const TS yn = av[v] + (TS)(cf.ca * kc);
+            y[at] = yn;
+            if (sa.copy_state) ynext[at] = (TY)yn;
           }
         } else {
           const TS kk = (TS)k[v];
@@ -193,7 +195,9 @@ __global__ void __launch_bounds__(256) k_stage_nss(PoolView pv, const TSRC* __re
             acc[at] = av[v] + cs.ca * kk;
             ynext[at] = (TY)(yv[v] + cs.cy * kk);
           } else {
-            y[at] = av[v] + cs.ca * kk;
+            const TS yn = av[v] + cs.ca * kk;
+            y[at] = yn;
+            if (sa.copy_state) ynext[at] = (TY)yn;
           }
         }
       }
@@ -205,9 +209,11 @@ __global__ void __launch_bounds__(256) k_stage_nss(PoolView pv, const TSRC* __re
 
 // ------------------------------------------------------- shock filter -------
 // Shock-capturing filter of Bogey, de Cacqueray & Bailly (2009), applied after
-// every time step in Sec. 4 (threshold r_th of the block's tree), on the
-// synchronised tile of the state y; the result goes to `out` (all interior
-// nodes, trees without a filter copied unchanged).  Per direction a, node n:
+// every time step in Sec. 4 (threshold r_th of the block's tree), in place on
+// the state y.  The synchronised tiles are gathered from `ys`, a copy of the
+// state in the stage type that no CTA writes meanwhile (the last RK stage
+// stores it), so every CTA updates its own block's interior in y while the
+// others read their ghosts.  Per direction a, node n:
 //   th_n = (u_{n+1} - u_{n-1}) / (2 dx) + (v_{n+1} - v_{n-1}) / (2 dx)  (each along its axis)
 //   Dth_n = (-th_{n+1} + 2 th_n - th_{n-1}) / 4
 //   M_n = ((Dth_n - Dth_{n+1})^2 + (Dth_n - Dth_{n-1})^2) / 2
@@ -216,10 +222,12 @@ __global__ void __launch_bounds__(256) k_stage_nss(PoolView pv, const TSRC* __re
 //   q_n <- q_n - sum_a (s_{n+1/2} F_{n+1/2} - s_{n-1/2} F_{n-1/2}),
 //   F_{n+1/2} = -(q_{n+1} - q_n) / 4, s_{n+1/2} = (s_n + s_{n+1}) / 2,
 // both directions from the unfiltered tile.  The stencil reaches four nodes
-// along a and one across.  Everything is evaluated in TC; with an FP64 state
-// and FP32 arithmetic the filter increment is formed in FP32 and subtracted
-// from the FP64 state (block-edge nodes owned by a neighbour first take the
-// owner's value, as in the first RK stage).
+// along a and one across.  Everything is evaluated in TC.  With TS = TC every
+// interior node becomes its synchronised value minus the increment (as in
+// the oracle); with an FP64 state and FP32 arithmetic the FP32 increment is
+// subtracted from the FP64 state where it is not zero (block-edge nodes owned
+// by a finer neighbour keep their own value until the next synchronisation
+// replaces it by the owner's, as after every RK stage).
 // KIND: MR_RHS_NS (q = rho, rho u, rho v, E) or MR_RHS_NS_SKEW (phi, psi, p).
 template <int B, typename TC>
 constexpr size_t filter_smem() {
@@ -228,7 +236,7 @@ constexpr size_t filter_smem() {
 }
 
 template <int B, typename TS, typename TC, int KIND>
-__global__ void __launch_bounds__(256) k_filter(PoolView pv, const TS* __restrict__ y, TS* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_filter(PoolView pv, const TC* __restrict__ ys, TS* __restrict__ y) {
   pdl_enter();
   using Gm = Geo<2, B>;
   constexpr int T = Gm::T, G = Gm::G;
@@ -253,28 +261,25 @@ __global__ void __launch_bounds__(256) k_filter(PoolView pv, const TS* __restric
     const BlockInfo b = plan_block<2>(splan);
     const TreeDev& td = pv.trees[b.tree];
     const int64_t base = (int64_t)b.slot * 4 * pv.vs;
-    if (!(td.rth > 0.0)) {
-      for (int idx = threadIdx.x; idx < 4 * Gm::NI; idx += blockDim.x) {
-        const int64_t at = base + (int64_t)(idx / Gm::NI) * pv.vs + idx % Gm::NI;
-        out[at] = y[at];
-      }
+    if (!(td.rth > 0.0)) {  // no filter on this tree
       __syncthreads();
       continue;
     }
     if ((splan[1] >> 30) & 1) {
-      gather_uniform<2, B, kG, 4, TS, TC>(pv, b, splan + PL::NBO, y, (TS*)y, tile, MIX);
+      gather_uniform<2, B, kG, 4, TC, TC>(pv, b, splan + PL::NBO, ys, (TC*)ys, tile, false);
     } else {
       load_regions<2, CtaGroup>(pv, p, R);
       __syncthreads();
-      fill_tile<2, B, TS, TC>(pv, b, y, (TS*)y, tile, MIX, R, cbox, pu, true);
+      fill_tile<2, B, TC, TC>(pv, b, ys, (TC*)ys, tile, false, R, cbox, pu, true);
     }
     __syncthreads();
-    TC gm1, gam, rth;
-    if constexpr (sizeof(TC) == 4) { gm1 = td.nsf[0]; gam = td.nsf[3]; rth = (float)td.rth; }
-    else { gm1 = td.nsd[0]; gam = td.nsd[3]; rth = td.rth; }
-    const double dxl = td.dx[b.lvl];
-    const TC h2 = (TC)(0.5 / dxl);
-    const TC dx2 = (TC)(dxl * dxl);
+    TC gm1, gam, rth, h2, dx2;
+    if constexpr (sizeof(TC) == 4) {
+      gm1 = td.nsf[0]; gam = td.nsf[3]; rth = td.rthf; h2 = td.fh2[b.lvl]; dx2 = td.fdx2[b.lvl];
+    } else {
+      const double dxl = td.dx[b.lvl];
+      gm1 = td.nsd[0]; gam = td.nsd[3]; rth = td.rth; h2 = 0.5 / dxl; dx2 = dxl * dxl;
+    }
     for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x) {
       const TC q0 = tile[idx], q1 = tile[Gm::TILE + idx], q2 = tile[2 * Gm::TILE + idx], q3 = tile[3 * Gm::TILE + idx];
       const TC u = q1 / q0, v = q2 / q0;
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(256) k_filter(PoolView pv, const TS* __restric
       const TC M = TC(0.5) * ((d0 - dp) * (d0 - dp) + (d0 - dm) * (d0 - dm));
       const TC r = M / (pc[I(i, j)] / dx2) + TC(1e-16);
       const TC z = TC(1) - rth / r;
-      (ax == 0 ? sgx : sgy)[e] = TC(0.5) * (z + fabs(z));
+      (ax == 0 ? sgx : sgy)[e] = TC(0.5) * (z + (z < TC(0) ? -z : z));
     }
     __syncthreads();
     auto sX = [&](int i, int j) { return sgx[j * (B + 2) + (i + 1)]; };
@@ -332,29 +337,29 @@ __global__ void __launch_bounds__(256) k_filter(PoolView pv, const TS* __restric
       const TC fyp = TC(-0.25) * (tv[I(i, j + 1)] - q0), fym = TC(-0.25) * (q0 - tv[I(i, j - 1)]);
       const TC ddx = sxp * fxp - sxm * fxm;
       const TC ddy = syp * fyp - sym * fym;
-      if constexpr (MIX) out[at] = y[at] - (TS)(ddx + ddy);
-      else out[at] = q0 - (ddx + ddy);
+      if constexpr (MIX) {
+        const TC d = ddx + ddy;
+        if (d != TC(0)) y[at] = y[at] - (TS)d;
+      } else {
+        y[at] = q0 - (ddx + ddy);
+      }
     }
     __syncthreads();
   }
 }
 
-// Copies the interiors (nvar x vs values) of every active block from `from`
-// to `to`, 16-byte vectors (vs is a multiple of 4, slot bases are 16-byte
-// aligned).
-template <typename TS>
-__global__ void k_copy_active(PoolView pv, const TS* __restrict__ from, TS* __restrict__ to) {
+// Copies the interiors (nvar x vs values) of every active block from the state
+// y to `to` in the stage type (the filter's source when it runs outside a step).
+template <typename TS, typename TC>
+__global__ void k_state_copy(PoolView pv, const TS* __restrict__ y, TC* __restrict__ to) {
   pdl_enter();
-  using V = std::conditional_t<sizeof(TS) == 8, double2, float4>;
-  constexpr int E = 16 / sizeof(TS);
   const int nact = pv.cnt->n_act;
-  const int64_t per = (int64_t)pv.nvar * pv.vs / E;
+  const int64_t per = (int64_t)pv.nvar * pv.vs;
   const int64_t n = (int64_t)nact * per;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const int p = (int)(k / per);
-    const int64_t o = k - (int64_t)p * per;
-    const int64_t at = (int64_t)pv.act[p] * pv.nvar * pv.vs / E + o;
-    reinterpret_cast<V*>(to)[at] = reinterpret_cast<const V*>(from)[at];
+    const int64_t at = (int64_t)pv.act[p] * per + (k - (int64_t)p * per);
+    to[at] = (TC)y[at];
   }
 }
 
