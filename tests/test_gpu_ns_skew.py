@@ -174,3 +174,42 @@ def test_filter_properties_at_full_size(mr):
             for v in range(4):
                 assert np.abs(d[:, v]).sum() > 1e-3
                 assert abs(d[:, v].sum()) <= 1e-12 * np.abs(f0[:, v, :16, :16]).sum(), v
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_skew_fp32_acc64_with_filter_on_adaptive_tree(mr, oracle_mod, seed):
+    # the benchmarked form (FP32 stages and filter, FP64 state) on a random graded
+    # tree with coarse-fine interfaces: two RK steps each followed by the filter,
+    # then a synchronisation on both sides (block-edge nodes owned by a finer
+    # block take the owner's value); relative L2 per variable group <= 1e-5
+    leaves = sorted(treegen.random_graded_tree(2, 2, 5, 6, seed))
+    lvl, crd = treegen.as_arrays(leaves)
+    c = dsl_cfg("ns_skew", Jmin=2, Jmax=5)
+    c["ic"] = "none"
+    o, g = make(mr, oracle_mod, c, precision="fp32_acc64", detail_fp64=True)
+    N = 16 << 5
+    f = np.zeros((len(leaves), 4, 17, 17))
+    for q in range(len(leaves)):
+        s = 1 << (5 - lvl[q])
+        n = (crd[q, 0] * 16 + np.arange(17)) * s
+        m = (crd[q, 1] * 16 + np.arange(17)) * s
+        Nn, Mm = np.meshgrid(n, m)
+        r, u, v, p = shock_like(Nn, Mm, N, w=4.0 / N)
+        f[q] = state("ns_skew", 1.0 + 0 * r + 0.3 * (r - 1.0), 0.3 * u, 0.3 * v, 2.0 + 0.5 * (p - 1.0))
+    o.set_blocks(lvl, crd, f)
+    g.set_blocks(lvl, crd, f)
+    dt = 0.25 * (8.0 / (16 << 5)) / 2.0
+    for s in range(2):
+        o.rk4(s * dt, dt)
+        o.filter()
+        g.rk_step(s * dt, dt)
+        g.filter()
+    o.sync()
+    g.sync_ghosts()
+    ob, gf = assert_same_tree(o, g)
+    ref = ob["fields"]
+    scale = [np.linalg.norm(ref[:, 0]), np.linalg.norm(ref[:, 1:3]), np.linalg.norm(ref[:, 1:3]),
+             np.linalg.norm(ref[:, 3])]
+    for v in range(4):
+        rel = np.linalg.norm(gf[:, v] - ref[:, v]) / scale[v]
+        assert rel < 1e-5, (v, rel)
