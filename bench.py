@@ -99,14 +99,18 @@ WORKLOADS = {
 }
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel, from one ncu capture per workload (profiles/), valid only for
-# the kernel sources it was taken on (digest below); otherwise reported as null.
-TRAFFIC_DIGEST = "2578dcc4b4eec205"
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), averaged
+# over the launches of one step (the four RK stages; the details of the
+# coarsening rounds; the filter), from an ncu capture per workload (profiles/),
+# valid only for the device sources it was taken on (digest below); otherwise
+# reported as null.
+TRAFFIC_DIGEST = "4998a210a394eeb8"
 TRAFFIC = {
-    "adv3d": ("k_stage_adv", 87.485696e6 + 14.678016e6),
-    "uniform2d": ("k_stage_adv_w", 957.044736e6 + 569.822976e6),
-    "forest": ("k_stage_adv_w", 34.798592e6 + 9.728e3),
+    "adv3d": {"stage": (36.10e6 + 99.00e6 + 98.95e6 + 60.54e6) / 4,
+              "details": (32.96e6 + 6.51e6 + 7.60e6 + 2.80e6) / 4},
+    "dsl": {"stage": (229.12e6 + 400.43e6 + 400.01e6 + 289.67e6) / 4,
+            "details": (114.32e6 + 11.19e6 + 4.95e6 + 2.66e6) / 4,
+            "filter": 71.47e6},
 }
 
 
@@ -115,7 +119,8 @@ def source_digest():
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1902_00088_gb300", "csrc")
-    for f in [os.path.join(csrc, n) for n in ("mr_device.cuh", "mr_internal.h", "mr_kernels.cuh", "mr_launch.cuh")]:
+    for f in [os.path.join(csrc, n) for n in ("mr_device.cuh", "mr_internal.h", "mr_kernels.cuh", "mr_launch.cuh",
+                                              "mr_ns.cuh")]:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -757,14 +762,15 @@ def main():
     dom = max(kern, key=lambda n: kern[n]["ms"])
     achieved = kern[dom]["achieved_gbs"]
     # DRAM bytes per launch of the dominant kernel from an ncu capture of the
-    # same device code (stage 2 launch), else null
+    # same device code, averaged over one step's launches of it, else null
     traffic, traffic_note = None, None
-    tr = TRAFFIC.get(args.workload)
-    if tr and dom == "stage" and source_digest() == TRAFFIC_DIGEST and not args.precision and not args.learned:
-        traffic = tr[1]
-        traffic_note = {"kernel": tr[0],
+    tr = TRAFFIC.get(args.workload, {}).get(dom)
+    if tr and source_digest() == TRAFFIC_DIGEST and not args.precision and not args.learned:
+        traffic = tr
+        traffic_note = {"kernel": kern[dom]["kernel"],
                         "algorithmic_bytes_per_launch": kern[dom]["bytes"] / max(1, kern[dom]["launches"]),
-                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one stage-2 launch, profiles/"}
+                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over one step's launches, "
+                                  "profiles/traffic_%s.md" % args.workload}
 
     err = None
     tnow = g.get_time() if graph else t
