@@ -308,10 +308,11 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,), bs=33):
+def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,), bs=33, uniform=False):
     """The swirl study of Sec. 3 (Fig. 4A-D as data): 33^2 blocks, blob beta 1e-2 at (0.5, 0.75), t_a 5,
     Jmin 1, CFL 0.5, plain FP64, steps replayed as CUDA graphs up to t_a; per run the error against the
-    initial field, the adapted grid's size against the uniform one and the time per step."""
+    initial field, the adapted grid's size against the uniform one and the time per step.  uniform: the
+    equidistant grid at each Jmax instead (Jmin = Jmax, one run per Jmax; Fig. 4D's comparison)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -319,10 +320,10 @@ def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,), bs=3
     import paper_1902_00088_gb300 as mr
     stream = torch.cuda.Stream()
     t_a = 5.0
-    for beta, jmax, eps in ((b, j, e) for b in betas for j in jmaxs for e in epss):
+    for beta, jmax, eps in ((b, j, e) for b in betas for j in jmaxs for e in (epss[:1] if uniform else epss)):
         # Sec. 3: phi_0 = exp(-r^2 / beta) = exp(-r^2 / (2 sigma^2)), sigma = sqrt(beta / 2)
-        tree = dict(Jmin=1, Jmax=jmax, eps=eps, ic="gauss", ic_params=(0.5, 0.75, 0.0, math.sqrt(beta / 2)),
-                    rhs_params=(t_a,))
+        tree = dict(Jmin=jmax if uniform else 1, Jmax=jmax, eps=eps, ic="gauss",
+                    ic_params=(0.5, 0.75, 0.0, math.sqrt(beta / 2)), rhs_params=(t_a,))
         g = mr.Forest(dim=2, Bs=bs, precision="fp64", rhs="swirl", trees=[tree], capacity=400_000,
                       stream=stream.cuda_stream)
         g.init_tree()
@@ -339,7 +340,8 @@ def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,), bs=3
         el = e0.elapsed_time(e1) / 1e3
         hist = g.step_history(reset=True)
         err = g.error(0, 0.0)
-        print(json.dumps(dict(study="swirl33", Bs=bs, beta=beta, Jmax=jmax, eps=eps, steps=n, l2=err["l2"], linf=err["linf"],
+        print(json.dumps(dict(study="swirl33", grid="uniform" if uniform else "adaptive", Bs=bs, beta=beta, Jmax=jmax,
+                              eps=None if uniform else eps, steps=n, l2=err["l2"], linf=err["linf"],
                               blocks_mean=float(np.mean(hist)), blocks_max=int(np.max(hist)),
                               uniform_blocks=4 ** jmax, ms_per_step=1e3 * el / (n - 1),
                               timing="CUDA events around graph replays 2..n on the context's stream")),
@@ -485,6 +487,8 @@ def main():
     ap.add_argument("--study-eps", default="1e-3,1e-4,1e-5,1e-6", help="swirl33: comma-separated eps values")
     ap.add_argument("--study-beta", default="1e-2", help="swirl33: comma-separated pulse widths beta")
     ap.add_argument("--study-bs", type=int, default=33, help="swirl33: block size (the paper's study uses 33)")
+    ap.add_argument("--study-uniform", action="store_true",
+                    help="swirl33: equidistant grids at each Jmax instead of adaptive ones (Fig. 4D comparison)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--spinup", type=int, default=-1,
                     help="untimed steps after init before warm-up (default per workload)")
@@ -529,7 +533,8 @@ def main():
         if rank == 0:
             swirl_study(jmaxs=[int(x) for x in args.study_jmax.split(",")],
                         epss=[float(x) for x in args.study_eps.split(",")],
-                        betas=[float(x) for x in args.study_beta.split(",")], bs=args.study_bs)
+                        betas=[float(x) for x in args.study_beta.split(",")], bs=args.study_bs,
+                        uniform=args.study_uniform)
         return
 
     import numpy as np

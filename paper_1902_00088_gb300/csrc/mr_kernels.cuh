@@ -809,6 +809,29 @@ __device__ __forceinline__ void block_max2(A& a, Bt& b, A* ra, Bt* rb) {
   }
 }
 
+// Maxima of a, b and c over the CTA in one reduction (one value per warp in
+// ra / rb / rc); every thread gets the results.
+template <typename A, typename Bt, typename Ct>
+__device__ __forceinline__ void block_max3(A& a, Bt& b, Ct& c, A* ra, Bt* rb, Ct* rc) {
+  for (int s = 16; s > 0; s >>= 1) {
+    a = fmax(a, (A)__shfl_xor_sync(0xffffffffu, a, s));
+    b = fmax(b, (Bt)__shfl_xor_sync(0xffffffffu, b, s));
+    c = fmax(c, (Ct)__shfl_xor_sync(0xffffffffu, c, s));
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x >> 5] = a;
+    rb[threadIdx.x >> 5] = b;
+    rc[threadIdx.x >> 5] = c;
+  }
+  __syncthreads();
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    a = fmax(a, ra[w]);
+    b = fmax(b, rb[w]);
+    c = fmax(c, rc[w]);
+  }
+}
+
 // 2D detail index tables (per CTA, shared memory): the x pass on coarse rows
 // yc in [-1, NC - 2] (entry (yc + 1) B + x: tile index of its first source node,
 // x odd = 4 sources two nodes apart) and the odd interior points in row-major
@@ -1012,23 +1035,37 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     __syncthreads();
     // Block maximum of |d| over the interior with arithmetic type A: x pass on
     // coarse rows (yc, zc) in [-1, NC-2] into X, then y (and z) per odd node.
-    auto pass = [&](auto tag, const TT* tv) -> decltype(tag) {
+    // 3D with EX: the same sweeps also give the interior's largest |value| and
+    // non-finite test (ex_mq, bad; the z sweep reads every interior node) and
+    // the coarse lattice's largest |value| (ex_mt; the x sweep reads every
+    // coarse node of the tile), reduced with the detail maximum in one step.
+    TT ex_mq = TT(0);
+    float ex_mt = 0.f;
+    bool bad = false;
+    auto pass = [&](auto tag, const TT* tv, auto exc) -> decltype(tag) {
       using A = decltype(tag);
+      constexpr bool EX = decltype(exc)::value;
       A* XA = reinterpret_cast<A*>(X);
       if constexpr (D == 2) {
         const A md = DetTab<B>::template max_detail<A>(xtab, otab, tv, XA, CtaGroup{});
         return block_max<A>(md, reinterpret_cast<A*>(red[0]));
       }
+      float mt = 0.f;
       for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
         const int x = idx % B, yc = (idx / B) % DG::NC - 1, zc = D == 3 ? idx / (B * DG::NC) - 1 : 0;
         const int yy = 2 * yc, zz = 2 * zc;
         A val;
         if ((x & 1) == 0) {
-          val = (A)tv[Bx::tix(x, yy, zz)];
+          const TT t = tv[Bx::tix(x, yy, zz)];
+          if constexpr (EX) mt = fmaxf(mt, fabsf((float)t));
+          val = (A)t;
         } else {
           const int n0 = (x - 1) / 2;
-          val = dd4((A)tv[Bx::tix(2 * n0 - 2, yy, zz)], (A)tv[Bx::tix(2 * n0, yy, zz)],
-                    (A)tv[Bx::tix(2 * n0 + 2, yy, zz)], (A)tv[Bx::tix(2 * n0 + 4, yy, zz)]);
+          const TT t0 = tv[Bx::tix(2 * n0 - 2, yy, zz)], t1 = tv[Bx::tix(2 * n0, yy, zz)],
+                   t2 = tv[Bx::tix(2 * n0 + 2, yy, zz)], t3 = tv[Bx::tix(2 * n0 + 4, yy, zz)];
+          if constexpr (EX)
+            mt = fmaxf(fmaxf(mt, fmaxf(fabsf((float)t0), fabsf((float)t1))), fmaxf(fabsf((float)t2), fabsf((float)t3)));
+          val = dd4((A)t0, (A)t1, (A)t2, (A)t3);
         }
         XA[idx] = val;
       }
@@ -1053,10 +1090,16 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         else return ypass(i, j, zc);
       };
       A md = A(0);  // a maximum of A values: exact in A
+      TT mq = TT(0);
       for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
         const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
+        const TT tq = tv[Bx::tix(i, j, k)];
+        if constexpr (EX) {
+          mq = fmax(mq, (TT)fabs(tq));
+          bad |= !isfinite(tq);
+        }
         if (((i | j | k) & 1) == 0) continue;
-        const A val = (A)tv[Bx::tix(i, j, k)];
+        const A val = (A)tq;
         A pr;
         if (D == 2) {
           pr = ypass(i, j, 0);
@@ -1069,11 +1112,51 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         const A d = val - pr;
         md = fmax(md, (A)fabs(d));
       }
+      if constexpr (EX) {
+        block_max3<A, TT, float>(md, mq, mt, reinterpret_cast<A*>(red[0]), reinterpret_cast<TT*>(red[1]),
+                                 reinterpret_cast<float*>(red[1]) + 32);
+        ex_mq = mq;
+        ex_mt = mt;
+        return md;
+      }
       return block_max<A>(md, reinterpret_cast<A*>(red[0]));
     };
-    bool bad = false;
     for (int v = 0; v < nv; ++v) {
       const TT* tv = tile + v * Bx::TILE;
+      constexpr bool cert = sizeof(TT) == 4 && sizeof(TD) == 8;
+      if constexpr (D == 3) {
+        // one x sweep and one z sweep give the detail maximum, the interior's
+        // largest |value|, the non-finite test and (certified FP32 decision)
+        // the largest |value| the evaluation reads
+        using A0 = std::conditional_t<cert, float, TD>;
+        const A0 m0 = pass(A0(0), tv, std::true_type{});
+        const TT mqt = ex_mq;
+        double md = 0.0;  // thread 0's value is stored
+        if constexpr (cert) {
+          // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
+          // one by at most ~20 u max|tile| (u = 2^-24, x/y/z passes of the
+          // 4-point rule and the subtraction); where its maximum is farther than
+          // 32 u max|tile| from eps the threshold decision (Sec. 2.3) is the
+          // FP64 one, otherwise the block is evaluated again in FP64.
+          const float mt = fmaxf(ex_mt, (float)mqt);
+          const float E = 0x1p-19f * mt + 1e-37f;
+          if (pv.norm_kind == 0 && certain_vs_eps(m0, E, td)) {
+            if (threadIdx.x == 0) md = (double)m0;
+          } else {
+            md = pass(double(0), tv, std::false_type{});
+          }
+        } else {
+          md = (double)m0;
+        }
+        if (threadIdx.x == 0) {
+          const double mq = (double)mqt;
+          pv.md[(int64_t)b.slot * nv + v] = md;
+          pv.bmax[(int64_t)b.slot * nv + v] = mq;
+          if (pv.norm_kind == 1) csv[v] = fmax(csv[v], mq);
+        }
+        __syncthreads();
+        continue;
+      }
       // one sweep over the interior: largest |value| (a maximum of stored
       // values, exact in their type) and non-finite values (NaN detection:
       // any makes the block norm NaN); for the certified FP32 decision also
@@ -1085,7 +1168,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         mqs = fmax(mqs, (TT)fabs(val));
         bad |= !isfinite(val);
       }
-      constexpr bool cert = sizeof(TT) == 4 && sizeof(TD) == 8;
       // the values the evaluation reads: the interior (mqs) and the coarse
       // lattice (even nodes) of the ghost layer
       float mt = 0.f;
@@ -1108,15 +1190,15 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         // 4-point rule and the subtraction); where its maximum is farther than
         // 32 u max|tile| from eps the threshold decision (Sec. 2.3) is the
         // FP64 one, otherwise the block is evaluated again in FP64.
-        const float m32 = pass(float(0), tv);
+        const float m32 = pass(float(0), tv, std::false_type{});
         const float E = 0x1p-19f * mt + 1e-37f;
         if (pv.norm_kind == 0 && certain_vs_eps(m32, E, td)) {
           if (threadIdx.x == 0) md = (double)m32;
         } else {
-          md = pass(double(0), tv);
+          md = pass(double(0), tv, std::false_type{});
         }
       } else {
-        md = (double)pass(TD(0), tv);
+        md = (double)pass(TD(0), tv, std::false_type{});
       }
       if (threadIdx.x == 0) {
         const double mq = (double)mqt;
