@@ -104,13 +104,13 @@ WORKLOADS = {
 # coarsening rounds; the filter), from an ncu capture per workload (profiles/),
 # valid only for the device sources it was taken on (digest below); otherwise
 # reported as null.
-TRAFFIC_DIGEST = "4998a210a394eeb8"
+TRAFFIC_DIGEST = "02a2bae73e68443b"
 TRAFFIC = {
-    "adv3d": {"stage": (36.10e6 + 99.00e6 + 98.95e6 + 60.54e6) / 4,
-              "details": (32.96e6 + 6.51e6 + 7.60e6 + 2.80e6) / 4},
-    "dsl": {"stage": (229.12e6 + 400.43e6 + 400.01e6 + 289.67e6) / 4,
-            "details": (114.32e6 + 11.19e6 + 4.95e6 + 2.66e6) / 4,
-            "filter": 71.47e6},
+    "adv3d": {"stage": (36.55e6 + 99.43e6 + 99.44e6 + 60.67e6) / 4,
+              "details": (32.93e6 + 6.51e6 + 7.59e6 + 2.80e6) / 4},
+    "dsl": {"stage": (228.41e6 + 399.50e6 + 399.15e6 + 289.59e6) / 4,
+            "details": (114.31e6 + 11.19e6 + 4.95e6 + 2.66e6) / 4,
+            "filter": 71.64e6},
 }
 
 
@@ -349,6 +349,74 @@ def swirl_study(jmaxs=(4, 5), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2,), bs=3
         del g
 
 
+def swirl_half_study(jmaxs=(5, 6), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2, 1e-4), bs=33, jref=7,
+                     uniform_jmaxs=(4, 5, 6)):
+    """Fig. 4D of Sec. 3 as data: error at t_a / 2 (the swirl's largest deformation) against a reference, for
+    adaptive grids (Jmin 1, Jmax, eps) and equidistant ones (Jmin = Jmax), with the GPU time to get there.
+    The paper's reference is pseudo-spectral; here it is the equidistant grid at level jref (4th order in
+    space and time, far finer than the runs compared).  Errors over the unique nodes of each run, relative,
+    L2 weighted by dx^2 and Linf; plain FP64, CFL 0.5 at each run's finest level, steps as graph replays."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_00088_gb300 as mr
+    stream = torch.cuda.Stream()
+    t_a = 5.0
+
+    def run(beta, jmin, jmax, eps):
+        tree = dict(Jmin=jmin, Jmax=jmax, eps=eps, ic="gauss", ic_params=(0.5, 0.75, 0.0, math.sqrt(beta / 2)),
+                    rhs_params=(t_a,))
+        g = mr.Forest(dim=2, Bs=bs, precision="fp64", rhs="swirl", trees=[tree], capacity=400_000,
+                      stream=stream.cuda_stream)
+        g.init_tree()
+        n = int(math.ceil(t_a / (0.5 / ((bs - 1) * (1 << jmax)))))
+        n += n % 2  # t_a / 2 after n / 2 steps
+        g.set_time(0.0, t_a / n)
+        g.step_graph(1)  # captures the step graph (untimed)
+        g.step_history(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step_graph(n // 2 - 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hist = g.step_history(reset=True)
+        info, f = g.get_blocks()
+        del g
+        return n // 2, e0.elapsed_time(e1) / (n // 2 - 1), float(np.mean(hist)), info, f
+
+    for beta in betas:
+        _, ref_ms, _, info, f = run(beta, jref, jref, 1e-3)
+        ref = uniform_field(info, f, bs, jref)[0]
+        Nr = ref.shape[0]
+        cases = [("uniform", j, j, None) for j in uniform_jmaxs] + [("adaptive", 1, j, e) for j in jmaxs for e in epss]
+        for kind, jmin, jmax, eps in cases:
+            steps, ms, bmean, info, f = run(beta, jmin, jmax, eps if eps else 1e-3)
+            e2 = r2 = 0.0
+            ei = ri = 0.0
+            for lv in np.unique(info["level"]):
+                sel = info["level"] == lv
+                sc = 1 << (jref - int(lv))
+                ii = np.arange(bs - 1)
+                cx = info["coords"][sel, 0].astype(np.int64)
+                cy = info["coords"][sel, 1].astype(np.int64)
+                X = ((cx[:, None] * (bs - 1) + ii[None, :]) * sc) % Nr
+                Y = ((cy[:, None] * (bs - 1) + ii[None, :]) * sc) % Nr
+                rv = ref[Y[:, :, None], X[:, None, :]]
+                d = f[sel, 0, : bs - 1, : bs - 1] - rv
+                w = (1.0 / ((bs - 1) << int(lv))) ** 2
+                e2 += w * float((d * d).sum())
+                r2 += w * float((rv * rv).sum())
+                ei = max(ei, float(np.abs(d).max()))
+                ri = max(ri, float(np.abs(rv).max()))
+            print(json.dumps(dict(study="swirl33_half", grid=kind, Bs=bs, beta=beta, Jmax=jmax, eps=eps,
+                                  steps=steps, l2=math.sqrt(e2 / r2), linf=ei / ri, blocks_mean=bmean,
+                                  ms_per_step=ms, gpu_s=ms * steps / 1e3, reference="equidistant level %d" % jref,
+                                  timing="CUDA events around graph replays 2..n/2 on the context's stream")),
+                  flush=True)
+
+
 def uniform_field(info, f, Bs, J):
     """Blocks all at level J -> the periodic node grid (n_var, N, N), N = (Bs-1) 2^J
     (each block's last node per axis is its neighbour's first and is dropped)."""
@@ -478,7 +546,7 @@ def main():
     ap.add_argument("--eager", action="store_true", help="host-driven steps instead of CUDA graph replays")
     ap.add_argument("--autotune", type=int, default=-1, help="steps per autotuner candidate (0 = off)")
     ap.add_argument("--overlap", action="store_true", help="programmatic dependent launch of the step's kernels")
-    ap.add_argument("--study", default="", choices=["", "swirl33", "dsl"],
+    ap.add_argument("--study", default="", choices=["", "swirl33", "swirl33_half", "dsl"],
                     help="instead of the benchmark: the paper's swirl study (33^2 blocks, eps x Jmax) or its double "
                          "shear layer (compression over time, energy spectra at t = 4), one JSON line per run")
     ap.add_argument("--study-t", type=float, default=4.0, help="dsl: end time")
@@ -528,6 +596,12 @@ def main():
             dsl_study(jmaxs=jm, fixed=[int(x) for x in args.study_fixed.split(",") if x],
                       eps=float(args.study_eps.split(",")[0]) if args.study_eps != "1e-3,1e-4,1e-5,1e-6" else 1e-3,
                       bs=args.study_bs if args.study_bs != 33 else 17, t_end=args.study_t)
+        return
+    if args.study == "swirl33_half":
+        if rank == 0:
+            swirl_half_study(jmaxs=[int(x) for x in args.study_jmax.split(",")],
+                             epss=[float(x) for x in args.study_eps.split(",")],
+                             betas=[float(x) for x in args.study_beta.split(",")], bs=args.study_bs)
         return
     if args.study:
         if rank == 0:

@@ -8,7 +8,7 @@ namespace mr {
 template <int B, typename TS, typename TY>
 static void stage_nss_impl(const PoolView& pv, const Fields& f, int stage, const StageArgs& sa,
                            const LaunchCfg& lc, cudaStream_t st) {
-  constexpr int threads = 256;
+  constexpr int threads = NssCfg<B>::NT;
   constexpr size_t smem = nss_smem<B, TY>();
   // stage s reads y, Ya, Yb, Ya and writes Ya, Yb, Ya, (Yb: the new state's copy for the filter)
   TY* ynext = (TY*)(stage == 1 || stage == 3 ? f.Yb : f.Ya);
@@ -43,7 +43,7 @@ template void launch_stage_nss<33>(const PoolView&, const Fields&, int, const St
 
 template <int B, typename TS, typename TC, int KIND>
 static void filter_impl(const PoolView& pv, const Fields& f, bool copy, const LaunchCfg& lc, cudaStream_t st) {
-  constexpr int threads = 256;
+  constexpr int threads = kFilterThreads;
   constexpr size_t smem = filter_smem<B, TC>();
   if (copy) {
     launch_k(lc.pdl, k_state_copy<TS, TC>, lc.num_sms * 8, 256, 0, st, pv, (const TS*)f.y, (TC*)f.Yb);
