@@ -104,7 +104,7 @@ WORKLOADS = {
 # coarsening rounds; the filter), from an ncu capture per workload (profiles/),
 # valid only for the device sources it was taken on (digest below); otherwise
 # reported as null.
-TRAFFIC_DIGEST = "02a2bae73e68443b"
+TRAFFIC_DIGEST = "3d3dd8560bf1794f"
 TRAFFIC = {
     "adv3d": {"stage": (36.55e6 + 99.43e6 + 99.44e6 + 60.67e6) / 4,
               "details": (32.93e6 + 6.51e6 + 7.59e6 + 2.80e6) / 4},
@@ -115,15 +115,18 @@ TRAFFIC = {
 
 
 def source_digest():
-    """Digest of the device code (kernels, device helpers, launch configuration)."""
+    """Digest of the device code (kernels, device helpers, launch configuration), without its
+    comments and blank lines (an edited comment does not change a kernel)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1902_00088_gb300", "csrc")
     for f in [os.path.join(csrc, n) for n in ("mr_device.cuh", "mr_internal.h", "mr_kernels.cuh", "mr_launch.cuh",
                                               "mr_ns.cuh")]:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f) as fh:
+            code = [re.sub(r"//.*", "", l).rstrip() for l in fh]
+        h.update("\n".join(l for l in code if l).encode())
     return h.hexdigest()[:16]
 
 

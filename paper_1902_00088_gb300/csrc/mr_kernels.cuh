@@ -468,7 +468,9 @@ __global__ void k_round_begin(PoolView pv, double v) {
 //   kap = mu gamma / ((gamma - 1) Pr)  (R_s cancels in the heat flux),
 // every derivative the 4th-order central D1.  Primitives on the whole tile,
 // gradients and fluxes on nodes -2..B+1, flux divergence on the interior; the
-// RK4 update is the same 3-register form as for advection, on 4 variables.
+// RK4 update is the same 3-register form as for advection, on 4 variables
+// (with StageArgs::copy_state the last stage also stores the new state in the
+// stage type into ynext, the shock filter's source).
 template <int B>
 struct NsGeo {
   static constexpr int NF = (B + 4) * B;  // F on i in [-2, B+1], j in [0, B-1]

@@ -20,7 +20,9 @@ namespace mr {
 // The stresses and kap D th are formed on the arms of the interior that their
 // second derivative reads (x-arm: i in [-2, B+1] on rows 0..B-1; y-arm: the
 // transpose), then every interior node evaluates its four rates at once and
-// applies the 3-register RK update of the advection stage.
+// applies the 3-register RK update of the advection stage; with
+// StageArgs::copy_state the last stage also stores the new state in the stage
+// type into ynext (the shock filter's source).
 template <int B>
 struct NssGeo {
   static constexpr int NX = (B + 4) * B;  // x-arm
