@@ -33,7 +33,7 @@ struct mr_ctx_s {
   int64_t S = 0, vs = 0, ntab = 0, ncells = 0, nlat = 0, nscan = 0;
   size_t ts = 8, ty = 8;  // bytes of state / stage types
   // device memory
-  void* y = nullptr; void* acc = nullptr; void* Ya = nullptr; void* Yb = nullptr;
+  void* y = nullptr; void* acc = nullptr; void* Ya = nullptr; void* Yb = nullptr; void* Yn = nullptr;
   int8_t *lvl = nullptr, *f1 = nullptr, *flag = nullptr, *mask = nullptr;
   int16_t* tree = nullptr;
   int32_t* stamp = nullptr;
@@ -132,7 +132,7 @@ PoolView view(mr_ctx c) {
   v.regs = c->regs;
   return v;
 }
-Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb}; }
+Fields fields(mr_ctx c) { return Fields{c->y, c->acc, c->Ya, c->Yb, c->Yn}; }
 
 
 // RHS-derived per-tree constants (creation and mr_set_rhs).
@@ -718,6 +718,8 @@ mr_status mr_create(const mr_params* p, const mr_tree_desc* trees, mr_ctx* out) 
     if ((e = dalloc(ctx, (char**)&ctx->acc, S * nv * ctx->vs * ctx->ts))) return e;
     if ((e = dalloc(ctx, (char**)&ctx->Ya, S * nv * ctx->vs * ctx->ty))) return e;
     if ((e = dalloc(ctx, (char**)&ctx->Yb, S * nv * ctx->vs * ctx->ty))) return e;
+    if (P.precision == MR_PREC_FP32_ACC64 && is_ns(P.rhs_kind))
+      if ((e = dalloc(ctx, (char**)&ctx->Yn, S * nv * ctx->vs * ctx->ty))) return e;
     if ((e = dalloc(ctx, &ctx->lvl, S))) return e;
     if ((e = dalloc(ctx, &ctx->f1, S))) return e;
     if ((e = dalloc(ctx, &ctx->flag, S))) return e;

@@ -142,12 +142,15 @@ struct PoolView {
 // ---------------------------------------------------------------- launchers --
 // Fields are passed as void* and interpreted by prec: y and acc hold the state
 // type (double for FP64 / FP32_ACC64, float for FP32), Ya/Yb the stage type
-// (double for FP64, float otherwise).
+// (double for FP64, float otherwise).  Yn (Navier-Stokes with FP32 stages and
+// an FP64 state only, else null): y_n rounded to the stage type, written by the
+// first RK stage and read by the next two instead of the FP64 state.
 struct Fields {
   void* y;
   void* acc;
   void* Ya;
   void* Yb;
+  void* Yn;
 };
 
 // Control of the coarsening rounds, folded into the kernel that ends a round:

@@ -480,7 +480,8 @@ struct NsGeo {
 template <int B, typename TS, typename TY, typename TSRC>
 __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __restrict__ src,
                                                   TS* __restrict__ y, TS* __restrict__ acc,
-                                                  TY* __restrict__ ynext, int stage, StageArgs sa) {
+                                                  TY* __restrict__ ynext, TY* __restrict__ yn, int stage,
+                                                  StageArgs sa) {
   pdl_enter();
   using Gm = Geo<2, B>;
   using NG = NsGeo<B>;
@@ -585,18 +586,33 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
     const int64_t base = (int64_t)b.slot * 4 * pv.vs;
     const TS cas = cs.ca, cys = cs.cy;  // RK weights in the state type
     const TC casf = cf.ca, cysf = cf.cy;  // and in the stage type
-    // UC points per thread at a time: state and accumulator loads first
+    // UC points per thread at a time: state and accumulator loads first.  With
+    // an FP64 state and FP32 stages the next stage field needs y_n only in FP32:
+    // stage 0 takes it from the tile (the committed state, rounded) and keeps
+    // it in yn for stages 1 and 2, which then read no FP64 state.
+    constexpr bool MIX = sizeof(TS) == 8 && sizeof(TC) == 4;
     constexpr int UC = 4, NT = 256;
     for (int i0 = threadIdx.x; i0 < 4 * Gm::NI; i0 += UC * NT) {
       TS yv[UC], av[UC];
+      TC yf[UC];
 #pragma unroll
       for (int u = 0; u < UC; ++u) {
         const int idx = i0 + u * NT;
         yv[u] = av[u] = TS(0);
+        yf[u] = TC(0);
         if (idx >= 4 * Gm::NI) continue;
-        const int64_t at = base + (int64_t)(idx / Gm::NI) * pv.vs + idx % Gm::NI;
-        if (stage <= 2) yv[u] = y[at];
+        const int v = idx / Gm::NI, q = idx % Gm::NI;
+        const int64_t at = base + (int64_t)v * pv.vs + q;
+        if (stage == 0 || (!MIX && stage <= 2)) yv[u] = y[at];
         if (stage >= 1) av[u] = acc[at];
+        if constexpr (MIX) {
+          if (stage == 0) {
+            yf[u] = tile[v * Gm::TILE + I(q % B, q / B)];
+            yn[at] = yf[u];
+          } else if (stage <= 2) {
+            yf[u] = yn[at];
+          }
+        }
       }
 #pragma unroll
       for (int u = 0; u < UC; ++u) {
@@ -617,10 +633,10 @@ __global__ void __launch_bounds__(256) k_stage_ns(PoolView pv, const TSRC* __res
           const TC kc = -(dFx + dGy);
           if (stage == 0) {
             acc[at] = yv[u] + (TS)(casf * kc);
-            ynext[at] = (TY)((TC)yv[u] + cysf * kc);
+            ynext[at] = (TY)(yf[u] + cysf * kc);
           } else if (stage == 1 || stage == 2) {
             acc[at] = av[u] + (TS)(casf * kc);
-            ynext[at] = (TY)((TC)yv[u] + cysf * kc);
+            ynext[at] = (TY)(yf[u] + cysf * kc);
           } else {
             const TS yn = av[u] + (TS)(casf * kc);
             y[at] = yn;

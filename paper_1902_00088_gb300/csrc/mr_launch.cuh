@@ -121,12 +121,12 @@ static void stage_ns_impl(const PoolView& pv, const Fields& f, int stage, const 
   if (stage == 0) {
     auto k = k_stage_ns<B, TS, TY, TS>;
     prep_smem(k, smem);
-    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, (const TS*)f.y, (TS*)f.y, (TS*)f.acc, ynext, (TY*)f.Yn, stage, sa);
   } else {
     const TY* src = (const TY*)(stage == 2 ? f.Yb : f.Ya);
     auto k = k_stage_ns<B, TS, TY, TY>;
     prep_smem(k, smem);
-    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, stage, sa);
+    launch_k(lc.pdl, k, persistent_grid(k, threads, smem, lc, lc.grid_mult), threads, smem, st, pv, src, (TS*)f.y, (TS*)f.acc, ynext, (TY*)f.Yn, stage, sa);
   }
   count_launch();
 }

@@ -49,7 +49,8 @@ constexpr size_t nss_smem() {
 template <int B, typename TS, typename TY, typename TSRC>
 __global__ void __launch_bounds__(NssCfg<B>::NT, NssCfg<B>::MINB) k_stage_nss(PoolView pv, const TSRC* __restrict__ src,
                                                    TS* __restrict__ y, TS* __restrict__ acc,
-                                                   TY* __restrict__ ynext, int stage, StageArgs sa) {
+                                                   TY* __restrict__ ynext, TY* __restrict__ yn, int stage,
+                                                   StageArgs sa) {
   pdl_enter();
   using Gm = Geo<2, B>;
   using NG = NssGeo<B>;
@@ -152,17 +153,31 @@ __global__ void __launch_bounds__(NssCfg<B>::NT, NssCfg<B>::MINB) k_stage_nss(Po
     const StageCoef<TS> cs(pv, sa, b.tree, stage);
     const StageCoef<TC> cf(pv, sa, b.tree, stage);
     const int64_t base = (int64_t)b.slot * 4 * pv.vs;
+    constexpr bool MIX = sizeof(TS) == 8 && sizeof(TC) == 4;
     for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
       const int i = q % B, j = q / B;
+      const int t0 = I(i, j);
+      // FP64 state, FP32 stages: the next stage field needs y_n only in FP32;
+      // stage 0 takes it from the tile (the committed state, rounded) and keeps
+      // it in yn for stages 1 and 2, which then read no FP64 state
       TS yv[4], av[4];
+      TC yf[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int64_t at = base + (int64_t)v * pv.vs + q;
-        yv[v] = stage <= 2 ? y[at] : TS(0);
+        yv[v] = (stage == 0 || (!MIX && stage <= 2)) ? y[at] : TS(0);
         av[v] = stage >= 1 ? acc[at] : TS(0);
+        if constexpr (MIX) {
+          if (stage == 0) yf[v] = tile[v * Gm::TILE + t0];
+          else if (stage <= 2) yf[v] = yn[at];
+        }
       }
-      const int t0 = I(i, j);
       const TC uu = pu[t0], vv = pw[t0], f = ph[t0];
+      if constexpr (MIX) {
+        if (stage == 0)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) yn[base + (int64_t)v * pv.vs + q] = yf[v];
+      }
       const TC phx = dx(ph, i, j), phy = dy(ph, i, j);
       const TC sxx = dx(sx, i, j), sxy = dy(sx, i, j), syx = dx(sy, i, j), syy = dy(sy, i, j);
       const TC px = dx(pr, i, j), py = dy(pr, i, j);
@@ -189,10 +204,10 @@ __global__ void __launch_bounds__(NssCfg<B>::NT, NssCfg<B>::MINB) k_stage_nss(Po
           const TC kc = k[v];
           if (stage == 0) {
             acc[at] = yv[v] + (TS)(cf.ca * kc);
-            ynext[at] = (TY)((TC)yv[v] + cf.cy * kc);
+            ynext[at] = (TY)(yf[v] + cf.cy * kc);
           } else if (stage == 1 || stage == 2) {
             acc[at] = av[v] + (TS)(cf.ca * kc);
-            ynext[at] = (TY)((TC)yv[v] + cf.cy * kc);
+            ynext[at] = (TY)(yf[v] + cf.cy * kc);
           } else {
             const TS yn = av[v] + (TS)(cf.ca * kc);
             y[at] = yn;
