@@ -392,32 +392,40 @@ def swirl_half_study(jmaxs=(5, 6), epss=(1e-3, 1e-4, 1e-5, 1e-6), betas=(1e-2, 1
     for beta in betas:
         _, ref_ms, _, info, f = run(beta, jref, jref, 1e-3)
         ref = uniform_field(info, f, bs, jref)[0]
-        Nr = ref.shape[0]
         cases = [("uniform", j, j, None) for j in uniform_jmaxs] + [("adaptive", 1, j, e) for j in jmaxs for e in epss]
         for kind, jmin, jmax, eps in cases:
             steps, ms, bmean, info, f = run(beta, jmin, jmax, eps if eps else 1e-3)
-            e2 = r2 = 0.0
-            ei = ri = 0.0
-            for lv in np.unique(info["level"]):
-                sel = info["level"] == lv
-                sc = 1 << (jref - int(lv))
-                ii = np.arange(bs - 1)
-                cx = info["coords"][sel, 0].astype(np.int64)
-                cy = info["coords"][sel, 1].astype(np.int64)
-                X = ((cx[:, None] * (bs - 1) + ii[None, :]) * sc) % Nr
-                Y = ((cy[:, None] * (bs - 1) + ii[None, :]) * sc) % Nr
-                rv = ref[Y[:, :, None], X[:, None, :]]
-                d = f[sel, 0, : bs - 1, : bs - 1] - rv
-                w = (1.0 / ((bs - 1) << int(lv))) ** 2
-                e2 += w * float((d * d).sum())
-                r2 += w * float((rv * rv).sum())
-                ei = max(ei, float(np.abs(d).max()))
-                ri = max(ri, float(np.abs(rv).max()))
+            l2, linf = error_vs_reference(info, f[:, 0], ref, bs, jref)
             print(json.dumps(dict(study="swirl33_half", grid=kind, Bs=bs, beta=beta, Jmax=jmax, eps=eps,
-                                  steps=steps, l2=math.sqrt(e2 / r2), linf=ei / ri, blocks_mean=bmean,
+                                  steps=steps, l2=l2, linf=linf, blocks_mean=bmean,
                                   ms_per_step=ms, gpu_s=ms * steps / 1e3, reference="equidistant level %d" % jref,
                                   timing="CUDA events around graph replays 2..n/2 on the context's stream")),
                   flush=True)
+
+
+def error_vs_reference(info, f, ref, Bs, jref):
+    """Relative errors (L2 weighted by dx^2, Linf) of the blocks' field f (n x Bs x Bs, 2D) against a
+    periodic reference on the uniform node grid of level jref; each block's unique nodes (its last node per
+    axis dropped) are nodes of the reference lattice."""
+    import numpy as np
+    Nr = ref.shape[0]
+    e2 = r2 = ei = ri = 0.0
+    ii = np.arange(Bs - 1)
+    for lv in np.unique(info["level"]):
+        sel = info["level"] == lv
+        sc = 1 << (jref - int(lv))
+        cx = info["coords"][sel, 0].astype(np.int64)
+        cy = info["coords"][sel, 1].astype(np.int64)
+        X = ((cx[:, None] * (Bs - 1) + ii[None, :]) * sc) % Nr
+        Y = ((cy[:, None] * (Bs - 1) + ii[None, :]) * sc) % Nr
+        rv = ref[Y[:, :, None], X[:, None, :]]
+        d = f[sel, : Bs - 1, : Bs - 1] - rv
+        w = (1.0 / ((Bs - 1) << int(lv))) ** 2
+        e2 += w * float((d * d).sum())
+        r2 += w * float((rv * rv).sum())
+        ei = max(ei, float(np.abs(d).max()))
+        ri = max(ri, float(np.abs(rv).max()))
+    return math.sqrt(e2 / r2), ei / ri
 
 
 def uniform_field(info, f, Bs, J):

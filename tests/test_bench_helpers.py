@@ -40,3 +40,28 @@ def test_uniform_field_places_blocks():
     u = bench.uniform_field(info, f, Bs, J)
     N = (Bs - 1) * n
     assert np.array_equal(u[0], 1000 * np.arange(N)[:, None] + np.arange(N)[None, :])
+
+
+def test_error_vs_reference_on_adaptive_blocks():
+    # blocks of levels 1 and 2 sampled from the function the reference (level
+    # 3) is sampled from: zero error; a perturbation of one node of known size
+    # gives the Linf error exactly
+    Bs, jref = 5, 3
+    Nr = (Bs - 1) << jref
+    F = lambda x, y: 2.0 + np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    x = np.arange(Nr) / Nr
+    ref = F(x[None, :], x[:, None])
+    leaves = [(1, (0, 0))] + [(2, (cx, cy)) for cx in range(4) for cy in range(4) if cx >= 2 or cy >= 2]
+    info = np.zeros(len(leaves), dtype=[("level", np.int32), ("coords", np.int32, 3)])
+    f = np.zeros((len(leaves), Bs, Bs))
+    for q, (lv, (cx, cy)) in enumerate(leaves):
+        info["level"][q] = lv
+        info["coords"][q] = (cx, cy, 0)
+        xs = (cx * (Bs - 1) + np.arange(Bs)) / ((Bs - 1) << lv)
+        ys = (cy * (Bs - 1) + np.arange(Bs)) / ((Bs - 1) << lv)
+        f[q] = F(xs[None, :], ys[:, None])
+    l2, linf = bench.error_vs_reference(info, f, ref, Bs, jref)
+    assert l2 < 1e-15 and linf < 1e-15
+    f[0, 1, 2] += 0.5
+    l2, linf = bench.error_vs_reference(info, f, ref, Bs, jref)
+    assert np.isclose(linf, 0.5 / np.abs(ref).max()) and l2 > 0
