@@ -859,8 +859,8 @@ def main():
         traffic = tr
         traffic_note = {"kernel": kern[dom]["kernel"],
                         "algorithmic_bytes_per_launch": kern[dom]["bytes"] / max(1, kern[dom]["launches"]),
-                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean over one step's launches, "
-                                  "profiles/traffic_%s.md" % args.workload}
+                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the same device code, "
+                                  "mean over one step's launches of the kernel"}
 
     err = None
     tnow = g.get_time() if graph else t
