@@ -225,7 +225,16 @@ class Forest:
         self._ck(self.lib.mr_num_blocks(self.h, tree, C.byref(n)))
         return n.value
 
-    def get_blocks(self, tree=-1, fields=True):
+    def get_blocks(self, tree=-1, fields=True, out=None):
+        """Blocks in canonical order: (info, fields).  out = (info_buf, fields_buf) writes into caller
+        buffers (e.g. pinned host memory) of room for the blocks and returns views of their first n
+        entries (MR_EINVAL if they are too small)."""
+        if out is not None:
+            ib, fb = out
+            n = C.c_int64()
+            self._ck(self.lib.mr_get_blocks(self.h, tree, len(ib), C.byref(n), _ptr(ib),
+                                            _ptr(fb) if fields else None))
+            return ib[:n.value], (fb[:n.value] if fields else None)
         n0 = self.num_blocks(tree)
         info = np.zeros(n0, BLOCK_INFO_DTYPE)
         f = np.zeros((n0, self.nvar) + (self.B,) * self.dim, np.float64) if fields else None

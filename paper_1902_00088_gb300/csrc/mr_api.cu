@@ -949,18 +949,21 @@ mr_status mr_get_blocks(mr_ctx ctx, int32_t tree, int64_t cap, int64_t* n, mr_bl
   int64_t ni = 1;
   for (int a = 0; a < ctx->p.dim; ++a) ni *= ctx->p.Bs;
   const int64_t per = ctx->p.nvar * ni;
+  // stream-ordered staging (no device-wide synchronisation of cudaMalloc /
+  // cudaFree); one synchronisation after the copies to the host
   mr_block_info* dinfo = nullptr;
   double* dfld = nullptr;
-  CK(cudaMalloc(&dinfo, std::max<int64_t>(h.n_act, 1) * sizeof(mr_block_info)));
-  if (flds) CK(cudaMalloc(&dfld, std::max<int64_t>(h.n_act, 1) * per * 8));
+  CK(cudaMallocAsync((void**)&dinfo, std::max<int64_t>(h.n_act, 1) * sizeof(mr_block_info), ctx->st));
+  if (flds) CK(cudaMallocAsync((void**)&dfld, std::max<int64_t>(h.n_act, 1) * per * 8, ctx->st));
   PoolView pv = view(ctx);
   by_dim(ctx, [&] { launch_export<2>(pv, fields(ctx), dinfo, dfld, nullptr, nullptr, ctx->lc, ctx->st); },
          [&] { launch_export<3>(pv, fields(ctx), dinfo, dfld, nullptr, nullptr, ctx->lc, ctx->st); });
+  if (info) CK(cudaMemcpyAsync(info, dinfo + first, cnt * sizeof(mr_block_info), cudaMemcpyDeviceToHost, ctx->st));
+  if (flds) CK(cudaMemcpyAsync(flds, dfld + first * per, cnt * per * 8, cudaMemcpyDeviceToHost, ctx->st));
+  cudaFreeAsync(dinfo, ctx->st);
+  if (dfld) cudaFreeAsync(dfld, ctx->st);
   CK(cudaStreamSynchronize(ctx->st));
-  if (info) CK(cudaMemcpy(info, dinfo + first, cnt * sizeof(mr_block_info), cudaMemcpyDeviceToHost));
-  if (flds) CK(cudaMemcpy(flds, dfld + first * per, cnt * per * 8, cudaMemcpyDeviceToHost));
-  cudaFree(dinfo);
-  if (dfld) cudaFree(dfld);
+  CK(cudaGetLastError());
   return MR_OK;
 }
 
