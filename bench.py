@@ -104,12 +104,12 @@ WORKLOADS = {
 # coarsening rounds; the filter), from an ncu capture per workload (profiles/),
 # valid only for the device sources it was taken on (digest below); otherwise
 # reported as null.
-TRAFFIC_DIGEST = "024723491bc1e667"
+TRAFFIC_DIGEST = "2e30af00e6b6dca7"
 TRAFFIC = {
-    "adv3d": {"stage": (36.21e6 + 99.43e6 + 99.44e6 + 60.67e6) / 4,
-              "details": (32.93e6 + 6.50e6 + 7.59e6 + 2.80e6) / 4},
-    "dsl": {"stage": (279.59e6 + 337.06e6 + 336.11e6 + 289.23e6) / 4,
-            "details": (114.32e6 + 11.19e6 + 4.94e6 + 2.66e6) / 4,
+    "adv3d": {"stage": (36.01e6 + 99.01e6 + 98.98e6 + 60.53e6) / 4,
+              "details": (32.93e6 + 6.51e6 + 7.59e6 + 2.80e6) / 4},
+    "dsl": {"stage": (279.42e6 + 336.95e6 + 336.15e6 + 289.20e6) / 4,
+            "details": (113.68e6 + 11.19e6 + 4.94e6 + 2.66e6) / 4,
             "filter": 71.52e6},
 }
 

@@ -900,6 +900,45 @@ struct DetTab {
     }
     return md;
   }
+  // the same, and from the same sweeps (per thread, not reduced): the largest
+  // |value| of the interior (mq; the odd points of the second sweep and the
+  // even-even interior nodes of the first) with a non-finite test (bad), and
+  // the largest |value| of the coarse lattice the first sweep reads (mt)
+  template <typename A, typename TV, typename G>
+  __device__ static A max_detail_ex(const int32_t* xtab, const int32_t* otab, const TV* tv, A* XA, G g, TV& mq,
+                                    float& mt, bool& bad) {
+    for (int idx = g.rank(); idx < DG::NX; idx += g.size()) {
+      const int e = xtab[idx];
+      const TV* t0 = tv + (e & 0xffff);
+      if (e >> 16) {
+        const TV a = t0[0], b = t0[2], c = t0[4], d = t0[6];
+        mt = fmaxf(fmaxf(mt, fmaxf(fabsf((float)a), fabsf((float)b))), fmaxf(fabsf((float)c), fabsf((float)d)));
+        XA[idx] = dd4((A)a, (A)b, (A)c, (A)d);
+      } else {
+        const TV a = t0[0];
+        mt = fmaxf(mt, fabsf((float)a));
+        const int row = idx / B;  // coarse row + 1: interior rows 1 .. (B + 1) / 2
+        if (row >= 1 && row <= (B + 1) / 2) {
+          mq = fmax(mq, (TV)fabs(a));
+          bad |= !isfinite(a);
+        }
+        XA[idx] = (A)a;
+      }
+    }
+    g.sync();
+    A md = A(0);
+    for (int k = g.rank(); k < NODD; k += g.size()) {
+      const int e = otab[k];
+      const TV tq = tv[e & 0xfff];
+      mq = fmax(mq, (TV)fabs(tq));
+      bad |= !isfinite(tq);
+      const A val = (A)tq;
+      const A* xa = XA + ((e >> 12) & 0xfff);
+      const A pr = (e >> 24) ? dd4(xa[0], xa[B], xa[2 * B], xa[3 * B]) : xa[0];
+      md = fmax(md, (A)fabs(val - pr));
+    }
+    return md;
+  }
 };
 
 // Shared-memory layout of k_details after the ring and the tile: the coarse
@@ -1065,8 +1104,19 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
       constexpr bool EX = decltype(exc)::value;
       A* XA = reinterpret_cast<A*>(X);
       if constexpr (D == 2) {
-        const A md = DetTab<B>::template max_detail<A>(xtab, otab, tv, XA, CtaGroup{});
-        return block_max<A>(md, reinterpret_cast<A*>(red[0]));
+        if constexpr (EX) {
+          TT mq = TT(0);
+          float mt = 0.f;
+          A md = DetTab<B>::template max_detail_ex<A>(xtab, otab, tv, XA, CtaGroup{}, mq, mt, bad);
+          block_max3<A, TT, float>(md, mq, mt, reinterpret_cast<A*>(red[0]), reinterpret_cast<TT*>(red[1]),
+                                   reinterpret_cast<float*>(red[1]) + 32);
+          ex_mq = mq;
+          ex_mt = mt;
+          return md;
+        } else {
+          const A md = DetTab<B>::template max_detail<A>(xtab, otab, tv, XA, CtaGroup{});
+          return block_max<A>(md, reinterpret_cast<A*>(red[0]));
+        }
       }
       float mt = 0.f;
       for (int idx = threadIdx.x; idx < DG::NX; idx += blockDim.x) {
@@ -1142,65 +1192,14 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
     for (int v = 0; v < nv; ++v) {
       const TT* tv = tile + v * Bx::TILE;
       constexpr bool cert = sizeof(TT) == 4 && sizeof(TD) == 8;
-      if constexpr (D == 3) {
-        // one x sweep and one z sweep give the detail maximum, the interior's
-        // largest |value|, the non-finite test and (certified FP32 decision)
-        // the largest |value| the evaluation reads
-        using A0 = std::conditional_t<cert, float, TD>;
-        const A0 m0 = pass(A0(0), tv, std::true_type{});
-        const TT mqt = ex_mq;
-        double md = 0.0;  // thread 0's value is stored
-        if constexpr (cert) {
-          // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
-          // one by at most ~20 u max|tile| (u = 2^-24, x/y/z passes of the
-          // 4-point rule and the subtraction); where its maximum is farther than
-          // 32 u max|tile| from eps the threshold decision (Sec. 2.3) is the
-          // FP64 one, otherwise the block is evaluated again in FP64.
-          const float mt = fmaxf(ex_mt, (float)mqt);
-          const float E = 0x1p-19f * mt + 1e-37f;
-          if (pv.norm_kind == 0 && certain_vs_eps(m0, E, td)) {
-            if (threadIdx.x == 0) md = (double)m0;
-          } else {
-            md = pass(double(0), tv, std::false_type{});
-          }
-        } else {
-          md = (double)m0;
-        }
-        if (threadIdx.x == 0) {
-          const double mq = (double)mqt;
-          pv.md[(int64_t)b.slot * nv + v] = md;
-          pv.bmax[(int64_t)b.slot * nv + v] = mq;
-          if (pv.norm_kind == 1) csv[v] = fmax(csv[v], mq);
-        }
-        __syncthreads();
-        continue;
-      }
-      // one sweep over the interior: largest |value| (a maximum of stored
-      // values, exact in their type) and non-finite values (NaN detection:
-      // any makes the block norm NaN); for the certified FP32 decision also
-      // the largest |value| over the tile, reduced together with it
-      TT mqs = TT(0);
-      for (int q = threadIdx.x; q < Gm::NI; q += blockDim.x) {
-        const int i = q % B, j = (q / B) % B, k = D == 3 ? q / (B * B) : 0;
-        const TT val = tv[Bx::tix(i, j, k)];
-        mqs = fmax(mqs, (TT)fabs(val));
-        bad |= !isfinite(val);
-      }
-      // the values the evaluation reads: the interior (mqs) and the coarse
-      // lattice (even nodes) of the ghost layer
-      float mt = 0.f;
-      if (cert) {
-        constexpr int NCO = (B + 1) / 2 + 2;  // coarse nodes -1 .. (B + 1) / 2 per axis
-        constexpr int NCT = NCO * NCO * (D == 3 ? NCO : 1);
-        for (int q = threadIdx.x; q < NCT; q += blockDim.x) {
-          const int x = 2 * (q % NCO) - 2, yy = 2 * ((q / NCO) % NCO) - 2, zz = D == 3 ? 2 * (q / (NCO * NCO)) - 2 : 0;
-          const bool in = x >= 0 && x <= B - 1 && yy >= 0 && yy <= B - 1 && zz >= 0 && zz <= B - 1;
-          if (!in) mt = fmaxf(mt, fabsf((float)tv[Bx::tix(x, yy, zz)]));
-        }
-      }
-      TT mqt = mqs;
-      block_max2<TT, float>(mqt, mt, reinterpret_cast<TT*>(red[1]), reinterpret_cast<float*>(red[0]));
-      mt = fmaxf(mt, (float)mqt);
+      // the first pass's sweeps (x and z in 3D, x and odd points in 2D) give the
+      // detail maximum, the interior's largest |value| (exact in its type), the
+      // non-finite test (any non-finite value makes the block norm NaN) and,
+      // for the certified FP32 decision, the largest |value| the evaluation
+      // reads (interior and coarse lattice), all in one CTA reduction
+      using A0 = std::conditional_t<cert, float, TD>;
+      const A0 m0 = pass(A0(0), tv, std::true_type{});
+      const TT mqt = ex_mq;
       double md = 0.0;  // thread 0's value is stored
       if constexpr (cert) {
         // FP32 values, FP64 decision: the FP32 evaluation differs from the FP64
@@ -1208,15 +1207,15 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 8 : (D == 3 ? 3 : 4)) k_detail
         // 4-point rule and the subtraction); where its maximum is farther than
         // 32 u max|tile| from eps the threshold decision (Sec. 2.3) is the
         // FP64 one, otherwise the block is evaluated again in FP64.
-        const float m32 = pass(float(0), tv, std::false_type{});
+        const float mt = fmaxf(ex_mt, (float)mqt);
         const float E = 0x1p-19f * mt + 1e-37f;
-        if (pv.norm_kind == 0 && certain_vs_eps(m32, E, td)) {
-          if (threadIdx.x == 0) md = (double)m32;
+        if (pv.norm_kind == 0 && certain_vs_eps(m0, E, td)) {
+          if (threadIdx.x == 0) md = (double)m0;
         } else {
           md = pass(double(0), tv, std::false_type{});
         }
       } else {
-        md = (double)pass(TD(0), tv, std::false_type{});
+        md = (double)m0;
       }
       if (threadIdx.x == 0) {
         const double mq = (double)mqt;
