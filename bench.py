@@ -102,27 +102,30 @@ WORKLOADS = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), averaged
 # over the launches of one step (the four RK stages; the details of the
 # coarsening rounds; the filter), from an ncu capture per workload (profiles/),
-# valid only for the device sources it was taken on (digest below); otherwise
-# reported as null.
-TRAFFIC_DIGEST = "2e30af00e6b6dca7"
+# valid only for the device sources it was taken on (the digest in each entry);
+# otherwise reported as null.
 TRAFFIC = {
-    "adv3d": {"stage": (36.01e6 + 99.01e6 + 98.98e6 + 60.53e6) / 4,
+    # workload: {kernel: DRAM bytes per launch}, plus the digest of the device sources it was taken on
+    "adv3d": {"digest": ("DEVICE", "1001c46c9ab0dc4b"), "stage": (36.01e6 + 99.01e6 + 98.98e6 + 60.53e6) / 4,
               "details": (32.93e6 + 6.51e6 + 7.59e6 + 2.80e6) / 4},
-    "dsl": {"stage": (279.42e6 + 336.95e6 + 336.15e6 + 289.20e6) / 4,
-            "details": (113.68e6 + 11.19e6 + 4.94e6 + 2.66e6) / 4,
-            "filter": 71.52e6},
+    "dsl": {"digest": ("NS", "2a19634679daf7a6"), "stage": (279.74e6 + 336.89e6 + 336.16e6 + 289.24e6) / 4,
+            "details": (113.75e6 + 11.25e6 + 4.95e6 + 2.66e6) / 4,
+            "filter": 71.71e6},
 }
 
 
-def source_digest():
-    """Digest of the device code (kernels, device helpers, launch configuration), without its
+DEVICE_SOURCES = ("mr_device.cuh", "mr_internal.h", "mr_kernels.cuh", "mr_launch.cuh")
+NS_SOURCES = DEVICE_SOURCES + ("mr_ns.cuh",)  # the skew-symmetric stage and the shock filter
+
+
+def source_digest(names=DEVICE_SOURCES):
+    """Digest of device code (kernels, device helpers, launch configuration), without its
     comments and blank lines (an edited comment does not change a kernel)."""
     import hashlib
     import re
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1902_00088_gb300", "csrc")
-    for f in [os.path.join(csrc, n) for n in ("mr_device.cuh", "mr_internal.h", "mr_kernels.cuh", "mr_launch.cuh",
-                                              "mr_ns.cuh")]:
+    for f in [os.path.join(csrc, n) for n in names]:
         h.update(os.path.basename(f).encode())
         with open(f) as fh:
             code = [re.sub(r"//.*", "", l).rstrip() for l in fh]
@@ -854,8 +857,10 @@ def main():
     # DRAM bytes per launch of the dominant kernel from an ncu capture of the
     # same device code, averaged over one step's launches of it, else null
     traffic, traffic_note = None, None
-    tr = TRAFFIC.get(args.workload, {}).get(dom)
-    if tr and source_digest() == TRAFFIC_DIGEST and not args.precision and not args.learned:
+    twl = TRAFFIC.get(args.workload, {})
+    tr = twl.get(dom)
+    dig_ok = bool(twl) and source_digest(NS_SOURCES if twl["digest"][0] == "NS" else DEVICE_SOURCES) == twl["digest"][1]
+    if tr and dig_ok and not args.precision and not args.learned:
         traffic = tr
         traffic_note = {"kernel": kern[dom]["kernel"],
                         "algorithmic_bytes_per_launch": kern[dom]["bytes"] / max(1, kern[dom]["launches"]),

@@ -102,9 +102,17 @@ __global__ void __launch_bounds__(NssCfg<B>::NT, NssCfg<B>::MINB) k_stage_nss(Po
     const TC* pr = tile + 3 * Gm::TILE;
     for (int idx = threadIdx.x; idx < Gm::TILE; idx += blockDim.x) {
       const TC f = ph[idx];
-      pu[idx] = sx[idx] / f;
-      pw[idx] = sy[idx] / f;
-      pth[idx] = pr[idx] / (f * f);
+      if constexpr (sizeof(TC) == 4) {
+        // FP32 stages: one reciprocal instead of three divisions
+        const TC rf = TC(1) / f;
+        pu[idx] = sx[idx] * rf;
+        pw[idx] = sy[idx] * rf;
+        pth[idx] = (pr[idx] * rf) * rf;
+      } else {
+        pu[idx] = sx[idx] / f;
+        pw[idx] = sy[idx] / f;
+        pth[idx] = pr[idx] / (f * f);
+      }
     }
     __syncthreads();
     auto dx = [&](const TC* f, int i, int j) {
@@ -190,8 +198,14 @@ __global__ void __launch_bounds__(NssCfg<B>::NT, NssCfg<B>::MINB) k_stage_nss(Po
       const TC cy = (dxm(sy, pu, i, j) + uu * syx) + (dym(sy, pw, i, j) + vv * syy);
       const TC fx = px - (dxa(ax, i, j) + dya(ay, i, j));
       const TC fy = py - (dxa(ax + NG::NX, i, j) + dya(ay + NG::NY, i, j));
-      k[1] = TC(-0.5) * cx - fx / f;
-      k[2] = TC(-0.5) * cy - fy / f;
+      if constexpr (sizeof(TC) == 4) {
+        const TC rf = TC(1) / f;
+        k[1] = TC(-0.5) * cx - fx * rf;
+        k[2] = TC(-0.5) * cy - fy * rf;
+      } else {
+        k[1] = TC(-0.5) * cx - fx / f;
+        k[2] = TC(-0.5) * cy - fy / f;
+      }
       // pressure
       const TC phiv = (ax[xI(i, j)] * ux + ax[NG::NX + xI(i, j)] * (uy + vx)) + ay[NG::NY + yI(i, j)] * vy;
       const TC heat = dxa(ax + 2 * NG::NX, i, j) + dya(ay + 2 * NG::NY, i, j);
