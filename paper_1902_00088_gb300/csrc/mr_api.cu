@@ -107,6 +107,34 @@ mr_status fail(mr_ctx c, mr_status s, const std::string& msg) {
       return fail(ctx, MR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
   } while (0)
 
+// Device buffer owned by one host call, released on every return path
+// (stream-ordered when allocated on a stream).
+template <typename T>
+struct TmpBuf {
+  T* p = nullptr;
+  cudaStream_t st = nullptr;
+  bool async = false;
+  TmpBuf() = default;
+  TmpBuf(const TmpBuf&) = delete;
+  TmpBuf& operator=(const TmpBuf&) = delete;
+  ~TmpBuf() {
+    if (!p) return;
+    if (async) cudaFreeAsync(p, st);
+    else cudaFree(p);
+  }
+  cudaError_t alloc(size_t bytes) { return cudaMalloc((void**)&p, bytes); }
+  T* release() {  // hands the buffer to the caller
+    T* q = p;
+    p = nullptr;
+    return q;
+  }
+  cudaError_t alloc_on(size_t bytes, cudaStream_t s) {
+    async = true;
+    st = s;
+    return cudaMallocAsync((void**)&p, bytes, s);
+  }
+};
+
 template <typename T>
 cudaError_t dalloc(mr_ctx c, T** p, size_t n) {
   void* q = nullptr;
@@ -341,25 +369,25 @@ int64_t feat_len(mr_ctx c) {
 mr_status ensure_cnn(mr_ctx ctx) {
   if (ctx->cnn_w) return MR_OK;
   if (ctx->p.dim != 2) return fail(ctx, MR_EINVAL, "the learned proposal is 2D");
-  CK(cudaMalloc(&ctx->cnn_w, kCnnParams * 4));
-  CK(cudaMalloc(&ctx->cnn_m, kCnnParams * 4));
-  CK(cudaMalloc(&ctx->cnn_v, kCnnParams * 4));
-  CK(cudaMalloc(&ctx->cnn_g, kCnnParams * 4));
-  CK(cudaMalloc(&ctx->cnn_wb, kCnnParams * 2));
-  CK(cudaMalloc(&ctx->skip, ctx->S));
-  CK(cudaMalloc(&ctx->skip_key, ctx->S * 4));
-  CK(cudaMalloc(&ctx->pcounts, 4 * 4));
-  CK(cudaMalloc(&ctx->gcounts, 5 * 4));
+  // each buffer joins the context's owned list as it is allocated (a failed
+  // call leaks nothing); cnn_w, which marks the set complete, is assigned last
+  float* w = nullptr;
+  CK(dalloc(ctx, &ctx->cnn_m, kCnnParams));
+  CK(dalloc(ctx, &ctx->cnn_v, kCnnParams));
+  CK(dalloc(ctx, &ctx->cnn_g, kCnnParams));
+  CK(dalloc(ctx, &ctx->cnn_wb, kCnnParams));
+  CK(dalloc(ctx, &ctx->skip, ctx->S));
+  CK(dalloc(ctx, &ctx->skip_key, ctx->S));
+  CK(dalloc(ctx, &ctx->pcounts, 4));
+  CK(dalloc(ctx, &ctx->gcounts, 5));
+  CK(dalloc(ctx, &w, kCnnParams));
   CK(cudaMemset(ctx->gcounts, 0, 5 * 4));
-  CK(cudaMemset(ctx->cnn_w, 0, kCnnParams * 4));
+  CK(cudaMemset(w, 0, kCnnParams * 4));
   CK(cudaMemset(ctx->cnn_m, 0, kCnnParams * 4));
   CK(cudaMemset(ctx->cnn_v, 0, kCnnParams * 4));
   CK(cudaMemset(ctx->cnn_g, 0, kCnnParams * 4));
   CK(cudaMemset(ctx->skip, 0, ctx->S));
-  for (void* q : {(void*)ctx->cnn_w, (void*)ctx->cnn_m, (void*)ctx->cnn_v, (void*)ctx->cnn_g,
-                  (void*)ctx->cnn_wb, (void*)ctx->skip, (void*)ctx->skip_key, (void*)ctx->pcounts,
-                  (void*)ctx->gcounts})
-    ctx->owned.push_back(q);
+  ctx->cnn_w = w;
   return MR_OK;
 }
 
@@ -369,6 +397,10 @@ mr_status ensure_feat(mr_ctx ctx, int64_t n) {
   const int64_t cap = std::max<int64_t>(n, ctx->feat_cap * 2);
   CK(cudaStreamSynchronize(ctx->st));
   if (ctx->feat) { cudaFree(ctx->feat); cudaFree(ctx->prob); cudaFree(ctx->mpre); }
+  ctx->feat = nullptr;
+  ctx->prob = nullptr;
+  ctx->mpre = nullptr;
+  ctx->feat_cap = 0;
   CK(cudaMalloc(&ctx->feat, cap * feat_len(ctx) * 4));
   CK(cudaMalloc(&ctx->prob, cap * 4));
   CK(cudaMalloc(&ctx->mpre, cap * 4));
@@ -528,24 +560,24 @@ mr_status rk_step(mr_ctx ctx, const double* t, const double* dt) {
 mr_status set_blocks_dev(mr_ctx ctx, int64_t n, const int32_t* lvl, const int32_t* tree,
                          const int32_t* crd, const double* fld) {
   // Host arrays -> device staging, then the device builds the pool.
-  int32_t *dl = nullptr, *dt = nullptr, *dc = nullptr;
-  double* df = nullptr;
+  TmpBuf<int32_t> dl, dt, dc;
+  TmpBuf<double> df;
   const int nv = ctx->p.nvar;
   int64_t ni = 1;
   for (int a = 0; a < ctx->p.dim; ++a) ni *= ctx->p.Bs;
-  CK(cudaMallocAsync((void**)&dl, std::max<int64_t>(n, 1) * 4, ctx->st));
-  CK(cudaMallocAsync((void**)&dc, std::max<int64_t>(n, 1) * 12, ctx->st));
-  if (tree) CK(cudaMallocAsync((void**)&dt, std::max<int64_t>(n, 1) * 4, ctx->st));
-  if (fld) CK(cudaMallocAsync((void**)&df, std::max<int64_t>(n, 1) * nv * ni * 8, ctx->st));
-  CK(cudaMemcpyAsync(dl, lvl, n * 4, cudaMemcpyHostToDevice, ctx->st));
-  CK(cudaMemcpyAsync(dc, crd, n * 12, cudaMemcpyHostToDevice, ctx->st));
-  if (tree) CK(cudaMemcpyAsync(dt, tree, n * 4, cudaMemcpyHostToDevice, ctx->st));
-  if (fld) CK(cudaMemcpyAsync(df, fld, n * nv * ni * 8, cudaMemcpyHostToDevice, ctx->st));
+  CK(dl.alloc_on(std::max<int64_t>(n, 1) * 4, ctx->st));
+  CK(dc.alloc_on(std::max<int64_t>(n, 1) * 12, ctx->st));
+  if (tree) CK(dt.alloc_on(std::max<int64_t>(n, 1) * 4, ctx->st));
+  if (fld) CK(df.alloc_on(std::max<int64_t>(n, 1) * nv * ni * 8, ctx->st));
+  CK(cudaMemcpyAsync(dl.p, lvl, n * 4, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(dc.p, crd, n * 12, cudaMemcpyHostToDevice, ctx->st));
+  if (tree) CK(cudaMemcpyAsync(dt.p, tree, n * 4, cudaMemcpyHostToDevice, ctx->st));
+  if (fld) CK(cudaMemcpyAsync(df.p, fld, n * nv * ni * 8, cudaMemcpyHostToDevice, ctx->st));
   PoolView pv = view(ctx);
   auto phase = [&](int ph) {
     by_dim(ctx,
-           [&] { launch_set_blocks<2>(pv, fields(ctx), ph, n, dl, dt, dc, df, ctx->ncells, ctx->p.ntrees, ctx->ntab, ctx->lc, ctx->st); },
-           [&] { launch_set_blocks<3>(pv, fields(ctx), ph, n, dl, dt, dc, df, ctx->ncells, ctx->p.ntrees, ctx->ntab, ctx->lc, ctx->st); });
+           [&] { launch_set_blocks<2>(pv, fields(ctx), ph, n, dl.p, dt.p, dc.p, df.p, ctx->ncells, ctx->p.ntrees, ctx->ntab, ctx->lc, ctx->st); },
+           [&] { launch_set_blocks<3>(pv, fields(ctx), ph, n, dl.p, dt.p, dc.p, df.p, ctx->ncells, ctx->p.ntrees, ctx->ntab, ctx->lc, ctx->st); });
   };
   phase(1);
   mr_status s0 = check_device(ctx);
@@ -554,10 +586,6 @@ mr_status set_blocks_dev(mr_ctx ctx, int64_t n, const int32_t* lvl, const int32_
     s0 = check_device(ctx);
   }
   if (s0 != MR_OK) phase(0);  // rejected input: leave an empty, consistent pool
-  cudaFreeAsync(dl, ctx->st);
-  cudaFreeAsync(dc, ctx->st);
-  if (dt) cudaFreeAsync(dt, ctx->st);
-  if (df) cudaFreeAsync(df, ctx->st);
   if (s0 != MR_OK) {
     std::string msg = ctx->err;
     check_device(ctx);
@@ -951,17 +979,15 @@ mr_status mr_get_blocks(mr_ctx ctx, int32_t tree, int64_t cap, int64_t* n, mr_bl
   const int64_t per = ctx->p.nvar * ni;
   // stream-ordered staging (no device-wide synchronisation of cudaMalloc /
   // cudaFree); one synchronisation after the copies to the host
-  mr_block_info* dinfo = nullptr;
-  double* dfld = nullptr;
-  CK(cudaMallocAsync((void**)&dinfo, std::max<int64_t>(h.n_act, 1) * sizeof(mr_block_info), ctx->st));
-  if (flds) CK(cudaMallocAsync((void**)&dfld, std::max<int64_t>(h.n_act, 1) * per * 8, ctx->st));
+  TmpBuf<mr_block_info> dinfo;
+  TmpBuf<double> dfld;
+  CK(dinfo.alloc_on(std::max<int64_t>(h.n_act, 1) * sizeof(mr_block_info), ctx->st));
+  if (flds) CK(dfld.alloc_on(std::max<int64_t>(h.n_act, 1) * per * 8, ctx->st));
   PoolView pv = view(ctx);
-  by_dim(ctx, [&] { launch_export<2>(pv, fields(ctx), dinfo, dfld, nullptr, nullptr, ctx->lc, ctx->st); },
-         [&] { launch_export<3>(pv, fields(ctx), dinfo, dfld, nullptr, nullptr, ctx->lc, ctx->st); });
-  if (info) CK(cudaMemcpyAsync(info, dinfo + first, cnt * sizeof(mr_block_info), cudaMemcpyDeviceToHost, ctx->st));
-  if (flds) CK(cudaMemcpyAsync(flds, dfld + first * per, cnt * per * 8, cudaMemcpyDeviceToHost, ctx->st));
-  cudaFreeAsync(dinfo, ctx->st);
-  if (dfld) cudaFreeAsync(dfld, ctx->st);
+  by_dim(ctx, [&] { launch_export<2>(pv, fields(ctx), dinfo.p, dfld.p, nullptr, nullptr, ctx->lc, ctx->st); },
+         [&] { launch_export<3>(pv, fields(ctx), dinfo.p, dfld.p, nullptr, nullptr, ctx->lc, ctx->st); });
+  if (info) CK(cudaMemcpyAsync(info, dinfo.p + first, cnt * sizeof(mr_block_info), cudaMemcpyDeviceToHost, ctx->st));
+  if (flds) CK(cudaMemcpyAsync(flds, dfld.p + first * per, cnt * per * 8, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   CK(cudaGetLastError());
   return MR_OK;
@@ -979,14 +1005,13 @@ mr_status mr_get_tiles(mr_ctx ctx, int32_t tree, int64_t cap, int64_t* n, double
   int64_t tile = 1;
   for (int a = 0; a < ctx->p.dim; ++a) tile *= ctx->p.Bs + 2 * ctx->p.ng;
   const int64_t per = ctx->p.nvar * tile;
-  double* dt = nullptr;
-  CK(cudaMalloc(&dt, std::max<int64_t>(h.n_act, 1) * per * 8));
+  TmpBuf<double> dt;
+  CK(dt.alloc(std::max<int64_t>(h.n_act, 1) * per * 8));
   PoolView pv = view(ctx);
-  by_dim(ctx, [&] { launch_sync<2>(pv, fields(ctx), dt, ctx->lc, ctx->st); },
-         [&] { launch_sync<3>(pv, fields(ctx), dt, ctx->lc, ctx->st); });
+  by_dim(ctx, [&] { launch_sync<2>(pv, fields(ctx), dt.p, ctx->lc, ctx->st); },
+         [&] { launch_sync<3>(pv, fields(ctx), dt.p, ctx->lc, ctx->st); });
   s = check_device(ctx);
-  if (!s) CK(cudaMemcpy(tiles, dt + first * per, cnt * per * 8, cudaMemcpyDeviceToHost));
-  cudaFree(dt);
+  if (!s) CK(cudaMemcpy(tiles, dt.p + first * per, cnt * per * 8, cudaMemcpyDeviceToHost));
   return s;
 }
 
@@ -999,23 +1024,21 @@ mr_status mr_get_neighbors(mr_ctx ctx, int32_t tree, int64_t cap, int32_t* nbr, 
   if (cap < cnt) return fail(ctx, MR_EINVAL, "output buffer too small");
   const Counters h = read_counters(ctx);
   const int R = ctx->nrel;
-  int32_t* dn = nullptr;
-  int8_t* dd = nullptr;
-  CK(cudaMalloc(&dn, std::max<int64_t>(h.n_act, 1) * R * 4));
-  CK(cudaMalloc(&dd, std::max<int64_t>(h.n_act, 1) * R));
+  TmpBuf<int32_t> dn;
+  TmpBuf<int8_t> dd;
+  CK(dn.alloc(std::max<int64_t>(h.n_act, 1) * R * 4));
+  CK(dd.alloc(std::max<int64_t>(h.n_act, 1) * R));
   // position of every slot in the list
   std::vector<int32_t> act(h.n_act), pos(ctx->S, -1);
   CK(cudaMemcpy(act.data(), ctx->act, h.n_act * 4, cudaMemcpyDeviceToHost));
   for (int64_t p = 0; p < h.n_act; ++p) pos[act[p]] = (int32_t)(p - first);
   CK(cudaMemcpy(ctx->pos, pos.data(), ctx->S * 4, cudaMemcpyHostToDevice));
   PoolView pv = view(ctx);
-  by_dim(ctx, [&] { launch_neighbors<2>(pv, ctx->rel, R, dn, dd, ctx->lc, ctx->st); },
-         [&] { launch_neighbors<3>(pv, ctx->rel, R, dn, dd, ctx->lc, ctx->st); });
+  by_dim(ctx, [&] { launch_neighbors<2>(pv, ctx->rel, R, dn.p, dd.p, ctx->lc, ctx->st); },
+         [&] { launch_neighbors<3>(pv, ctx->rel, R, dn.p, dd.p, ctx->lc, ctx->st); });
   CK(cudaStreamSynchronize(ctx->st));
-  CK(cudaMemcpy(nbr, dn + first * R, cnt * R * 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(dl, dd + first * R, cnt * R, cudaMemcpyDeviceToHost));
-  cudaFree(dn);
-  cudaFree(dd);
+  CK(cudaMemcpy(nbr, dn.p + first * R, cnt * R * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dl, dd.p + first * R, cnt * R, cudaMemcpyDeviceToHost));
   return MR_OK;
 }
 
@@ -1027,18 +1050,16 @@ mr_status mr_get_flags(mr_ctx ctx, int32_t tree, int64_t cap, int8_t* flg, doubl
   const int64_t cnt = range_of_tree(ctx, tree, &first);
   if (cap < cnt) return fail(ctx, MR_EINVAL, "output buffer too small");
   const Counters h = read_counters(ctx);
-  int8_t* df = nullptr;
-  double* dm = nullptr;
-  CK(cudaMalloc(&df, std::max<int64_t>(h.n_act, 1)));
-  CK(cudaMalloc(&dm, std::max<int64_t>(h.n_act, 1) * 8));
+  TmpBuf<int8_t> df;
+  TmpBuf<double> dm;
+  CK(df.alloc(std::max<int64_t>(h.n_act, 1)));
+  CK(dm.alloc(std::max<int64_t>(h.n_act, 1) * 8));
   PoolView pv = view(ctx);
-  by_dim(ctx, [&] { launch_export<2>(pv, fields(ctx), nullptr, nullptr, df, dm, ctx->lc, ctx->st); },
-         [&] { launch_export<3>(pv, fields(ctx), nullptr, nullptr, df, dm, ctx->lc, ctx->st); });
+  by_dim(ctx, [&] { launch_export<2>(pv, fields(ctx), nullptr, nullptr, df.p, dm.p, ctx->lc, ctx->st); },
+         [&] { launch_export<3>(pv, fields(ctx), nullptr, nullptr, df.p, dm.p, ctx->lc, ctx->st); });
   CK(cudaStreamSynchronize(ctx->st));
-  if (flg) CK(cudaMemcpy(flg, df + first, cnt, cudaMemcpyDeviceToHost));
-  if (mdet) CK(cudaMemcpy(mdet, dm + first, cnt * 8, cudaMemcpyDeviceToHost));
-  cudaFree(df);
-  cudaFree(dm);
+  if (flg) CK(cudaMemcpy(flg, df.p + first, cnt, cudaMemcpyDeviceToHost));
+  if (mdet) CK(cudaMemcpy(mdet, dm.p + first, cnt * 8, cudaMemcpyDeviceToHost));
   return MR_OK;
 }
 
@@ -1068,20 +1089,18 @@ mr_status mr_error(mr_ctx ctx, int32_t tree, double t, double* out) {
       ex[a * N + U] = std::exp(-(dd * dd) / (2.0 * s * s));
     }
   }
-  double *dex = nullptr, *dout = nullptr;
-  CK(cudaMalloc(&dex, 3 * N * 8));
-  CK(cudaMalloc(&dout, 4 * 8));
-  CK(cudaMemcpy(dex, ex.data(), 3 * N * 8, cudaMemcpyHostToDevice));
-  CK(cudaMemset(dout, 0, 32));
+  TmpBuf<double> dex, dout;
+  CK(dex.alloc(3 * N * 8));
+  CK(dout.alloc(4 * 8));
+  CK(cudaMemcpy(dex.p, ex.data(), 3 * N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemset(dout.p, 0, 32));
   PoolView pv = view(ctx);
-  by_dim(ctx, [&] { launch_error<2>(pv, fields(ctx), tree, dex, dout, ctx->lc, ctx->st); },
-         [&] { launch_error<3>(pv, fields(ctx), tree, dex, dout, ctx->lc, ctx->st); });
+  by_dim(ctx, [&] { launch_error<2>(pv, fields(ctx), tree, dex.p, dout.p, ctx->lc, ctx->st); },
+         [&] { launch_error<3>(pv, fields(ctx), tree, dex.p, dout.p, ctx->lc, ctx->st); });
   CK(cudaStreamSynchronize(ctx->st));
   double o[4];
-  CK(cudaMemcpy(o, dout, 32, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(o, dout.p, 32, cudaMemcpyDeviceToHost));
   out[0] = std::sqrt(o[0]); out[1] = std::sqrt(o[1]); out[2] = o[2]; out[3] = o[3];
-  cudaFree(dex);
-  cudaFree(dout);
   return MR_OK;
 }
 
@@ -1410,20 +1429,20 @@ mr_status mr_proposal_collect(mr_ctx ctx, int32_t on, int64_t capacity) {
   if (s) return s;
   if (on && capacity > ctx->ds_cap) {
     CK(cudaStreamSynchronize(ctx->st));
-    float *f = nullptr, *l = nullptr, *mp = nullptr;
-    int32_t* k = nullptr;
-    CK(cudaMalloc(&f, capacity * feat_len(ctx) * 4));
-    CK(cudaMalloc(&l, capacity * 4));
-    CK(cudaMalloc(&mp, capacity * 4));
-    CK(cudaMalloc(&k, capacity * 16));
+    TmpBuf<float> f, l, mp;
+    TmpBuf<int32_t> k;
+    CK(f.alloc(capacity * feat_len(ctx) * 4));
+    CK(l.alloc(capacity * 4));
+    CK(mp.alloc(capacity * 4));
+    CK(k.alloc(capacity * 16));
     if (ctx->ds_n > 0) {
-      CK(cudaMemcpy(f, ctx->ds_feat, ctx->ds_n * feat_len(ctx) * 4, cudaMemcpyDeviceToDevice));
-      CK(cudaMemcpy(l, ctx->ds_label, ctx->ds_n * 4, cudaMemcpyDeviceToDevice));
-      CK(cudaMemcpy(mp, ctx->ds_mpre, ctx->ds_n * 4, cudaMemcpyDeviceToDevice));
-      CK(cudaMemcpy(k, ctx->ds_key, ctx->ds_n * 16, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(f.p, ctx->ds_feat, ctx->ds_n * feat_len(ctx) * 4, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(l.p, ctx->ds_label, ctx->ds_n * 4, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(mp.p, ctx->ds_mpre, ctx->ds_n * 4, cudaMemcpyDeviceToDevice));
+      CK(cudaMemcpy(k.p, ctx->ds_key, ctx->ds_n * 16, cudaMemcpyDeviceToDevice));
     }
     if (ctx->ds_feat) { cudaFree(ctx->ds_feat); cudaFree(ctx->ds_label); cudaFree(ctx->ds_mpre); cudaFree(ctx->ds_key); }
-    ctx->ds_feat = f; ctx->ds_label = l; ctx->ds_mpre = mp; ctx->ds_key = k;
+    ctx->ds_feat = f.release(); ctx->ds_label = l.release(); ctx->ds_mpre = mp.release(); ctx->ds_key = k.release();
     ctx->ds_cap = capacity;
   }
   ctx->collect = on != 0;
@@ -1501,13 +1520,13 @@ mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32
   int64_t stride = 7919;
   while (std::gcd(stride, ntr) != 1) ++stride;
   for (int64_t i = 0; i < ntr; ++i) order[i] = valid[(i * stride) % ntr];
-  int32_t* didx = nullptr;
-  float *dloss = nullptr, *dprob = nullptr;
-  CK(cudaMalloc(&didx, std::max<int64_t>(nv, 1) * 4));
-  CK(cudaMalloc(&dloss, 4));
-  CK(cudaMalloc(&dprob, std::max<int64_t>(nv, 1) * 4));
-  CK(cudaMemcpy(didx, order.data(), ntr * 4, cudaMemcpyHostToDevice));
-  if (nho > 0) CK(cudaMemcpy(didx + ntr, valid.data() + ntr, nho * 4, cudaMemcpyHostToDevice));
+  TmpBuf<int32_t> didx;
+  TmpBuf<float> dloss, dprob;
+  CK(didx.alloc(std::max<int64_t>(nv, 1) * 4));
+  CK(dloss.alloc(4));
+  CK(dprob.alloc(std::max<int64_t>(nv, 1) * 4));
+  CK(cudaMemcpy(didx.p, order.data(), ntr * 4, cudaMemcpyHostToDevice));
+  if (nho > 0) CK(cudaMemcpy(didx.p + ntr, valid.data() + ntr, nho * 4, cudaMemcpyHostToDevice));
   if (init) {
     CK(cudaMemcpy(ctx->cnn_w, init, kCnnParams * 4, cudaMemcpyHostToDevice));
     CK(cudaMemset(ctx->cnn_m, 0, kCnnParams * 4));
@@ -1517,32 +1536,32 @@ mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32
   CK(cudaMemset(ctx->cnn_g, 0, kCnnParams * 4));
   float last = 0.f;
   for (int e = 0; e < epochs; ++e) {
-    CK(cudaMemsetAsync(dloss, 0, 4, ctx->st));
+    CK(cudaMemsetAsync(dloss.p, 0, 4, ctx->st));
     for (int64_t s0 = 0; s0 < ntr; s0 += batch) {
       const int nb = (int)std::min<int64_t>(batch, ntr - s0);
-      launch_train(ctx->p.Bs, ctx->ds_feat, ctx->ds_label, didx, s0, nb, ctx->cnn_w, w_pos, ctx->cnn_g,
-                   dloss, nullptr, ctx->lc.num_sms, ctx->st);
+      launch_train(ctx->p.Bs, ctx->ds_feat, ctx->ds_label, didx.p, s0, nb, ctx->cnn_w, w_pos, ctx->cnn_g,
+                   dloss.p, nullptr, ctx->lc.num_sms, ctx->st);
       launch_adam(ctx->cnn_w, ctx->cnn_m, ctx->cnn_v, ctx->cnn_g, lr, ++ctx->cnn_t, ctx->cnn_wb, ctx->st);
     }
-    CK(cudaMemcpyAsync(&last, dloss, 4, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(&last, dloss.p, 4, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
   }
   launch_to_bf16(ctx->cnn_w, ctx->cnn_wb, ctx->st);
   // threshold: largest tau keeping recall >= target on the held-out samples
   // (all samples when there is no hold-out), with the BF16 inference weights
   const int64_t ne = nho > 0 ? nho : ntr;
-  const int32_t* eidx = nho > 0 ? didx + ntr : didx;
-  float* gfeat = nullptr;
-  CK(cudaMalloc(&gfeat, ne * feat_len(ctx) * 4));
+  const int32_t* eidx = nho > 0 ? didx.p + ntr : didx.p;
+  TmpBuf<float> gfeat;
+  CK(gfeat.alloc(ne * feat_len(ctx) * 4));
   std::vector<int32_t> hidx(ne);
   CK(cudaMemcpy(hidx.data(), eidx, ne * 4, cudaMemcpyDeviceToHost));
   for (int64_t i = 0; i < ne; ++i)
-    CK(cudaMemcpyAsync(gfeat + i * feat_len(ctx), ctx->ds_feat + (int64_t)hidx[i] * feat_len(ctx),
+    CK(cudaMemcpyAsync(gfeat.p + i * feat_len(ctx), ctx->ds_feat + (int64_t)hidx[i] * feat_len(ctx),
                        feat_len(ctx) * 4, cudaMemcpyDeviceToDevice, ctx->st));
   PoolView pv = view(ctx);
-  launch_infer(pv, ctx->p.Bs, gfeat, ctx->cnn_wb, dprob, ne, ctx->lc.num_sms, ctx->st);
+  launch_infer(pv, ctx->p.Bs, gfeat.p, ctx->cnn_wb, dprob.p, ne, ctx->lc.num_sms, ctx->st);
   std::vector<float> pr(ne);
-  CK(cudaMemcpyAsync(pr.data(), dprob, ne * 4, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(pr.data(), dprob.p, ne * 4, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   std::vector<float> ppos;
   for (int64_t i = 0; i < ne; ++i)
@@ -1556,10 +1575,6 @@ mr_status mr_proposal_train(mr_ctx ctx, const float* init, int32_t epochs, int32
   drop_graph(ctx);
   ctx->cnn_tau = tau;
   ctx->cnn_ready = true;
-  cudaFree(gfeat);
-  cudaFree(didx);
-  cudaFree(dloss);
-  cudaFree(dprob);
   if (tau_out) *tau_out = tau;
   if (loss_out) *loss_out = last;
   return MR_OK;
@@ -1585,24 +1600,23 @@ mr_status mr_cnn_eval(mr_ctx ctx, const float* params, const float* x, const flo
   mr_status s = ensure_cnn(ctx);
   if (s) return s;
   const int64_t fl = feat_len(ctx);
-  float *dx = nullptr, *dy = nullptr, *dw = nullptr, *dg = nullptr, *dl = nullptr, *dp = nullptr;
-  CK(cudaMalloc(&dx, n * fl * 4));
-  CK(cudaMalloc(&dy, n * 4));
-  CK(cudaMalloc(&dw, kCnnParams * 4));
-  CK(cudaMalloc(&dg, kCnnParams * 4));
-  CK(cudaMalloc(&dl, 4));
-  CK(cudaMalloc(&dp, n * 4));
-  CK(cudaMemcpy(dx, x, n * fl * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(dy, y, n * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(dw, params, kCnnParams * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemset(dg, 0, kCnnParams * 4));
-  CK(cudaMemset(dl, 0, 4));
-  launch_train(ctx->p.Bs, dx, dy, nullptr, 0, (int)n, dw, w_pos, dg, dl, dp, ctx->lc.num_sms, ctx->st);
+  TmpBuf<float> dx, dy, dw, dg, dl, dp;
+  CK(dx.alloc(n * fl * 4));
+  CK(dy.alloc(n * 4));
+  CK(dw.alloc(kCnnParams * 4));
+  CK(dg.alloc(kCnnParams * 4));
+  CK(dl.alloc(4));
+  CK(dp.alloc(n * 4));
+  CK(cudaMemcpy(dx.p, x, n * fl * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dy.p, y, n * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dw.p, params, kCnnParams * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemset(dg.p, 0, kCnnParams * 4));
+  CK(cudaMemset(dl.p, 0, 4));
+  launch_train(ctx->p.Bs, dx.p, dy.p, nullptr, 0, (int)n, dw.p, w_pos, dg.p, dl.p, dp.p, ctx->lc.num_sms, ctx->st);
   CK(cudaStreamSynchronize(ctx->st));
-  if (prob) CK(cudaMemcpy(prob, dp, n * 4, cudaMemcpyDeviceToHost));
-  if (grad) CK(cudaMemcpy(grad, dg, kCnnParams * 4, cudaMemcpyDeviceToHost));
-  if (loss) CK(cudaMemcpy(loss, dl, 4, cudaMemcpyDeviceToHost));
-  for (float* q : {dx, dy, dw, dg, dl, dp}) cudaFree(q);
+  if (prob) CK(cudaMemcpy(prob, dp.p, n * 4, cudaMemcpyDeviceToHost));
+  if (grad) CK(cudaMemcpy(grad, dg.p, kCnnParams * 4, cudaMemcpyDeviceToHost));
+  if (loss) CK(cudaMemcpy(loss, dl.p, 4, cudaMemcpyDeviceToHost));
   return MR_OK;
 }
 
