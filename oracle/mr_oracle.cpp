@@ -16,6 +16,10 @@
 //                                             redundant nodes of coarser ones)
 //   * 4th-order central FD + RK4 ........... Sec. 3 and Sec. 4
 //   * swirl test velocity .................. Sec. 3, Eq. (1)
+//   * compressible Navier-Stokes ........... Sec. 4 (flux form and the
+//                                             skew-symmetric form, 2D and 3D;
+//                                             the shock-capturing filter after
+//                                             each step; double shear layer)
 // Everything is written per point with std::map lookups so that it can be
 // checked against the text by eye; nothing is blocked, fused or reordered.
 // Compile with -O2 -ffp-contract=off so every a*b+c is a rounded product
@@ -34,8 +38,9 @@
 
 extern "C" {
 // Parameters of one tree.  rhs_kind: 0 constant-velocity advection,
-// 1 swirl (Sec. 3), 2 compressible Navier-Stokes (Sec. 4, 2D) in flux form,
-// 3 the same in the skew-symmetric form on square-root variables; for 2 and 3
+// 1 swirl (Sec. 3), 2 compressible Navier-Stokes (Sec. 4; 2D with nvar 4,
+// 3D with nvar 5) in flux form, 3 the same in the skew-symmetric form on
+// square-root variables; for 2 and 3
 // rhs = {gamma, mu, Pr, r_th}, r_th > 0 enabling the shock filter after each
 // step.  ic_kind: 0 separable Gaussian blob, 1 temporal mixing layer, 2 none
 // (set_blocks), 3 the double shear layer of Sec. 4.
@@ -938,10 +943,189 @@ struct Tree {
         kk[3 * nb + n] = rp;
       }
   }
+  // ------------------------------------------------ Navier-Stokes, 3D -----
+  // The two formulations above in three dimensions (Sec. 5 names 3D runs as
+  // the next step): q = (rho, rho u, rho v, rho w, E) for the flux form and
+  // q = (phi, psi_x, psi_y, psi_z, p) for the skew-symmetric form, nvar = 5.
+  // The equations are the 2D ones with the index sums running over three
+  // axes.  Every sum over the axes is evaluated as ((x + y) + z) and every
+  // sum over velocity components the same way, so a state that does not vary
+  // along z and has w = 0 gives the 2D values bit for bit (the z terms are
+  // exact zeros).  Tile arrays cover nodes -g..B+g-1 per axis; stresses and
+  // fluxes are formed on nodes -2..B+1 per axis and differentiated again.
+  size_t I3(int i, int j, int k) const {
+    size_t R = (size_t)(B + 2 * g);
+    return ((size_t)(k + g) * R + (size_t)(j + g)) * R + (size_t)(i + g);
+  }
+  // 4th-order D1 along axis a of a tile array, and of the product of two
+  double D3(const std::vector<double>& f, int a, int i, int j, int k, double c) const {
+    int o[3] = {0, 0, 0};
+    o[a] = 1;
+    auto at = [&](int s) { return f[I3(i + s * o[0], j + s * o[1], k + s * o[2])]; };
+    return ((at(-2) - at(2)) + 8.0 * (at(1) - at(-1))) * c;
+  }
+  double D3m(const std::vector<double>& f, const std::vector<double>& h, int a, int i, int j, int k,
+             double c) const {
+    int o[3] = {0, 0, 0};
+    o[a] = 1;
+    auto m = [&](int s) {
+      size_t q = I3(i + s * o[0], j + s * o[1], k + s * o[2]);
+      return f[q] * h[q];
+    };
+    return ((m(-2) - m(2)) + 8.0 * (m(1) - m(-1))) * c;
+  }
+  // Viscous stress tau_ab = mu (D_b u_a + D_a u_b) - (2/3) mu div delta_ab at a node.
+  void stress3(const std::vector<double>* vel, int i, int j, int k, double c, double mu,
+               double du[3][3], double tau[3][3]) const {
+    for (int a = 0; a < 3; ++a)
+      for (int e = 0; e < 3; ++e) du[a][e] = D3(vel[a], e, i, j, k, c);
+    double div = (du[0][0] + du[1][1]) + du[2][2];
+    for (int a = 0; a < 3; ++a)
+      for (int e = 0; e < 3; ++e)
+        tau[a][e] = a == e ? mu * (2.0 * du[a][a] - (2.0 / 3.0) * div) : mu * (du[a][e] + du[e][a]);
+  }
+  // Flux form, 3D: N(q) = -sum_a D_a F_a,
+  //   F_a = (rho u_a, rho u_a u_b + p delta_ab - tau_ab,
+  //          (E + p) u_a - sum_b u_b tau_ab - kap D_a th).
+  void rhs_ns3(const Leaf& b, std::vector<double>& kk) const {
+    double gam = p.rhs[0], mu = p.rhs[1], Pr = p.rhs[2];
+    double kap = mu * gam / ((gam - 1.0) * Pr);
+    double c = cD(b.lvl);
+    size_t R = (size_t)(B + 2 * g), RR = R * R * R;
+    std::vector<double> vel[3], pr(RR), th(RR);
+    for (int a = 0; a < 3; ++a) vel[a].assign(RR, 0.0);
+    for (int k = -g; k < B + g; ++k)
+      for (int j = -g; j < B + g; ++j)
+        for (int i = -g; i < B + g; ++i) {
+          double r = b.t[ix(0, i, j, k)], E = b.t[ix(4, i, j, k)];
+          double m[3] = {b.t[ix(1, i, j, k)], b.t[ix(2, i, j, k)], b.t[ix(3, i, j, k)]};
+          double uu = m[0] / r, vv = m[1] / r, ww = m[2] / r;
+          double pp = (gam - 1.0) * (E - 0.5 * ((m[0] * uu + m[1] * vv) + m[2] * ww));
+          size_t q = I3(i, j, k);
+          vel[0][q] = uu; vel[1][q] = vv; vel[2][q] = ww;
+          pr[q] = pp; th[q] = pp / r;
+        }
+    std::vector<double> F[3][5];
+    for (int a = 0; a < 3; ++a)
+      for (int v = 0; v < 5; ++v) F[a][v].assign(RR, 0.0);
+    for (int k = -2; k < B + 2; ++k)
+      for (int j = -2; j < B + 2; ++j)
+        for (int i = -2; i < B + 2; ++i) {
+          double du[3][3], tau[3][3];
+          stress3(vel, i, j, k, c, mu, du, tau);
+          size_t q = I3(i, j, k);
+          double E = b.t[ix(4, i, j, k)];
+          double m[3] = {b.t[ix(1, i, j, k)], b.t[ix(2, i, j, k)], b.t[ix(3, i, j, k)]};
+          double uvw[3] = {vel[0][q], vel[1][q], vel[2][q]}, pp = pr[q];
+          for (int a = 0; a < 3; ++a) {
+            F[a][0][q] = m[a];
+            for (int e = 0; e < 3; ++e)
+              F[a][1 + e][q] = a == e ? (m[a] * uvw[e] + pp) - tau[a][e] : m[a] * uvw[e] - tau[a][e];
+            double work = (uvw[0] * tau[a][0] + uvw[1] * tau[a][1]) + uvw[2] * tau[a][2];
+            F[a][4][q] = ((E + pp) * uvw[a] - work) - kap * D3(th, a, i, j, k, c);
+          }
+        }
+    size_t nb = (size_t)B * B * B;
+    for (int v = 0; v < 5; ++v)
+      for (int k = 0; k < B; ++k)
+        for (int j = 0; j < B; ++j)
+          for (int i = 0; i < B; ++i)
+            kk[v * nb + ((size_t)k * B + j) * B + i] =
+                -((D3(F[0][v], 0, i, j, k, c) + D3(F[1][v], 1, i, j, k, c)) + D3(F[2][v], 2, i, j, k, c));
+  }
+  // Skew-symmetric form, 3D, on (phi, psi, p): the 2D equations with
+  // j = x, y, z in every sum, Phi = sum_ij tau_ij D_j u_i.
+  void rhs_ns_skew3(const Leaf& b, std::vector<double>& kk) const {
+    double gam = p.rhs[0], mu = p.rhs[1], Pr = p.rhs[2];
+    double gm1 = gam - 1.0;
+    double kap = mu * gam / ((gam - 1.0) * Pr);
+    double c = cD(b.lvl);
+    size_t R = (size_t)(B + 2 * g), RR = R * R * R;
+    std::vector<double> ph(RR), ps[3], pr(RR), vel[3], th(RR);
+    for (int a = 0; a < 3; ++a) { ps[a].assign(RR, 0.0); vel[a].assign(RR, 0.0); }
+    for (int k = -g; k < B + g; ++k)
+      for (int j = -g; j < B + g; ++j)
+        for (int i = -g; i < B + g; ++i) {
+          size_t q = I3(i, j, k);
+          double f = b.t[ix(0, i, j, k)];
+          ph[q] = f;
+          for (int a = 0; a < 3; ++a) {
+            ps[a][q] = b.t[ix(1 + a, i, j, k)];
+            vel[a][q] = ps[a][q] / f;
+          }
+          pr[q] = b.t[ix(4, i, j, k)];
+          th[q] = pr[q] / (f * f);
+        }
+    // stresses and heat flux kap D th on nodes -2..B+1
+    std::vector<double> tau[3][3], qh[3];
+    for (int a = 0; a < 3; ++a) {
+      qh[a].assign(RR, 0.0);
+      for (int e = 0; e < 3; ++e) tau[a][e].assign(RR, 0.0);
+    }
+    for (int k = -2; k < B + 2; ++k)
+      for (int j = -2; j < B + 2; ++j)
+        for (int i = -2; i < B + 2; ++i) {
+          double du[3][3], t3[3][3];
+          stress3(vel, i, j, k, c, mu, du, t3);
+          size_t q = I3(i, j, k);
+          for (int a = 0; a < 3; ++a) {
+            for (int e = 0; e < 3; ++e) tau[a][e][q] = t3[a][e];
+            qh[a][q] = kap * D3(th, a, i, j, k, c);
+          }
+        }
+    size_t nb = (size_t)B * B * B;
+    for (int k = 0; k < B; ++k)
+      for (int j = 0; j < B; ++j)
+        for (int i = 0; i < B; ++i) {
+          size_t q = I3(i, j, k);
+          double f = ph[q], u[3] = {vel[0][q], vel[1][q], vel[2][q]};
+          double dph[3], dp[3], ds[3][3], du[3][3];
+          for (int a = 0; a < 3; ++a) {
+            dph[a] = D3(ph, a, i, j, k, c);
+            dp[a] = D3(pr, a, i, j, k, c);
+            for (int e = 0; e < 3; ++e) {
+              ds[a][e] = D3(ps[a], e, i, j, k, c);
+              du[a][e] = D3(vel[a], e, i, j, k, c);
+            }
+          }
+          // mass
+          double rphi = -0.5 * (((ds[0][0] + u[0] * dph[0]) + (ds[1][1] + u[1] * dph[1])) +
+                                (ds[2][2] + u[2] * dph[2]));
+          // momentum
+          double rps[3];
+          for (int a = 0; a < 3; ++a) {
+            double conv = ((D3m(ps[a], vel[0], 0, i, j, k, c) + u[0] * ds[a][0]) +
+                           (D3m(ps[a], vel[1], 1, i, j, k, c) + u[1] * ds[a][1])) +
+                          (D3m(ps[a], vel[2], 2, i, j, k, c) + u[2] * ds[a][2]);
+            double visc = (D3(tau[a][0], 0, i, j, k, c) + D3(tau[a][1], 1, i, j, k, c)) +
+                          D3(tau[a][2], 2, i, j, k, c);
+            double fa = dp[a] - visc;
+            rps[a] = -0.5 * conv - fa / f;
+          }
+          // pressure
+          double t00 = tau[0][0][q], t01 = tau[0][1][q], t11 = tau[1][1][q];
+          double t02 = tau[0][2][q], t12 = tau[1][2][q], t22 = tau[2][2][q];
+          double phi_v = ((t00 * du[0][0] + t01 * (du[0][1] + du[1][0])) + t11 * du[1][1]) +
+                         ((t02 * (du[0][2] + du[2][0]) + t12 * (du[1][2] + du[2][1])) + t22 * du[2][2]);
+          double heat = (D3(qh[0], 0, i, j, k, c) + D3(qh[1], 1, i, j, k, c)) + D3(qh[2], 2, i, j, k, c);
+          double dpu = (D3m(pr, vel[0], 0, i, j, k, c) + D3m(pr, vel[1], 1, i, j, k, c)) +
+                       D3m(pr, vel[2], 2, i, j, k, c);
+          double adv = (u[0] * dp[0] + u[1] * dp[1]) + u[2] * dp[2];
+          double rp = (-gam * dpu + gm1 * adv) + gm1 * (phi_v + heat);
+          size_t n = ((size_t)k * B + j) * B + i;
+          kk[n] = rphi;
+          for (int a = 0; a < 3; ++a) kk[(1 + a) * nb + n] = rps[a];
+          kk[4 * nb + n] = rp;
+        }
+  }
   void rhs(const Leaf& b, double ts, std::vector<double>& kk) const {
-    if (p.rhs_kind == 2) rhs_ns(b, kk);
-    else if (p.rhs_kind == 3) rhs_ns_skew(b, kk);
-    else rhs_advection(b, ts, kk);
+    if (p.rhs_kind == 2) {
+      if (d == 3) rhs_ns3(b, kk);
+      else rhs_ns(b, kk);
+    } else if (p.rhs_kind == 3) {
+      if (d == 3) rhs_ns_skew3(b, kk);
+      else rhs_ns_skew(b, kk);
+    } else rhs_advection(b, ts, kk);
   }
 
   // ------------------------------------------------------- shock filter -----
@@ -964,6 +1148,10 @@ struct Tree {
     double rth = p.rhs[3];
     if (!(rth > 0.0) || (p.rhs_kind != 2 && p.rhs_kind != 3)) return;
     sync();
+    if (d == 3) {
+      filter3();
+      return;
+    }
     double gam = p.rhs[0];
     int R = B + 2 * g;
     auto I = [&](int i, int j) { return (size_t)(j + g) * R + (i + g); };
@@ -1028,6 +1216,93 @@ struct Tree {
             double ddy = syp * fyp - sym * fym;
             nt[ix(var, i, j, 0)] = q(i, j) - (ddx + ddy);
           }
+      out[kv.first] = nt;
+    }
+    for (auto& kv : lv) kv.second.t = out[kv.first];
+  }
+
+  // The same filter in 3D: the dilatation sums the three central differences,
+  // ((du/dx + dv/dy) + dw/dz), and the update the three directions,
+  // q_n <- q_n - ((dd_x + dd_y) + dd_z); a state that does not vary along z
+  // with w = 0 is filtered exactly as in 2D (the z strength is zero).
+  void filter3() {
+    double rth = p.rhs[3], gam = p.rhs[0];
+    size_t R = (size_t)(B + 2 * g), RR = R * R * R;
+    std::map<Key, std::vector<double>> out;
+    for (auto& kv : lv) {
+      const Leaf& b = kv.second;
+      double dxl = p.L / (double)((int64_t)(B - 1) << b.lvl);
+      std::vector<double> vel[3], cc(RR);
+      for (int a = 0; a < 3; ++a) vel[a].assign(RR, 0.0);
+      for (int k = -g; k < B + g; ++k)
+        for (int j = -g; j < B + g; ++j)
+          for (int i = -g; i < B + g; ++i) {
+            size_t q = I3(i, j, k);
+            double q0 = b.t[ix(0, i, j, k)], q4 = b.t[ix(4, i, j, k)];
+            double m[3] = {b.t[ix(1, i, j, k)], b.t[ix(2, i, j, k)], b.t[ix(3, i, j, k)]};
+            for (int a = 0; a < 3; ++a) vel[a][q] = m[a] / q0;
+            double rho, pp;
+            if (p.rhs_kind == 2) {
+              rho = q0;
+              pp = (gam - 1.0) * (q4 - 0.5 * ((m[0] * vel[0][q] + m[1] * vel[1][q]) + m[2] * vel[2][q]));
+            } else {
+              rho = q0 * q0;
+              pp = q4;
+            }
+            cc[q] = gam * pp / rho;
+          }
+      double h2 = 0.5 / dxl;
+      auto theta = [&](int i, int j, int k) {
+        return ((vel[0][I3(i + 1, j, k)] - vel[0][I3(i - 1, j, k)]) * h2 +
+                (vel[1][I3(i, j + 1, k)] - vel[1][I3(i, j - 1, k)]) * h2) +
+               (vel[2][I3(i, j, k + 1)] - vel[2][I3(i, j, k - 1)]) * h2;
+      };
+      // strength at node (i, j, k) for direction a
+      auto strength = [&](int a, int i, int j, int k) {
+        int o[3] = {0, 0, 0};
+        o[a] = 1;
+        auto Dth = [&](int s) {
+          int ii = i + s * o[0], jj = j + s * o[1], kk = k + s * o[2];
+          return (-theta(ii + o[0], jj + o[1], kk + o[2]) + 2.0 * theta(ii, jj, kk) -
+                  theta(ii - o[0], jj - o[1], kk - o[2])) / 4.0;
+        };
+        double d0 = Dth(0), dp = Dth(1), dm = Dth(-1);
+        double M = 0.5 * ((d0 - dp) * (d0 - dp) + (d0 - dm) * (d0 - dm));
+        double r = M / (cc[I3(i, j, k)] / (dxl * dxl)) + 1e-16;
+        double z = 1.0 - rth / r;
+        return 0.5 * (z + std::fabs(z));
+      };
+      // strengths along a on nodes -1..B along a and 0..B-1 across
+      std::vector<double> sg[3];
+      for (int a = 0; a < 3; ++a) sg[a].assign(RR, 0.0);
+      for (int k = -1; k <= B; ++k)
+        for (int j = -1; j <= B; ++j)
+          for (int i = -1; i <= B; ++i) {
+            int ijk[3] = {i, j, k};
+            for (int a = 0; a < 3; ++a) {
+              bool inside = true;
+              for (int e = 0; e < 3; ++e)
+                if (e != a && (ijk[e] < 0 || ijk[e] >= B)) inside = false;
+              if (inside) sg[a][I3(i, j, k)] = strength(a, i, j, k);
+            }
+          }
+      std::vector<double> nt = b.t;
+      for (int var = 0; var < nv; ++var)
+        for (int k = 0; k < B; ++k)
+          for (int j = 0; j < B; ++j)
+            for (int i = 0; i < B; ++i) {
+              double dd[3];
+              for (int a = 0; a < 3; ++a) {
+                int o[3] = {0, 0, 0};
+                o[a] = 1;
+                auto q = [&](int s) { return b.t[ix(var, i + s * o[0], j + s * o[1], k + s * o[2])]; };
+                auto sa = [&](int s) { return sg[a][I3(i + s * o[0], j + s * o[1], k + s * o[2])]; };
+                double sp = 0.5 * (sa(0) + sa(1)), sm = 0.5 * (sa(-1) + sa(0));
+                double fp = -0.25 * (q(1) - q(0)), fm = -0.25 * (q(0) - q(-1));
+                dd[a] = sp * fp - sm * fm;
+              }
+              nt[ix(var, i, j, k)] = b.t[ix(var, i, j, k)] - ((dd[0] + dd[1]) + dd[2]);
+            }
       out[kv.first] = nt;
     }
     for (auto& kv : lv) kv.second.t = out[kv.first];
