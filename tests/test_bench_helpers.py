@@ -1,6 +1,6 @@
-"""Host-side analysis helpers of bench.py (no GPU): the kinetic energy
-spectrum of the double shear layer study and the assembly of a uniform grid
-from exported blocks."""
+"""Host-side helpers of bench.py (no GPU): the kinetic energy spectrum of the
+double shear layer study, the assembly of a uniform grid from exported blocks,
+the error against a fine reference and the clock summary of the timed region."""
 import numpy as np
 
 import bench
@@ -65,3 +65,21 @@ def test_error_vs_reference_on_adaptive_blocks():
     f[0, 1, 2] += 0.5
     l2, linf = bench.error_vs_reference(info, f, ref, Bs, jref)
     assert np.isclose(linf, 0.5 / np.abs(ref).max()) and l2 > 0
+
+
+def test_clock_summary_median_and_reasons():
+    # nvidia-smi csv rows (index, clocks.sm, clocks.max.sm, power, active mask, hw_slowdown,
+    # hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap); malformed rows are skipped
+    c = bench.Clocks(0)
+    c.lines = ["0, 1980, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "0, 2070, 2070, 1000.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "0, 2010, 2070, 950.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "0, [N/A], 2070",
+               "garbage"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2010.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = ["0, 1500, 2070, 700.0, 0x0000000000000048, Active, Active, Not Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() is None
