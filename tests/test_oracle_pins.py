@@ -12,7 +12,9 @@ a wrong sign, index or coefficient, a transposed operand) fails it:
 * ghost synchronisation of a cubic on an adaptive graded tree is exact;
 * neighbour table equals brute-force geometric point location; 16 / 74
   relations (Sec. 2.2);
-* flag fixpoint independent of visit order; compression -> 1 as eps -> 0.
+* flag fixpoint independent of visit order; compression -> 1 as eps -> 0;
+* only status +1 is refined (Sec. 2.3); the error norms weight each physical
+  node once by dx^d (the L2 norm of a Gaussian in closed form).
 """
 import itertools
 import math
@@ -296,11 +298,13 @@ def _expected_neighbours(dim, leaves, leaf, rel):
     return out
 
 
-@pytest.mark.parametrize("dim,jmax,seed", [(2, 4, 1), (2, 4, 2), (2, 5, 3), (3, 3, 4)])
-def test_neighbour_table_matches_point_location(oracle_mod, dim, jmax, seed):
-    leaves = treegen.random_graded_tree(dim, 1, jmax, 6 if dim == 2 else 3, seed)
+@pytest.mark.parametrize("dim,jmin,jmax,seed", [(2, 1, 4, 1), (2, 1, 4, 2), (2, 1, 5, 3), (3, 1, 3, 4),
+                                                (2, 2, 4, 5), (3, 2, 3, 6)])
+def test_neighbour_table_matches_point_location(oracle_mod, dim, jmin, jmax, seed):
+    # jmin 2: leaves at Jmin itself touch finer leaves (coarser neighbours at Jmin)
+    leaves = treegen.random_graded_tree(dim, jmin, jmax, 6 if dim == 2 else 3, seed)
     B, g = (17, 4) if dim == 2 else (9, 2)
-    o = mk(oracle_mod, dim=dim, Bs=B, ng=g, Jmin=1, Jmax=jmax)
+    o = mk(oracle_mod, dim=dim, Bs=B, ng=g, Jmin=jmin, Jmax=jmax)
     o.set_blocks(*treegen.as_arrays(leaves))
     assert o.nrel == {2: 16, 3: 74}[dim]  # Sec. 2.2
     rel = _relations(dim)
@@ -406,3 +410,57 @@ def test_sync_makes_redundant_edge_nodes_single_valued(oracle_mod):
                     key = (((cx * 16 + ii) * s) % 256, ((cy * 16 + jj) * s) % 256)
                     v = b["fields"][n, 0, jj, ii]
                     assert vals.setdefault(key, v) == v, (key, v, vals[key])
+
+
+# --------------------------------------------- refinement status, error norm --
+def test_refine_flagged_refines_only_status_plus_one(oracle_mod):
+    # Sec. 2.3: only blocks with status +1 are refined (not -1, -2 or 0), and
+    # blocks at Jmax never
+    leaves = treegen.random_graded_tree(2, 2, 4, 5, 9)
+    o = mk(oracle_mod, Jmin=2, Jmax=4)
+    o.set_blocks(*treegen.as_arrays(leaves))
+    b = o.blocks(fields=False)
+    rng = np.random.default_rng(3)
+    flags = rng.choice(np.array([-2, -1, 0, 1], np.int8), o.n)
+    o.set_flags(flags)
+    o.refine(1)
+    after = o.blocks(fields=False)
+    got = sorted((int(l), tuple(int(x) for x in c[:2])) for l, c in zip(after["level"], after["coords"]))
+    exp = set()
+    for n in range(len(flags)):
+        leaf = (int(b["level"][n]), tuple(int(x) for x in b["coords"][n][:2]))
+        if flags[n] == 1 and leaf[0] < 4:
+            exp.update(treegen.refine_leaf(2, leaf))
+        else:
+            exp.add(leaf)
+    assert got == sorted(exp)
+    assert np.sum((flags == 1) & (b["level"] < 4)) > 2 and np.sum(flags < 0) > 2
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_error_norms_count_each_node_once_with_cell_weights(oracle_mod, dim):
+    # error against the analytic field: the L2 norms carry the weight dx^d and
+    # count each physical node once (a block's last node per axis is its
+    # neighbour's first); the L2 norm of the Gaussian is (pi sigma^2)^(d/4)
+    sig, lvl = 0.06, 3
+    B, g = (17, 4) if dim == 2 else (9, 2)
+    c = (0.5, 0.375, 0.625)
+    o = mk(oracle_mod, dim=dim, Bs=B, ng=g, Jmin=lvl, Jmax=lvl, ic="gauss", ic_params=c + (sig,))
+    o.init_tree()
+    e0 = o.error(0.0)
+    assert e0["l2_abs"] == 0.0 and e0["linf_abs"] == 0.0
+    h = 1.0 / ((B - 1) << lvl)
+    b = o.blocks()
+    delta = 1e-3
+    for where, counted in (((1,) * dim, True), ((B - 1,) * dim, False)):
+        f = b["fields"].copy()
+        f[0][(0,) + where[::-1]] += delta  # block 0, node (i, j[, k]) at [z][y][x]
+        o.set_blocks(b["level"], b["coords"], f)
+        e = o.error(0.0)
+        if counted:
+            assert abs(e["l2_abs"] - delta * h ** (dim / 2)) <= 1e-12 * delta
+            assert e["linf_abs"] == pytest.approx(delta, rel=1e-9)
+            l2_exact = e["l2_abs"] / e["l2"]
+            assert abs(l2_exact - (np.pi * sig * sig) ** (dim / 4)) <= 1e-9 * l2_exact
+        else:
+            assert e["l2_abs"] == 0.0 and e["linf_abs"] == 0.0
