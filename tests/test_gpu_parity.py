@@ -88,6 +88,32 @@ def test_sync_tiles_bit_exact_on_random_adaptive_tree(mr, oracle_mod):
     assert np.array_equal(f, ob["fields"])
 
 
+@pytest.mark.parametrize("seed", [2, 4])
+def test_sync_tiles_bit_exact_on_random_adaptive_tree_3d(mr, oracle_mod, seed):
+    # the 3D ghost synchronisation on its own (copies, finer-block injection,
+    # tensor-product prediction from coarser blocks) with random values, so no
+    # node agrees by accident; levels 1-2 (seed 2) and 2-3 (seed 4)
+    rng = np.random.default_rng(6)
+    leaves = treegen.random_graded_tree(3, 1, 3, 3, seed)
+    lvl, crd = treegen.as_arrays(leaves)
+    assert len(set(lvl.tolist())) == 2
+    fields = rng.standard_normal((len(leaves), 1, 17, 17, 17))
+    o, g = make_pair(mr, oracle_mod, cfg2d(dim=3, Jmin=1, Jmax=3, ic="none", rhs_params=(1.0, 1.0, 1.0)))
+    o.set_blocks(lvl, crd, fields)
+    g.set_blocks(lvl, crd, fields)
+    assert_same_tree(o, g)
+    o.sync()
+    ot = o.tiles()
+    gt = g.get_tiles()
+    assert o.errors == 0
+    assert gt.shape == ot.shape
+    bad = np.argwhere(gt != ot)
+    assert len(bad) == 0, bad[:10]
+    ob = o.blocks()
+    _, f = g.get_blocks()
+    assert np.array_equal(f, ob["fields"])
+
+
 def test_neighbors_bit_exact(mr, oracle_mod):
     for dim, jmax, seed in ((2, 5, 3), (3, 3, 4)):
         leaves = treegen.random_graded_tree(dim, 1, jmax, 8 if dim == 2 else 3, seed)
