@@ -124,6 +124,30 @@ def test_skew_fp32_acc64_within_tolerance(mr, oracle_mod):
         assert rel < 1e-5, (v, rel)
 
 
+@pytest.mark.parametrize("form", ["ns_skew", "ns"])
+def test_fp32_state_within_tolerance(mr, oracle_mod, form):
+    # FP32 state, stages and filter (no FP64 anywhere on the field path):
+    # three RK steps each followed by the filter on a uniform grid; relative
+    # L2 per variable group <= 1e-5 (each step adds a few u = 2^-24)
+    c = dsl_cfg(form, Jmin=4, Jmax=4)
+    o, g = make(mr, oracle_mod, c, precision="fp32", detail_fp64=True)
+    o.init_tree()
+    g.init_tree()
+    dt = dsl_dt(c)
+    for s in range(3):
+        o.rk4(s * dt, dt)
+        o.filter()
+        g.rk_step(s * dt, dt)
+        g.filter()
+    ob, f = assert_same_tree(o, g)
+    ref = ob["fields"]
+    scale = [np.linalg.norm(ref[:, 0]), np.linalg.norm(ref[:, 1:3]), np.linalg.norm(ref[:, 1:3]),
+             np.linalg.norm(ref[:, 3])]
+    for v in range(4):
+        rel = np.linalg.norm(f[:, v] - ref[:, v]) / scale[v]
+        assert rel < 1e-5, (form, v, rel)
+
+
 def test_graph_steps_equal_eager_steps_with_filter(mr):
     c = dsl_cfg("ns_skew", Jmin=2, Jmax=5)
     runs = []
