@@ -287,7 +287,7 @@ mr_status mr_enable_timing(mr_ctx ctx, int32_t on);
  * is evaluated with the device cos in this mode.  Errors are reported by the next
  * synchronising call.  The graph is captured on a private stream and replayed on
  * the context's stream.  In MR_REFINE_LEARNED mode the captured step runs the
- * proposal (features, network, fallback, gradedness closure) and the judge on
+ * proposal (features, network, fallback, gradedness closure) and the miss check on
  * the device; mr_set_refine_mode, mr_proposal_set with a new tau and
  * mr_proposal_train make the next call capture the step again.  While training
  * samples are being collected (mr_proposal_collect) this call fails with
@@ -355,7 +355,7 @@ mr_status mr_reset_stats(mr_ctx ctx);
  * refinement is kept).  In mode 1 a block below Jmax is refined when p >= tau
  * OR its own largest detail is >= eps (exact fallback); the +1 flags are then
  * closed under gradedness.  After the step a block left unrefined whose details
- * are >= eps counts as a miss (the judge). */
+ * are >= eps counts as a miss (the miss check). */
 #define MR_REFINE_ALL 0
 #define MR_REFINE_LEARNED 1
 mr_status mr_set_refine_mode(mr_ctx ctx, int32_t mode);  /* MR_EINVAL without a network */
@@ -363,7 +363,7 @@ mr_status mr_set_refine_mode(mr_ctx ctx, int32_t mode);  /* MR_EINVAL without a 
 /* Training data: while on, every mr_step records (features, label) of each
  * block before the refinement; label 1 iff the refinement was needed: after the
  * step the block's region is subdivided (the refinement was kept), or the block
- * is a leaf again with details >= eps (the judge's miss event); 0 otherwise; no
+ * is a leaf again with details >= eps (the miss check's event); 0 otherwise; no
  * label for blocks at Jmax or with own details >= eps (the fallback refines
  * those anyway).
  * capacity: samples to reserve (device memory: capacity x 2 x (Bs+8)^2 floats). */

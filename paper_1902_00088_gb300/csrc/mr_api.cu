@@ -457,7 +457,7 @@ mr_status refine_flagged(mr_ctx ctx) {
 
 // Refinement of a step: refine all, or the learned proposal (network or
 // fallback), closed under gradedness, with the unrefined blocks remembered for
-// the judge.  Also records training samples when collecting.
+// the miss check.  Also records training samples when collecting.
 mr_status refine_for_step(mr_ctx ctx, int64_t* collected) {
   *collected = 0;
   if (ctx->refine_mode == 0 && !ctx->collect) {
@@ -506,7 +506,7 @@ mr_status after_step(mr_ctx ctx, int64_t collected) {
   }
   if (ctx->refine_mode == 1) {
     CK(cudaMemsetAsync(ctx->pcounts, 0, 16, ctx->st));
-    launch_judge(pv, ctx->skip, ctx->skip_key, ctx->pcounts, ctx->st);
+    launch_miss_check(pv, ctx->skip, ctx->skip_key, ctx->pcounts, ctx->st);
     int32_t cnt[4];
     CK(cudaMemcpyAsync(cnt, ctx->pcounts, 16, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
@@ -1177,7 +1177,7 @@ void enqueue_epilogue(mr_ctx ctx, cudaStream_t st) {
   const int nt = ctx->p.ntrees;
   if (ctx->refine_mode == 1) {
     PoolView pv = view(ctx);
-    launch_judge(pv, ctx->skip, ctx->skip_key, ctx->gcounts, st);
+    launch_miss_check(pv, ctx->skip, ctx->skip_key, ctx->gcounts, st);
   }
   k_time_advance<<<(nt + 127) / 128, 128, 0, st>>>(ctx->ttime, nt);
   count_launch();

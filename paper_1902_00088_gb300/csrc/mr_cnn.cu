@@ -1,7 +1,7 @@
 // Learned refinement proposal (2D): a small per-block CNN predicts whether the
 // safety refinement of a block (Sec. 2.1 step 1) will be kept after the step.
 // Exact detail thresholding stays the fallback (a block whose own details are
-// >= eps is always refined) and the judge (misses are counted after the step).
+// >= eps is always refined) and the miss check (misses are counted after the step).
 //
 // Network on x[2][T][T] (T = Bs + 2 ng, the synchronised tile):
 //   h1 = relu(conv3x3 s1 (2 -> 16)), h2 = relu(conv3x3 s2 (16 -> 16)),
@@ -478,7 +478,7 @@ __global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
 
 // ------------------------------------------------------ proposal at step -----
 // flag = 1 (refine) if the block is below Jmax and (p >= tau or its own largest
-// normalised detail >= eps); skip marks blocks left unrefined (for the judge).
+// normalised detail >= eps); skip marks blocks left unrefined (for the miss check).
 __global__ void k_propose(PoolView pv, const float* prob, const float* mpre, float tau, int8_t* skip,
                           int32_t* counts) {
   pdl_enter();
@@ -542,8 +542,8 @@ __global__ void k_mask_flags(PoolView pv, const int8_t* mask) {
   }
 }
 
-// Judge: a block left unrefined whose details after the step are >= eps.
-__global__ void k_judge(PoolView pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts) {
+// Miss check: a block left unrefined whose details after the step are >= eps.
+__global__ void k_miss_check(PoolView pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts) {
   pdl_enter();
   const int nact = pv.cnt->n_act;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += gridDim.x * blockDim.x) {
@@ -566,7 +566,7 @@ __global__ void k_skip_key(PoolView pv, const int8_t* skip, int32_t* skip_key) {
 
 // Labels of the samples recorded before a step: 1 iff the refinement was needed
 // -- the block's region is subdivided after the step (its refinement was kept),
-// or the block is a leaf again and its details reached eps (what the judge
+// or the block is a leaf again and its details reached eps (what the miss check
 // counts as a miss when the block was left unrefined) -- 0 otherwise; -1 for
 // blocks at Jmax.
 // Samples whose own details were >= eps (mpre) are refined by the exact
@@ -580,7 +580,7 @@ __global__ void k_label(PoolView pv, const int32_t* key, const float* mpre, int6
     if (l >= td.Jmax || (double)mpre[i] >= td.eps) { label[i] = -1.f; continue; }
     int64_t c[3] = {key[4 * i + 2], key[4 * i + 3], 0};
     const int self = tab_get<2>(pv, td, l, c);
-    if (self >= 0) {  // merged back: positive iff its details reached eps (the judge's event)
+    if (self >= 0) {  // merged back: positive iff its details reached eps (the miss check's event)
       label[i] = pv.mdet[self] >= td.eps ? 1.f : 0.f;
       continue;
     }
@@ -691,9 +691,9 @@ void launch_mask_flags(const PoolView& pv, const int8_t* mask, cudaStream_t st) 
   k_mask_flags<<<256, 256, 0, st>>>(pv, mask);
   count_launch();
 }
-void launch_judge(const PoolView& pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts,
+void launch_miss_check(const PoolView& pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts,
                   cudaStream_t st) {
-  k_judge<<<256, 256, 0, st>>>(pv, skip, skip_key, counts);
+  k_miss_check<<<256, 256, 0, st>>>(pv, skip, skip_key, counts);
   count_launch();
 }
 void launch_skip_key(const PoolView& pv, const int8_t* skip, int32_t* skip_key, cudaStream_t st) {

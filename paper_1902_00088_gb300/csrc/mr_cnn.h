@@ -22,7 +22,7 @@ void launch_propose(const PoolView& pv, const float* prob, const float* mpre, fl
                     int32_t* counts, cudaStream_t st);
 void launch_close(const PoolView& pv, int8_t* skip, int32_t* changed, cudaStream_t st);
 void launch_mask_flags(const PoolView& pv, const int8_t* mask, cudaStream_t st);
-void launch_judge(const PoolView& pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts,
+void launch_miss_check(const PoolView& pv, const int8_t* skip, const int32_t* skip_key, int32_t* counts,
                   cudaStream_t st);
 void launch_skip_key(const PoolView& pv, const int8_t* skip, int32_t* skip_key, cudaStream_t st);
 void launch_sample_keys(const PoolView& pv, int32_t* key, int64_t base, cudaStream_t st);

@@ -83,7 +83,7 @@ def test_learned_proposal_gain_over_refine_all(mr):
 
 def test_learned_graph_steps_equal_eager_steps(mr):
     # The captured step runs the proposal, its closure (fixed passes) and the
-    # judge on the device: same grid, fields and counters as host-driven steps.
+    # miss check on the device: same grid, fields and counters as host-driven steps.
     params = synthetic.cnn_init_params(cnn.SHAPES, seed=7)
     tree = dict(Jmin=2, Jmax=6, eps=1e-4, ic="gauss", ic_params=(0.4, 0.6, 0.0, 0.04),
                 rhs_params=(1.0, 0.5, 0.0))
