@@ -91,7 +91,7 @@ def test_rk4_local_order_with_time_dependent_swirl(oracle_mod):
     leaves = treegen.uniform_tree(2, lvl)
     errs = []
     for dt in (0.004, 0.002):
-        lv, crd = fill(o, leaves, f)
+        fill(o, leaves, f)
         o.rk4(t0, dt)
         one = o.blocks()["fields"]
         fill(o, leaves, f)

@@ -13,7 +13,6 @@ point), independently of the oracle's neighbour relations and treecodes.
 import itertools
 
 import numpy as np
-import pytest
 
 from tests import treegen
 

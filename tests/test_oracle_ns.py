@@ -13,7 +13,6 @@
 import math
 
 import numpy as np
-import pytest
 
 from tests import treegen
 

@@ -51,11 +51,6 @@ def state3(form, r, u, v, w, p):
     return [ph, ph * u, ph * v, ph * w, p + 0 * r]
 
 
-def node_grid(lvl):
-    N = 16 << lvl
-    return N, np.arange(N)
-
-
 def set_global(o, lvl, A):
     """Uniform tree at lvl with the periodic global arrays A[v][z][y][x] (N^3 nodes)."""
     N = 16 << lvl
