@@ -185,6 +185,7 @@ def test_shear_layer_initial_state(oracle_mod, form):
     o.init_tree()
     b = o.blocks()
     h = 8.0 / (16 * 8)
+    n_mid = 0
     for n in range(o.n):
         cx, cy = b["coords"][n][:2]
         x = (cx * 16 + np.arange(17)) * h
@@ -197,11 +198,13 @@ def test_shear_layer_initial_state(oracle_mod, form):
         else:
             rho, u, v, p = f[0] ** 2, f[1] / f[0], f[2] / f[0], f[3]
         far = np.abs(X - 4.0) > 1.0
-        assert np.allclose(rho[far], 1.0, atol=1e-12) and np.allclose(v[far], -1.0, atol=1e-12)
-        mid = np.abs(X - 4.0) < 0.05  # well inside the layer pair (lw = 1/30)
-        assert np.allclose(rho[mid], 2.0, atol=1e-12) and np.allclose(v[mid], 1.0, atol=1e-12)
-        assert np.allclose(u, 0.1 * np.sin(2 * np.pi * (Y - 4.0)), atol=1e-12)
-        assert np.allclose(p, 2.5, atol=1e-12)
+        assert np.allclose(rho[far], 1.0, rtol=0, atol=1e-12) and np.allclose(v[far], -1.0, rtol=0, atol=1e-12)
+        mid = np.abs(X - 4.0) < 0.05  # between the layers (lw = 1/30): 1 - tanh(7.5) = 6.1e-7 from the plateau
+        n_mid += int(mid.sum())
+        assert np.allclose(rho[mid], 2.0, rtol=0, atol=1e-6) and np.allclose(v[mid], 1.0, rtol=0, atol=2e-6)
+        assert np.allclose(u, 0.1 * np.sin(2 * np.pi * (Y - 4.0)), rtol=0, atol=1e-12)
+        assert np.allclose(p, 2.5, rtol=0, atol=1e-12)
         # the jump sits at x = 4 -+ 0.25, halfway values there
         at = np.isclose(X, 3.75)
-        assert np.allclose(rho[at], 1.5, atol=1e-12)
+        assert np.allclose(rho[at], 1.5, rtol=0, atol=1e-12)
+    assert n_mid > 0
