@@ -143,5 +143,71 @@ MR_NS3_HD void rhs_skew(const A& ph, const A* ps, const A& pr, const A* vel, con
   out[4] = (-gam * dpu + gm1 * adv) + gm1 * (phi_v + heat);
 }
 
+// ----------------------------------------------------------------------------
+// Shock-capturing filter of Bogey, de Cacqueray & Bailly (2009), applied after
+// every step in Sec. 4, in three dimensions.  Per direction a and node n:
+//   dilatation  th = ((u_{i+1} - u_{i-1}) + (v_{j+1} - v_{j-1}) + (w_{k+1} - w_{k-1})) / (2 dx)
+//               (each difference scaled separately, summed as ((x + y) + z)),
+//   high-pass   Dth_n = (-th_{n+1} + 2 th_n - th_{n-1}) / 4 along a,
+//   magnitude   M_n = ((Dth_n - Dth_{n+1})^2 + (Dth_n - Dth_{n-1})^2) / 2,
+//   sensor      r_n = M_n / (c_n^2 / dx^2) + 1e-16, c^2 = gamma p / rho,
+//   strength    s_n = (z + |z|) / 2, z = 1 - r_th / r_n,
+//   update      q_n <- q_n - sum_a (s_{n+1/2} F_{n+1/2} - s_{n-1/2} F_{n-1/2}),
+//               F_{n+1/2} = -(q_{n+1} - q_n) / 4, s_{n+1/2} = (s_n + s_{n+1}) / 2.
+
+// Velocity and c^2 of a node; kind 2 flux-form state, kind 3 skew-symmetric state.
+template <typename T>
+MR_NS3_HD void filter_prims(int kind, T gam, const T q[5], T vel[3], T& cc) {
+  for (int a = 0; a < 3; ++a) vel[a] = q[1 + a] / q[0];
+  T rho, p;
+  if (kind == 2) {
+    rho = q[0];
+    p = (gam - T(1)) * (q[4] - T(0.5) * ((q[1] * vel[0] + q[2] * vel[1]) + q[3] * vel[2]));
+  } else {
+    rho = q[0] * q[0];
+    p = q[4];
+  }
+  cc = gam * p / rho;
+}
+
+// Dilatation at a node from the velocity accessors; h2 = 1 / (2 dx).
+template <typename T, typename V>
+MR_NS3_HD T dilatation(const V* vel, int i, int j, int k, T h2) {
+  return ((vel[0](i + 1, j, k) - vel[0](i - 1, j, k)) * h2 + (vel[1](i, j + 1, k) - vel[1](i, j - 1, k)) * h2) +
+         (vel[2](i, j, k + 1) - vel[2](i, j, k - 1)) * h2;
+}
+
+// Strength along axis a at a node from the dilatation accessor th (needed at
+// +-2 along a) and the node's c^2; dx2 = dx^2.
+template <typename T, typename D>
+MR_NS3_HD T strength(const D& th, T cc, int a, int i, int j, int k, T dx2, T rth) {
+  const int o0 = a == 0, o1 = a == 1, o2 = a == 2;
+  auto Dth = [&](int s) {
+    const int ii = i + s * o0, jj = j + s * o1, kk = k + s * o2;
+    return (-th(ii + o0, jj + o1, kk + o2) + T(2) * th(ii, jj, kk) - th(ii - o0, jj - o1, kk - o2)) / T(4);
+  };
+  const T d0 = Dth(0), dp = Dth(1), dm = Dth(-1);
+  const T M = T(0.5) * ((d0 - dp) * (d0 - dp) + (d0 - dm) * (d0 - dm));
+  const T r = M / (cc / dx2) + T(1e-16);
+  const T z = T(1) - rth / r;
+  return T(0.5) * (z + (z < T(0) ? -z : z));
+}
+
+// Filtered value of a variable at an interior node: q its accessor, sg[a] the
+// strengths along a (needed at -1..+1 along a).
+template <typename T, typename Q, typename S>
+MR_NS3_HD T filter_update(const Q& q, const S* sg, int i, int j, int k) {
+  T dd[3];
+  for (int a = 0; a < 3; ++a) {
+    const int o0 = a == 0, o1 = a == 1, o2 = a == 2;
+    const T sp = T(0.5) * (sg[a](i, j, k) + sg[a](i + o0, j + o1, k + o2));
+    const T sm = T(0.5) * (sg[a](i - o0, j - o1, k - o2) + sg[a](i, j, k));
+    const T fp = T(-0.25) * (q(i + o0, j + o1, k + o2) - q(i, j, k));
+    const T fm = T(-0.25) * (q(i, j, k) - q(i - o0, j - o1, k - o2));
+    dd[a] = sp * fp - sm * fm;
+  }
+  return q(i, j, k) - ((dd[0] + dd[1]) + dd[2]);
+}
+
 }  // namespace ns3
 }  // namespace mr
