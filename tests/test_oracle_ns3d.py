@@ -19,7 +19,10 @@ skew-symmetric form.
 * discrete invariants on a periodic grid: mass, momentum and energy rates sum
   to zero, and the skew form's convection conserves kinetic energy;
 * filter: transfer function and sensor strength of a four-node velocity wave
-  along each axis; conservation of every conserved variable.
+  along each axis; conservation of every conserved variable;
+* steps: RK4 + filter conserve every sum of the flux form on a periodic tree;
+  a full adaptive step (refine, RK4, filter, coarsen) on an octree stays
+  graded and finite.
 """
 import math
 
@@ -341,3 +344,52 @@ def test_filter_rotation_and_conservation(oracle_mod, form):
             d = f[v_] - q[v_]
             assert np.abs(d).sum() > 1e-3, v_
             assert abs(d.sum()) <= 1e-12 * np.abs(q[v_]).sum(), v_
+
+
+# ------------------------------------------------------------------- steps ---
+
+def test_flux_form_steps_conserve_every_sum(oracle_mod):
+    # two RK4 steps, each followed by the filter, on a periodic uniform tree: the
+    # right-hand side is a flux divergence and the filter a flux difference, so
+    # the sums of rho, rho u, rho v, rho w and E over the unique nodes stay put
+    lvl = 1
+    N = 16 << lvl
+    n = np.arange(N)
+    Z, Y, X = np.meshgrid(n, n, n, indexing="ij")
+    r, u, v, p = shock_like(X, Y, N)
+    _, w, _, _ = shock_like(Z, Y, N)
+    q = np.stack(state3("ns", r, u, v, 0.6 * w, p))
+    o = oracle3(oracle_mod, "ns", lvl, mu=0.01, rth=RTH)
+    set_global(o, lvl, q)
+    s0 = q.reshape(5, -1).sum(axis=1)
+    dt = 0.2 / N / 2.5
+    for s in range(2):
+        o.rk4(s * dt, dt)
+        o.filter()
+    f = to_global(o, o.blocks()["fields"], N)
+    assert np.abs(f - q).max() > 1e-4
+    s1 = f.reshape(5, -1).sum(axis=1)
+    scale = np.abs(q).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(s1 - s0) <= 1e-12 * scale), (s1 - s0, scale)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_adaptive_step_in_3d(oracle_mod, form):
+    # refine, RK4, filter, coarsen with five variables on an octree: graded,
+    # finite, no stencil outside a tile
+    lvl0 = 1
+    o = oracle_mod.Oracle(dict(dim=3, Bs=17, ng=4, nvar=5, Jmin=1, Jmax=2, eps=1e-2, rhs=form,
+                               rhs_params=(GAM, 1e-3, PR, RTH), ic="none", norm_kind=1))
+    N = 16 << lvl0
+    n = np.arange(N)
+    Z, Y, X = np.meshgrid(n, n, n, indexing="ij")
+    r, u, v, p = shock_like(X, Y, N, w=4.0 / N)
+    set_global(o, lvl0, np.stack(state3(form, r, 0.3 * u, 0.3 * v, 0.1 + 0 * r, p)))
+    dt = 0.1 / (16 << 2) / 2.5
+    for s in range(2):
+        o.step(s * dt, dt)
+    b = o.blocks()
+    leaves = {(int(l), tuple(int(x) for x in c)) for l, c in zip(b["level"], b["coords"])}
+    assert o.errors == 0 and np.isfinite(b["fields"]).all()
+    assert treegen.is_graded(3, leaves)
+    assert set(b["level"].tolist()) <= {1, 2}
